@@ -1,0 +1,362 @@
+#!/usr/bin/env python3
+"""Throughput of the N-FHMM variational sweep on GB300: frame-iterations/s.
+
+One step = one separation job of the paper-size workload (S=2 sources, N=40
+dictionaries of K=10 elements, F=513 bins, T=3000 frames) taken through the
+whole hot path: initial state from the job's inputs, 50 sweeps (Eq. 6,
+Eqs. 7 and 8, forward-backward per source) and the variational bound.
+frame-iterations per step = T * 50.
+
+* ``value``: inputs already resident in HBM; the step runs through the
+  library's C ABI from device pointers.  L2 (129 MB) is flushed by a 256 MB
+  write before every timed step; each step is timed with CUDA events on the
+  stream that launches it.
+* ``e2e``: the same step through the same public API from pinned host
+  buffers: host->device copies of V, W, A, pi and the device->host read of the
+  posteriors and bound are inside the timed region.
+* ``roofline``: the stage with the largest summed CUDA-event time inside the
+  timed region, its algorithmic flops or bytes per launch over its mean
+  launch time, against the measured peaks.
+* ``cpu_baseline``: the FP64 oracle on a bounded sample of the same
+  workload, timed on this host's cores (rank 0, one GPU only).
+
+``--impl reference`` times the FP64 oracle alone (the reference arm).
+Multi-GPU (torchrun): each rank runs its own independent jobs (replicas, no
+collective on the data path); ``value`` is all ranks' frame-iterations over
+the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "VI frame·iterations/s (S=2,N=40,K=10,F=513) vs roofline; p50/p99 job latency"
+UNIT = "frame·iterations/s"
+SWEEPS = 50
+FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
+TF32_OVER_BF16 = 1.1 / 2.25                              # nominal dense ratio
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--sweeps", type=int, default=SWEEPS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"],
+                "bf16_tflops_sustained": d.get("bf16_tflops_sustained", d["bf16_tflops"]),
+                "source": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "source": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample(seconds_hint: float = 20.0, sweeps: int = None):
+    """Time the FP64 oracle on the paper-size workload (a bounded number of
+    sweeps from the initial state).  Returns (frame-its/s, cores, sample)."""
+    import numpy as np  # noqa: F401
+    from oracle import vi
+    from paper_1206_6468_gb300 import synth
+    p = synth.make_problem(seed=0, **synth.PAPER_SIZE)
+    B = vi.element_mask(p.S, p.N, p.K)
+    counts, dhat = vi.init_state(p.V, p.W, p.S, p.N, p.K)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        st = vi.sweep(p.V, p.W, p.A, p.pi, p.S, p.N, p.K, p.gamma, counts, dhat, B)
+        counts, dhat = st["counts"], st["dhat"]
+        n += 1
+        el = time.perf_counter() - t0
+        if (sweeps is not None and n >= sweeps) or (sweeps is None and el >= seconds_hint):
+            break
+    vi.bound(p.V, p.W, st["alpha"], st["logZ"], p.gamma, p.S, p.K, Vhat=st["Vhat"])
+    el = time.perf_counter() - t0
+    cores = int(os.environ.get("OPENBLAS_NUM_THREADS", os.cpu_count() or 1))
+    return p.T * n / el, cores, f"{n} sweeps + bound of S2 N40 K10 F513 T3000 (FP64 NumPy)"
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from oracle import vi
+    from paper_1206_6468_gb300 import synth
+    p = synth.make_problem(seed=0, **synth.PAPER_SIZE)
+    B = vi.element_mask(p.S, p.N, p.K)
+    counts, dhat = vi.init_state(p.V, p.W, p.S, p.N, p.K)
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        st = vi.sweep(p.V, p.W, p.A, p.pi, p.S, p.N, p.K, p.gamma, counts, dhat, B)
+        counts, dhat = st["counts"], st["dhat"]
+        el = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(el)
+    tot = sum(times)
+    value = p.T * len(times) / tot
+    cores = int(os.environ.get("OPENBLAS_NUM_THREADS", os.cpu_count() or 1))
+    sample = "one sweep of S2 N40 K10 F513 T3000 per step (FP64 NumPy oracle)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "S2 N40 K10 F513 T3000, one sweep per step", "S": 2,
+                       "N": 40, "K": 10, "F": 513, "T": 3000},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def stage_cost(stage, p, precision, tc):
+    """Algorithmic work per launch of one stage: (bound, amount, unit, peak_key)."""
+    S, N, K, F, T = p.S, p.N, p.K, p.F, p.T
+    M = S * N * K
+    if stage in ("gemm1", "gemm2"):
+        flops = 2.0 * T * F * M
+        if tc:
+            return "tensor", flops, "TFLOP/s"
+        return "alu", flops, "TFLOP/s"
+    if stage == "weights":
+        return "hbm", 4.0 * (3 * T * M + 2 * S * T * N), "GB/s"
+    if stage == "fb":
+        return "hbm", 4.0 * (2 * S * T * N + S * N * N), "GB/s"
+    if stage == "bound":
+        return "hbm", 4.0 * T * M, "GB/s"
+    return "hbm", 0.0, "GB/s"
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import numpy as np
+    import torch
+
+    from paper_1206_6468_gb300 import nfhmm, synth
+    assert torch.cuda.is_available(), "bench.py needs a GPU"
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    p = synth.make_problem(seed=rank, **synth.PAPER_SIZE)
+    f32 = p.as_f32()
+    d_in = {k: torch.from_numpy(v).to(dev) for k, v in f32.items()}
+    h_in = {k: torch.from_numpy(v).pin_memory() for k, v in f32.items()}
+    h_dhat = torch.empty((p.S, p.T, p.N), dtype=torch.float32).pin_memory()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    ctx = nfhmm.VIContext(d_in["V"], d_in["W"], d_in["A"], d_in["pi"], p.S, p.N, p.K,
+                          gamma=p.gamma, precision=args.precision)
+    sweeps = args.sweeps
+
+    def step_device():
+        ctx.reinit(d_in["V"], d_in["W"], d_in["A"], d_in["pi"])
+        return ctx.sweep(sweeps, bound=True)
+
+    def step_e2e():
+        ctx.reinit(h_in["V"], h_in["W"], h_in["A"], h_in["pi"])
+        L = ctx.sweep(sweeps, bound=True)
+        ctx.posteriors(out=h_dhat)
+        return L
+
+    for _ in range(args.warmup):
+        step_device()
+    torch.cuda.synchronize()
+
+    def timed(step_fn, nsteps):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(nsteps)]
+        barrier(world)
+        torch.cuda.synchronize()
+        for e0, e1 in evs:
+            flush.zero_()
+            e0.record(stream)
+            step_fn()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        return [e0.elapsed_time(e1) for e0, e1 in evs]
+
+    sampler = ClockSampler(local if "CUDA_VISIBLE_DEVICES" not in os.environ else
+                           int(os.environ["CUDA_VISIBLE_DEVICES"].split(",")[local]))
+    sampler.start()
+    ctx.profile_enable(True)
+    for st in nfhmm.STAGES:
+        ctx.profile_read(st, reset=True)
+    l0 = ctx.kernel_launches()
+    ms = timed(step_device, args.steps)
+    launches = ctx.kernel_launches() - l0
+    prof = {st: ctx.profile_read(st, reset=True) for st in nfhmm.STAGES}
+    ctx.profile_enable(False)
+    # end-to-end through host buffers
+    step_e2e()
+    ms_e2e = timed(step_e2e, args.steps)
+    clocks = sampler.stop()
+
+    frames_its = p.T * sweeps
+    tot_ms = max_over_ranks(sum(ms), world)
+    tot_e2e = max_over_ranks(sum(ms_e2e), world)
+    value = world * frames_its * args.steps / (tot_ms / 1e3)
+    e2e_value = world * frames_its * args.steps / (tot_e2e / 1e3)
+
+    peaks = load_peaks()
+    tc = bool(ctx.query("tensor_cores"))
+    dom = max((s for s in prof if s != "init"), key=lambda s: prof[s][0])
+    dom_ms, dom_inv, dom_launches = prof[dom]
+    bound_kind, amount, unit = stage_cost(dom, p, args.precision, tc)
+    avg_s = dom_ms / 1e3 / max(dom_inv, 1)
+    if unit == "TFLOP/s":
+        achieved = amount / avg_s / 1e12
+        if bound_kind == "tensor":
+            peak = peaks["bf16_tflops_sustained"] * (1.0 if args.precision == "bf16" else TF32_OVER_BF16)
+            peak_note = f"{peaks['source']} bf16 sustained" + ("" if args.precision == "bf16" else " x 1.1/2.25 (tf32)")
+        else:
+            peak = FP32_SIMT_PEAK_TFLOPS
+            peak_note = "derived FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 x 2.07 GHz"
+    else:
+        achieved = amount / avg_s / 1e9
+        peak = peaks["hbm_gbs"]
+        peak_note = f"{peaks['source']} HBM copy bandwidth"
+    stage_ms = {s: round(prof[s][0] / args.steps, 4) for s in prof}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "bf16",
+        "data": "synthetic",
+        "config": {"workload": f"S2 N40 K10 F513 T3000, {sweeps} sweeps + bound per step",
+                   "S": p.S, "N": p.N, "K": p.K, "F": p.F, "T": p.T, "sweeps_per_step": sweeps,
+                   "precision": args.precision, "contractions": "tcgen05" if tc else "fp32 SIMT",
+                   "l2": "flushed between steps (256 MB write)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": bound_kind, "kernel": dom, "achieved": achieved, "peak": peak,
+                     "unit": unit, "frac": achieved / peak, "traffic": None,
+                     "peak_source": peak_note, "launch_ms": 1e3 * avg_s,
+                     "launches_per_invocation": dom_launches / max(dom_inv, 1),
+                     "stage_ms_per_step": stage_ms, "fb_chunk": ctx.query("fb_chunk")},
+        "e2e": {"value": e2e_value, "unit": UNIT,
+                "h2d_bytes_per_step": int(sum(v.numel() * 4 for v in h_in.values())),
+                "d2h_bytes_per_step": int(h_dhat.numel() * 4 + 8)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, sample = oracle_sample(seconds_hint=15.0)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": sample}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

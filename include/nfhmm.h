@@ -1,0 +1,215 @@
+/*
+ * nfhmm.h -- C ABI of the GB300 (sm_103a) library for variational inference
+ * in the Bayesian non-negative factorial HMM (N-FHMM) of Mysore & Sahani,
+ * "Variational Inference in Non-negative Factorial Hidden Markov Models for
+ * Efficient Audio Source Separation" (ICML 2012).
+ *
+ * The library computes, on one GPU, the sweep of Section 3.2:
+ *   Eq. 6   alpha_tk = sum_l V_lt z_tlk + gamma sum_s sum_n d_tn^(s) B_snk + 1
+ *   Eq. 7   log z_tlk = log beta_l(k) + psi(alpha_tk) - psi(sum_k alpha_tk) - kappa
+ *   Eq. 8   phi_tn^(s) = gamma sum_k B_snk (psi(alpha_tk) - psi(sum_k alpha_tk))
+ *   forward-backward on each source's chain with emissions exp(phi^(s))
+ * plus the variational lower bound and the separation of Section 4.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Sizes: S sources, N states (dictionaries) per source, K elements per
+ * dictionary, M = S*N*K elements, F frequency bins, T frames.  Element index
+ * k = (s*N + n)*K + j: the mask B_snk of Section 2.2 is implicit (block
+ * (s, n) is the K consecutive elements starting at (s*N + n)*K).
+ * Layouts are row-major, C order:
+ *   V     T x F    spectrogram, V[t*F + l] = V_lt >= 0 (quanta may be fractional)
+ *   W     M x F    dictionary elements, W[k*F + l] = beta_l(k); each row sums to 1
+ *   A     S x N x N  A[(s*N + i)*N + j] = P(D_t = j | D_{t-1} = i), rows sum to 1
+ *                  (the paper's rho^(s) holds the same numbers by columns, Sec. 2.1)
+ *   pi    S x N    initial state distributions, rows sum to 1
+ *   dhat  S x T x N  state marginals d-hat_tn^(s) of q(D^(s))
+ *   alpha T x M    Dirichlet parameters alpha-hat_tk of q(theta_t)
+ *   counts T x M   sum_l V_lt z-hat_tlk (first term of Eq. 6)
+ *   out   S x T x F  separated spectrograms
+ * Ownership: the caller owns every buffer it passes; the library copies what
+ * it keeps.  A context owns its device memory until nfhmm_destroy.
+ * Pointers flagged "on device" are CUDA device pointers of the current
+ * device; otherwise they are host pointers (pinned or pageable).
+ * Streams: a context orders all its work after the work already queued on
+ * the stream given to nfhmm_vi_init, and the stream waits for the context's
+ * work before anything queued later.  Calls return once the work is queued,
+ * except calls that write host memory or return a bound, which synchronise.
+ * Errors: every int-returning call returns NFHMM_OK (0) or a negative code;
+ * nfhmm_last_error() gives a message for the calling thread's last failure.
+ * A call that fails validation leaves the context unchanged.  Every call
+ * accepts a NULL context and returns NFHMM_EINVAL.
+ */
+#ifndef NFHMM_H
+#define NFHMM_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define NFHMM_API __attribute__((visibility("default")))
+#else
+#define NFHMM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NFHMM_OK        0
+#define NFHMM_EINVAL   (-1)  /* bad sizes, NULL pointers, invalid inputs      */
+#define NFHMM_ENOMEM   (-2)  /* device allocation failed                      */
+#define NFHMM_ECUDA    (-3)  /* a CUDA call failed                            */
+#define NFHMM_ETIMEOUT (-4)  /* a bounded device wait gave up                 */
+#define NFHMM_ENUMERIC (-5)  /* reconstruction vanished where V > 0, or NaN   */
+#define NFHMM_ESTATE   (-6)  /* call needs a state the context does not have  */
+
+#define NFHMM_FP32 0  /* contractions reach FP32 accuracy (split TF32 on tensor cores) */
+#define NFHMM_BF16 1  /* contractions in BF16 with FP32 accumulation                  */
+
+#define NFHMM_INIT_UNIFORM 0  /* d-hat = 1/N                 */
+#define NFHMM_INIT_PRIOR   1  /* d-hat = pi A^t (prior marginals) */
+
+#define NFHMM_SEP_MEAN        0  /* weights v_t alpha_tk / sum_k alpha_tk (posterior mean) */
+#define NFHMM_SEP_EXPECTATION 1  /* weights exp(psi(alpha_tk)), the weights of Eq. 7      */
+
+typedef struct nfhmm_ctx nfhmm_ctx;
+
+typedef struct {
+  int S, N, K, F, T;  /* all >= 1                                          */
+  double gamma;       /* Dirichlet concentration of Eq. 1 (paper: 1), >= 0 */
+  int precision;      /* NFHMM_FP32 or NFHMM_BF16                          */
+  int init_mode;      /* NFHMM_INIT_UNIFORM or NFHMM_INIT_PRIOR            */
+} nfhmm_dims;
+
+/*
+ * nfhmm_vi_init -- create a context for one spectrogram (Section 3.2).
+ * Copies V, W, A, pi into device memory, validates them (V finite and >= 0;
+ * W, A, pi non-negative with rows summing to 1 within 1e-4) and sets the
+ * initial state: z-hat from equal weights (z_tlk = beta_lk / sum_k' beta_lk')
+ * and d-hat from init_mode.  The paper gives no initial state; this is the
+ * library's reading.  inputs_on_device: 1 if V, W, A, pi are device
+ * pointers.  cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * On success *out holds the new context; on failure *out is NULL.
+ */
+NFHMM_API int nfhmm_vi_init(nfhmm_ctx **out, const nfhmm_dims *d,
+                  const float *V, const float *W, const float *A, const float *pi,
+                  int inputs_on_device, void *cuda_stream);
+
+/*
+ * nfhmm_vi_reinit -- load a new spectrogram and model of the same sizes into
+ * an existing context (its device memory is reused) and reset it to the
+ * initial state, as nfhmm_vi_init does.  On failure the context holds no
+ * usable state: every call but another nfhmm_vi_reinit or nfhmm_destroy
+ * returns NFHMM_ESTATE.  Synchronises once.
+ */
+NFHMM_API int nfhmm_vi_reinit(nfhmm_ctx *c, const float *V, const float *W, const float *A,
+                              const float *pi, int inputs_on_device);
+
+/*
+ * nfhmm_vi_sweep -- run n_sweeps sweeps of Section 3.2.  Each sweep applies
+ * Eq. 6 to the current (counts, d-hat), then recomputes counts (Eq. 7 into
+ * Eq. 6's first term), phi-hat (Eq. 8) and d-hat (forward-backward per
+ * source) from that alpha-hat.  bound_out: NULL, or receives the bound after
+ * the last sweep (synchronises).  n_sweeps >= 0.
+ */
+NFHMM_API int nfhmm_vi_sweep(nfhmm_ctx *c, int n_sweeps, double *bound_out);
+
+/*
+ * nfhmm_bound -- the variational lower bound of the current state
+ * (alpha-hat of the last sweep with its optimal z-hat and d-hat), reduced in
+ * FP64.  The paper prints no bound; it follows from Eq. 1 and the factorised
+ * posterior of Section 3.2.  Needs at least one sweep (else NFHMM_ESTATE).
+ * Synchronises.
+ */
+NFHMM_API int nfhmm_bound(nfhmm_ctx *c, double *out);
+
+/*
+ * nfhmm_separate -- separated spectrograms of Section 4, S x T x F.
+ * masked = 0: Vhat^(s)_lt, a combination of source s's elements weighted by
+ * the estimated mixture weights (weights: NFHMM_SEP_MEAN or
+ * NFHMM_SEP_EXPECTATION); masked = 1: V*^(s)_lt = V_lt Vhat^(s)_lt /
+ * sum_s' Vhat^(s')_lt (V/S where the denominator is 0).  Needs at least one
+ * sweep.  out_on_device: 1 if out is a device pointer (then asynchronous).
+ */
+NFHMM_API int nfhmm_separate(nfhmm_ctx *c, float *out, int masked, int weights, int out_on_device);
+
+/* nfhmm_get_posteriors -- d-hat (S x T x N) of the current state. */
+NFHMM_API int nfhmm_get_posteriors(nfhmm_ctx *c, float *dhat, int on_device);
+
+/* nfhmm_get_weights -- alpha-hat (T x M) of the last sweep (Eq. 6).  Needs a sweep. */
+NFHMM_API int nfhmm_get_weights(nfhmm_ctx *c, float *alpha, int on_device);
+
+/* nfhmm_get_surrogate -- phi-hat (S x T x N) of the last sweep, stored
+ * without the per-frame constant -gamma*K*psi(sum_k alpha_tk) of Eq. 8
+ * (it cancels in d-hat).  Needs a sweep. */
+NFHMM_API int nfhmm_get_surrogate(nfhmm_ctx *c, float *phi, int on_device);
+
+/* nfhmm_get_state / nfhmm_set_state -- checkpoint: (counts T x M,
+ * d-hat S x T x N, sweeps done).  A sweep after set_state starts from Eq. 6
+ * on these values; resuming from a saved state is bit-identical. */
+NFHMM_API int nfhmm_get_state(nfhmm_ctx *c, float *counts, float *dhat, int *sweeps_done, int on_device);
+NFHMM_API int nfhmm_set_state(nfhmm_ctx *c, const float *counts, const float *dhat, int sweeps_done,
+                    int on_device);
+
+/* nfhmm_destroy -- free the context and its device memory (waits for its work). */
+NFHMM_API void nfhmm_destroy(nfhmm_ctx *c);
+
+/* nfhmm_last_error -- message of the calling thread's last failure ("" if none). */
+NFHMM_API const char *nfhmm_last_error(void);
+
+/*
+ * nfhmm_forward_backward -- stateless forward-backward for S independent
+ * chains (the q(D^(s)) step of Section 3.2), all pointers on device:
+ * phi S x T x N (emissions exp(phi)), A S x N x N row-stochastic, pi S x N;
+ * writes dhat S x T x N and logZ[S] (FP64 log normalisers).  chunk_len: frames
+ * per time chunk of the parallel-in-time form (0 = library default, >= T =
+ * one serial chunk).  Allocates its scratch on the stream.  Asynchronous.
+ */
+NFHMM_API int nfhmm_forward_backward(int S, int N, int T, const float *phi, const float *A,
+                           const float *pi, float *dhat, double *logZ, int chunk_len,
+                           void *cuda_stream);
+
+/*
+ * nfhmm_digamma -- the library's device psi and exp(psi) on n values x >= 1
+ * (device pointers; psi_out or w_out may be NULL).  Asynchronous.
+ */
+NFHMM_API int nfhmm_digamma(const float *x, float *psi_out, float *w_out, size_t n, void *cuda_stream);
+
+/*
+ * Profiling: with profiling on, every kernel stage a context runs is
+ * bracketed by CUDA events on the stream it runs on.  nfhmm_profile_read
+ * synchronises and returns, for one stage since the last reset, the summed
+ * event time (ms), the number of stage invocations and of kernel launches.
+ */
+#define NFHMM_STAGE_WEIGHTS 0  /* Eq. 6, psi, Eq. 8                        */
+#define NFHMM_STAGE_GEMM1   1  /* reconstruction Vhat and ratio V/Vhat     */
+#define NFHMM_STAGE_GEMM2   2  /* back-projection and counts (Eq. 7 -> 6)  */
+#define NFHMM_STAGE_FB      3  /* forward-backward, all phases             */
+#define NFHMM_STAGE_BOUND   4  /* bound reduction                          */
+#define NFHMM_STAGE_INIT    5  /* inputs, validation and initial state     */
+#define NFHMM_NUM_STAGES    6
+NFHMM_API int nfhmm_profile_enable(nfhmm_ctx *c, int on);
+NFHMM_API int nfhmm_profile_read(nfhmm_ctx *c, int stage, double *ms_total,
+                                 long long *invocations, long long *launches, int reset);
+
+/* nfhmm_kernel_launches -- number of kernels this context has launched. */
+NFHMM_API long long nfhmm_kernel_launches(nfhmm_ctx *c);
+
+/*
+ * nfhmm_query -- read one property of a context into *value:
+ *   NFHMM_Q_TENSOR_CORES  1 if the contractions run on tcgen05 tensor cores
+ *   NFHMM_Q_FB_CHUNK      frames per time chunk of the forward-backward
+ *   NFHMM_Q_SWEEPS_DONE   sweeps run since the initial state
+ *   NFHMM_Q_DEVICE_BYTES  device memory the context holds
+ */
+#define NFHMM_Q_TENSOR_CORES 0
+#define NFHMM_Q_FB_CHUNK     1
+#define NFHMM_Q_SWEEPS_DONE  2
+#define NFHMM_Q_DEVICE_BYTES 3
+NFHMM_API int nfhmm_query(nfhmm_ctx *c, int key, long long *value);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NFHMM_H */

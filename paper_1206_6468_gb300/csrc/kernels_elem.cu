@@ -1,0 +1,362 @@
+// Elementwise and reduction kernels of the sweep:
+//  * the weights kernel: Eq. 6 (alpha-hat), psi and w = exp(psi) (the
+//    weights of Eq. 7), and Eq. 8 (phi-hat) as a warp-shuffle segmented
+//    reduction over each dictionary's K consecutive elements;
+//  * the bound reduction (FP64 accumulation);
+//  * initialisation, validation, layout and separation helpers.
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include "nfhmm_device.cuh"
+#include "nfhmm_kernels.h"
+
+namespace nfhmm {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// ------------------------------------------------------------ weights (Eq. 6, 8)
+// One warp per frame t.  Elements are visited in chunks of 32 consecutive k;
+// phi-hat for block g = k / K is the inclusive segmented scan of psi at the
+// block's last element, with the partial sum of a block that straddles a
+// chunk boundary carried in a register (deterministic order, no atomics).
+template <int FMT>
+__global__ void __launch_bounds__(256) k_weights(WeightsArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (t >= a.T) return;
+  const float* crow = a.counts + (size_t)t * a.Mp;
+  float* arow = a.alpha + (size_t)t * a.Mp;
+  float* wrow = a.w32 + (size_t)t * a.Mp;
+  float carry = 0.f;
+  int carry_key = -1;
+  unsigned bad = 0;
+  for (int base = 0; base < a.Mp; base += 32) {
+    const int k = base + lane;
+    const bool el = k < a.M;
+    float alpha = 0.f, psi = 0.f, w = 0.f;
+    int g = -2 - lane;  // padding lanes never match a key
+    if (el) {
+      g = k / a.K;
+      const int s = g / a.N, n = g - s * a.N;
+      alpha = crow[k] + a.gamma * a.dhat[((size_t)s * a.T + t) * a.N + n] + 1.f;
+      digamma_exp(alpha, psi, w);
+      if (!isfinite(psi) || !isfinite(w)) bad |= ERR_NONFINITE;
+    }
+    if (k < a.Mp) {
+      arow[k] = alpha;
+      wrow[k] = w;
+      if (FMT == WF_TF32X2) {
+        const float hi = tf32_hi(w);
+        reinterpret_cast<float*>(a.wop_hi)[(size_t)t * a.Mp + k] = hi;
+        reinterpret_cast<float*>(a.wop_lo)[(size_t)t * a.Mp + k] = tf32_hi(w - hi);
+      } else if (FMT == WF_BF16) {
+        reinterpret_cast<__nv_bfloat16*>(a.wop_hi)[(size_t)t * a.Mp + k] = __float2bfloat16_rn(w);
+      }
+    }
+    // inclusive segmented scan of psi keyed by block g
+    float x = psi;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const float y = __shfl_up_sync(FULL, x, d);
+      const int gy = __shfl_up_sync(FULL, g, d);
+      if (lane >= d && gy == g) x += y;
+    }
+    if (g == carry_key) x += carry;
+    if (el && (k + 1) % a.K == 0) {
+      const int s = g / a.N, n = g - s * a.N;
+      a.phi[((size_t)s * a.T + t) * a.N + n] = a.gamma * x;
+    }
+    const float x31 = __shfl_sync(FULL, x, 31);
+    const int g31 = __shfl_sync(FULL, g, 31);
+    const int k31 = base + 31;
+    if (k31 < a.M && (k31 + 1) % a.K != 0) {
+      carry = x31;
+      carry_key = g31;
+    } else {
+      carry = 0.f;
+      carry_key = -1;
+    }
+  }
+  bad = __reduce_or_sync(FULL, bad);
+  if (bad && lane == 0) atomicOr(a.err, bad);
+}
+
+void launch_weights(const WeightsArgs& a, int fmt, cudaStream_t st) {
+  const int warps = 8;
+  dim3 grid((a.T + warps - 1) / warps);
+  switch (fmt) {
+    case WF_TF32X2: k_weights<WF_TF32X2><<<grid, warps * 32, 0, st>>>(a); break;
+    case WF_BF16: k_weights<WF_BF16><<<grid, warps * 32, 0, st>>>(a); break;
+    default: k_weights<WF_F32><<<grid, warps * 32, 0, st>>>(a); break;
+  }
+}
+
+// ------------------------------------------------------------------- fills
+__global__ void k_fill_rows(float* buf, int T, int M, int ld, float value) {
+  const size_t n = (size_t)T * ld;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(i % ld);
+    buf[i] = k < M ? value : 0.f;
+  }
+}
+void launch_fill_rows(float* buf, int T, int M, int ld, float value, cudaStream_t st) {
+  const size_t n = (size_t)T * ld;
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  k_fill_rows<<<blocks, 256, 0, st>>>(buf, T, M, ld, value);
+}
+void launch_fill(float* buf, size_t n, float value, cudaStream_t st) {
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  k_fill_rows<<<blocks, 256, 0, st>>>(buf, 1, (int)n, (int)n, value);
+}
+
+// ---------------------------------------------------------------- row sums
+__global__ void k_row_sums(const float* V, int T, int F, int Fp, double* v) {
+  const int lane = threadIdx.x & 31;
+  const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (t >= T) return;
+  double s = 0.0;
+  for (int l = lane; l < F; l += 32) s += (double)V[(size_t)t * Fp + l];
+  s = warp_sum_d(s);
+  if (lane == 0) v[t] = s;
+}
+void launch_row_sums(const float* V, int T, int F, int Fp, double* v, cudaStream_t st) {
+  k_row_sums<<<(T + 7) / 8, 256, 0, st>>>(V, T, F, Fp, v);
+}
+
+// -------------------------------------------------------------- validation
+// One warp per row of W, A or pi (rows must be >= 0 and sum to 1 within 1e-4);
+// grid-stride over V (finite, >= 0).
+__global__ void k_validate(const float* V, int T, int F, int Fp, const float* W, int M,
+                           const float* A, const float* pi, int S, int N, unsigned* err) {
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int nw = gridDim.x * (blockDim.x >> 5);
+  unsigned bad = 0;
+  const int rowsW = M, rowsA = S * N, rowsP = S;
+  for (int r = gw; r < rowsW + rowsA + rowsP; r += nw) {
+    const float* row;
+    int len;
+    if (r < rowsW) {
+      row = W + (size_t)r * Fp;
+      len = F;
+    } else if (r < rowsW + rowsA) {
+      row = A + (size_t)(r - rowsW) * N;
+      len = N;
+    } else {
+      row = pi + (size_t)(r - rowsW - rowsA) * N;
+      len = N;
+    }
+    double s = 0.0;
+    unsigned b = 0;
+    for (int i = lane; i < len; i += 32) {
+      const float x = row[i];
+      if (!(x >= 0.f) || !isfinite(x)) b = 1;
+      s += (double)x;
+    }
+    s = warp_sum_d(s);
+    b = __reduce_or_sync(FULL, b);
+    if (b || fabs(s - 1.0) > 1e-4) bad = 1;
+  }
+  const size_t nv = (size_t)T * F;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nv;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const float x = V[(i / F) * Fp + (i % F)];
+    if (!(x >= 0.f) || !isfinite(x)) bad = 1;
+  }
+  bad = __reduce_or_sync(FULL, bad);
+  if (bad && lane == 0) atomicOr(err, ERR_BAD_INPUT);
+}
+void launch_validate(const float* V, int T, int F, int Fp, const float* W, int M, const float* A,
+                     const float* pi, int S, int N, unsigned* err, cudaStream_t st) {
+  k_validate<<<256, 256, 0, st>>>(V, T, F, Fp, W, M, A, pi, S, N, err);
+}
+
+// --------------------------------------------------------------- transpose
+__global__ void k_transpose(const float* in, int R, int Cc, int ldi, float* out, int ldo, int Rp,
+                            int Cp) {
+  __shared__ float tile[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int r = r0 + i, c = c0 + threadIdx.x;
+    tile[i][threadIdx.x] = (r < R && c < Cc) ? in[(size_t)r * ldi + c] : 0.f;
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int c = c0 + i, r = r0 + threadIdx.x;
+    if (c < Cp && r < Rp) out[(size_t)c * ldo + r] = tile[threadIdx.x][i];
+  }
+}
+void launch_transpose(const float* in, int R, int Cc, int ldi, float* out, int ldo, int Rp, int Cp,
+                      cudaStream_t st) {
+  dim3 grid((Cp + 31) / 32, (Rp + 31) / 32);
+  k_transpose<<<grid, dim3(32, 8), 0, st>>>(in, R, Cc, ldi, out, ldo, Rp, Cp);
+}
+
+__global__ void k_split_tf32(const float* in, float* hi, float* lo, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const float x = in[i];
+    const float h = tf32_hi(x);
+    hi[i] = h;
+    lo[i] = tf32_hi(x - h);
+  }
+}
+void launch_split_tf32(const float* in, float* hi, float* lo, size_t n, cudaStream_t st) {
+  k_split_tf32<<<1024, 256, 0, st>>>(in, hi, lo, n);
+}
+__global__ void k_to_bf16(const float* in, __nv_bfloat16* out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    out[i] = __float2bfloat16_rn(in[i]);
+}
+void launch_to_bf16(const float* in, void* out, size_t n, cudaStream_t st) {
+  k_to_bf16<<<1024, 256, 0, st>>>(in, reinterpret_cast<__nv_bfloat16*>(out), n);
+}
+
+// -------------------------------------------------------------------- bound
+// Per frame t (one warp): FP64 accumulation of
+//   sum_l V log Vhat (from the contraction's partials) - v_t psi(a0)
+//   + konst - lnGamma(a0) + sum_k g(alpha_tk) + psi(a0) (a0 - M) - S gamma K psi(a0)
+// with a0 = sum_k alpha_tk and g(a) = lnGamma(a) - (a - 1) psi(a).  The last
+// term converts the forward-backward log normalisers, computed on phi-hat
+// without its per-frame constant -gamma K psi(a0), back to Eq. 8's phi-hat.
+__global__ void k_bound_frames(BoundArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (t >= a.T) return;
+  const float* row = a.alpha + (size_t)t * a.Mp;
+  double s0 = 0.0, sg = 0.0;
+  for (int k = lane; k < a.M; k += 32) {
+    const float x = row[k];
+    s0 += (double)x;
+    sg += bound_g_elem(x);
+  }
+  s0 = warp_sum_d(s0);
+  sg = warp_sum_d(sg);
+  if (lane == 0) {
+    double vl = 0.0;
+    for (int j = 0; j < a.nbpart; ++j) vl += a.bpart[(size_t)t * a.nbpart + j];
+    const double psi0 = digamma_d(s0);
+    const double term = vl - a.v[t] * psi0 + a.konst - lgamma(s0) + sg + psi0 * (s0 - (double)a.M) -
+                        (double)a.S * (double)a.gamma * (double)a.K * psi0;
+    a.frame_terms[t] = term;
+  }
+}
+
+__global__ void k_bound_final(BoundArgs a) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int t = threadIdx.x; t < a.T; t += blockDim.x) s += a.frame_terms[t];
+  s = warp_sum_d(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double r = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    r = warp_sum_d(r);
+    if (threadIdx.x == 0) {
+      for (int i = 0; i < a.S; ++i) r += a.logZ[i];
+      a.out[0] = r;
+    }
+  }
+}
+
+void launch_bound(const BoundArgs& a, cudaStream_t st, int* launches) {
+  k_bound_frames<<<(a.T + 7) / 8, 256, 0, st>>>(a);
+  k_bound_final<<<1, 1024, 0, st>>>(a);
+  if (launches) *launches += 2;
+}
+
+// -------------------------------------------------------------- separation
+__global__ void k_sep_weights(const float* alpha, const double* v, int T, int M, int Mp, int mode,
+                              float* wts) {
+  const int lane = threadIdx.x & 31;
+  const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (t >= T) return;
+  const float* row = alpha + (size_t)t * Mp;
+  float* out = wts + (size_t)t * Mp;
+  if (mode == 0) {
+    double s = 0.0;
+    for (int k = lane; k < M; k += 32) s += (double)row[k];
+    s = warp_sum_d(s);
+    const double scale = v[t] / s;
+    for (int k = lane; k < Mp; k += 32) out[k] = k < M ? (float)(scale * (double)row[k]) : 0.f;
+  } else {
+    for (int k = lane; k < Mp; k += 32) {
+      float p, w = 0.f;
+      if (k < M) digamma_exp(row[k], p, w);
+      out[k] = w;
+    }
+  }
+}
+void launch_sep_weights(const float* alpha, const double* v, int T, int M, int Mp, int mode,
+                        float* wts, cudaStream_t st) {
+  k_sep_weights<<<(T + 7) / 8, 256, 0, st>>>(alpha, v, T, M, Mp, mode, wts);
+}
+
+__global__ void k_sep_mask(const float* V, int Fp, float* out, int S, int T, int F) {
+  const size_t n = (size_t)T * F;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const size_t t = i / F, l = i % F;
+    const float vv = V[t * Fp + l];
+    float den = 0.f;
+    for (int s = 0; s < S; ++s) den += out[(size_t)s * n + i];
+    for (int s = 0; s < S; ++s) {
+      const float x = out[(size_t)s * n + i];
+      out[(size_t)s * n + i] = den > 0.f ? vv * (x / den) : vv / (float)S;
+    }
+  }
+}
+void launch_sep_mask(const float* V, int Fp, float* out, int S, int T, int F, cudaStream_t st) {
+  k_sep_mask<<<1024, 256, 0, st>>>(V, Fp, out, S, T, F);
+}
+
+// ----------------------------------------------------------------- digamma
+__global__ void k_digamma(const float* x, float* psi, float* w, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    float p, e;
+    digamma_exp(x[i], p, e);
+    if (psi) psi[i] = p;
+    if (w) w[i] = e;
+  }
+}
+void launch_digamma(const float* x, float* psi, float* w, size_t n, cudaStream_t st) {
+  k_digamma<<<512, 256, 0, st>>>(x, psi, w, n);
+}
+
+// --------------------------------------------------------- prior marginals
+// dhat[s][0] = pi_s, dhat[s][t] = dhat[s][t-1] A_s (one block per source).
+__global__ void k_prior_marginals(const float* A, const float* pi, int S, int N, int T,
+                                  float* dhat) {
+  extern __shared__ float sm[];
+  float* As = sm;          // N*N
+  float* d = sm + N * N;   // N
+  const int s = blockIdx.x;
+  for (int i = threadIdx.x; i < N * N; i += blockDim.x) As[i] = A[(size_t)s * N * N + i];
+  for (int i = threadIdx.x; i < N; i += blockDim.x) d[i] = pi[(size_t)s * N + i];
+  __syncthreads();
+  for (int t = 0; t < T; ++t) {
+    float nj = 0.f;
+    const int j = threadIdx.x;
+    if (j < N) {
+      dhat[((size_t)s * T + t) * N + j] = d[j];
+      for (int i = 0; i < N; ++i) nj += d[i] * As[i * N + j];
+    }
+    __syncthreads();
+    if (j < N) d[j] = nj;
+    __syncthreads();
+  }
+}
+void launch_prior_marginals(const float* A, const float* pi, int S, int N, int T, float* dhat,
+                            cudaStream_t st) {
+  const int threads = ((N + 31) / 32) * 32;
+  k_prior_marginals<<<S, threads, (N * N + N) * sizeof(float), st>>>(A, pi, S, N, T, dhat);
+}
+
+}  // namespace nfhmm

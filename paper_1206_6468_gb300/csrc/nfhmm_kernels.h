@@ -1,0 +1,118 @@
+// Host-side launchers of the library's kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace nfhmm {
+
+// Error word bits set by kernels (read by the host after a synchronise).
+enum : unsigned {
+  ERR_VHAT_ZERO = 1u,  // Vhat <= 0 (or not finite) where V > 0
+  ERR_NONFINITE = 2u,  // NaN/Inf in a state array
+  ERR_BAD_INPUT = 4u,  // input validation failed
+  ERR_FB_ZERO = 8u,    // forward-backward normaliser vanished
+};
+
+// Formats of the weight operand w = exp(psi(alpha)) written by the weights kernel.
+enum WFormat { WF_F32 = 0, WF_TF32X2 = 1, WF_BF16 = 2 };
+
+struct WeightsArgs {
+  int T, M, Mp, S, N, K;
+  float gamma;
+  const float* counts;  // T x Mp
+  const float* dhat;    // S x T x N
+  float* alpha;         // T x Mp
+  float* w32;           // T x Mp, w in float (always written)
+  void* wop_hi;         // format-specific operand copies (may be null)
+  void* wop_lo;
+  float* phi;           // S x T x N (without the -gamma K psi(alpha_t0) constant)
+  unsigned* err;
+};
+void launch_weights(const WeightsArgs& a, int fmt, cudaStream_t st);
+
+// Fill buf[t*ld + k] = (k < M) ? value : 0 for t < T, k < ld.
+void launch_fill_rows(float* buf, int T, int M, int ld, float value, cudaStream_t st);
+void launch_fill(float* buf, size_t n, float value, cudaStream_t st);
+
+// v[t] = sum_l V[t*Fp + l] in double.
+void launch_row_sums(const float* V, int T, int F, int Fp, double* v, cudaStream_t st);
+
+// Validation of V (T x Fp, first F columns), W (M x Fp), A (S*N rows of N), pi (S rows of N).
+void launch_validate(const float* V, int T, int F, int Fp, const float* W, int M, const float* A,
+                     const float* pi, int S, int N, unsigned* err, cudaStream_t st);
+
+// out[c*ldo + r] = in[r*ldi + c] for r < R, c < Cc; zero elsewhere up to (Cp, Rp).
+void launch_transpose(const float* in, int R, int Cc, int ldi, float* out, int ldo, int Rp, int Cp,
+                      cudaStream_t st);
+
+// Simple split copies used by the tensor-core path.
+void launch_split_tf32(const float* in, float* hi, float* lo, size_t n, cudaStream_t st);
+void launch_to_bf16(const float* in, void* out, size_t n, cudaStream_t st);
+
+// SIMT FP32 contraction C[t][n] = sum_k A[t][k] B[n][k] with epilogues.
+enum Epilogue { EPI_RATIO = 0, EPI_SCALE = 1, EPI_STORE = 2 };
+struct GemmArgs {
+  int rows, cols, kdim;
+  const float* A; int lda;
+  const float* B; int ldb;
+  // EPI_RATIO: Q = V / C (0 where V == 0), bound partial V log C per (row, column tile)
+  const float* V; int ldv;
+  float* out; int ldo;           // Q (RATIO), counts (SCALE), output (STORE)
+  const float* w; int ldw;       // SCALE: out = w * C
+  double* bpart; int nbpart;     // RATIO: bpart[row * nbpart + column tile] (may be null)
+  unsigned* err;
+};
+void launch_gemm_simt(const GemmArgs& g, int epi, cudaStream_t st);
+int gemm_simt_col_tiles(int cols);
+
+// Forward-backward, parallel in time over chunks of L frames.
+struct FBArgs {
+  int S, N, T, L, C;
+  const float* phi;  // S x T x N
+  const float* A;    // S x N x N row-stochastic
+  const float* pi;   // S x N
+  float* dhat;       // S x T x N
+  double* logZ;      // S
+  // scratch
+  float* P;          // S x C x N x N
+  double* Plog;      // S x C
+  float* fwd;        // S x C x N
+  double* fwdlog;    // S x C
+  float* bwd;        // S x C x N
+  unsigned* err;
+};
+size_t fb_scratch_bytes(int S, int N, int T, int L);
+void fb_carve_scratch(FBArgs& a, void* base);
+int fb_default_chunk(int N, int T);
+int fb_max_states();
+void launch_fb(const FBArgs& a, cudaStream_t st, int* launches);
+
+// Bound.
+struct BoundArgs {
+  int T, M, Mp, S, K;
+  float gamma;
+  double konst;            // lnGamma(M + gamma S K) - S K lnGamma(1 + gamma)
+  const float* alpha;      // T x Mp
+  const double* v;         // T
+  const double* bpart; int nbpart;
+  const double* logZ;      // S
+  double* frame_terms;     // T
+  double* out;             // 1
+};
+void launch_bound(const BoundArgs& a, cudaStream_t st, int* launches);
+
+// Separation helpers.
+void launch_sep_weights(const float* alpha, const double* v, int T, int M, int Mp, int mode,
+                        float* wts, cudaStream_t st);
+void launch_sep_mask(const float* V, int Fp, float* out, int S, int T, int F, cudaStream_t st);
+
+// Digamma test entry.
+void launch_digamma(const float* x, float* psi, float* w, size_t n, cudaStream_t st);
+
+// Prior marginals dhat[s][t] = pi A^t (sequential in t, one block per source).
+void launch_prior_marginals(const float* A, const float* pi, int S, int N, int T, float* dhat,
+                            cudaStream_t st);
+
+}  // namespace nfhmm

@@ -1,0 +1,45 @@
+// Tensor-core (tcgen05 + TMEM + TMA) form of the two contractions (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+namespace nfhmm {
+
+struct TcPlan {
+  int precision = 0;   // NFHMM_FP32 (split TF32, three passes) or NFHMM_BF16
+  int w_format = 0;    // WFormat the weights kernel must write
+  int T = 0, M = 0, Mp = 0, F = 0, Fp = 0;
+  // operand copies owned by the plan
+  void* w_hi = nullptr;   // T x Mp  (tf32 hi as float, or bf16)
+  void* w_lo = nullptr;   // T x Mp  (tf32 lo as float; null for bf16)
+  void* q_hi = nullptr;   // T x Fp
+  void* q_lo = nullptr;
+  void* bF_hi = nullptr;  // Fp x Mp  (beta by frequency)
+  void* bF_lo = nullptr;
+  void* bM_hi = nullptr;  // Mp x Fp  (beta by element)
+  void* bM_lo = nullptr;
+  // borrowed from the context
+  const float* V = nullptr;
+  const float* w32 = nullptr;
+  float* Q = nullptr;
+  float* c = nullptr;
+  unsigned* err = nullptr;
+  // opaque tensor maps (CUtensorMap, 128 bytes each)
+  alignas(64) unsigned char maps[8][128];
+};
+
+bool tc_available();
+std::string tc_last_error();
+int tc_col_tiles_gemm1(int Fp);
+int tc_plan(TcPlan& p, int precision, int T, int M, int Mp, int F, int Fp, const float* V,
+            const float* WM, const float* WF, const float* w32, float* Q, float* c,
+            unsigned* err, cudaStream_t st);
+// Refresh the operand copies of beta from WM/WF (returns launches).
+int tc_refresh_beta(TcPlan& p, cudaStream_t st);
+int tc_gemm1(TcPlan& p, double* bpart, cudaStream_t st);  // returns launches
+int tc_gemm2(TcPlan& p, cudaStream_t st);
+void tc_free(TcPlan& p);
+
+}  // namespace nfhmm

@@ -1,0 +1,285 @@
+"""ctypes binding of libnfhmm.so (the C ABI in include/nfhmm.h).
+
+Argument marshalling only: every step of the sweep runs in the library's
+CUDA kernels.  Host arrays are numpy float32 (C-contiguous); device arrays
+are torch CUDA tensors (float32, contiguous), passed by data pointer, with
+torch's current stream as the stream.  Importing this module loads the
+library and raises ImportError if it has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libnfhmm.so")
+HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "nfhmm.h")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libnfhmm.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+_lib = ctypes.CDLL(LIB_PATH)
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENUMERIC, ESTATE = 0, -1, -2, -3, -4, -5, -6
+FP32, BF16 = 0, 1
+INIT_UNIFORM, INIT_PRIOR = 0, 1
+SEP_MEAN, SEP_EXPECTATION = 0, 1
+STAGES = {"weights": 0, "gemm1": 1, "gemm2": 2, "fb": 3, "bound": 4, "init": 5}
+QUERIES = {"tensor_cores": 0, "fb_chunk": 1, "sweeps_done": 2, "device_bytes": 3}
+
+
+class Dims(ctypes.Structure):
+    _fields_ = [("S", ctypes.c_int), ("N", ctypes.c_int), ("K", ctypes.c_int),
+                ("F", ctypes.c_int), ("T", ctypes.c_int), ("gamma", ctypes.c_double),
+                ("precision", ctypes.c_int), ("init_mode", ctypes.c_int)]
+
+
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_sigs = {
+    "nfhmm_vi_init": (_i, [ctypes.POINTER(_vp), ctypes.POINTER(Dims), _vp, _vp, _vp, _vp, _i, _vp]),
+    "nfhmm_vi_reinit": (_i, [_vp, _vp, _vp, _vp, _vp, _i]),
+    "nfhmm_vi_sweep": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_double)]),
+    "nfhmm_bound": (_i, [_vp, ctypes.POINTER(ctypes.c_double)]),
+    "nfhmm_separate": (_i, [_vp, _vp, _i, _i, _i]),
+    "nfhmm_get_posteriors": (_i, [_vp, _vp, _i]),
+    "nfhmm_get_weights": (_i, [_vp, _vp, _i]),
+    "nfhmm_get_surrogate": (_i, [_vp, _vp, _i]),
+    "nfhmm_get_state": (_i, [_vp, _vp, _vp, ctypes.POINTER(_i), _i]),
+    "nfhmm_set_state": (_i, [_vp, _vp, _vp, _i, _i]),
+    "nfhmm_destroy": (None, [_vp]),
+    "nfhmm_last_error": (ctypes.c_char_p, []),
+    "nfhmm_forward_backward": (_i, [_i, _i, _i, _vp, _vp, _vp, _vp, _vp, _i, _vp]),
+    "nfhmm_digamma": (_i, [_vp, _vp, _vp, ctypes.c_size_t, _vp]),
+    "nfhmm_profile_enable": (_i, [_vp, _i]),
+    "nfhmm_profile_read": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(ctypes.c_longlong),
+                                ctypes.POINTER(ctypes.c_longlong), _i]),
+    "nfhmm_query": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_longlong)]),
+    "nfhmm_kernel_launches": (ctypes.c_longlong, [_vp]),
+}
+for _name, (_res, _args) in _sigs.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+def declared_functions(header: str = HEADER_PATH):
+    """Names of the functions include/nfhmm.h declares."""
+    text = open(header).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(nfhmm_\w+)\s*\(", text)))
+
+
+class NfhmmError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = _lib.nfhmm_last_error().decode()
+        super().__init__(f"{where} failed with code {code}: {msg}")
+        self.code = code
+
+
+def _check(code: int, where: str):
+    if code != OK:
+        raise NfhmmError(code, where)
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    """(pointer, on_device) of a numpy array or a torch tensor."""
+    if _is_torch(x):
+        import torch
+        if x.dtype != torch.float32 and x.dtype != torch.float64:
+            raise TypeError("tensors must be float32 (float64 for logZ)")
+        if not x.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return ctypes.c_void_p(x.data_ptr()), int(x.is_cuda)
+    if not (isinstance(x, np.ndarray) and x.flags.c_contiguous):
+        raise TypeError("host arrays must be C-contiguous numpy arrays")
+    return ctypes.c_void_p(x.ctypes.data), 0
+
+
+def _stream(stream=None):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:  # pragma: no cover
+        pass
+    return ctypes.c_void_p(0)
+
+
+def _f32(x):
+    if _is_torch(x):
+        return x
+    return np.ascontiguousarray(x, dtype=np.float32)
+
+
+class VIContext:
+    """One spectrogram's variational inference state on the GPU.
+
+    V (T, F), W (M, F), A (S, N, N), pi (S, N): numpy arrays (host) or torch
+    CUDA tensors (device), float32.  precision: "fp32" or "bf16"."""
+
+    def __init__(self, V, W, A, pi, S: int, N: int, K: int, gamma: float = 1.0,
+                 precision: str = "fp32", init_mode: int = INIT_UNIFORM, stream=None):
+        V, W, A, pi = _f32(V), _f32(W), _f32(A), _f32(pi)
+        T, F = V.shape
+        self.S, self.N, self.K, self.F, self.T = S, N, K, F, T
+        self.M = S * N * K
+        self.gamma = gamma
+        d = Dims(S, N, K, F, T, gamma, {"fp32": FP32, "bf16": BF16}[precision], init_mode)
+        pv, dv = _ptr(V)
+        pw, dw = _ptr(W)
+        pa, da = _ptr(A)
+        pp, dp = _ptr(pi)
+        if len({dv, dw, da, dp}) != 1:
+            raise ValueError("V, W, A, pi must all be on the host or all on the device")
+        self._keep = (V, W, A, pi)
+        h = ctypes.c_void_p()
+        _check(_lib.nfhmm_vi_init(ctypes.byref(h), ctypes.byref(d), pv, pw, pa, pp, dv,
+                                  _stream(stream)), "nfhmm_vi_init")
+        self._h = h
+        self._keep = None
+
+    def reinit(self, V, W, A, pi):
+        """Load new inputs of the same sizes and reset to the initial state."""
+        V, W, A, pi = _f32(V), _f32(W), _f32(A), _f32(pi)
+        ptrs = [_ptr(x) for x in (V, W, A, pi)]
+        if len({d for _, d in ptrs}) != 1:
+            raise ValueError("V, W, A, pi must all be on the host or all on the device")
+        _check(_lib.nfhmm_vi_reinit(self._h, *[p for p, _ in ptrs], ptrs[0][1]),
+               "nfhmm_vi_reinit")
+
+    # -- sweeps and bound
+    def sweep(self, n: int = 1, bound: bool = False) -> Optional[float]:
+        if bound:
+            out = ctypes.c_double()
+            _check(_lib.nfhmm_vi_sweep(self._h, n, ctypes.byref(out)), "nfhmm_vi_sweep")
+            return out.value
+        _check(_lib.nfhmm_vi_sweep(self._h, n, None), "nfhmm_vi_sweep")
+        return None
+
+    def bound(self) -> float:
+        out = ctypes.c_double()
+        _check(_lib.nfhmm_bound(self._h, ctypes.byref(out)), "nfhmm_bound")
+        return out.value
+
+    # -- outputs
+    def _out(self, shape, out):
+        if out is None:
+            out = np.empty(shape, dtype=np.float32)
+        if tuple(out.shape) != tuple(shape):
+            raise ValueError(f"output must have shape {shape}")
+        return out
+
+    def separate(self, masked: bool = True, weights: str = "mean", out=None):
+        out = self._out((self.S, self.T, self.F), out)
+        p, dev = _ptr(out)
+        _check(_lib.nfhmm_separate(self._h, p, int(masked),
+                                   {"mean": SEP_MEAN, "expectation": SEP_EXPECTATION}[weights],
+                                   dev), "nfhmm_separate")
+        return out
+
+    def posteriors(self, out=None):
+        out = self._out((self.S, self.T, self.N), out)
+        p, dev = _ptr(out)
+        _check(_lib.nfhmm_get_posteriors(self._h, p, dev), "nfhmm_get_posteriors")
+        return out
+
+    def weights(self, out=None):
+        out = self._out((self.T, self.M), out)
+        p, dev = _ptr(out)
+        _check(_lib.nfhmm_get_weights(self._h, p, dev), "nfhmm_get_weights")
+        return out
+
+    def surrogate(self, out=None):
+        out = self._out((self.S, self.T, self.N), out)
+        p, dev = _ptr(out)
+        _check(_lib.nfhmm_get_surrogate(self._h, p, dev), "nfhmm_get_surrogate")
+        return out
+
+    def get_state(self):
+        counts = np.empty((self.T, self.M), dtype=np.float32)
+        dhat = np.empty((self.S, self.T, self.N), dtype=np.float32)
+        n = ctypes.c_int()
+        _check(_lib.nfhmm_get_state(self._h, _ptr(counts)[0], _ptr(dhat)[0], ctypes.byref(n), 0),
+               "nfhmm_get_state")
+        return counts, dhat, n.value
+
+    def set_state(self, counts, dhat, sweeps_done: int = 0):
+        counts, dhat = _f32(counts), _f32(dhat)
+        pc, dc = _ptr(counts)
+        pd, dd = _ptr(dhat)
+        if dc != dd:
+            raise ValueError("counts and dhat must be on the same side")
+        _check(_lib.nfhmm_set_state(self._h, pc, pd, sweeps_done, dc), "nfhmm_set_state")
+
+    # -- profiling
+    def profile_enable(self, on: bool = True):
+        _check(_lib.nfhmm_profile_enable(self._h, int(on)), "nfhmm_profile_enable")
+
+    def profile_read(self, stage: str, reset: bool = False):
+        """(summed event ms, stage invocations, kernel launches) of one stage."""
+        ms = ctypes.c_double()
+        inv = ctypes.c_longlong()
+        n = ctypes.c_longlong()
+        _check(_lib.nfhmm_profile_read(self._h, STAGES[stage], ctypes.byref(ms), ctypes.byref(inv),
+                                       ctypes.byref(n), int(reset)), "nfhmm_profile_read")
+        return ms.value, inv.value, n.value
+
+    def query(self, key: str) -> int:
+        v = ctypes.c_longlong()
+        _check(_lib.nfhmm_query(self._h, QUERIES[key], ctypes.byref(v)), "nfhmm_query")
+        return v.value
+
+    def kernel_launches(self) -> int:
+        return int(_lib.nfhmm_kernel_launches(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.nfhmm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def forward_backward(phi, A, pi, chunk_len: int = 0, stream=None):
+    """d-hat and log Z of S independent chains (torch CUDA tensors in/out)."""
+    import torch
+    S, T, N = phi.shape
+    dhat = torch.empty_like(phi)
+    logZ = torch.empty(S, dtype=torch.float64, device=phi.device)
+    _check(_lib.nfhmm_forward_backward(S, N, T, _ptr(phi)[0], _ptr(A)[0], _ptr(pi)[0],
+                                       _ptr(dhat)[0], _ptr(logZ)[0], chunk_len, _stream(stream)),
+           "nfhmm_forward_backward")
+    return dhat, logZ
+
+
+def digamma(x, stream=None):
+    """(psi(x), exp(psi(x))) from the library's device digamma (torch CUDA tensors)."""
+    import torch
+    psi = torch.empty_like(x)
+    w = torch.empty_like(x)
+    _check(_lib.nfhmm_digamma(_ptr(x)[0], _ptr(psi)[0], _ptr(w)[0], x.numel(), _stream(stream)),
+           "nfhmm_digamma")
+    return psi, w
+
+
+def call_raw(name: str):
+    """The raw ctypes function (for tests of the ABI's error handling)."""
+    return getattr(_lib, name)

@@ -1,0 +1,351 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (FP32 path): state posteriors d-hat max-abs <= 1e-5 and the bound
+relative <= 1e-6, as the task states them; alpha-hat and counts relative
+<= 2e-5, derived from FP32 contractions over <= ~1000 terms (each product
+carries <= ~7e-7 relative error in the split-TF32 form, sums of positive
+terms keep that relative error) plus FP32 rounding of the psi terms.
+"""
+import numpy as np
+import pytest
+from scipy.special import digamma as sp_digamma
+
+from oracle import vi
+from paper_1206_6468_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+D_TOL = 1e-5
+BOUND_RTOL = 1e-6
+REL_TOL = 2e-5
+
+
+@pytest.fixture(scope="module")
+def nf():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1206_6468_gb300 import build
+    build.build()
+    from paper_1206_6468_gb300 import nfhmm
+    return nfhmm
+
+
+def rel(a, b):
+    return float(np.max(np.abs(np.asarray(a, np.float64) - b) / np.maximum(np.abs(b), 1e-30)))
+
+
+def maxabs(a, b):
+    return float(np.max(np.abs(np.asarray(a, np.float64) - b)))
+
+
+def _ctx(nf, p, precision="fp32", device=False, init_mode=0):
+    f = p.as_f32()
+    if device:
+        import torch
+        f = {k: torch.from_numpy(v).cuda() for k, v in f.items()}
+    return nf.VIContext(f["V"], f["W"], f["A"], f["pi"], p.S, p.N, p.K, gamma=p.gamma,
+                        precision=precision, init_mode=init_mode)
+
+
+# ------------------------------------------------------------------ digamma
+
+def test_digamma_and_weights(nf):
+    import torch
+    x = np.concatenate([1 + np.linspace(0, 10, 20001), np.logspace(0, 7, 20001),
+                        1 + np.random.default_rng(0).gamma(0.5, 20.0, 20000)]).astype(np.float32)
+    psi, w = nf.digamma(torch.from_numpy(x).cuda())
+    psi = psi.cpu().numpy().astype(np.float64)
+    w = w.cpu().numpy().astype(np.float64)
+    ref = sp_digamma(x.astype(np.float64))
+    assert np.max(np.abs(psi - ref) / (1.0 + np.abs(ref))) < 6e-7
+    assert rel(w, np.exp(ref)) < 1e-6
+
+
+# -------------------------------------------------------- forward-backward
+
+@pytest.mark.parametrize("S,N,T,L,scale", [
+    (2, 40, 3000, 0, 20.0),   # paper-like chains, default chunking
+    (1, 1, 5, 0, 3.0),        # single state
+    (2, 3, 1, 0, 3.0),        # single frame
+    (3, 7, 130, 16, 10.0),    # ragged last chunk
+    (2, 64, 257, 64, 30.0),   # largest N, ragged
+    (1, 5, 100, 1, 5.0),      # one frame per chunk
+    (1, 5, 100, 128, 5.0),    # one chunk
+    (2, 40, 1000, 7, 50.0),   # odd chunk length, sharp posteriors
+])
+def test_forward_backward(nf, S, N, T, L, scale):
+    import torch
+    rng = np.random.default_rng(S * 1000 + N * 10 + T)
+    A = np.stack([0.5 * rng.dirichlet(np.ones(N), size=N) + 0.5 * synth.transition_matrix(N, 0.9)
+                  for _ in range(S)])
+    pi = rng.dirichlet(np.ones(N), size=S)
+    phi = scale * rng.standard_normal((S, T, N))
+    dg, lzg = nf.forward_backward(torch.tensor(phi, dtype=torch.float32).cuda(),
+                                  torch.tensor(A, dtype=torch.float32).cuda(),
+                                  torch.tensor(pi, dtype=torch.float32).cuda(), chunk_len=L)
+    torch.cuda.synchronize()
+    dg, lzg = dg.cpu().numpy(), lzg.cpu().numpy()
+    A32 = A.astype(np.float32).astype(np.float64)
+    pi32 = pi.astype(np.float32).astype(np.float64)
+    phi32 = phi.astype(np.float32).astype(np.float64)
+    for s in range(S):
+        d, lz = vi.forward_backward(phi32[s], A32[s], pi32[s])
+        assert maxabs(dg[s], d) <= D_TOL
+        assert abs(lzg[s] - lz) <= 1e-6 * max(1.0, abs(lz))
+
+
+# ------------------------------------------------------------ state/sweep
+
+def _oracle_state(p, n_sweeps):
+    B = vi.element_mask(p.S, p.N, p.K)
+    counts, dhat = vi.init_state(p.V, p.W, p.S, p.N, p.K)
+    st = None
+    for _ in range(n_sweeps):
+        st = vi.sweep(p.V, p.W, p.A, p.pi, p.S, p.N, p.K, p.gamma, counts, dhat, B)
+        counts, dhat = st["counts"], st["dhat"]
+    return counts, dhat, st
+
+
+def _f32_problem(p):
+    """The problem with its inputs rounded to float32 (what the GPU sees)."""
+    q = synth.Problem(**{k: getattr(p, k) for k in
+                         ("S", "N", "K", "F", "T", "gamma", "V", "W", "A", "pi", "D", "seed")})
+    q.V = p.V.astype(np.float32).astype(np.float64)
+    q.W = p.W.astype(np.float32).astype(np.float64)
+    q.A = p.A.astype(np.float32).astype(np.float64)
+    q.pi = p.pi.astype(np.float32).astype(np.float64)
+    return q
+
+
+def test_initial_state(nf):
+    p = _f32_problem(synth.make_problem(seed=1, **synth.SMALL))
+    with _ctx(nf, p) as ctx:
+        counts, dhat, n = ctx.get_state()
+    c_ref, d_ref = vi.init_state(p.V, p.W, p.S, p.N, p.K)
+    assert n == 0
+    assert rel(counts[c_ref > 1e-3], c_ref[c_ref > 1e-3]) <= REL_TOL
+    assert maxabs(counts, c_ref) <= 1e-5 * np.abs(c_ref).max()
+    assert maxabs(dhat, d_ref) == 0.0
+
+
+def test_initial_state_prior_marginals(nf):
+    p = _f32_problem(synth.make_problem(seed=2, **synth.SMALL))
+    with _ctx(nf, p, init_mode=1) as ctx:
+        _, dhat, _ = ctx.get_state()
+    _, d_ref = vi.init_state(p.V, p.W, p.S, p.N, p.K, p.A, p.pi, mode=1)
+    assert maxabs(dhat, d_ref) <= 1e-6
+
+
+@pytest.mark.parametrize("workload,k", [("SMALL", 0), ("SMALL", 5), ("PAPER_SIZE", 2)])
+def test_one_sweep_from_oracle_state(nf, workload, k):
+    """One sweep started from the oracle's state after k sweeps: every output
+    of the sweep against the oracle's same sweep."""
+    cfg = getattr(synth, workload)
+    p = _f32_problem(synth.make_problem(seed=3, **cfg))
+    counts, dhat, _ = _oracle_state(p, k)
+    c32 = counts.astype(np.float32)
+    d32 = dhat.astype(np.float32)
+    B = vi.element_mask(p.S, p.N, p.K)
+    ref = vi.sweep(p.V, p.W, p.A, p.pi, p.S, p.N, p.K, p.gamma, c32.astype(np.float64),
+                   d32.astype(np.float64), B)
+    L_ref = vi.bound(p.V, p.W, ref["alpha"], ref["logZ"], p.gamma, p.S, p.K, Vhat=ref["Vhat"])
+    with _ctx(nf, p) as ctx:
+        ctx.set_state(c32, d32, k)
+        L = ctx.sweep(1, bound=True)
+        alpha = ctx.weights()
+        phi = ctx.surrogate()
+        counts_g, dhat_g, n = ctx.get_state()
+    assert n == k + 1
+    assert rel(alpha, ref["alpha"]) <= REL_TOL
+    # phi-hat up to its per-frame constant -gamma K psi(alpha_t0)
+    a0 = ref["alpha"].sum(axis=1)
+    phi_ref = ref["phi"] + p.gamma * p.K * sp_digamma(a0)[None, :, None]
+    assert np.max(np.abs(phi - phi_ref) / (1.0 + np.abs(phi_ref))) <= REL_TOL
+    big = ref["counts"] > 1e-2 * ref["counts"].max()
+    assert rel(counts_g[big], ref["counts"][big]) <= REL_TOL
+    assert maxabs(counts_g, ref["counts"]) <= REL_TOL * ref["counts"].max()
+    assert maxabs(dhat_g, ref["dhat"]) <= D_TOL
+    assert abs(L - L_ref) <= BOUND_RTOL * abs(L_ref)
+
+
+def test_end_to_end_small(nf):
+    """20 sweeps of the small workload from the initial state: the bound
+    after every sweep and the final posteriors."""
+    p = _f32_problem(synth.make_problem(seed=0, **synth.SMALL))
+    ref = vi.run(p.V, p.W, p.A, p.pi, p.S, p.N, p.K, p.gamma, 20)
+    bounds = []
+    with _ctx(nf, p, device=True) as ctx:
+        for _ in range(20):
+            bounds.append(ctx.sweep(1, bound=True))
+        dhat = ctx.posteriors()
+        alpha = ctx.weights()
+    bounds = np.array(bounds)
+    assert np.all(np.abs(bounds - ref["bounds"]) <= BOUND_RTOL * np.abs(ref["bounds"]))
+    assert np.all(np.diff(bounds) >= -1e-6 * np.abs(bounds[1:]))
+    assert maxabs(dhat, ref["dhat"]) <= D_TOL
+    assert rel(alpha, ref["alpha"]) <= 1e-4
+
+
+def test_end_to_end_paper_size(nf):
+    """A few sweeps at S2 N40 K10 F513 T3000 from the initial state."""
+    p = _f32_problem(synth.make_problem(seed=0, **synth.PAPER_SIZE))
+    n = 4
+    ref = vi.run(p.V, p.W, p.A, p.pi, p.S, p.N, p.K, p.gamma, n)
+    with _ctx(nf, p, device=True) as ctx:
+        L = ctx.sweep(n, bound=True)
+        dhat = ctx.posteriors()
+    assert maxabs(dhat, ref["dhat"]) <= D_TOL
+    assert abs(L - ref["bounds"][-1]) <= BOUND_RTOL * abs(ref["bounds"][-1])
+
+
+@pytest.mark.parametrize("shape", [
+    dict(S=1, N=1, K=1, F=1, T=1),
+    dict(S=1, N=2, K=1, F=3, T=2),
+    dict(S=3, N=2, K=3, F=17, T=5),
+    dict(S=2, N=5, K=7, F=33, T=129),
+    dict(S=2, N=64, K=1, F=40, T=70),
+])
+def test_edge_shapes(nf, shape):
+    p = _f32_problem(synth.make_problem(seed=4, self_prob=0.8, energy_sigma=0.5,
+                                        quanta_scale=20.0, **shape))
+    n = 3
+    ref = vi.run(p.V, p.W, p.A, p.pi, p.S, p.N, p.K, p.gamma, n)
+    with _ctx(nf, p) as ctx:
+        L = ctx.sweep(n, bound=True)
+        dhat = ctx.posteriors()
+    assert maxabs(dhat, ref["dhat"]) <= D_TOL
+    assert abs(L - ref["bounds"][-1]) <= BOUND_RTOL * abs(ref["bounds"][-1])
+
+
+# -------------------------------------------------------------- separation
+
+@pytest.mark.parametrize("masked", [True, False])
+@pytest.mark.parametrize("weights", ["mean", "expectation"])
+def test_separation(nf, masked, weights):
+    p = _f32_problem(synth.make_problem(seed=5, **synth.SMALL))
+    n = 3
+    with _ctx(nf, p) as ctx:
+        ctx.sweep(n)
+        alpha = ctx.weights().astype(np.float64)
+        out = ctx.separate(masked=masked, weights=weights)
+    ref = vi.separate(p.V, p.W, alpha, p.S, p.N, p.K, masked=masked, weights=weights)
+    scale = np.abs(ref).max()
+    assert maxabs(out, ref) <= 2e-6 * scale
+    if masked:
+        assert maxabs(out.sum(axis=0), p.V) <= 2e-6 * np.abs(p.V).max()
+
+
+def test_separation_device_output(nf):
+    import torch
+    p = _f32_problem(synth.make_problem(seed=6, **synth.SMALL))
+    with _ctx(nf, p) as ctx:
+        ctx.sweep(2)
+        host = ctx.separate()
+        dev = torch.empty((p.S, p.T, p.F), dtype=torch.float32, device="cuda")
+        ctx.separate(out=dev)
+        torch.cuda.synchronize()
+    assert np.array_equal(host, dev.cpu().numpy())
+
+
+# ------------------------------------------------ checkpoint and determinism
+
+def test_checkpoint_resume_is_bit_identical(nf):
+    p = _f32_problem(synth.make_problem(seed=7, **synth.SMALL))
+    with _ctx(nf, p) as a:
+        a.sweep(4)
+        counts, dhat, n = a.get_state()
+        a.sweep(3)
+        d_cont = a.posteriors()
+        L_cont = a.bound()
+    with _ctx(nf, p) as b:
+        b.set_state(counts, dhat, n)
+        b.sweep(3)
+        d_res = b.posteriors()
+        L_res = b.bound()
+    assert np.array_equal(d_cont, d_res)
+    assert L_cont == L_res
+
+
+def test_device_and_host_inputs_agree(nf):
+    p = _f32_problem(synth.make_problem(seed=8, **synth.SMALL))
+    with _ctx(nf, p, device=False) as a:
+        La = a.sweep(5, bound=True)
+        da = a.posteriors()
+    with _ctx(nf, p, device=True) as b:
+        Lb = b.sweep(5, bound=True)
+        db = b.posteriors()
+    assert np.array_equal(da, db) and La == Lb
+
+
+# ----------------------------------------------------------------- errors
+
+def test_invalid_inputs_rejected(nf):
+    p = synth.make_problem(seed=9, S=2, N=3, K=2, F=16, T=20)
+    f = p.as_f32()
+    bad_v = f["V"].copy()
+    bad_v[3, 4] = np.nan
+    with pytest.raises(nf.NfhmmError) as e:
+        nf.VIContext(bad_v, f["W"], f["A"], f["pi"], p.S, p.N, p.K)
+    assert e.value.code == nf.EINVAL
+    bad_v[3, 4] = -1.0
+    with pytest.raises(nf.NfhmmError):
+        nf.VIContext(bad_v, f["W"], f["A"], f["pi"], p.S, p.N, p.K)
+    bad_w = f["W"] * 1.01
+    with pytest.raises(nf.NfhmmError):
+        nf.VIContext(f["V"], bad_w, f["A"], f["pi"], p.S, p.N, p.K)
+    bad_a = f["A"].copy()
+    bad_a[0, 0, 0] += 0.1
+    with pytest.raises(nf.NfhmmError):
+        nf.VIContext(f["V"], f["W"], bad_a, f["pi"], p.S, p.N, p.K)
+    with nf.VIContext(f["V"], f["W"], f["A"], f["pi"], p.S, p.N, p.K) as ctx:
+        with pytest.raises(nf.NfhmmError) as e:
+            ctx.bound()
+        assert e.value.code == nf.ESTATE
+        with pytest.raises(nf.NfhmmError):
+            ctx.separate()
+        ctx.sweep(1)
+        ctx.bound()  # the context is still usable
+
+
+def test_zero_reconstruction_is_reported(nf):
+    """A frequency with V > 0 that no dictionary element covers makes Vhat
+    vanish there: NFHMM_ENUMERIC, not silent garbage."""
+    p = synth.make_problem(seed=10, S=1, N=2, K=2, F=8, T=6, quanta_scale=10.0)
+    f = p.as_f32()
+    W = f["W"].copy()
+    W[:, 5] = 0.0
+    W /= W.sum(axis=1, keepdims=True)
+    V = f["V"].copy()
+    V[:, 5] = 1.0
+    with pytest.raises(nf.NfhmmError) as e:
+        nf.VIContext(V, W, f["A"], f["pi"], p.S, p.N, p.K)
+    assert e.value.code == nf.ENUMERIC
+
+
+def test_reinit_matches_fresh_context(nf):
+    p1 = _f32_problem(synth.make_problem(seed=11, **synth.SMALL))
+    p2 = _f32_problem(synth.make_problem(seed=12, **synth.SMALL))
+    with _ctx(nf, p1) as a:
+        a.sweep(3)
+        f = p2.as_f32()
+        a.reinit(f["V"], f["W"], f["A"], f["pi"])
+        assert a.query("sweeps_done") == 0
+        La = a.sweep(4, bound=True)
+        da = a.posteriors()
+    with _ctx(nf, p2) as b:
+        Lb = b.sweep(4, bound=True)
+        db = b.posteriors()
+    assert np.array_equal(da, db) and La == Lb
+
+
+def test_profiling_counts_stages(nf):
+    p = _f32_problem(synth.make_problem(seed=13, **synth.SMALL))
+    with _ctx(nf, p) as ctx:
+        ctx.profile_enable(True)
+        ctx.sweep(3, bound=True)
+        for st in ("weights", "gemm1", "gemm2", "fb"):
+            ms, inv, launches = ctx.profile_read(st)
+            assert inv == 3 and launches >= 3 and ms > 0
+        ms, inv, _ = ctx.profile_read("bound")
+        assert inv == 1
