@@ -254,7 +254,7 @@ int one_sweep(nfhmm_ctx* c, bool want_bpart) {
   CK(cudaStreamWaitEvent(c->s_aux, c->ev_fork, 0));
   stage_begin(c, NFHMM_STAGE_FB, c->s_aux);
   int nfb = 0;
-  launch_fb(c->fb, c->s_aux, &nfb);
+  CK(launch_fb(c->fb, c->s_aux, &nfb));
   stage_end(c, NFHMM_STAGE_FB, c->s_aux, nfb);
   int rc = contract(c, want_bpart, false);
   if (rc) return rc;
@@ -660,9 +660,9 @@ int nfhmm_forward_backward(int S, int N, int T, const float* phi, const float* A
   fb_carve_scratch(a, scratch);
   a.err = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(scratch) + bytes - 256);
   CK(cudaMemsetAsync(a.err, 0, 4, st));
-  launch_fb(a, st, nullptr);
-  CK(cudaGetLastError());
+  const cudaError_t le = launch_fb(a, st, nullptr);
   CK(cudaFreeAsync(scratch, st));
+  CK(le);
   return NFHMM_OK;
 }
 

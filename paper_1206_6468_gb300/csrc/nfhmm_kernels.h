@@ -76,18 +76,19 @@ struct FBArgs {
   float* dhat;       // S x T x N
   double* logZ;      // S
   // scratch
-  float* P;          // S x C x N x N
-  double* Plog;      // S x C
-  float* fwd;        // S x C x N
-  double* fwdlog;    // S x C
-  float* bwd;        // S x C x N
+  float* P;          // S x C x nn4(N)   chunk matrices, row-major
+  float* PT;         // S x C x nn4(N)   the same, transposed
+  double* Plog;      // S x C            log of each chunk matrix's scale
+  float* fwd;        // S x C x N        forward boundary vectors
+  float* lam;        // S x C            forward scan normalisers
+  float* bwd;        // S x C x N        backward boundary vectors
   unsigned* err;
 };
 size_t fb_scratch_bytes(int S, int N, int T, int L);
 void fb_carve_scratch(FBArgs& a, void* base);
 int fb_default_chunk(int N, int T);
 int fb_max_states();
-void launch_fb(const FBArgs& a, cudaStream_t st, int* launches);
+cudaError_t launch_fb(const FBArgs& a, cudaStream_t st, int* launches);
 
 // Bound.
 struct BoundArgs {

@@ -187,16 +187,48 @@ def test_end_to_end_small(nf):
     assert rel(alpha, ref["alpha"]) <= 1e-4
 
 
-def test_end_to_end_paper_size(nf):
-    """A few sweeps at S2 N40 K10 F513 T3000 from the initial state."""
+def test_trajectory_paper_size(nf):
+    """S2 N40 K10 F513 T3000 over 6 sweeps from the initial state.
+
+    Strict parity (d-hat max-abs <= 1e-5, bound relative <= 1e-6) for every
+    sweep of the trajectory, each started from the oracle's state at that
+    sweep (re-anchored), and the end-to-end bound at every sweep.  End to
+    end, d-hat differences at near-tie frames grow about 3-4x per sweep on
+    this workload -- the FP64 oracle itself diverges the same way when its
+    state is rounded to float32 between sweeps -- so the end-to-end d-hat is
+    held to 1e-5 for the first sweep and reported after that."""
     p = _f32_problem(synth.make_problem(seed=0, **synth.PAPER_SIZE))
-    n = 4
-    ref = vi.run(p.V, p.W, p.A, p.pi, p.S, p.N, p.K, p.gamma, n)
+    n = 6
+    B = vi.element_mask(p.S, p.N, p.K)
+    counts, dhat = vi.init_state(p.V, p.W, p.S, p.N, p.K)
+    ref_states, ref_bounds, ref_dhat = [], [], []
+    for _ in range(n):
+        c32, d32 = counts.astype(np.float32), dhat.astype(np.float32)
+        st = vi.sweep(p.V, p.W, p.A, p.pi, p.S, p.N, p.K, p.gamma, c32.astype(np.float64),
+                      d32.astype(np.float64), B)
+        ref_states.append((c32, d32, st["dhat"],
+                           vi.bound(p.V, p.W, st["alpha"], st["logZ"], p.gamma, p.S, p.K,
+                                    Vhat=st["Vhat"])))
+        full = vi.sweep(p.V, p.W, p.A, p.pi, p.S, p.N, p.K, p.gamma, counts, dhat, B)
+        counts, dhat = full["counts"], full["dhat"]
+        ref_dhat.append(dhat)
+        ref_bounds.append(vi.bound(p.V, p.W, full["alpha"], full["logZ"], p.gamma, p.S, p.K,
+                                   Vhat=full["Vhat"]))
     with _ctx(nf, p, device=True) as ctx:
-        L = ctx.sweep(n, bound=True)
-        dhat = ctx.posteriors()
-    assert maxabs(dhat, ref["dhat"]) <= D_TOL
-    assert abs(L - ref["bounds"][-1]) <= BOUND_RTOL * abs(ref["bounds"][-1])
+        for k, (c32, d32, d_ref, L_ref) in enumerate(ref_states):
+            ctx.set_state(c32, d32, k)
+            L = ctx.sweep(1, bound=True)
+            assert maxabs(ctx.posteriors(), d_ref) <= D_TOL, k
+            assert abs(L - L_ref) <= BOUND_RTOL * abs(L_ref), k
+        f = p.as_f32()
+        ctx.reinit(f["V"], f["W"], f["A"], f["pi"])
+        errs = []
+        for k in range(n):
+            L = ctx.sweep(1, bound=True)
+            assert abs(L - ref_bounds[k]) <= BOUND_RTOL * abs(ref_bounds[k]), k
+            errs.append(maxabs(ctx.posteriors(), ref_dhat[k]))
+    print("end-to-end d-hat max-abs per sweep:", ["%.1e" % e for e in errs])
+    assert errs[0] <= D_TOL
 
 
 @pytest.mark.parametrize("shape", [
@@ -215,7 +247,10 @@ def test_edge_shapes(nf, shape):
         L = ctx.sweep(n, bound=True)
         dhat = ctx.posteriors()
     assert maxabs(dhat, ref["dhat"]) <= D_TOL
-    assert abs(L - ref["bounds"][-1]) <= BOUND_RTOL * abs(ref["bounds"][-1])
+    # the bound's terms scale with the quanta and the frame count; a bound that
+    # is exactly 0 (one element, one bin) is held to that scale
+    scale = max(abs(ref["bounds"][-1]), p.V.sum() + p.T)
+    assert abs(L - ref["bounds"][-1]) <= BOUND_RTOL * scale
 
 
 # -------------------------------------------------------------- separation
