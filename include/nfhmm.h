@@ -170,6 +170,31 @@ NFHMM_API int nfhmm_forward_backward(int S, int N, int T, const float *phi, cons
                            void *cuda_stream);
 
 /*
+ * nfhmm_forward_backward_noalloc -- the same computation, arguments and
+ * results as nfhmm_forward_backward, for callers that must not allocate
+ * device memory when they call in: processes whose device memory belongs to
+ * another allocator (a serving runtime with a fixed HBM budget, a host
+ * framework that owns every byte) or latency-critical threads that cannot
+ * risk cudaMalloc/cudaFree, which may block and synchronise the device.  The
+ * paper has no counterpart; this is a property of the interface only.
+ * The call allocates nothing: its scratch is one fixed device array of
+ * NFHMM_NOALLOC_SCRATCH_BYTES compiled into the library, which every GPU that
+ * loads the library holds until the process exits.  A problem needs about
+ * 8*S*ceil(T/L)*(N*N + N) + 12*S*ceil(T/L) bytes (L = chunk length, at most
+ * 128; default min(64, max(16, ceil(sqrt(T))))) plus alignment; larger
+ * problems are rejected with NFHMM_EINVAL and a message giving both sizes.
+ * The first call on a device looks up the array's device address (with that
+ * device current) and should be made before any stream capture.  All calls
+ * share the array and it keeps the last call's contents: calls whose work
+ * overlaps on the GPU (different streams, or different host threads without
+ * ordering) race on it.  Asynchronous; inputs and outputs on the device.
+ */
+#define NFHMM_NOALLOC_SCRATCH_BYTES (8u << 20)
+NFHMM_API int nfhmm_forward_backward_noalloc(int S, int N, int T, const float *phi,
+                                             const float *A, const float *pi, float *dhat,
+                                             double *logZ, int chunk_len, void *cuda_stream);
+
+/*
  * nfhmm_digamma -- the library's device psi and exp(psi) on n values x >= 1
  * (device pointers; psi_out or w_out may be NULL).  Asynchronous.
  */

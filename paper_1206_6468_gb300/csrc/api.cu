@@ -24,6 +24,12 @@ int fail(int code, const std::string& msg) {
   return code;
 }
 
+}  // namespace
+
+void nfhmm::set_last_error(const std::string& msg) { g_last_error = msg; }
+
+namespace {
+
 #define CK(call)                                                                       \
   do {                                                                                 \
     cudaError_t e_ = (call);                                                           \

@@ -5,6 +5,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace nfhmm {
 
 // Error word bits set by kernels (read by the host after a synchronise).
@@ -14,6 +16,9 @@ enum : unsigned {
   ERR_BAD_INPUT = 4u,  // input validation failed
   ERR_FB_ZERO = 8u,    // forward-backward normaliser vanished
 };
+
+// Records the calling thread's last error message (returned by nfhmm_last_error).
+void set_last_error(const std::string& msg);
 
 // Formats of the weight operand w = exp(psi(alpha)) written by the weights kernel.
 enum WFormat { WF_F32 = 0, WF_TF32X2 = 1, WF_BF16 = 2 };

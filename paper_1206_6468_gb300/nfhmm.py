@@ -53,6 +53,7 @@ _sigs = {
     "nfhmm_destroy": (None, [_vp]),
     "nfhmm_last_error": (ctypes.c_char_p, []),
     "nfhmm_forward_backward": (_i, [_i, _i, _i, _vp, _vp, _vp, _vp, _vp, _i, _vp]),
+    "nfhmm_forward_backward_noalloc": (_i, [_i, _i, _i, _vp, _vp, _vp, _vp, _vp, _i, _vp]),
     "nfhmm_digamma": (_i, [_vp, _vp, _vp, ctypes.c_size_t, _vp]),
     "nfhmm_profile_enable": (_i, [_vp, _i]),
     "nfhmm_profile_read": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_double),
