@@ -180,9 +180,10 @@ NFHMM_API int nfhmm_forward_backward(int S, int N, int T, const float *phi, cons
  * The call allocates nothing: its scratch is one fixed device array of
  * NFHMM_NOALLOC_SCRATCH_BYTES compiled into the library, which every GPU that
  * loads the library holds until the process exits.  A problem needs about
- * 8*S*ceil(T/L)*(N*N + N) + 12*S*ceil(T/L) bytes (L = chunk length, at most
- * 128; default min(64, max(16, ceil(sqrt(T))))) plus alignment; larger
- * problems are rejected with NFHMM_EINVAL and a message giving both sizes.
+ * 8*S*C*(P*P + N) + 12*S*C bytes, C = ceil(T/L), P = 8*ceil(N/8) (L = chunk
+ * length, at most 128; by default min(48, max(16, ceil(sqrt(T)) - 6))), plus
+ * alignment; larger problems are rejected with NFHMM_EINVAL and a message
+ * giving both sizes.
  * The first call on a device looks up the array's device address (with that
  * device current) and should be made before any stream capture.  All calls
  * share the array and it keeps the last call's contents: calls whose work
