@@ -63,8 +63,9 @@ extern "C" {
 #define NFHMM_ENUMERIC (-5)  /* reconstruction vanished where V > 0, or NaN   */
 #define NFHMM_ESTATE   (-6)  /* call needs a state the context does not have  */
 
-#define NFHMM_FP32 0  /* contractions reach FP32 accuracy (split TF32 on tensor cores) */
-#define NFHMM_BF16 1  /* contractions in BF16 with FP32 accumulation                  */
+#define NFHMM_FP32      0  /* contractions on tcgen05 tensor cores in split TF32 (FP32 accuracy) */
+#define NFHMM_BF16      1  /* contractions on tcgen05 tensor cores, BF16 operands, FP32 accumulate */
+#define NFHMM_FP32_SIMT 2  /* contractions on CUDA cores in FP32 (the plain GPU path)            */
 
 #define NFHMM_INIT_UNIFORM 0  /* d-hat = 1/N                 */
 #define NFHMM_INIT_PRIOR   1  /* d-hat = pi A^t (prior marginals) */
@@ -77,7 +78,7 @@ typedef struct nfhmm_ctx nfhmm_ctx;
 typedef struct {
   int S, N, K, F, T;  /* all >= 1                                          */
   double gamma;       /* Dirichlet concentration of Eq. 1 (paper: 1), >= 0 */
-  int precision;      /* NFHMM_FP32 or NFHMM_BF16                          */
+  int precision;      /* NFHMM_FP32, NFHMM_BF16 or NFHMM_FP32_SIMT         */
   int init_mode;      /* NFHMM_INIT_UNIFORM or NFHMM_INIT_PRIOR            */
 } nfhmm_dims;
 

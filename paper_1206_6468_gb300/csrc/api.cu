@@ -163,6 +163,8 @@ int sync_check(nfhmm_ctx* c) {
   if (e) {
     cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->s_main);
     cudaStreamSynchronize(c->s_main);
+    if (e & ERR_TIMEOUT)
+      return fail(NFHMM_ETIMEOUT, "a bounded device wait gave up (tensor-core pipeline)");
     if (e & ERR_BAD_INPUT)
       return fail(NFHMM_EINVAL,
                   "input validation failed: V must be finite and >= 0; rows of W, A and pi "
@@ -184,10 +186,12 @@ int contract(nfhmm_ctx* c, bool want_bpart, bool init) {
   cudaStream_t st = c->s_main;
   if (c->use_tc && !init) {
     stage_begin(c, NFHMM_STAGE_GEMM1, st);
-    int n1 = tc_gemm1(c->tc, want_bpart ? c->bpart : nullptr, st);
+    const int n1 = tc_gemm1(c->tc, want_bpart ? c->bpart : nullptr, st);
+    if (n1 < 0) return fail(NFHMM_ECUDA, "tensor-core contraction: " + tc_last_error());
     stage_end(c, NFHMM_STAGE_GEMM1, st, n1);
     stage_begin(c, NFHMM_STAGE_GEMM2, st);
-    int n2 = tc_gemm2(c->tc, st);
+    const int n2 = tc_gemm2(c->tc, st);
+    if (n2 < 0) return fail(NFHMM_ECUDA, "tensor-core contraction: " + tc_last_error());
     stage_end(c, NFHMM_STAGE_GEMM2, st, n2);
     return NFHMM_OK;
   }
@@ -377,8 +381,8 @@ int nfhmm_vi_init(nfhmm_ctx** out, const nfhmm_dims* dp, const float* V, const f
   if (d.N > fb_max_states())
     return fail(NFHMM_EINVAL, "N must be <= " + std::to_string(fb_max_states()));
   if (!(d.gamma >= 0.0) || !isfinite(d.gamma)) return fail(NFHMM_EINVAL, "gamma must be >= 0");
-  if (d.precision != NFHMM_FP32 && d.precision != NFHMM_BF16)
-    return fail(NFHMM_EINVAL, "precision must be NFHMM_FP32 or NFHMM_BF16");
+  if (d.precision != NFHMM_FP32 && d.precision != NFHMM_BF16 && d.precision != NFHMM_FP32_SIMT)
+    return fail(NFHMM_EINVAL, "precision must be NFHMM_FP32, NFHMM_BF16 or NFHMM_FP32_SIMT");
   if (d.init_mode != NFHMM_INIT_UNIFORM && d.init_mode != NFHMM_INIT_PRIOR)
     return fail(NFHMM_EINVAL, "init_mode must be NFHMM_INIT_UNIFORM or NFHMM_INIT_PRIOR");
 
@@ -449,13 +453,14 @@ int nfhmm_vi_init(nfhmm_ctx** out, const nfhmm_dims* dp, const float* V, const f
   c->fb.err = c->err;
 
   // tensor-core plan (operand copies of beta, tensor maps)
-  if (tc_available()) {
+  if (d.precision != NFHMM_FP32_SIMT) {
+    if (!tc_available())
+      return bail(fail(NFHMM_EINVAL, "tensor-core contractions need an sm_103 device"));
     rc = tc_plan(c->tc, d.precision, d.T, c->M, c->Mp, d.F, c->Fp, c->V, c->WM, c->WF, c->w32,
                  c->Q, c->c, c->err, c->s_main);
     if (rc != 0) return bail(fail(NFHMM_ECUDA, "tensor-core plan: " + tc_last_error()));
+    c->tc.nbpart = c->nbpart;
     c->use_tc = true;
-  } else if (d.precision == NFHMM_BF16) {
-    return bail(fail(NFHMM_EINVAL, "BF16 contractions need the tensor-core path"));
   }
   rc = load_and_init(c, V, W, A, pi, inputs_on_device);
   if (rc) return bail(rc);

@@ -1,18 +1,624 @@
-// Tensor-core contractions: not yet enabled; the SIMT FP32 path runs.
+// Tensor-core form of the two contractions of Eq. 7 on sm_103a:
+//   reconstruction   Vhat[t][l] = sum_k w[t][k] beta[l][k]   -> Q = V / Vhat (+ bound partial)
+//   back-projection  R[t][k]    = sum_l Q[t][l] beta[k][l]   -> counts = w * R
+// Both are C[t][n] = sum_k A[t][k] B[n][k] with K contiguous in both operands.
+//
+// One CTA computes one 128 x BN output tile; the accumulator lives in TMEM.
+// Warp 0 streams K-blocks of A and B into a ring of shared-memory stages with
+// TMA (128-byte swizzle), warp 1 issues tcgen05.mma from one thread and frees
+// each stage with tcgen05.commit, warps 2-5 read the accumulator back with
+// tcgen05.ld and apply the epilogue.  Every mbarrier wait is bounded: a wait
+// that gives up sets ERR_TIMEOUT in the error word and the CTA winds down
+// (outstanding copies are awaited, TMEM is freed) instead of hanging.
+//
+// FP32 mode ("split TF32"): each operand x is stored as hi = tf32(x) and
+// lo = tf32(x - hi); each K-step issues hi*hi, hi*lo and lo*hi (~22
+// significant bits per product).  BF16 mode: one pass over BF16 operands.
+// The tensor core's FP32 accumulation does not round to nearest at every
+// addition, so a long chain of additions into one accumulator drifts (a few
+// 1e-6 relative after ~300 MMAs).  The accumulator is therefore split over
+// all 512 TMEM columns: the hi*hi (or BF16) products of K-block kb go to
+// accumulator kb % NMAIN, the small cross terms to one more accumulator, and
+// the epilogue adds them in FP32 with round-to-nearest.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "nfhmm_device.cuh"
+#include "nfhmm_kernels.h"
 #include "nfhmm_tc.h"
 
 namespace nfhmm {
 
-bool tc_available() { return false; }
-std::string tc_last_error() { return "tensor-core path not built"; }
-int tc_col_tiles_gemm1(int) { return 0; }
-int tc_plan(TcPlan&, int, int, int, int, int, int, const float*, const float*, const float*,
-            const float*, float*, float*, unsigned*, cudaStream_t) {
-  return -1;
+namespace {
+
+constexpr int BM = 128;
+constexpr int BN1 = 128;           // reconstruction: columns = frequencies
+constexpr int BN2 = 160;           // back-projection: columns = elements
+constexpr int NUM_THREADS = 192;   // 6 warps
+constexpr uint32_t SPIN_LIMIT = 1u << 30;          // iteration cap of a wait
+constexpr unsigned long long WAIT_NS = 2000000000ull; // and its time limit (2 s)
+
+enum Kind { KIND_TF32X3 = 0, KIND_BF16 = 1 };
+enum TcEpi { TEPI_RATIO = 0, TEPI_SCALE = 1 };
+
+template <int KIND>
+struct KindCfg;
+template <>
+struct KindCfg<KIND_TF32X3> {
+  static constexpr int ES = 4;            // element bytes
+  static constexpr int BK = 32;           // 128 bytes of K per stage row
+  static constexpr int KSTEP = 8;         // K per MMA instruction
+  static constexpr int NOPS = 2;          // hi and lo copies
+  static constexpr int STAGES = 3;
+};
+template <>
+struct KindCfg<KIND_BF16> {
+  static constexpr int ES = 2;
+  static constexpr int BK = 64;
+  static constexpr int KSTEP = 16;
+  static constexpr int NOPS = 1;
+  static constexpr int STAGES = 6;
+};
+
+template <int KIND, int BN>
+struct TileCfg {
+  using K = KindCfg<KIND>;
+  static constexpr int A_BYTES = BM * 128;          // one operand copy of A per stage
+  static constexpr int B_BYTES = BN * 128;
+  static constexpr int STAGE_BYTES = K::NOPS * (A_BYTES + B_BYTES);
+  static constexpr int SMEM = K::STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+  static constexpr int TMEM_COLS = 512;
+  static constexpr int NACC = 512 / BN;                          // accumulators of BN columns
+  static constexpr int NMAIN = K::NOPS == 2 ? NACC - 1 : NACC;   // for hi*hi (or BF16) products
+};
+
+struct Maps {
+  CUtensorMap a_hi, a_lo, b_hi, b_lo;
+};
+
+struct TcArgs {
+  int rows, cols, kdim;           // T, output columns, K
+  int nbpart;
+  const float* V;                 // RATIO: T x ldv
+  int ldv;
+  const float* w;                 // SCALE: T x ldw (w in float)
+  int ldw;
+  float* out_f32;                 // RATIO: Q hi (tf32) or unused; SCALE: counts
+  float* out_lo;                  // RATIO tf32: Q lo
+  __nv_bfloat16* out_bf16;        // RATIO bf16: Q
+  int ldo;
+  double* bpart;                  // RATIO: bound partial per (row, column tile), may be null
+  unsigned* err;
+};
+
+// ----------------------------------------------------------------- PTX
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
 }
-int tc_refresh_beta(TcPlan&, cudaStream_t) { return 0; }
-int tc_gemm1(TcPlan&, double*, cudaStream_t) { return 0; }
-int tc_gemm2(TcPlan&, cudaStream_t) { return 0; }
-void tc_free(TcPlan&) {}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait for the phase with the given parity; false if it gave up
+// (after WAIT_NS nanoseconds or SPIN_LIMIT polls, whichever comes first).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t addr = smem_u32(bar);
+  const unsigned long long t0 = globaltimer();
+  for (uint32_t i = 0; i < SPIN_LIMIT; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((i & 255) == 255 && globaltimer() - t0 > WAIT_NS) return false;
+  }
+  return false;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(dst)),
+               "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+template <int KIND>
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                    uint32_t acc) {
+  if (KIND == KIND_TF32X3) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  }
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle,
+// 8-row groups 1024 bytes apart (SBO), version 1 (sm_100 family).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;                 // leading byte offset (unused with swizzle)
+  d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset
+  d |= (uint64_t)1 << 46;                 // descriptor version
+  d |= (uint64_t)2 << 61;                 // SWIZZLE_128B
+  return d;
+}
+// Instruction descriptor: FP32 accumulator, A/B K-major, M x N.
+template <int KIND>
+__host__ __device__ constexpr uint32_t idesc(int M, int N) {
+  return (1u << 4) | ((KIND == KIND_TF32X3 ? 2u : 1u) << 7) |
+         ((KIND == KIND_TF32X3 ? 2u : 1u) << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+// ------------------------------------------------------------------ kernel
+template <int KIND, int BN, int EPI>
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+    k_tc_gemm(const __grid_constant__ Maps maps, const TcArgs p) {
+  using K = KindCfg<KIND>;
+  using Cfg = TileCfg<KIND, BN>;
+  constexpr int STAGES = K::STAGES;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * Cfg::STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* accum = empty + STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int col0 = blockIdx.x * BN, row0 = blockIdx.y * BM;
+  const int nkb = (p.kdim + K::BK - 1) / K::BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accum, 1);
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, Cfg::TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  auto stage_ptr = [&](int s, int which) {  // 0: A hi, 1: A lo, 2: B hi, 3: B lo
+    uint8_t* base = smem + s * Cfg::STAGE_BYTES;
+    if (which == 0) return base;
+    if (which == 1) return base + Cfg::A_BYTES;
+    return base + K::NOPS * Cfg::A_BYTES + (which - 2) * Cfg::B_BYTES;
+  };
+
+  if (warp == 0) {
+    // ---------------- TMA producer
+    if (lane == 0) {
+      int issued = 0;
+      for (int kb = 0; kb < nkb && !*abort_flag; ++kb) {
+        const int s = kb % STAGES;
+        if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) - 1) & 1)) {
+          *abort_flag = 1;
+          atomicOr(p.err, ERR_TIMEOUT);
+          break;
+        }
+        mbar_expect_tx(&full[s], Cfg::STAGE_BYTES);
+        const int kx = kb * K::BK;
+        tma_load_2d(stage_ptr(s, 0), &maps.a_hi, &full[s], kx, row0);
+        tma_load_2d(stage_ptr(s, 2), &maps.b_hi, &full[s], kx, col0);
+        if (K::NOPS == 2) {
+          tma_load_2d(stage_ptr(s, 1), &maps.a_lo, &full[s], kx, row0);
+          tma_load_2d(stage_ptr(s, 3), &maps.b_lo, &full[s], kx, col0);
+        }
+        issued = kb + 1;
+      }
+      // every copy issued must have landed before the CTA may exit
+      for (int kb = issued - STAGES > 0 ? issued - STAGES : 0; kb < issued; ++kb) {
+        if (!mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1)) atomicOr(p.err, ERR_TIMEOUT);
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t ID = idesc<KIND>(BM, BN);
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb % STAGES;
+        if (*abort_flag || !mbar_wait(&full[s], (kb / STAGES) & 1)) {
+          *abort_flag = 1;
+          atomicOr(p.err, ERR_TIMEOUT);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(stage_ptr(s, 0)), a1 = smem_u32(stage_ptr(s, 1));
+        const uint32_t b0 = smem_u32(stage_ptr(s, 2)), b1 = smem_u32(stage_ptr(s, 3));
+        const uint32_t d_main = tmem + (uint32_t)((kb % Cfg::NMAIN) * BN);
+        const uint32_t d_cross = tmem + (uint32_t)(Cfg::NMAIN * BN);
+#pragma unroll
+        for (int kk = 0; kk < K::BK / K::KSTEP; ++kk) {
+          const uint32_t off = kk * K::KSTEP * K::ES;  // bytes along K inside the swizzle atom
+          mma<KIND>(d_main, sdesc(a0 + off), sdesc(b0 + off), ID,
+                    (kb >= Cfg::NMAIN || kk > 0) ? 1u : 0u);
+          if (K::NOPS == 2) {
+            mma<KIND>(d_cross, sdesc(a0 + off), sdesc(b1 + off), ID, (kb > 0 || kk > 0) ? 1u : 0u);
+            mma<KIND>(d_cross, sdesc(a1 + off), sdesc(b0 + off), ID, 1u);
+          }
+        }
+        mma_commit(&empty[s]);
+      }
+      mma_commit(accum);  // fires once every MMA issued above has completed
+    }
+  } else {
+    // ---------------- epilogue: warps 2..5, TMEM lanes 32*(warp % 4) ...
+    const int quarter = warp & 3;
+    const int r = quarter * 32 + lane;
+    const int t = row0 + r;
+    const bool ok = mbar_wait(accum, 0);
+    if (!ok) atomicOr(p.err, ERR_TIMEOUT);
+    tc_fence_after();
+    double part = 0.0;
+    unsigned bad = 0;
+    const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16);
+    const int nmain = nkb < Cfg::NMAIN ? nkb : Cfg::NMAIN;   // accumulators written
+#pragma unroll 1
+    for (int cc = 0; cc < BN; cc += 16) {
+      float acc[16];
+      tmem_ld16(taddr + cc, acc);
+#pragma unroll 1
+      for (int j = 1; j < Cfg::NACC; ++j) {
+        if (j < nmain || (K::NOPS == 2 && j == Cfg::NMAIN)) {
+          float part_j[16];
+          tmem_ld16(taddr + (uint32_t)(j * BN) + cc, part_j);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) acc[i] += part_j[i];
+        }
+      }
+      const int c = col0 + cc;
+      if (!ok || t >= p.rows || c >= p.cols) continue;   // cols is a multiple of 16
+      if (EPI == TEPI_RATIO) {
+        const float4* vp = reinterpret_cast<const float4*>(p.V + (size_t)t * p.ldv + c);
+        float q[16];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float4 v4 = vp[i];
+          const float vv[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const float v = vv[j], x = acc[4 * i + j];
+            float qq = 0.f;
+            if (v > 0.f) {
+              if (x > 0.f && isfinite(x)) {
+                qq = v / x;
+                part += (double)v * (double)logf(x);
+              } else {
+                bad |= ERR_VHAT_ZERO;
+              }
+            }
+            q[4 * i + j] = qq;
+          }
+        }
+        if (KIND == KIND_TF32X3) {
+          float4* hp = reinterpret_cast<float4*>(p.out_f32 + (size_t)t * p.ldo + c);
+          float4* lp = reinterpret_cast<float4*>(p.out_lo + (size_t)t * p.ldo + c);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            float h[4], l[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              h[j] = tf32_hi(q[4 * i + j]);
+              l[j] = tf32_hi(q[4 * i + j] - h[j]);
+            }
+            hp[i] = make_float4(h[0], h[1], h[2], h[3]);
+            lp[i] = make_float4(l[0], l[1], l[2], l[3]);
+          }
+        } else {
+          uint4* bp = reinterpret_cast<uint4*>(p.out_bf16 + (size_t)t * p.ldo + c);
+#pragma unroll
+          for (int i = 0; i < 2; ++i) {
+            uint32_t u[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const __nv_bfloat162 b2 = __floats2bfloat162_rn(q[8 * i + 2 * j], q[8 * i + 2 * j + 1]);
+              u[j] = *reinterpret_cast<const uint32_t*>(&b2);
+            }
+            bp[i] = make_uint4(u[0], u[1], u[2], u[3]);
+          }
+        }
+      } else {
+        const float4* wp = reinterpret_cast<const float4*>(p.w + (size_t)t * p.ldw + c);
+        float4* op = reinterpret_cast<float4*>(p.out_f32 + (size_t)t * p.ldo + c);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float4 w4 = wp[i];
+          op[i] = make_float4(w4.x * acc[4 * i], w4.y * acc[4 * i + 1], w4.z * acc[4 * i + 2],
+                              w4.w * acc[4 * i + 3]);
+        }
+      }
+    }
+    if (EPI == TEPI_RATIO && p.bpart && ok && t < p.rows)
+      p.bpart[(size_t)t * p.nbpart + blockIdx.x] = part;
+    if (bad) atomicOr(p.err, bad);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, Cfg::TMEM_COLS);
+  }
+}
+
+// ---------------------------------------------------------------- host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+thread_local std::string g_tc_err;
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+bool make_map(CUtensorMap* m, const void* base, int elem_bytes, int inner, int outer, int ld,
+              int box_inner, int box_outer) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) {
+    g_tc_err = "cuTensorMapEncodeTiled unavailable";
+    return false;
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * elem_bytes};
+  const cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_outer};
+  const cuuint32_t es[2] = {1, 1};
+  const CUresult r = fn(m, elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                           : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                        2, const_cast<void*>(base), dims, strides, box, es,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    g_tc_err = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
+    return false;
+  }
+  return true;
+}
+
+template <int KIND, int BN, int EPI>
+cudaError_t launch_gemm(const Maps& maps, const TcArgs& a, cudaStream_t st) {
+  using Cfg = TileCfg<KIND, BN>;
+  static cudaError_t attr = cudaErrorNotReady;
+  if (attr == cudaErrorNotReady)
+    attr = cudaFuncSetAttribute(k_tc_gemm<KIND, BN, EPI>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+  if (attr != cudaSuccess) return attr;
+  dim3 grid((a.cols + BN - 1) / BN, (a.rows + BM - 1) / BM);
+  k_tc_gemm<KIND, BN, EPI><<<grid, NUM_THREADS, Cfg::SMEM, st>>>(maps, a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tc_available() {
+  int dev = 0, major = 0, minor = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  return major == 10 && minor == 3 && encode_fn() != nullptr;
+}
+
+std::string tc_last_error() { return g_tc_err; }
+
+int tc_col_tiles_gemm1(int Fp) { return (Fp + BN1 - 1) / BN1; }
+
+static Maps* maps_of(TcPlan& p, int which) {
+  return reinterpret_cast<Maps*>(&p.maps[which * 4][0]);
+}
+
+int tc_plan(TcPlan& p, int precision, int T, int M, int Mp, int F, int Fp, const float* V,
+            const float* WM, const float* WF, const float* w32, float* Q, float* c, unsigned* err,
+            cudaStream_t st) {
+  (void)WM;
+  (void)WF;
+  (void)Q;
+  (void)st;
+  static_assert(sizeof(TcPlan::maps) >= 8 * sizeof(CUtensorMap), "tensor map storage");
+  p.precision = precision;
+  p.T = T;
+  p.M = M;
+  p.Mp = Mp;
+  p.F = F;
+  p.Fp = Fp;
+  p.V = V;
+  p.w32 = w32;
+  p.c = c;
+  p.err = err;
+  const bool bf = precision == 1;
+  p.w_format = bf ? WF_BF16 : WF_TF32X2;
+  const int es = bf ? 2 : 4;
+  const int bk = bf ? KindCfg<KIND_BF16>::BK : KindCfg<KIND_TF32X3>::BK;
+  auto alloc = [&](void** ptr, size_t bytes) {
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+      g_tc_err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+      return false;
+    }
+    cudaMemset(*ptr, 0, bytes);
+    return true;
+  };
+  const size_t tM = (size_t)T * Mp * es, tF = (size_t)T * Fp * es, MF = (size_t)Mp * Fp * es;
+  if (!alloc(&p.w_hi, tM) || !alloc(&p.q_hi, tF) || !alloc(&p.bF_hi, MF) || !alloc(&p.bM_hi, MF))
+    return -1;
+  if (!bf && (!alloc(&p.w_lo, tM) || !alloc(&p.q_lo, tF) || !alloc(&p.bF_lo, MF) ||
+              !alloc(&p.bM_lo, MF)))
+    return -1;
+  Maps* m1 = maps_of(p, 0);
+  Maps* m2 = maps_of(p, 1);
+  bool ok = make_map(&m1->a_hi, p.w_hi, es, Mp, T, Mp, bk, BM) &&
+            make_map(&m1->b_hi, p.bF_hi, es, Mp, Fp, Mp, bk, BN1) &&
+            make_map(&m2->a_hi, p.q_hi, es, Fp, T, Fp, bk, BM) &&
+            make_map(&m2->b_hi, p.bM_hi, es, Fp, Mp, Fp, bk, BN2);
+  if (ok && !bf)
+    ok = make_map(&m1->a_lo, p.w_lo, es, Mp, T, Mp, bk, BM) &&
+         make_map(&m1->b_lo, p.bF_lo, es, Mp, Fp, Mp, bk, BN1) &&
+         make_map(&m2->a_lo, p.q_lo, es, Fp, T, Fp, bk, BM) &&
+         make_map(&m2->b_lo, p.bM_lo, es, Fp, Mp, Fp, bk, BN2);
+  if (!ok) return -1;
+  if (bf) {  // unused lo maps: copies of hi (never read)
+    m1->a_lo = m1->a_hi;
+    m1->b_lo = m1->b_hi;
+    m2->a_lo = m2->a_hi;
+    m2->b_lo = m2->b_hi;
+  }
+  p.bF_src = WF;
+  p.bM_src = WM;
+  return 0;
+}
+
+int tc_refresh_beta(TcPlan& p, cudaStream_t st) {
+  const size_t n = (size_t)p.Mp * p.Fp;
+  if (p.precision == 1) {
+    launch_to_bf16(p.bF_src, p.bF_hi, n, st);
+    launch_to_bf16(p.bM_src, p.bM_hi, n, st);
+  } else {
+    launch_split_tf32(p.bF_src, (float*)p.bF_hi, (float*)p.bF_lo, n, st);
+    launch_split_tf32(p.bM_src, (float*)p.bM_hi, (float*)p.bM_lo, n, st);
+  }
+  return 2;
+}
+
+int tc_gemm1(TcPlan& p, double* bpart, cudaStream_t st) {
+  TcArgs a{};
+  a.rows = p.T;
+  a.cols = p.Fp;
+  a.kdim = p.Mp;
+  a.nbpart = p.nbpart;
+  a.V = p.V;
+  a.ldv = p.Fp;
+  a.ldo = p.Fp;
+  a.bpart = bpart;
+  a.err = p.err;
+  cudaError_t e;
+  if (p.precision == 1) {
+    a.out_bf16 = reinterpret_cast<__nv_bfloat16*>(p.q_hi);
+    e = launch_gemm<KIND_BF16, BN1, TEPI_RATIO>(*maps_of(p, 0), a, st);
+  } else {
+    a.out_f32 = reinterpret_cast<float*>(p.q_hi);
+    a.out_lo = reinterpret_cast<float*>(p.q_lo);
+    e = launch_gemm<KIND_TF32X3, BN1, TEPI_RATIO>(*maps_of(p, 0), a, st);
+  }
+  if (e != cudaSuccess) {
+    g_tc_err = cudaGetErrorString(e);
+    return -1;
+  }
+  return 1;
+}
+
+int tc_gemm2(TcPlan& p, cudaStream_t st) {
+  TcArgs a{};
+  a.rows = p.T;
+  a.cols = p.Mp;
+  a.kdim = p.Fp;
+  a.w = p.w32;
+  a.ldw = p.Mp;
+  a.out_f32 = p.c;
+  a.ldo = p.Mp;
+  a.err = p.err;
+  cudaError_t e;
+  if (p.precision == 1)
+    e = launch_gemm<KIND_BF16, BN2, TEPI_SCALE>(*maps_of(p, 1), a, st);
+  else
+    e = launch_gemm<KIND_TF32X3, BN2, TEPI_SCALE>(*maps_of(p, 1), a, st);
+  if (e != cudaSuccess) {
+    g_tc_err = cudaGetErrorString(e);
+    return -1;
+  }
+  return 1;
+}
+
+void tc_free(TcPlan& p) {
+  void* bufs[] = {p.w_hi, p.w_lo, p.q_hi, p.q_lo, p.bF_hi, p.bF_lo, p.bM_hi, p.bM_lo};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  p.w_hi = p.w_lo = p.q_hi = p.q_lo = p.bF_hi = p.bF_lo = p.bM_hi = p.bM_lo = nullptr;
+}
 
 }  // namespace nfhmm

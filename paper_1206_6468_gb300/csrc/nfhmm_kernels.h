@@ -15,6 +15,7 @@ enum : unsigned {
   ERR_NONFINITE = 2u,  // NaN/Inf in a state array
   ERR_BAD_INPUT = 4u,  // input validation failed
   ERR_FB_ZERO = 8u,    // forward-backward normaliser vanished
+  ERR_TIMEOUT = 16u,   // a bounded device wait gave up
 };
 
 // Records the calling thread's last error message (returned by nfhmm_last_error).

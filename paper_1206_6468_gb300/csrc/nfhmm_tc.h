@@ -21,6 +21,9 @@ struct TcPlan {
   void* bM_hi = nullptr;  // Mp x Fp  (beta by element)
   void* bM_lo = nullptr;
   // borrowed from the context
+  const float* bF_src = nullptr;  // beta by frequency (Fp x Mp), float
+  const float* bM_src = nullptr;  // beta by element (Mp x Fp), float
+  int nbpart = 0;                 // columns of the bound-partial array
   const float* V = nullptr;
   const float* w32 = nullptr;
   float* Q = nullptr;

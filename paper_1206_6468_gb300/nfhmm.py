@@ -24,7 +24,7 @@ if not os.path.exists(LIB_PATH):
 _lib = ctypes.CDLL(LIB_PATH)
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENUMERIC, ESTATE = 0, -1, -2, -3, -4, -5, -6
-FP32, BF16 = 0, 1
+FP32, BF16, FP32_SIMT = 0, 1, 2
 INIT_UNIFORM, INIT_PRIOR = 0, 1
 SEP_MEAN, SEP_EXPECTATION = 0, 1
 STAGES = {"weights": 0, "gemm1": 1, "gemm2": 2, "fb": 3, "bound": 4, "init": 5}
@@ -127,7 +127,8 @@ class VIContext:
     """One spectrogram's variational inference state on the GPU.
 
     V (T, F), W (M, F), A (S, N, N), pi (S, N): numpy arrays (host) or torch
-    CUDA tensors (device), float32.  precision: "fp32" or "bf16"."""
+    CUDA tensors (device), float32.  precision: "fp32" (split-TF32 tensor
+    cores), "bf16" (BF16 tensor cores) or "fp32_simt" (FP32 CUDA cores)."""
 
     def __init__(self, V, W, A, pi, S: int, N: int, K: int, gamma: float = 1.0,
                  precision: str = "fp32", init_mode: int = INIT_UNIFORM, stream=None):
@@ -136,7 +137,8 @@ class VIContext:
         self.S, self.N, self.K, self.F, self.T = S, N, K, F, T
         self.M = S * N * K
         self.gamma = gamma
-        d = Dims(S, N, K, F, T, gamma, {"fp32": FP32, "bf16": BF16}[precision], init_mode)
+        d = Dims(S, N, K, F, T, gamma,
+                 {"fp32": FP32, "bf16": BF16, "fp32_simt": FP32_SIMT}[precision], init_mode)
         pv, dv = _ptr(V)
         pw, dw = _ptr(W)
         pa, da = _ptr(A)
