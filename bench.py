@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
     ap.add_argument("--sweeps", type=int, default=SWEEPS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu-case", action="store_true",
+                    help="run one context for 3 sweeps and exit (a small case for ncu)")
     return ap.parse_args()
 
 
@@ -76,6 +78,16 @@ def barrier(world):
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
+
+
+def job_seed(rank: int) -> int:
+    """Each rank separates its own job: the replicas share no data."""
+    return rank
+
+
+def aggregate(frame_its_per_rank: float, steps: int, world: int, slowest_ms: float) -> float:
+    """Whole-job frame-iterations/s: all ranks' work over the slowest rank's time."""
+    return world * frame_its_per_rank * steps / (slowest_ms / 1e3)
 
 
 def max_over_ranks(x: float, world: int) -> float:
@@ -243,7 +255,7 @@ def main():
     assert torch.cuda.is_available(), "bench.py needs a GPU"
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    p = synth.make_problem(seed=rank, **synth.PAPER_SIZE)
+    p = synth.make_problem(seed=job_seed(rank), **synth.PAPER_SIZE)
     f32 = p.as_f32()
     d_in = {k: torch.from_numpy(v).to(dev) for k, v in f32.items()}
     h_in = {k: torch.from_numpy(v).pin_memory() for k, v in f32.items()}
@@ -254,6 +266,10 @@ def main():
     ctx = nfhmm.VIContext(d_in["V"], d_in["W"], d_in["A"], d_in["pi"], p.S, p.N, p.K,
                           gamma=p.gamma, precision=args.precision)
     sweeps = args.sweeps
+    if args.ncu_case:
+        print("bound after 3 sweeps:", ctx.sweep(3, bound=True), flush=True)
+        ctx.close()
+        return
 
     def step_device():
         ctx.reinit(d_in["V"], d_in["W"], d_in["A"], d_in["pi"])
@@ -302,8 +318,8 @@ def main():
     frames_its = p.T * sweeps
     tot_ms = max_over_ranks(sum(ms), world)
     tot_e2e = max_over_ranks(sum(ms_e2e), world)
-    value = world * frames_its * args.steps / (tot_ms / 1e3)
-    e2e_value = world * frames_its * args.steps / (tot_e2e / 1e3)
+    value = aggregate(frames_its, args.steps, world, tot_ms)
+    e2e_value = aggregate(frames_its, args.steps, world, tot_e2e)
 
     peaks = load_peaks()
     tc = bool(ctx.query("tensor_cores"))

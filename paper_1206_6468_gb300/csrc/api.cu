@@ -75,6 +75,7 @@ struct nfhmm_ctx {
   double* logZ = nullptr;   // S
   double* bound_dev = nullptr;
   unsigned* err = nullptr;
+  int2* ktab = nullptr;      // Mp element table
   void* fb_scratch = nullptr;
   FBArgs fb{};
   TcPlan tc{};
@@ -117,7 +118,7 @@ void free_ctx(nfhmm_ctx* c) {
   if (c->s_aux) cudaStreamSynchronize(c->s_aux);
   void* bufs[] = {c->V, c->WM, c->WF, c->A, c->pi, c->alpha, c->w32, c->c, c->Q, c->phi,
                   c->dhat, c->wts, c->sep_tmp, c->v, c->bpart, c->frame_terms, c->logZ,
-                  c->bound_dev, c->err, c->fb_scratch};
+                  c->bound_dev, c->err, c->ktab, c->fb_scratch};
   for (void* p : bufs)
     if (p) cudaFree(p);
   tc_free(c->tc);
@@ -244,6 +245,7 @@ int one_sweep(nfhmm_ctx* c, bool want_bpart) {
   wa.N = d.N;
   wa.K = d.K;
   wa.gamma = (float)d.gamma;
+  wa.ktab = c->ktab;
   wa.counts = c->c;
   wa.dhat = c->dhat;
   wa.alpha = c->alpha;
@@ -333,7 +335,8 @@ int load_and_init(nfhmm_ctx* c, const float* V, const float* W, const float* A, 
   launch_validate(c->V, d.T, d.F, c->Fp, c->WM, c->M, c->A, c->pi, d.S, d.N, c->err, st);
   launch_transpose(c->WM, c->Mp, c->Fp, c->Fp, c->WF, c->Mp, c->Mp, c->Fp, st);
   launch_row_sums(c->V, d.T, d.F, c->Fp, c->v, st);
-  int n = 3;
+  launch_element_table(c->M, c->Mp, d.K, d.N, d.T, c->ktab, st);
+  int n = 4;
   if (c->use_tc) n += tc_refresh_beta(c->tc, st);
   // initial state: equal weights (w = 1) through the FP32 contractions
   launch_fill_rows(c->w32, d.T, c->M, c->Mp, 1.f, st);
@@ -435,6 +438,7 @@ int nfhmm_vi_init(nfhmm_ctx** out, const nfhmm_dims* dp, const float* V, const f
   DMALLOC(c->logZ, S * 8);
   DMALLOC(c->bound_dev, 8);
   DMALLOC(c->err, 4);
+  DMALLOC(c->ktab, Mp * sizeof(int2));
   CKI(cudaMallocHost(&c->h_bound, 8));
   CKI(cudaMallocHost(&c->h_err, 4));
   // forward-backward plan and scratch

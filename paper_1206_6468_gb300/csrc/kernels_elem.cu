@@ -7,6 +7,8 @@
 #include <cuda_bf16.h>
 #include <math.h>
 
+#include <climits>
+
 #include "nfhmm_device.cuh"
 #include "nfhmm_kernels.h"
 
@@ -19,39 +21,37 @@ constexpr unsigned FULL = 0xffffffffu;
 // phi-hat for block g = k / K is the inclusive segmented scan of psi at the
 // block's last element, with the partial sum of a block that straddles a
 // chunk boundary carried in a register (deterministic order, no atomics).
+// The element table ktab[k] = (g, s*T*N + n) (g < 0 for padding) replaces
+// integer division by K and N on the hot path.
 template <int FMT>
 __global__ void __launch_bounds__(256) k_weights(WeightsArgs a) {
   const int lane = threadIdx.x & 31;
   const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (t >= a.T) return;
-  const float* crow = a.counts + (size_t)t * a.Mp;
-  float* arow = a.alpha + (size_t)t * a.Mp;
-  float* wrow = a.w32 + (size_t)t * a.Mp;
+  const size_t row = (size_t)t * a.Mp;
+  const size_t toff = (size_t)t * a.N;
   float carry = 0.f;
-  int carry_key = -1;
+  int carry_key = INT_MIN;
   unsigned bad = 0;
   for (int base = 0; base < a.Mp; base += 32) {
     const int k = base + lane;
-    const bool el = k < a.M;
+    const int2 kt = a.ktab[k];          // Mp is a multiple of 32: k < Mp
+    const int g = kt.x;
+    const bool el = g >= 0;
     float alpha = 0.f, psi = 0.f, w = 0.f;
-    int g = -2 - lane;  // padding lanes never match a key
     if (el) {
-      g = k / a.K;
-      const int s = g / a.N, n = g - s * a.N;
-      alpha = crow[k] + a.gamma * a.dhat[((size_t)s * a.T + t) * a.N + n] + 1.f;
+      alpha = a.counts[row + k] + a.gamma * a.dhat[kt.y + toff] + 1.f;
       digamma_exp(alpha, psi, w);
       if (!isfinite(psi) || !isfinite(w)) bad |= ERR_NONFINITE;
     }
-    if (k < a.Mp) {
-      arow[k] = alpha;
-      wrow[k] = w;
-      if (FMT == WF_TF32X2) {
-        const float hi = tf32_hi(w);
-        reinterpret_cast<float*>(a.wop_hi)[(size_t)t * a.Mp + k] = hi;
-        reinterpret_cast<float*>(a.wop_lo)[(size_t)t * a.Mp + k] = tf32_hi(w - hi);
-      } else if (FMT == WF_BF16) {
-        reinterpret_cast<__nv_bfloat16*>(a.wop_hi)[(size_t)t * a.Mp + k] = __float2bfloat16_rn(w);
-      }
+    a.alpha[row + k] = alpha;
+    a.w32[row + k] = w;
+    if (FMT == WF_TF32X2) {
+      const float hi = tf32_hi(w);
+      reinterpret_cast<float*>(a.wop_hi)[row + k] = hi;
+      reinterpret_cast<float*>(a.wop_lo)[row + k] = tf32_hi(w - hi);
+    } else if (FMT == WF_BF16) {
+      reinterpret_cast<__nv_bfloat16*>(a.wop_hi)[row + k] = __float2bfloat16_rn(w);
     }
     // inclusive segmented scan of psi keyed by block g
     float x = psi;
@@ -62,23 +62,36 @@ __global__ void __launch_bounds__(256) k_weights(WeightsArgs a) {
       if (lane >= d && gy == g) x += y;
     }
     if (g == carry_key) x += carry;
-    if (el && (k + 1) % a.K == 0) {
-      const int s = g / a.N, n = g - s * a.N;
-      a.phi[((size_t)s * a.T + t) * a.N + n] = a.gamma * x;
-    }
+    int gnext = __shfl_down_sync(FULL, g, 1);
+    if (lane == 31) gnext = (k + 1 < a.Mp) ? a.ktab[k + 1].x : INT_MIN;
+    if (el && gnext != g) a.phi[kt.y + toff] = a.gamma * x;   // last element of block g
     const float x31 = __shfl_sync(FULL, x, 31);
     const int g31 = __shfl_sync(FULL, g, 31);
-    const int k31 = base + 31;
-    if (k31 < a.M && (k31 + 1) % a.K != 0) {
+    const int gn31 = __shfl_sync(FULL, gnext, 31);
+    if (g31 >= 0 && gn31 == g31) {
       carry = x31;
       carry_key = g31;
     } else {
       carry = 0.f;
-      carry_key = -1;
+      carry_key = INT_MIN;
     }
   }
   bad = __reduce_or_sync(FULL, bad);
   if (bad && lane == 0) atomicOr(a.err, bad);
+}
+
+__global__ void k_element_table(int M, int Mp, int K, int N, int T, int2* ktab) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= Mp) return;
+  if (k < M) {
+    const int g = k / K, s = g / N, n = g - s * N;
+    ktab[k] = make_int2(g, (int)((size_t)s * T * N + n));
+  } else {
+    ktab[k] = make_int2(-1 - k, 0);
+  }
+}
+void launch_element_table(int M, int Mp, int K, int N, int T, int2* ktab, cudaStream_t st) {
+  k_element_table<<<(Mp + 255) / 256, 256, 0, st>>>(M, Mp, K, N, T, ktab);
 }
 
 void launch_weights(const WeightsArgs& a, int fmt, cudaStream_t st) {

@@ -7,16 +7,23 @@
 // matrix P_c = G_t0 ... G_{t1-1} (for c = 0 the first factor is diag(e_0)),
 // so that a_{t1-1} = a_{t0-1} P_c (a_{L-1} = pi P_0) and b_{t0-1} = P_c b_{t1-1}.
 // Three launches:
-//   1. products: P_c of every chunk (N^3 per frame, all chunks in parallel);
+//   1. products: P_c of every chunk on the tensor cores.  Row i of P_c is
+//      the forward recursion started from state i, so each row evolves on
+//      its own: a 128-row tile holds the rows of floor(128/NP) chunks, one
+//      TMEM lane per row, and every frame is one split-TF32 tcgen05.mma of
+//      the tile by A followed by a thread-local epilogue (emission, per-row
+//      rescaling, split back into the shared-memory operand).
 //   2. scan:     forward and backward boundary vectors across chunks, one
 //                warp per (source, direction), serial over C with the next
 //                chunk matrices prefetched by cp.async; and log Z;
-//   3. replay:   inside each chunk, a forward warp and a backward warp run
+//   3. replay:   inside each chunk a forward warp and a backward warp run
 //                concurrently from the chunk's boundary vectors; then
 //                d-hat_t = a_t b_t / sum_n a_tn b_tn.
-// Vectors and matrices are rescaled at every step.  The scale factors are
-// kept in shared or global memory and their logs are summed in double after
-// the serial loops, so no double-precision work sits on a serial path.
+// In the serial loops a vector is rescaled by the sum computed one step
+// earlier, so the warp reduction of a step overlaps the next step's
+// arithmetic.  Scale factors are kept as exact (mantissa, exponent) products
+// or in memory and turned into logs in double after the loops, so no
+// double-precision work sits on a serial path.
 // States are padded to NP = 8*ceil(N/8) with zero rows/columns in A, zero
 // emissions and zero initial probability, so padded states never carry mass;
 // every kernel is instantiated per NP and its loops unroll fully.
@@ -25,6 +32,7 @@
 
 #include "nfhmm_device.cuh"
 #include "nfhmm_kernels.h"
+#include "tc_ptx.cuh"
 
 namespace nfhmm {
 
@@ -37,58 +45,32 @@ constexpr size_t SMEM_OPTIN = 227 * 1024;
 
 __host__ __device__ constexpr int pad8(int n) { return (n + 7) & ~7; }
 
-__device__ __forceinline__ float block_max(float x, float* red, int& parity) {
-  const int nw = blockDim.x >> 5;
-  x = warp_max(x);
-  float* r = red + parity * 32;
-  if ((threadIdx.x & 31) == 0) r[threadIdx.x >> 5] = x;
-  __syncthreads();
-  float s = r[0];
-  for (int i = 1; i < nw; ++i) s = fmaxf(s, r[i]);
-  parity ^= 1;
-  return s;
+// Factor that brings a vector with sum (or maximum) x > 0 back towards 1:
+// 1/x, or the exact power of two 2^100 when 1/x could overflow (x tiny or
+// subnormal); 1 for x == 0 (an all-zero vector stays zero).
+constexpr float BOOST = 0x1p100f;
+__device__ __forceinline__ float renorm_factor(float x) {
+  if (x >= 1e-30f) return 1.f / x;
+  return x > 0.f ? BOOST : 1.f;
+}
+// The factor the vector was divided by: x, or 2^-100 after a boost.
+__device__ __forceinline__ float removed_scale(float x) {
+  if (x >= 1e-30f) return x;
+  return x > 0.f ? 0x1p-100f : 1.f;
 }
 
-// Block-wide double sum (all threads get the result).
-__device__ __forceinline__ double block_sum_d(double x, double* red) {
-  const int nw = blockDim.x >> 5;
-  x = warp_sum_d(x);
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
-  __syncthreads();
-  double s = 0.0;
-  for (int i = 0; i < nw; ++i) s += red[i];
-  return s;
-}
-
-// Emissions of frames [t0, t0 + len) of one source into e[f*NP + n] (padded
-// states 0): the chunk's phi rows are contiguous in global memory and are
-// first copied with coalesced loads by the whole block, then one warp per
-// frame takes max and exp.  Returns the warp's sum of frame maxima (double,
-// valid in every lane).
-template <int NP>
-__device__ double load_emissions(const float* phi_s, int N, int t0, int len, float* e) {
-  const float* src = phi_s + (size_t)t0 * N;
-  const int tot = len * N;
-  for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-    const int f = i / N, n = i - f * N;
-    e[f * NP + n] = src[i];
+// Running product of positive scale factors as mantissa in [0.5, 1) and a
+// power of two: exact apart from one rounding per factor.
+struct ScaleAcc {
+  float m = 1.f;
+  int e = 0;
+  __device__ __forceinline__ void mul(float s) {
+    int ex;
+    m = frexpf(m * s, &ex);
+    e += ex;
   }
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
-  double msum = 0.0;
-  for (int f = threadIdx.x >> 5; f < len; f += blockDim.x >> 5) {
-    float* row = e + f * NP;
-    const float x0 = lane < N ? row[lane] : -INFINITY;
-    const float x1 = lane + 32 < N ? row[lane + 32] : -INFINITY;
-    const float m = warp_max(fmaxf(x0, x1));
-    __syncwarp();
-    if (lane < NP) row[lane] = lane < N ? expf(x0 - m) : 0.f;
-    if (lane + 32 < NP) row[lane + 32] = lane + 32 < N ? expf(x1 - m) : 0.f;
-    msum += (double)m;
-  }
-  return msum;
-}
+  __device__ __forceinline__ double log() const { return (double)e * 0.6931471805599453 + ::log((double)m); }
+};
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -104,193 +86,273 @@ __device__ __forceinline__ void cp_async_wait() {
 int fb_max_states() { return FB_MAX_N; }
 
 int fb_default_chunk(int N, int T) {
-  // The chunk products are the bulk of the work and run one chunk per block;
-  // chunks of up to ~48 frames keep a paper-size job (S = 2, T = 3000) to
-  // about one wave on 152 SMs while the serial scan stays ~T/48 steps long.
-  int L = (int)ceil(sqrt((double)T)) - 6;
+  // products cost ~L serial tensor-core steps, the scan ~T/L warp steps:
+  // chunks of ~sqrt(T)/2 frames balance them (16..64).
+  int L = (int)ceil(0.5 * sqrt((double)T));
   if (L < 16) L = 16;
-  if (L > 48) L = 48;
+  if (L > 64) L = 64;
   if (L > T) L = T;
   (void)N;
   return L;
 }
 
-// P and P^T of one chunk are stored padded: NP x NP floats each.
 static inline size_t mat_floats(int N) { return (size_t)pad8(N) * pad8(N); }
 
 // --------------------------------------------------------------- 1. products
-// Thread (ti, tj) owns rows 4ti..4ti+3 and columns TC*tj..TC*tj+TC-1 of P.
-// Its TC columns of A stay in registers for the whole chunk; P^T is double
-// buffered in shared memory (one float4 read per k).  The matrix is scaled by
-// its maximum after every step.
 template <int NP>
 struct ProdCfg {
-  static constexpr int TC = NP <= 40 ? 4 : 2;   // columns per thread
-  static constexpr int NI = NP / 4, NJ = NP / TC;
-  static constexpr int THREADS = ((NI * NJ + 31) / 32) * 32;
+  static constexpr int RCH = 128 / NP;              // chunks per 128-row tile
+  static constexpr int NOUT = (NP + 15) & ~15;      // MMA N (multiple of 16)
+  static constexpr int KSTEPS = NP / 8;             // tf32 MMA K = 8
+  static constexpr int KATOMS = (NP + 31) / 32;     // 128-byte swizzle atoms along K
+  static constexpr int ROWS_BYTES = KATOMS * 128 * 128;
+  static constexpr int B_BYTES = KATOMS * NOUT * 128;
+  static constexpr int TMEM_COLS = 2 * NOUT <= 32 ? 32 : 2 * NOUT <= 64 ? 64 : 128;
+  static constexpr int SMEM_FIXED = 2 * ROWS_BYTES + 2 * B_BYTES;
 };
 
+// byte offset of element (row r, k) in a K-major tile of 128-byte rows with
+// 128-byte swizzle: 8-row groups 1024 bytes apart, 16-byte chunks XOR row%8
+__device__ __forceinline__ uint32_t sw128_off(int r, int k, int atom_bytes) {
+  const int atom = k >> 5, kk = k & 31;
+  return atom * atom_bytes + (r >> 3) * 1024 + (r & 7) * 128 + ((((kk >> 2) ^ (r & 7))) << 4) +
+         ((kk & 3) << 2);
+}
+
 template <int NP>
-__global__ void __launch_bounds__(ProdCfg<NP>::THREADS) k_fb_products(FBArgs a) {
+__global__ void __launch_bounds__(128, 1) k_fb_products(FBArgs a) {
+  using namespace tc;
   using Cfg = ProdCfg<NP>;
-  constexpr int TC = Cfg::TC;
-  extern __shared__ float sm[];
-  const int N = a.N, L = a.L;
-  const int c = blockIdx.x, s = blockIdx.y;
-  const int t0 = c * L;
-  const int len = min(a.T, t0 + L) - t0;
-  double* dred = reinterpret_cast<double*>(sm);  // 32 doubles
-  float* PT0 = sm + 64;                          // NP x NP, P[i][k] at k*NP + i
-  float* PT1 = PT0 + NP * NP;
-  float* e = PT1 + NP * NP;                      // L x NP
-  float* scl = e + L * NP;                       // L
-  float* red = scl + FB_MAX_L;                   // 64
+  constexpr int NOUT = Cfg::NOUT;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint8_t* rows_hi = smem;
+  uint8_t* rows_lo = rows_hi + Cfg::ROWS_BYTES;
+  uint8_t* b_hi = rows_lo + Cfg::ROWS_BYTES;
+  uint8_t* b_lo = b_hi + Cfg::B_BYTES;
+  float* e = reinterpret_cast<float*>(b_lo + Cfg::B_BYTES);   // RCH x L x NP
+  float* rho = e + Cfg::RCH * a.L * NP;                        // 128 (as double: 2 floats each)
+  double* rhod = reinterpret_cast<double*>(rho);
+  double* msum = rhod + 128;                                   // RCH
+  uint64_t* bar = reinterpret_cast<uint64_t*>(msum + Cfg::RCH);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
 
-  const int ti = threadIdx.x / Cfg::NJ, tj = threadIdx.x % Cfg::NJ;
-  const bool act = threadIdx.x < Cfg::NI * Cfg::NJ;
-  // this thread's columns of A, padded with zeros
-  float Ar[NP][TC];
-  const float* As_g = a.A + (size_t)s * N * N;
-#pragma unroll
-  for (int k = 0; k < NP; ++k)
-#pragma unroll
-    for (int q = 0; q < TC; ++q) {
-      const int j = TC * tj + q;
-      Ar[k][q] = (act && k < N && j < N) ? As_g[k * N + j] : 0.f;
+  const int N = a.N, L = a.L, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int s = blockIdx.y;
+  const int cbase = blockIdx.x * Cfg::RCH;
+
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_barrier_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(tslot, Cfg::TMEM_COLS);
+    tmem_relinquish();
+  }
+  // B operand: B[j][k] = A[k][j] (zero outside N x N), split into tf32 hi/lo
+  const float* Ag = a.A + (size_t)s * N * N;
+  for (int idx = tid; idx < NOUT * Cfg::KATOMS * 32; idx += blockDim.x) {
+    const int j = idx / (Cfg::KATOMS * 32), k = idx - j * (Cfg::KATOMS * 32);
+    const float v = (j < N && k < N) ? Ag[k * N + j] : 0.f;
+    const float h = tf32_hi(v);
+    const uint32_t off = sw128_off(j, k, NOUT * 128);
+    *reinterpret_cast<float*>(b_hi + off) = h;
+    *reinterpret_cast<float*>(b_lo + off) = tf32_hi(v - h);
+  }
+  // emissions of the tile's chunks
+  for (int q = 0; q < Cfg::RCH; ++q) {
+    const int c = cbase + q;
+    if (c >= a.C) break;
+    const int t0 = c * L, len = min(a.T, t0 + L) - t0;
+    const float* src = a.phi + ((size_t)s * a.T + t0) * N;
+    float* eq = e + q * L * NP;
+    for (int i = tid; i < len * N; i += blockDim.x) {
+      const int f = i / N, n = i - f * N;
+      eq[f * NP + n] = src[i];
     }
-  double msum = load_emissions<NP>(a.phi + (size_t)s * a.T * N, N, t0, len, e);
+  }
   __syncthreads();
-  int parity = 0;
+  for (int q = 0; q < Cfg::RCH; ++q) {
+    const int c = cbase + q;
+    if (c >= a.C) break;
+    const int t0 = c * L, len = min(a.T, t0 + L) - t0;
+    float* eq = e + q * L * NP;
+    double ms = 0.0;
+    for (int f = warp; f < len; f += 4) {
+      float* row = eq + f * NP;
+      const float x0 = lane < N ? row[lane] : -INFINITY;
+      const float x1 = lane + 32 < N ? row[lane + 32] : -INFINITY;
+      const float m = warp_max(fmaxf(x0, x1));
+      __syncwarp();
+      if (lane < NP) row[lane] = lane < N ? expf(x0 - m) : 0.f;
+      if (lane + 32 < NP) row[lane + 32] = lane + 32 < N ? expf(x1 - m) : 0.f;
+      ms += (double)m;
+    }
+    if (lane == 0) rhod[warp] = ms;
+    __syncthreads();
+    if (tid == 0) msum[q] = rhod[0] + rhod[1] + rhod[2] + rhod[3];
+    __syncthreads();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
 
-  float out[4][TC];
-  float lmax = 0.f;
-  // first factor: A diag(e_t0), or diag(e_0) for the chunk that starts at pi
+  // this thread's row: chunk q, basis state i
+  const int r = tid;
+  const int q = r / NP, i = r - (r / NP) * NP;
+  const int c = cbase + q;
+  const bool live = q < Cfg::RCH && c < a.C && i < N;
+  const int len = live ? min(a.T, c * L + L) - c * L : 0;
+  const float* eq = e + (q < Cfg::RCH ? q : 0) * L * NP;
+  float cur[NOUT];
+  ScaleAcc sc;
+  bool zero_row = false;   // once zero, a row stays zero: its scale is then -inf
 #pragma unroll
-  for (int r = 0; r < 4; ++r)
+  for (int j = 0; j < NOUT; ++j) {
+    float v = 0.f;
+    if (live && j < N) v = (c == 0) ? (j == i ? eq[j] : 0.f) : Ag[i * N + j] * eq[j];
+    cur[j] = v;
+  }
+  auto normalise_and_store = [&]() {
+    float m = 0.f;
 #pragma unroll
-    for (int q = 0; q < TC; ++q) {
-      const int i = 4 * ti + r, j = TC * tj + q;
-      float v = 0.f;
-      if (act) {
-        if (c == 0) {
-          v = (i == j) ? e[j] : 0.f;
-        } else {
-#pragma unroll
-          for (int k = 0; k < NP; ++k)
-            if (k == i) v = Ar[k][q] * e[j];
-        }
+    for (int j = 0; j < NOUT; ++j) m = fmaxf(m, cur[j]);
+    if (live) {
+      // an all-zero row is legitimate (state i cannot start this chunk)
+      if (!isfinite(m)) {
+        atomicOr(a.err, ERR_FB_ZERO);
+        m = 0.f;
       }
-      out[r][q] = v;
-      lmax = fmaxf(lmax, v);
+      if (m == 0.f) zero_row = true;
+      const float f = renorm_factor(m);
+#pragma unroll
+      for (int j = 0; j < NOUT; ++j) cur[j] *= f;
+      sc.mul(removed_scale(m));
     }
-  float* cur = PT0;
-  float* nxt = PT1;
-  if (act) {
 #pragma unroll
-    for (int q = 0; q < TC; ++q)
-      *reinterpret_cast<float4*>(&cur[(TC * tj + q) * NP + 4 * ti]) =
-          make_float4(out[0][q], out[1][q], out[2][q], out[3][q]);
-  }
-  float gmax = block_max(lmax, red, parity);  // barrier publishes cur
-  for (int f = 1; f < len; ++f) {
-    if (!(gmax > 0.f) || !isfinite(gmax)) {
-      if (threadIdx.x == 0) atomicOr(a.err, ERR_FB_ZERO);
-      gmax = 1.f;
-    }
-    if (threadIdx.x == 0) scl[f - 1] = gmax;
-    const float inv = 1.f / gmax;
-    float acc[4][TC];
+    for (int cc = 0; cc < NP / 4; ++cc) {
+      float h[4], l[4];
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-      for (int q = 0; q < TC; ++q) acc[r][q] = 0.f;
-    if (act) {
-#pragma unroll
-      for (int k = 0; k < NP; ++k) {
-        const float4 p = *reinterpret_cast<const float4*>(&cur[k * NP + 4 * ti]);
-#pragma unroll
-        for (int q = 0; q < TC; ++q) {
-          acc[0][q] = fmaf(p.x, Ar[k][q], acc[0][q]);
-          acc[1][q] = fmaf(p.y, Ar[k][q], acc[1][q]);
-          acc[2][q] = fmaf(p.z, Ar[k][q], acc[2][q]);
-          acc[3][q] = fmaf(p.w, Ar[k][q], acc[3][q]);
-        }
+      for (int u = 0; u < 4; ++u) {
+        h[u] = tf32_hi(cur[4 * cc + u]);
+        l[u] = tf32_hi(cur[4 * cc + u] - h[u]);
       }
+      const uint32_t off = sw128_off(r, 4 * cc, 128 * 128);
+      *reinterpret_cast<float4*>(rows_hi + off) = make_float4(h[0], h[1], h[2], h[3]);
+      *reinterpret_cast<float4*>(rows_lo + off) = make_float4(l[0], l[1], l[2], l[3]);
     }
-    lmax = 0.f;
-    const float* ef = e + f * NP;
+  };
+  normalise_and_store();
+
+  constexpr uint32_t ID = idesc<KIND_TF32X3>(128, NOUT);
+  const uint32_t rh = smem_u32(rows_hi), rl = smem_u32(rows_lo);
+  const uint32_t bh = smem_u32(b_hi), bl = smem_u32(b_lo);
+  const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+  bool ok = true;
+  for (int f = 1; f < L; ++f) {
+    fence_proxy_async_smem();   // the operand rows written above, to the tensor core
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
 #pragma unroll
-    for (int q = 0; q < TC; ++q) {
-      const float sc = act ? ef[TC * tj + q] * inv : 0.f;
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        out[r][q] = acc[r][q] * sc;
-        lmax = fmaxf(lmax, out[r][q]);
+      for (int kk = 0; kk < Cfg::KSTEPS; ++kk) {
+        const uint32_t ao = (kk >> 2) * (128 * 128) + (kk & 3) * 32;
+        const uint32_t bo = (kk >> 2) * (NOUT * 128) + (kk & 3) * 32;
+        mma<KIND_TF32X3>(tmem, sdesc(rh + ao), sdesc(bh + bo), ID, kk > 0 ? 1u : 0u);
+        mma<KIND_TF32X3>(tmem + NOUT, sdesc(rh + ao), sdesc(bl + bo), ID, kk > 0 ? 1u : 0u);
+        mma<KIND_TF32X3>(tmem + NOUT, sdesc(rl + ao), sdesc(bh + bo), ID, 1u);
       }
+      mma_commit(bar);
     }
-    if (act) {
-#pragma unroll
-      for (int q = 0; q < TC; ++q)
-        *reinterpret_cast<float4*>(&nxt[(TC * tj + q) * NP + 4 * ti]) =
-            make_float4(out[0][q], out[1][q], out[2][q], out[3][q]);
+    if (!mbar_wait(bar, (f - 1) & 1)) {
+      ok = false;
+      if (lane == 0) atomicOr(a.err, ERR_TIMEOUT);
     }
-    float* tmp = cur;
-    cur = nxt;
-    nxt = tmp;
-    gmax = block_max(lmax, red, parity);
-  }
-  if (!(gmax > 0.f) || !isfinite(gmax)) {
-    if (threadIdx.x == 0) atomicOr(a.err, ERR_FB_ZERO);
-    gmax = 1.f;
-  }
-  if (threadIdx.x == 0) scl[len - 1] = gmax;
-  const float inv = 1.f / gmax;
-  const size_t base = ((size_t)s * a.C + c) * NP * NP;
-  float* Pg = a.P + base;
-  float* PTg = a.PT + base;
-  if (act) {
+    // the decision to stop must be the same in every thread (barriers follow)
+    ok = !__syncthreads_or(!ok);
+    tc_fence_after();
+    float y[NOUT];
 #pragma unroll
-    for (int q = 0; q < TC; ++q) {
-      const float4 v = make_float4(out[0][q] * inv, out[1][q] * inv, out[2][q] * inv,
-                                   out[3][q] * inv);
-      *reinterpret_cast<float4*>(&PTg[(TC * tj + q) * NP + 4 * ti]) = v;
+    for (int cc = 0; cc < NOUT; cc += 16) {
+      float m16[16], x16[16];
+      tmem_ld16(taddr + cc, m16);
+      tmem_ld16(taddr + NOUT + cc, x16);
 #pragma unroll
-      for (int r = 0; r < 4; ++r) Pg[(4 * ti + r) * NP + TC * tj + q] = out[r][q] * inv;
+      for (int u = 0; u < 16; ++u) y[cc + u] = m16[u] + x16[u];
     }
+    if (live && f < len) {
+      const float* ef = eq + f * NP;
+#pragma unroll
+      for (int j = 0; j < NOUT; ++j) cur[j] = j < NP ? y[j] * ef[j] : 0.f;
+    }
+    normalise_and_store();
+    if (!ok) break;
   }
-  __syncthreads();  // scl complete
-  double lg = msum * ((threadIdx.x & 31) == 0 ? 1.0 : 0.0);
-  for (int f = threadIdx.x; f < len; f += blockDim.x) lg += log((double)scl[f]);
-  lg = block_sum_d(lg, dred);
-  if (threadIdx.x == 0) a.Plog[(size_t)s * a.C + c] = lg;
+  // common scale for the chunk: P_c = exp(rho_max) * (rows scaled to it)
+  const double lr = zero_row ? -INFINITY : sc.log();
+  rhod[r] = live ? lr : -INFINITY;
+  __syncthreads();
+  if (q < Cfg::RCH && c < a.C && i < NP) {
+    double rmax = -INFINITY;
+    for (int ii = 0; ii < N; ++ii) rmax = fmax(rmax, rhod[q * NP + ii]);
+    // rmax = -inf only if every row of the chunk vanished (flagged by the scan)
+    const float f = (live && rmax > -INFINITY) ? (float)exp(lr - rmax) : 0.f;
+    if (rmax == -INFINITY) rmax = 0.0;
+    const size_t base = ((size_t)s * a.C + c) * NP * NP;
+    float* Pg = a.P + base;
+    float* PTg = a.PT + base;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      const float v = live ? cur[j] * f : 0.f;
+      Pg[i * NP + j] = v;
+      PTg[j * NP + i] = v;
+    }
+    if (i == 0) a.Plog[(size_t)s * a.C + c] = msum[q] + rmax;
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, Cfg::TMEM_COLS);
+  }
 }
 
 // ------------------------------------------------------------------- 2. scan
 // One warp per (source, direction); lane j holds states j and j + 32.
 // blockIdx.y == 0: forward boundaries fwd[c] = normalised a at the end of
-// chunk c (c = 0..C-1) and log Z = sum_c (Plog_c + log lambda_c).
+// chunk c (c = 0..C-1) and log Z = sum_c (Plog_c + log lambda_c);
+// y_j = sum_i v_i P[i][j] reads row j of P^T.
 // blockIdx.y == 1: backward boundaries bwd[c] = normalised b at the end of
-// chunk c (bwd[C-1] = 1), from P^T.
+// chunk c (bwd[C-1] = 1); y_i = sum_j P[i][j] v_j reads row i of P.
+// Matrices are staged with rows padded to NP + 4 floats (conflict-free
+// float4 reads).  The vector is rescaled by the previous step's sum.
 template <int NP>
 __global__ void __launch_bounds__(32) k_fb_scan(FBArgs a) {
   extern __shared__ float sm[];
-  constexpr int NN = NP * NP;
+  constexpr int LD = NP + 4;
+  constexpr int NN = NP * LD;
   const int N = a.N, C = a.C;
   const int s = blockIdx.x;
   const bool fwd = blockIdx.y == 0;
   const int lane = threadIdx.x;
-  float* ring = sm;                      // RING x NN
-  float* v = ring + RING * NN;           // 64 (+ padding)
+  float* ring = sm;                      // RING x NP x LD
+  float* v = ring + RING * NN;           // 64
   const size_t base = (size_t)s * C;
-  const float* src = fwd ? a.P : a.PT;
+  const float* src = fwd ? a.PT : a.P;
   const int nsteps = fwd ? C : C - 1;
   auto chunk_of = [&](int q) { return fwd ? q : C - 1 - q; };
   auto prefetch = [&](int q) {
     if (q < nsteps) {
-      const float* g = src + (base + chunk_of(q)) * NN;
+      const float* g = src + (base + chunk_of(q)) * NP * NP;
       float* d = ring + (q % RING) * NN;
 #pragma unroll
-      for (int i = lane * 4; i < NN; i += 128) cp_async16(d + i, g + i);
+      for (int i = lane * 4; i < NP * NP; i += 128) {
+        const int row = i / NP, col = i - (i / NP) * NP;
+        cp_async16(d + row * LD + col, g + i);
+      }
     }
     cp_async_commit();
   };
@@ -298,57 +360,75 @@ __global__ void __launch_bounds__(32) k_fb_scan(FBArgs a) {
   for (int q = 0; q < RING - 1; ++q) prefetch(q);
 
   const bool h0 = lane < N, h1 = lane + 32 < N;
-  float v0 = 0.f, v1 = 0.f;
+  const int j0 = lane < NP ? lane : 0, j1 = lane + 32 < NP ? lane + 32 : 0;
+  float r0 = 0.f, r1 = 0.f;
   if (fwd) {
-    if (h0) v0 = a.pi[(size_t)s * N + lane];
-    if (h1) v1 = a.pi[(size_t)s * N + lane + 32];
+    if (h0) r0 = a.pi[(size_t)s * N + lane];
+    if (h1) r1 = a.pi[(size_t)s * N + lane + 32];
   } else {
-    v0 = h0 ? 1.f : 0.f;
-    v1 = h1 ? 1.f : 0.f;
+    r0 = h0 ? 1.f : 0.f;
+    r1 = h1 ? 1.f : 0.f;
     if (h0) a.bwd[(base + C - 1) * N + lane] = 1.f;
     if (h1) a.bwd[(base + C - 1) * N + lane + 32] = 1.f;
   }
-  v[lane] = v0;
-  v[lane + 32] = v1;
+  // u_prev: the previous step's output, not yet normalised; its sum (the
+  // previous chunk's normaliser) is reduced while this step's products run.
+  float u0 = r0, u1 = r1;
+  auto emit = [&](int qq, float lam_q, float w0, float w1) {  // outputs of step qq
+    const float il = renorm_factor(lam_q);
+    const int c = chunk_of(qq);
+    if (fwd) {
+      if (h0) a.fwd[(base + c) * N + lane] = w0 * il;
+      if (h1) a.fwd[(base + c) * N + lane + 32] = w1 * il;
+      if (lane == 0) a.lam[base + c] = removed_scale(lam_q);
+    } else {
+      if (h0) a.bwd[(base + c - 1) * N + lane] = w0 * il;
+      if (h1) a.bwd[(base + c - 1) * N + lane + 32] = w1 * il;
+    }
+  };
   for (int q = 0; q < nsteps; ++q) {
     prefetch(q + RING - 1);
+    __syncwarp();
+    v[lane] = u0;
+    v[lane + 32] = u1;
     cp_async_wait<RING - 1>();
     __syncwarp();
+    float lam_prev = warp_sum(u0 + u1);
+    if (q > 0 && (!(lam_prev > 0.f) || !isfinite(lam_prev))) {
+      if (lane == 0) atomicOr(a.err, ERR_FB_ZERO);
+      lam_prev = 1.f;
+    }
     const float* P = ring + (q % RING) * NN;
-    // y_j = sum_i v_i P[i][j]  (P^T for the backward direction)
     float y0[4] = {0.f, 0.f, 0.f, 0.f}, y1[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int i = 0; i < NP; i += 4) {
       const float4 vv = *reinterpret_cast<const float4*>(&v[i]);
-      const float vi[4] = {vv.x, vv.y, vv.z, vv.w};
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (lane < NP) y0[u] = fmaf(vi[u], P[(i + u) * NP + lane], y0[u]);
-        if (lane + 32 < NP) y1[u] = fmaf(vi[u], P[(i + u) * NP + lane + 32], y1[u]);
+      const float4 p0 = *reinterpret_cast<const float4*>(&P[j0 * LD + i]);
+      y0[0] = fmaf(vv.x, p0.x, y0[0]);
+      y0[1] = fmaf(vv.y, p0.y, y0[1]);
+      y0[2] = fmaf(vv.z, p0.z, y0[2]);
+      y0[3] = fmaf(vv.w, p0.w, y0[3]);
+      if (NP > 32) {
+        const float4 p1 = *reinterpret_cast<const float4*>(&P[j1 * LD + i]);
+        y1[0] = fmaf(vv.x, p1.x, y1[0]);
+        y1[1] = fmaf(vv.y, p1.y, y1[1]);
+        y1[2] = fmaf(vv.z, p1.z, y1[2]);
+        y1[3] = fmaf(vv.w, p1.w, y1[3]);
       }
     }
-    float r0 = (y0[0] + y0[1]) + (y0[2] + y0[3]);
-    float r1 = (y1[0] + y1[1]) + (y1[2] + y1[3]);
-    float lam = warp_sum(r0 + r1);
+    // the start vector (pi, or ones) enters unnormalised
+    const float inv = q > 0 ? renorm_factor(lam_prev) : 1.f;
+    if (q > 0) emit(q - 1, lam_prev, u0, u1);
+    u0 = h0 ? ((y0[0] + y0[1]) + (y0[2] + y0[3])) * inv : 0.f;
+    u1 = h1 ? ((y1[0] + y1[1]) + (y1[2] + y1[3])) * inv : 0.f;
+  }
+  if (nsteps > 0) {
+    float lam = warp_sum(u0 + u1);
     if (!(lam > 0.f) || !isfinite(lam)) {
       if (lane == 0) atomicOr(a.err, ERR_FB_ZERO);
       lam = 1.f;
     }
-    const float inv = 1.f / lam;
-    r0 *= inv;
-    r1 *= inv;
-    __syncwarp();
-    v[lane] = r0;
-    v[lane + 32] = r1;
-    const int c = chunk_of(q);
-    if (fwd) {
-      if (h0) a.fwd[(base + c) * N + lane] = r0;
-      if (h1) a.fwd[(base + c) * N + lane + 32] = r1;
-      if (lane == 0) a.lam[base + c] = lam;
-    } else {
-      if (h0) a.bwd[(base + c - 1) * N + lane] = r0;
-      if (h1) a.bwd[(base + c - 1) * N + lane + 32] = r1;
-    }
+    emit(nsteps - 1, lam, u0, u1);
   }
   cp_async_wait<0>();
   if (fwd) {
@@ -365,6 +445,7 @@ __global__ void __launch_bounds__(32) k_fb_scan(FBArgs a) {
 // Two warps per chunk: warp 2q runs the forward recursion of chunk q (A's
 // columns j, j+32 in registers), warp 2q+1 the backward recursion (A's rows
 // j, j+32 in registers), concurrently; then both combine a_t b_t into d-hat.
+// Vectors are stored unnormalised and rescaled by the previous step's sum.
 template <int NP>
 __global__ void __launch_bounds__(R_CHUNKS_MAX * 64) k_fb_replay(FBArgs a) {
   extern __shared__ float sm[];
@@ -448,8 +529,7 @@ __global__ void __launch_bounds__(R_CHUNKS_MAX * 64) k_fb_replay(FBArgs a) {
     }
     // forward: vec[0] then f = 1..len-1; backward: vec[len-1] then f = len-2..0
     int f = is_fwd ? 0 : len - 1;
-    float lam = warp_sum(r0 + r1);
-    float inv = lam > 0.f ? 1.f / lam : 1.f;
+    const float inv = renorm_factor(warp_sum(r0 + r1));
     r0 *= inv;
     r1 *= inv;
     if (lane < NP) vec[f * NP + lane] = r0;
@@ -466,6 +546,8 @@ __global__ void __launch_bounds__(R_CHUNKS_MAX * 64) k_fb_replay(FBArgs a) {
         x[lane + 32] = lane + 32 < NP ? r1 * ef[lane + 32] : 0.f;
       }
       __syncwarp();
+      // the sum of the stored vector, used to rescale the next one
+      const float sprev = warp_sum(r0 + r1);
       float p0[4] = {0.f, 0.f, 0.f, 0.f}, p1[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
       for (int i = 0; i < NP; i += 4) {
@@ -487,10 +569,9 @@ __global__ void __launch_bounds__(R_CHUNKS_MAX * 64) k_fb_replay(FBArgs a) {
         y0 = lane < NP ? y0 * en[lane] : 0.f;
         y1 = lane + 32 < NP ? y1 * en[lane + 32] : 0.f;
       }
-      lam = warp_sum(y0 + y1);
-      inv = lam > 0.f ? 1.f / lam : 1.f;
-      r0 = y0 * inv;
-      r1 = y1 * inv;
+      const float inv_prev = renorm_factor(sprev);
+      r0 = y0 * inv_prev;
+      r1 = y1 * inv_prev;
       if (lane < NP) vec[f * NP + lane] = r0;
       if (lane + 32 < NP) vec[f * NP + lane + 32] = r1;
     }
@@ -500,8 +581,12 @@ __global__ void __launch_bounds__(R_CHUNKS_MAX * 64) k_fb_replay(FBArgs a) {
     float* dh = a.dhat + ((size_t)s * a.T + t0) * N;
     unsigned bad = 0;
     for (int f = is_fwd ? 0 : 1; f < len; f += 2) {
-      const float d0 = h0 ? av[f * NP + lane] * bv[f * NP + lane] : 0.f;
-      const float d1 = h1 ? av[f * NP + lane + 32] * bv[f * NP + lane + 32] : 0.f;
+      // the stored vectors are only roughly normalised: rescale each first
+      const float a0 = h0 ? av[f * NP + lane] : 0.f, a1 = h1 ? av[f * NP + lane + 32] : 0.f;
+      const float b0 = h0 ? bv[f * NP + lane] : 0.f, b1 = h1 ? bv[f * NP + lane + 32] : 0.f;
+      const float fa = renorm_factor(warp_sum(a0 + a1)), fb = renorm_factor(warp_sum(b0 + b1));
+      const float d0 = (a0 * fa) * (b0 * fb);
+      const float d1 = (a1 * fa) * (b1 * fb);
       float z = warp_sum(d0 + d1);
       if (!(z > 0.f) || !isfinite(z)) {
         bad = 1;
@@ -517,12 +602,14 @@ __global__ void __launch_bounds__(R_CHUNKS_MAX * 64) k_fb_replay(FBArgs a) {
 
 // ------------------------------------------------------------------ launch
 template <int NP>
-static size_t smem_products() {
-  return (size_t)(64 + 2 * NP * NP + FB_MAX_L * NP + FB_MAX_L + 64) * sizeof(float);
+static size_t smem_products(int L) {
+  using Cfg = ProdCfg<NP>;
+  return 1024 + Cfg::SMEM_FIXED + (size_t)Cfg::RCH * L * NP * sizeof(float) +
+         128 * sizeof(double) + Cfg::RCH * sizeof(double) + 64;
 }
 template <int NP>
 static size_t smem_scan() {
-  return (size_t)(RING * NP * NP + 128) * sizeof(float);
+  return (size_t)(RING * NP * (NP + 4) + 64) * sizeof(float);
 }
 static size_t smem_replay_chunk(int NP, int L) { return (size_t)(3 * L * NP + 128) * sizeof(float); }
 static int replay_chunks(int NP, int L) {
@@ -536,7 +623,7 @@ static cudaError_t launch_np(const FBArgs& a, cudaStream_t st) {
   static cudaError_t attr = cudaErrorNotReady;
   if (attr == cudaErrorNotReady) {
     attr = cudaFuncSetAttribute(k_fb_products<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem_products<NP>());
+                                (int)smem_products<NP>(FB_MAX_L));
     if (attr == cudaSuccess)
       attr = cudaFuncSetAttribute(k_fb_scan<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem_scan<NP>());
@@ -545,8 +632,10 @@ static cudaError_t launch_np(const FBArgs& a, cudaStream_t st) {
                                   (int)SMEM_OPTIN);
   }
   if (attr != cudaSuccess) return attr;
+  using Cfg = ProdCfg<NP>;
   const int rc = replay_chunks(NP, a.L);
-  k_fb_products<NP><<<dim3(a.C, a.S), ProdCfg<NP>::THREADS, smem_products<NP>(), st>>>(a);
+  k_fb_products<NP><<<dim3((a.C + Cfg::RCH - 1) / Cfg::RCH, a.S), 128, smem_products<NP>(a.L),
+                      st>>>(a);
   k_fb_scan<NP><<<dim3(a.S, 2), 32, smem_scan<NP>(), st>>>(a);
   k_fb_replay<NP><<<dim3((a.C + rc - 1) / rc, a.S), rc * 64, rc * smem_replay_chunk(NP, a.L),
                     st>>>(a);

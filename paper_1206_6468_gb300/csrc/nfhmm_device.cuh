@@ -24,12 +24,13 @@ __device__ __forceinline__ void digamma_exp(float x, float& psi, float& w) {
   }
   float acc = 0.f;
   // x > 0: the first step lands in [1, ...), five more reach x >= 6.
+  // __frcp_rn: the correctly rounded reciprocal (same value as 1.f / x)
 #pragma unroll 1
   for (int i = 0; i < 7 && x < 6.f; ++i) {
-    acc += 1.f / x;
+    acc += __frcp_rn(x);
     x += 1.f;
   }
-  const float r = 1.f / x;
+  const float r = __frcp_rn(x);
   const float r2 = r * r;
   const float series =
       r2 * (1.f / 12.f -
@@ -75,7 +76,7 @@ __device__ __forceinline__ double bound_g_elem(float a) {
   if (a < 4.f) {
     return (double)(lgammaf(a) - (a - 1.f) * digamma_f(a));
   }
-  const float r = 1.f / a;
+  const float r = __frcp_rn(a);
   const float poly =
       r * (-1.f / 3.f +
            r * (-1.f / 12.f +

@@ -27,6 +27,7 @@ enum WFormat { WF_F32 = 0, WF_TF32X2 = 1, WF_BF16 = 2 };
 struct WeightsArgs {
   int T, M, Mp, S, N, K;
   float gamma;
+  const int2* ktab;     // Mp entries: (block g, s*T*N + n), g < 0 for padding
   const float* counts;  // T x Mp
   const float* dhat;    // S x T x N
   float* alpha;         // T x Mp
@@ -37,6 +38,7 @@ struct WeightsArgs {
   unsigned* err;
 };
 void launch_weights(const WeightsArgs& a, int fmt, cudaStream_t st);
+void launch_element_table(int M, int Mp, int K, int N, int T, int2* ktab, cudaStream_t st);
 
 // Fill buf[t*ld + k] = (k < M) ? value : 0 for t < T, k < ld.
 void launch_fill_rows(float* buf, int T, int M, int ld, float value, cudaStream_t st);

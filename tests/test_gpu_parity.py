@@ -73,6 +73,9 @@ def test_digamma_and_weights(nf):
     (1, 5, 100, 1, 5.0),      # one frame per chunk
     (1, 5, 100, 128, 5.0),    # one chunk
     (2, 40, 1000, 7, 50.0),   # odd chunk length, sharp posteriors
+    (1, 16, 3000, 0, 20.0),   # tiles exactly full of chunk rows; emissions underflow
+    (2, 24, 2000, 0, 80.0),   # very sharp emissions: rows vanish, sums go subnormal
+    (1, 8, 777, 0, 20.0),     # many chunks per tile, ragged tail
 ])
 def test_forward_backward(nf, S, N, T, L, scale):
     import torch
