@@ -73,8 +73,8 @@ struct ScaleAcc {
 };
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N>
@@ -120,10 +120,11 @@ __device__ __forceinline__ uint32_t sw128_off(int r, int k, int atom_bytes) {
 }
 
 template <int NP>
-__global__ void __launch_bounds__(128, 1) k_fb_products(FBArgs a) {
+__global__ void __launch_bounds__(256, 1) k_fb_products(FBArgs a) {
   using namespace tc;
   using Cfg = ProdCfg<NP>;
   constexpr int NOUT = Cfg::NOUT;
+  constexpr int HC = NOUT / 2;   // columns per thread: two warps share each TMEM lane quarter
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -132,10 +133,10 @@ __global__ void __launch_bounds__(128, 1) k_fb_products(FBArgs a) {
   uint8_t* b_hi = rows_lo + Cfg::ROWS_BYTES;
   uint8_t* b_lo = b_hi + Cfg::B_BYTES;
   float* e = reinterpret_cast<float*>(b_lo + Cfg::B_BYTES);   // RCH x L x NP
-  float* rho = e + Cfg::RCH * a.L * NP;                        // 128 (as double: 2 floats each)
-  double* rhod = reinterpret_cast<double*>(rho);
+  double* rhod = reinterpret_cast<double*>(e + Cfg::RCH * a.L * NP);  // 128
   double* msum = rhod + 128;                                   // RCH
-  uint64_t* bar = reinterpret_cast<uint64_t*>(msum + Cfg::RCH);
+  float* pmax = reinterpret_cast<float*>(msum + Cfg::RCH);     // 2 x 128
+  uint64_t* bar = reinterpret_cast<uint64_t*>(pmax + 256);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
 
   const int N = a.N, L = a.L, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(128, 1) k_fb_products(FBArgs a) {
     const int t0 = c * L, len = min(a.T, t0 + L) - t0;
     float* eq = e + q * L * NP;
     double ms = 0.0;
-    for (int f = warp; f < len; f += 4) {
+    for (int f = warp; f < len; f += 8) {
       float* row = eq + f * NP;
       const float x0 = lane < N ? row[lane] : -INFINITY;
       const float x1 = lane + 32 < N ? row[lane + 32] : -INFINITY;
@@ -191,7 +192,11 @@ __global__ void __launch_bounds__(128, 1) k_fb_products(FBArgs a) {
     }
     if (lane == 0) rhod[warp] = ms;
     __syncthreads();
-    if (tid == 0) msum[q] = rhod[0] + rhod[1] + rhod[2] + rhod[3];
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < 8; ++w) t += rhod[w];
+      msum[q] = t;
+    }
     __syncthreads();
   }
   tc_fence_before();
@@ -199,49 +204,59 @@ __global__ void __launch_bounds__(128, 1) k_fb_products(FBArgs a) {
   tc_fence_after();
   const uint32_t tmem = *tslot;
 
-  // this thread's row: chunk q, basis state i
-  const int r = tid;
+  // this thread: row r (chunk q, basis state i), columns [j0, j0 + HC)
+  const int half = warp >> 2;
+  const int r = (warp & 3) * 32 + lane;
+  const int j0 = half * HC;
   const int q = r / NP, i = r - (r / NP) * NP;
   const int c = cbase + q;
   const bool live = q < Cfg::RCH && c < a.C && i < N;
   const int len = live ? min(a.T, c * L + L) - c * L : 0;
   const float* eq = e + (q < Cfg::RCH ? q : 0) * L * NP;
-  float cur[NOUT];
+  float cur[HC];
   ScaleAcc sc;
   bool zero_row = false;   // once zero, a row stays zero: its scale is then -inf
 #pragma unroll
-  for (int j = 0; j < NOUT; ++j) {
+  for (int u = 0; u < HC; ++u) {
+    const int j = j0 + u;
     float v = 0.f;
     if (live && j < N) v = (c == 0) ? (j == i ? eq[j] : 0.f) : Ag[i * N + j] * eq[j];
-    cur[j] = v;
+    cur[u] = v;
   }
+  // rescale the row by its maximum (both halves agree through shared memory)
+  // and write it, split into tf32 hi/lo, into the swizzled operand tile
   auto normalise_and_store = [&]() {
     float m = 0.f;
 #pragma unroll
-    for (int j = 0; j < NOUT; ++j) m = fmaxf(m, cur[j]);
+    for (int u = 0; u < HC; ++u) m = fmaxf(m, cur[u]);
+    pmax[half * 128 + r] = m;
+    __syncthreads();
+    m = fmaxf(pmax[r], pmax[128 + r]);
     if (live) {
       // an all-zero row is legitimate (state i cannot start this chunk)
       if (!isfinite(m)) {
-        atomicOr(a.err, ERR_FB_ZERO);
+        if (half == 0) atomicOr(a.err, ERR_FB_ZERO);
         m = 0.f;
       }
       if (m == 0.f) zero_row = true;
       const float f = renorm_factor(m);
 #pragma unroll
-      for (int j = 0; j < NOUT; ++j) cur[j] *= f;
+      for (int u = 0; u < HC; ++u) cur[u] *= f;
       sc.mul(removed_scale(m));
     }
 #pragma unroll
-    for (int cc = 0; cc < NP / 4; ++cc) {
-      float h[4], l[4];
+    for (int cc = 0; cc < HC / 4; ++cc) {
+      if (j0 + 4 * cc < NP) {
+        float h[4], l[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        h[u] = tf32_hi(cur[4 * cc + u]);
-        l[u] = tf32_hi(cur[4 * cc + u] - h[u]);
+        for (int u = 0; u < 4; ++u) {
+          h[u] = tf32_hi(cur[4 * cc + u]);
+          l[u] = tf32_hi(cur[4 * cc + u] - h[u]);
+        }
+        const uint32_t off = sw128_off(r, j0 + 4 * cc, 128 * 128);
+        *reinterpret_cast<float4*>(rows_hi + off) = make_float4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<float4*>(rows_lo + off) = make_float4(l[0], l[1], l[2], l[3]);
       }
-      const uint32_t off = sw128_off(r, 4 * cc, 128 * 128);
-      *reinterpret_cast<float4*>(rows_hi + off) = make_float4(h[0], h[1], h[2], h[3]);
-      *reinterpret_cast<float4*>(rows_lo + off) = make_float4(l[0], l[1], l[2], l[3]);
     }
   };
   normalise_and_store();
@@ -249,7 +264,7 @@ __global__ void __launch_bounds__(128, 1) k_fb_products(FBArgs a) {
   constexpr uint32_t ID = idesc<KIND_TF32X3>(128, NOUT);
   const uint32_t rh = smem_u32(rows_hi), rl = smem_u32(rows_lo);
   const uint32_t bh = smem_u32(b_hi), bl = smem_u32(b_lo);
-  const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+  const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)j0;
   bool ok = true;
   for (int f = 1; f < L; ++f) {
     fence_proxy_async_smem();   // the operand rows written above, to the tensor core
@@ -274,26 +289,37 @@ __global__ void __launch_bounds__(128, 1) k_fb_products(FBArgs a) {
     // the decision to stop must be the same in every thread (barriers follow)
     ok = !__syncthreads_or(!ok);
     tc_fence_after();
-    float y[NOUT];
+    float y[HC], x[HC];
 #pragma unroll
-    for (int cc = 0; cc < NOUT; cc += 16) {
-      float m16[16], x16[16];
-      tmem_ld16(taddr + cc, m16);
-      tmem_ld16(taddr + NOUT + cc, x16);
-#pragma unroll
-      for (int u = 0; u < 16; ++u) y[cc + u] = m16[u] + x16[u];
+    for (int cc = 0; cc + 16 <= HC; cc += 16) {
+      tmem_ld16(taddr + cc, *reinterpret_cast<float(*)[16]>(&y[cc]));
+      tmem_ld16(taddr + NOUT + cc, *reinterpret_cast<float(*)[16]>(&x[cc]));
+    }
+    if (HC % 16 == 8) {
+      tmem_ld8(taddr + (HC - 8), &y[HC - 8]);
+      tmem_ld8(taddr + NOUT + (HC - 8), &x[HC - 8]);
     }
     if (live && f < len) {
-      const float* ef = eq + f * NP;
+      const float* ef = eq + f * NP + j0;
 #pragma unroll
-      for (int j = 0; j < NOUT; ++j) cur[j] = j < NP ? y[j] * ef[j] : 0.f;
+      for (int u = 0; u < HC; u += 4) {
+        if (j0 + u < NP) {
+          const float4 e4 = *reinterpret_cast<const float4*>(ef + u);
+          cur[u] = (y[u] + x[u]) * e4.x;
+          cur[u + 1] = (y[u + 1] + x[u + 1]) * e4.y;
+          cur[u + 2] = (y[u + 2] + x[u + 2]) * e4.z;
+          cur[u + 3] = (y[u + 3] + x[u + 3]) * e4.w;
+        } else {
+          cur[u] = cur[u + 1] = cur[u + 2] = cur[u + 3] = 0.f;
+        }
+      }
     }
     normalise_and_store();
     if (!ok) break;
   }
   // common scale for the chunk: P_c = exp(rho_max) * (rows scaled to it)
   const double lr = zero_row ? -INFINITY : sc.log();
-  rhod[r] = live ? lr : -INFINITY;
+  if (half == 0) rhod[r] = live ? lr : -INFINITY;
   __syncthreads();
   if (q < Cfg::RCH && c < a.C && i < NP) {
     double rmax = -INFINITY;
@@ -305,12 +331,15 @@ __global__ void __launch_bounds__(128, 1) k_fb_products(FBArgs a) {
     float* Pg = a.P + base;
     float* PTg = a.PT + base;
 #pragma unroll
-    for (int j = 0; j < NP; ++j) {
-      const float v = live ? cur[j] * f : 0.f;
-      Pg[i * NP + j] = v;
-      PTg[j * NP + i] = v;
+    for (int u = 0; u < HC; ++u) {
+      const int j = j0 + u;
+      if (j < NP) {
+        const float v = live ? cur[u] * f : 0.f;
+        Pg[i * NP + j] = v;
+        PTg[j * NP + i] = v;
+      }
     }
-    if (i == 0) a.Plog[(size_t)s * a.C + c] = msum[q] + rmax;
+    if (i == 0 && half == 0) a.Plog[(size_t)s * a.C + c] = msum[q] + rmax;
   }
   tc_fence_before();
   __syncthreads();
@@ -334,6 +363,7 @@ __global__ void __launch_bounds__(32) k_fb_scan(FBArgs a) {
   extern __shared__ float sm[];
   constexpr int LD = NP + 4;
   constexpr int NN = NP * LD;
+  constexpr int CPL = (NP * NP / 4 + 31) / 32;   // 16-byte copies per lane per matrix
   const int N = a.N, C = a.C;
   const int s = blockIdx.x;
   const bool fwd = blockIdx.y == 0;
@@ -344,15 +374,21 @@ __global__ void __launch_bounds__(32) k_fb_scan(FBArgs a) {
   const float* src = fwd ? a.PT : a.P;
   const int nsteps = fwd ? C : C - 1;
   auto chunk_of = [&](int q) { return fwd ? q : C - 1 - q; };
+  // this lane's 16-byte pieces of a matrix: source and padded destination offsets
+  int soff[CPL], doff[CPL];
+#pragma unroll
+  for (int m = 0; m < CPL; ++m) {
+    const int i = (lane + 32 * m) * 4;
+    soff[m] = i < NP * NP ? i : -1;
+    doff[m] = (i / NP) * LD + (i % NP);
+  }
   auto prefetch = [&](int q) {
     if (q < nsteps) {
       const float* g = src + (base + chunk_of(q)) * NP * NP;
       float* d = ring + (q % RING) * NN;
 #pragma unroll
-      for (int i = lane * 4; i < NP * NP; i += 128) {
-        const int row = i / NP, col = i - (i / NP) * NP;
-        cp_async16(d + row * LD + col, g + i);
-      }
+      for (int m = 0; m < CPL; ++m)
+        if (soff[m] >= 0) cp_async16(d + doff[m], g + soff[m]);
     }
     cp_async_commit();
   };
@@ -605,7 +641,7 @@ template <int NP>
 static size_t smem_products(int L) {
   using Cfg = ProdCfg<NP>;
   return 1024 + Cfg::SMEM_FIXED + (size_t)Cfg::RCH * L * NP * sizeof(float) +
-         128 * sizeof(double) + Cfg::RCH * sizeof(double) + 64;
+         128 * sizeof(double) + Cfg::RCH * sizeof(double) + 256 * sizeof(float) + 64;
 }
 template <int NP>
 static size_t smem_scan() {
@@ -634,7 +670,7 @@ static cudaError_t launch_np(const FBArgs& a, cudaStream_t st) {
   if (attr != cudaSuccess) return attr;
   using Cfg = ProdCfg<NP>;
   const int rc = replay_chunks(NP, a.L);
-  k_fb_products<NP><<<dim3((a.C + Cfg::RCH - 1) / Cfg::RCH, a.S), 128, smem_products<NP>(a.L),
+  k_fb_products<NP><<<dim3((a.C + Cfg::RCH - 1) / Cfg::RCH, a.S), 256, smem_products<NP>(a.L),
                       st>>>(a);
   k_fb_scan<NP><<<dim3(a.S, 2), 32, smem_scan<NP>(), st>>>(a);
   k_fb_replay<NP><<<dim3((a.C + rc - 1) / rc, a.S), rc * 64, rc * smem_replay_chunk(NP, a.L),

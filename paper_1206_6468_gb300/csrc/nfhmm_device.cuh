@@ -103,14 +103,14 @@ __device__ __forceinline__ float warp_max(float v) {
   return v;
 }
 
-// tf32 split: hi keeps the top 10 explicit mantissa bits (round to nearest,
-// ties away), lo = x - hi is exact in float.  The tensor core reads only the
-// tf32 bits of each operand, so hi*hi + hi*lo + lo*hi recovers ~22 bits.
+// tf32 split: hi = x rounded to tf32 (10 explicit mantissa bits, round to
+// nearest with ties away from zero: cvt.rna.tf32.f32), lo = x - hi (exact in
+// float) rounded again.  The tensor core reads only the tf32 bits of each
+// operand, so hi*hi + hi*lo + lo*hi recovers ~22 bits of each product.
 __device__ __forceinline__ float tf32_hi(float x) {
-  uint32_t u = __float_as_uint(x);
-  if ((u & 0x7f800000u) == 0x7f800000u) return x;  // inf/nan unchanged
-  u = (u + 0x1000u) & 0xffffe000u;
-  return __uint_as_float(u);
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
 }
 
 }  // namespace nfhmm
