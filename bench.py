@@ -36,6 +36,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -57,6 +59,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-case", action="store_true",
                     help="run one context for 3 sweeps and exit (a small case for ncu)")
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "serving"],
+                    help="single: one S2 N40 K10 F513 T3000 job per step (the headline); "
+                         "batched: 64 jobs, T ~ U[500, 8000], in one batch per step; "
+                         "serving: Poisson arrivals served by continuous batching")
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-saturate", action="store_true",
+                    help="serving: every request queued at the start (peak throughput)")
     return ap.parse_args()
 
 
@@ -242,13 +252,220 @@ def stage_cost(stage, p, precision, tc):
     return "hbm", 0.0, "GB/s"
 
 
+def roofline_of(prof, steps, T, S, N, K, F, precision, tc, peaks):
+    """Roofline object of the stage with the largest summed event time."""
+    class _P:
+        pass
+    q = _P()
+    q.S, q.N, q.K, q.F, q.T = S, N, K, F, T
+    dom = max((s for s in prof if s != "init"), key=lambda s: prof[s][0])
+    dom_ms, dom_inv, dom_launches = prof[dom]
+    bound_kind, amount, unit = stage_cost(dom, q, precision, tc)
+    avg_s = dom_ms / 1e3 / max(dom_inv, 1)
+    if unit == "TFLOP/s":
+        achieved = amount / avg_s / 1e12
+        if bound_kind == "tensor":
+            peak = peaks["bf16_tflops_sustained"] * (1.0 if precision == "bf16" else TF32_OVER_BF16)
+            note = f"{peaks['source']} bf16 sustained" + ("" if precision == "bf16" else " x 1.1/2.25 (tf32)")
+        else:
+            peak = FP32_SIMT_PEAK_TFLOPS
+            note = "derived FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 x 2.07 GHz"
+    else:
+        achieved = amount / avg_s / 1e9
+        peak = peaks["hbm_gbs"]
+        note = f"{peaks['source']} HBM copy bandwidth"
+    return {"bound": bound_kind, "kernel": dom, "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": achieved / peak, "traffic": None, "peak_source": note,
+            "launch_ms": 1e3 * avg_s, "launches_per_invocation": dom_launches / max(dom_inv, 1),
+            "stage_ms_per_step": {s: round(prof[s][0] / steps, 4) for s in prof}}
+
+
+def run_batched(args, rank, world, local):
+    """64 jobs of T ~ U[500, 8000] frames sharing one S2 N40 K10 F513 model,
+    run as one batch: one step = initial state + 50 sweeps + bound of all."""
+    import torch
+
+    from paper_1206_6468_gb300 import nfhmm, synth
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    lengths = synth.batched_lengths(64, 500, 8000, seed=job_seed(rank))
+    jobs = synth.make_jobs(2, 40, 10, 513, lengths, self_prob=0.95, energy_sigma=1.5,
+                           seed=job_seed(rank))
+    f32 = {"V": jobs.stacked_V()}
+    for k in ("W", "A", "pi"):
+        f32[k] = np.ascontiguousarray(getattr(jobs, k), dtype=np.float32)
+    T = int(lengths.sum())
+    d_in = {k: torch.from_numpy(v).to(dev) for k, v in f32.items()}
+    h_in = {k: torch.from_numpy(v).pin_memory() for k, v in f32.items()}
+    h_dhat = torch.empty((jobs.S, T, jobs.N), dtype=torch.float32).pin_memory()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    ctx = nfhmm.VIContext(d_in["V"], d_in["W"], d_in["A"], d_in["pi"], jobs.S, jobs.N, jobs.K,
+                          precision=args.precision, job_frames=lengths.tolist())
+    sweeps = args.sweeps
+
+    def step_device():
+        ctx.reinit(d_in["V"], d_in["W"], d_in["A"], d_in["pi"])
+        return ctx.sweep(sweeps, bound=True)
+
+    def step_e2e():
+        ctx.reinit(h_in["V"], h_in["W"], h_in["A"], h_in["pi"])
+        L = ctx.sweep(sweeps, bound=True)
+        ctx.posteriors(out=h_dhat)
+        return L
+
+    for _ in range(args.warmup):
+        step_device()
+    torch.cuda.synchronize()
+
+    def timed(fn, n):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(n)]
+        barrier(world)
+        torch.cuda.synchronize()
+        for e0, e1 in evs:
+            flush.zero_()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        return [e0.elapsed_time(e1) for e0, e1 in evs]
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    ctx.profile_enable(True)
+    for st in nfhmm.STAGES:
+        ctx.profile_read(st, reset=True)
+    l0 = ctx.kernel_launches()
+    ms = timed(step_device, args.steps)
+    launches = ctx.kernel_launches() - l0
+    prof = {st: ctx.profile_read(st, reset=True) for st in nfhmm.STAGES}
+    ctx.profile_enable(False)
+    ms_e2e = timed(step_e2e, args.steps)
+    clocks = sampler.stop()
+    tot_ms = max_over_ranks(sum(ms), world)
+    tot_e2e = max_over_ranks(sum(ms_e2e), world)
+    fit = T * sweeps
+    peaks = load_peaks()
+    tc = bool(ctx.query("tensor_cores"))
+    line = {
+        "metric": METRIC, "value": aggregate(fit, args.steps, world, tot_ms), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "bf16",
+        "data": "synthetic",
+        "config": {"workload": f"batched: 64 jobs, T ~ U[500, 8000] (sum {T}), S2 N40 K10 F513, "
+                               f"{sweeps} sweeps + bound per step",
+                   "jobs": len(lengths), "frames": T, "sweeps_per_step": sweeps,
+                   "precision": args.precision, "contractions": "tcgen05" if tc else "fp32 SIMT",
+                   "l2": "inputs larger than L2; flushed between steps (256 MB write)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": dict(roofline_of(prof, args.steps, T, 2, 40, 10, 513, args.precision, tc,
+                                     peaks), fb_chunk=ctx.query("fb_chunk")),
+        "e2e": {"value": aggregate(fit, args.steps, world, tot_e2e), "unit": UNIT,
+                "h2d_bytes_per_step": int(sum(v.numel() * 4 for v in h_in.values())),
+                "d2h_bytes_per_step": int(h_dhat.numel() * 4 + 8)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_serving(args, rank, world, local):
+    """Continuous batching: requests arrive as a Poisson process (rate
+    --serve-rate per second for --serve-seconds), T log-uniform in
+    [200, 10000], half on an S=2 and half on an S=3 model (N40 K10 F513);
+    each runs until its bound moves by less than 1e-5 relative or 100 sweeps."""
+    import torch
+
+    from paper_1206_6468_gb300 import nfhmm, synth
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    rng = np.random.Generator(np.random.PCG64(1000 + job_seed(rank)))
+    pool_n, t_max = 8, 10000
+    models = [synth.make_jobs(S, 40, 10, 513, [t_max] * pool_n, self_prob=0.95,
+                              energy_sigma=1.5, seed=100 * S + job_seed(rank)) for S in (2, 3)]
+    pools = [[np.ascontiguousarray(v, dtype=np.float32) for v in m.V] for m in models]
+    n_req = int(rng.poisson(args.serve_rate * args.serve_seconds))
+    arrivals = np.sort(rng.uniform(0.0, args.serve_seconds, size=n_req))
+    Ts = np.exp(rng.uniform(np.log(200), np.log(t_max), size=n_req)).astype(int)
+    which = rng.integers(0, 2, size=n_req)
+    item = rng.integers(0, pool_n, size=n_req)
+    reqs = [(int(which[r]), pools[which[r]][item[r]][:Ts[r]], float(arrivals[r]))
+            for r in range(n_req)]
+    capacity, max_jobs = 1 << 17, 512
+
+    def batches():
+        return [nfhmm.Batch(np.ascontiguousarray(m.W, dtype=np.float32),
+                            np.ascontiguousarray(m.A, dtype=np.float32),
+                            np.ascontiguousarray(m.pi, dtype=np.float32), m.S, m.N, m.K,
+                            capacity=capacity, max_jobs=max_jobs, precision=args.precision)
+                for m in models]
+
+    warm = batches()
+    nfhmm.serve(warm, reqs[:8], max_sweeps=5, realtime=False, want_posteriors=False)
+    for b in warm:
+        b.close()
+    bs = batches()
+    l0 = sum(b.kernel_launches() for b in bs)
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier(world)
+    t0 = time.perf_counter()
+    res, _ = nfhmm.serve(bs, reqs, rel_tol=1e-5, max_sweeps=100,
+                         realtime=not args.serve_saturate, want_posteriors=True)
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    launches = sum(b.kernel_launches() for b in bs) - l0
+    ok = [r for r in res if r["status"] == nfhmm.OK]
+    fit = sum(Ts[i] * res[i]["sweeps"] for i in range(n_req) if res[i]["status"] == nfhmm.OK)
+    lat = np.array([(r["done_s"] - (0.0 if args.serve_saturate else arrivals[i])) * 1e3
+                    for i, r in enumerate(res) if r["status"] == nfhmm.OK])
+    value = fit / wall
+    line = {
+        "metric": METRIC, "value": value * world, "unit": UNIT, "n_gpus": world, "steps": 1,
+        "warmup": 1, "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "bf16",
+        "data": "synthetic",
+        "config": {"workload": ("serving, all queued at start" if args.serve_saturate else
+                                f"serving, Poisson {args.serve_rate:g} jobs/s for "
+                                f"{args.serve_seconds:g} s") +
+                               ", T log-uniform [200, 10000], S in {2, 3}, N40 K10 F513, "
+                               "until |dL| < 1e-5 |L| or 100 sweeps",
+                   "requests": n_req, "completed": len(ok), "frames": int(Ts.sum()),
+                   "batch_capacity_frames": capacity, "max_jobs": max_jobs,
+                   "precision": args.precision, "parallelism": f"replicas x{world}"},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "max": float(lat.max())},
+        "sweeps": {"mean": float(np.mean([r["sweeps"] for r in ok])),
+                   "max": int(max(r["sweeps"] for r in ok))},
+        "e2e": {"value": value * world, "unit": UNIT,
+                "h2d_bytes_per_step": int(sum(Ts) * 513 * 4),
+                "d2h_bytes_per_step": int(sum(Ts[i] * (2 + which[i]) * 40 * 4 for i in range(n_req)))},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    for b in bs:
+        b.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
-    import numpy as np
+    if args.workload == "batched":
+        run_batched(args, rank, world, local)
+        return
+    if args.workload == "serving":
+        run_serving(args, rank, world, local)
+        return
     import torch
 
     from paper_1206_6468_gb300 import nfhmm, synth

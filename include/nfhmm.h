@@ -62,6 +62,7 @@ extern "C" {
 #define NFHMM_ETIMEOUT (-4)  /* a bounded device wait gave up                 */
 #define NFHMM_ENUMERIC (-5)  /* reconstruction vanished where V > 0, or NaN   */
 #define NFHMM_ESTATE   (-6)  /* call needs a state the context does not have  */
+#define NFHMM_EFULL    (-7)  /* a batch has no room (frames or job slots)     */
 
 #define NFHMM_FP32      0  /* contractions on tcgen05 tensor cores in split TF32 (FP32 accuracy) */
 #define NFHMM_BF16      1  /* contractions on tcgen05 tensor cores, BF16 operands, FP32 accumulate */
@@ -152,6 +153,110 @@ NFHMM_API int nfhmm_get_state(nfhmm_ctx *c, float *counts, float *dhat, int *swe
 NFHMM_API int nfhmm_set_state(nfhmm_ctx *c, const float *counts, const float *dhat, int sweeps_done,
                     int on_device);
 
+/*
+ * Batches of jobs.  A job is one spectrogram to separate; the jobs of a
+ * batch share one model (W, A, pi) and sizes S, N, K, F, and each job has
+ * its own number of frames.  The posterior of Section 3.2 factorises over
+ * jobs (the model treats them as independent), so a batch is the sweep of
+ * Section 3.2 run for every job at once: the contractions and Eqs. 6-8 over
+ * all their frames together, forward-backward on one chain per (job,
+ * source), and the bound as a sum of per-job bounds.  A job's results do not
+ * depend on which other jobs share its batch.
+ * A batch context keeps its jobs' frames back to back in a frame store of
+ * d->T frames, in the order they were added; removing a job moves the later
+ * jobs down.  Every call above applies to a batch context over the frames
+ * of all its jobs in that order, with T the frames held (nfhmm_batch_info);
+ * nfhmm_vi_init makes a batch of one job.  The sweep counter and the bound
+ * of nfhmm_vi_sweep cover all jobs; a job added after a sweep starts from
+ * the initial state.  Calls that need "a sweep" need one since the last
+ * change of the job list.
+ */
+
+/* nfhmm_vi_init_batch -- a batch of n_jobs jobs of job_frames[j] >= 1 frames
+ * (d->T = sum of job_frames); V holds their spectrograms back to back
+ * (d->T x F).  job_ids: NULL or n_jobs ids, as from nfhmm_batch_add. */
+NFHMM_API int nfhmm_vi_init_batch(nfhmm_ctx **out, const nfhmm_dims *d, int n_jobs,
+                                  const int *job_frames, const float *V, const float *W,
+                                  const float *A, const float *pi, int inputs_on_device,
+                                  void *cuda_stream, long long *job_ids);
+
+/* nfhmm_batch_create -- an empty batch with room for d->T frames and
+ * max_jobs jobs, holding the model (W, A, pi; validated).  Device memory is
+ * allocated here, in proportion to d->T: a batch never allocates when jobs
+ * come and go. */
+NFHMM_API int nfhmm_batch_create(nfhmm_ctx **out, const nfhmm_dims *d, int max_jobs,
+                                 const float *W, const float *A, const float *pi,
+                                 int inputs_on_device, void *cuda_stream);
+
+/* nfhmm_batch_add -- append a job of T >= 1 frames (V: T x F), validate it
+ * and set its initial state (as nfhmm_vi_init does).  *job_id receives its
+ * id (unique within the context).  NFHMM_EFULL if the frames or job slots
+ * left are too few; on any failure the batch is unchanged.  Synchronises. */
+NFHMM_API int nfhmm_batch_add(nfhmm_ctx *c, int T, const float *V, int on_device,
+                              long long *job_id);
+
+/* nfhmm_batch_remove -- drop a job and free its frames (asynchronous). */
+NFHMM_API int nfhmm_batch_remove(nfhmm_ctx *c, long long job_id);
+
+/* nfhmm_batch_info -- number of jobs, frames held, and per job (arrays of at
+ * least n_jobs entries, each may be NULL): id, first frame, frames, sweeps
+ * run since the job was added. */
+NFHMM_API int nfhmm_batch_info(nfhmm_ctx *c, int *n_jobs, int *frames_held, long long *ids,
+                               int *t0, int *T, int *sweeps);
+
+/* nfhmm_job_bounds -- the bound of each job (in job order; they sum to
+ * nfhmm_bound).  Needs a sweep.  Synchronises. */
+NFHMM_API int nfhmm_job_bounds(nfhmm_ctx *c, double *bounds);
+
+/* nfhmm_job_posteriors -- d-hat of one job, S x T_job x N. */
+NFHMM_API int nfhmm_job_posteriors(nfhmm_ctx *c, long long job_id, float *dhat, int on_device);
+
+/*
+ * nfhmm_set_option -- tune a context:
+ *   NFHMM_OPT_FB_CHUNK  frames per time chunk of the forward-backward
+ *                       (1..128; results change only by rounding)
+ */
+#define NFHMM_OPT_FB_CHUNK 0
+NFHMM_API int nfhmm_set_option(nfhmm_ctx *c, int key, long long value);
+
+/*
+ * nfhmm_serve -- continuous batching of separation requests over batch
+ * contexts (one per model; created empty with nfhmm_batch_create).  Each
+ * request runs sweeps until its own bound changes by less than
+ * rel_tol * |bound| between two sweeps (after at least min_sweeps), or
+ * max_sweeps; it then leaves with its posteriors.  A request is admitted to
+ * its model's batch, in arrival order, once it has arrived and the batch has
+ * room for its frames (else it waits; a request larger than an empty batch
+ * fails with NFHMM_EFULL).  Every tick runs one sweep of each non-empty
+ * batch.  Times are seconds from the start of the call.  With realtime = 1 a
+ * request arrives at arrival_s on the host clock; with 0 all have arrived at
+ * the start.  Synchronises; returns when every request is done.  The paper
+ * has no serving loop: convergence by relative bound change is the
+ * library's reading of "until convergence".
+ */
+typedef struct {
+  int model;          /* index of the batch context that serves it          */
+  int T;              /* frames (>= 1)                                      */
+  const float *V;     /* T x F, host memory                                 */
+  double arrival_s;   /* arrival time                                        */
+  float *dhat_out;    /* NULL, or S x T x N host buffer for the posteriors  */
+} nfhmm_request;
+typedef struct {
+  double rel_tol;     /* convergence tolerance on the bound (e.g. 1e-5)     */
+  int min_sweeps;     /* >= 1                                               */
+  int max_sweeps;     /* >= min_sweeps                                      */
+  int realtime;       /* 1: honour arrival_s; 0: everything queued at start */
+} nfhmm_serve_opts;
+typedef struct {
+  double admit_s;     /* time the request joined its batch (-1 if never)   */
+  double done_s;      /* time its posteriors were out                       */
+  int sweeps;         /* sweeps it ran                                      */
+  double bound;       /* its bound after the last sweep                     */
+  int status;         /* NFHMM_OK or the error that ended it                */
+} nfhmm_result;
+NFHMM_API int nfhmm_serve(nfhmm_ctx **batches, int n_batches, const nfhmm_request *reqs,
+                          int n_reqs, const nfhmm_serve_opts *opts, nfhmm_result *results);
+
 /* nfhmm_destroy -- free the context and its device memory (waits for its work). */
 NFHMM_API void nfhmm_destroy(nfhmm_ctx *c);
 
@@ -182,7 +287,7 @@ NFHMM_API int nfhmm_forward_backward(int S, int N, int T, const float *phi, cons
  * NFHMM_NOALLOC_SCRATCH_BYTES compiled into the library, which every GPU that
  * loads the library holds until the process exits.  A problem needs about
  * 8*S*C*(P*P + N) + 12*S*C bytes, C = ceil(T/L), P = 8*ceil(N/8) (L = chunk
- * length, at most 128; by default min(48, max(16, ceil(sqrt(T)) - 6))), plus
+ * length, at most 128; by default ceil(sqrt(T)/2) clamped to [16, 64]), plus
  * alignment; larger problems are rejected with NFHMM_EINVAL and a message
  * giving both sizes.
  * The first call on a device looks up the array's device address (with that

@@ -49,12 +49,24 @@ struct StageEvents {
 
 }  // namespace
 
+struct Job {
+  long long id;
+  int t0, T, sweeps;
+};
+
+// A context is a batch of jobs sharing one model (W, A, pi): their frames lie
+// back to back in [0, T_active) of a frame store of d.T frames.  nfhmm_vi_init
+// makes a batch of one job holding all d.T frames.
 struct nfhmm_ctx {
-  nfhmm_dims d{};
+  nfhmm_dims d{};           // d.T = frame capacity
   int M = 0, Mp = 0, Fp = 0, NK = 0;
+  int T_active = 0;         // frames held by the jobs
+  int max_jobs = 1;
+  std::vector<Job> jobs;
+  long long next_id = 0;
   cudaStream_t user = nullptr, s_main = nullptr, s_aux = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_fork = nullptr, ev_join = nullptr;
-  // device buffers
+  // device buffers (frame-indexed ones hold d.T frames)
   float* V = nullptr;       // T x Fp
   float* WM = nullptr;      // Mp x Fp   (beta by element: W[k][l])
   float* WF = nullptr;      // Fp x Mp   (beta by frequency)
@@ -72,20 +84,26 @@ struct nfhmm_ctx {
   double* bpart = nullptr;  // T x nbpart
   int nbpart = 0;
   double* frame_terms = nullptr;  // T
-  double* logZ = nullptr;   // S
-  double* bound_dev = nullptr;
+  double* logZ = nullptr;   // S x max_jobs
+  double* bound_dev = nullptr;    // max_jobs + 1
   unsigned* err = nullptr;
   int2* ktab = nullptr;      // Mp element table
+  // job tables on the device: job_t0[max_jobs + 1] | chain_c0[max_jobs + 1] |
+  // chain_len[max_jobs] | chunk_chain[Cmax]
+  int* d_tab = nullptr;
+  int Cmax = 0;              // chunk capacity of the forward-backward scratch
   void* fb_scratch = nullptr;
   FBArgs fb{};
   TcPlan tc{};
   bool use_tc = false;
   double konst = 0.0;
   // host staging (pinned)
-  double* h_bound = nullptr;
+  double* h_bound = nullptr;  // max_jobs + 1
   unsigned* h_err = nullptr;
   int sweeps_done = 0;
-  bool have_alpha = false;
+  bool have_alpha = false;    // alpha-hat, phi-hat of a sweep over the current jobs
+  bool bpart_ok = false;      // bound partials of the current alpha-hat
+  bool bound_ok = false;      // h_bound holds the bound of the current state
   bool inputs_ok = false;
   bool profiling = false;
   StageEvents stages[NFHMM_NUM_STAGES];
@@ -118,7 +136,7 @@ void free_ctx(nfhmm_ctx* c) {
   if (c->s_aux) cudaStreamSynchronize(c->s_aux);
   void* bufs[] = {c->V, c->WM, c->WF, c->A, c->pi, c->alpha, c->w32, c->c, c->Q, c->phi,
                   c->dhat, c->wts, c->sep_tmp, c->v, c->bpart, c->frame_terms, c->logZ,
-                  c->bound_dev, c->err, c->ktab, c->fb_scratch};
+                  c->bound_dev, c->err, c->ktab, c->fb_scratch, c->d_tab};
   for (void* p : bufs)
     if (p) cudaFree(p);
   tc_free(c->tc);
@@ -181,52 +199,54 @@ int sync_check(nfhmm_ctx* c) {
 }
 
 // Reconstruction + ratio (GEMM1) and back-projection + counts (GEMM2) from
-// the weights in w32 (and the operand copies of the tensor-core path).
-int contract(nfhmm_ctx* c, bool want_bpart, bool init) {
-  const nfhmm_dims& d = c->d;
+// the weights in w32 (and the operand copies of the tensor-core path), for
+// frames [t0, t0 + rows).  The tensor-core form runs from frame 0 only.
+int contract(nfhmm_ctx* c, bool want_bpart, bool init, int t0, int rows) {
   cudaStream_t st = c->s_main;
+  if (rows <= 0) return NFHMM_OK;
   if (c->use_tc && !init) {
     stage_begin(c, NFHMM_STAGE_GEMM1, st);
-    const int n1 = tc_gemm1(c->tc, want_bpart ? c->bpart : nullptr, st);
+    const int n1 = tc_gemm1(c->tc, rows, want_bpart ? c->bpart : nullptr, st);
     if (n1 < 0) return fail(NFHMM_ECUDA, "tensor-core contraction: " + tc_last_error());
     stage_end(c, NFHMM_STAGE_GEMM1, st, n1);
     stage_begin(c, NFHMM_STAGE_GEMM2, st);
-    const int n2 = tc_gemm2(c->tc, st);
+    const int n2 = tc_gemm2(c->tc, rows, st);
     if (n2 < 0) return fail(NFHMM_ECUDA, "tensor-core contraction: " + tc_last_error());
     stage_end(c, NFHMM_STAGE_GEMM2, st, n2);
     return NFHMM_OK;
   }
   const int stage1 = init ? NFHMM_STAGE_INIT : NFHMM_STAGE_GEMM1;
   const int stage2 = init ? NFHMM_STAGE_INIT : NFHMM_STAGE_GEMM2;
+  const size_t oM = (size_t)t0 * c->Mp, oF = (size_t)t0 * c->Fp;
   GemmArgs g1{};
-  g1.rows = d.T;
+  g1.rows = rows;
   g1.cols = c->Fp;
   g1.kdim = c->Mp;
-  g1.A = c->w32;
+  g1.A = c->w32 + oM;
   g1.lda = c->Mp;
   g1.B = c->WF;
   g1.ldb = c->Mp;
-  g1.V = c->V;
+  g1.V = c->V + oF;
   g1.ldv = c->Fp;
-  g1.out = c->Q;
+  g1.out = c->Q + oF;
   g1.ldo = c->Fp;
-  g1.bpart = want_bpart ? c->bpart : nullptr;
+  g1.bpart = want_bpart ? c->bpart + (size_t)t0 * c->nbpart : nullptr;
   g1.nbpart = c->nbpart;
   g1.err = c->err;
   stage_begin(c, stage1, st);
   launch_gemm_simt(g1, EPI_RATIO, st);
   stage_end(c, stage1, st, 1);
   GemmArgs g2{};
-  g2.rows = d.T;
+  g2.rows = rows;
   g2.cols = c->Mp;
   g2.kdim = c->Fp;
-  g2.A = c->Q;
+  g2.A = c->Q + oF;
   g2.lda = c->Fp;
   g2.B = c->WM;
   g2.ldb = c->Fp;
-  g2.out = c->c;
+  g2.out = c->c + oM;
   g2.ldo = c->Mp;
-  g2.w = c->w32;
+  g2.w = c->w32 + oM;
   g2.ldw = c->Mp;
   g2.err = c->err;
   stage_begin(c, stage2, st);
@@ -237,8 +257,9 @@ int contract(nfhmm_ctx* c, bool want_bpart, bool init) {
 
 int one_sweep(nfhmm_ctx* c, bool want_bpart) {
   const nfhmm_dims& d = c->d;
+  if (c->T_active == 0) return NFHMM_OK;
   WeightsArgs wa{};
-  wa.T = d.T;
+  wa.T = c->T_active;
   wa.M = c->M;
   wa.Mp = c->Mp;
   wa.S = d.S;
@@ -268,20 +289,29 @@ int one_sweep(nfhmm_ctx* c, bool want_bpart) {
   int nfb = 0;
   CK(launch_fb(c->fb, c->s_aux, &nfb));
   stage_end(c, NFHMM_STAGE_FB, c->s_aux, nfb);
-  int rc = contract(c, want_bpart, false);
+  int rc = contract(c, want_bpart, false, 0, c->T_active);
   if (rc) return rc;
   CK(cudaEventRecord(c->ev_join, c->s_aux));
   CK(cudaStreamWaitEvent(c->s_main, c->ev_join, 0));
   return NFHMM_OK;
 }
 
-int compute_bound(nfhmm_ctx* c, double* out) {
+// Bound of every job and their sum into h_bound (synchronises).
+int compute_bound(nfhmm_ctx* c) {
+  const int nj = (int)c->jobs.size();
+  if (nj == 0) {
+    c->h_bound[0] = 0.0;
+    c->bound_ok = true;
+    return NFHMM_OK;
+  }
   BoundArgs b{};
-  b.T = c->d.T;
+  b.T = c->T_active;
   b.M = c->M;
   b.Mp = c->Mp;
   b.S = c->d.S;
   b.K = c->d.K;
+  b.njobs = nj;
+  b.job_t0 = c->d_tab;
   b.gamma = (float)c->d.gamma;
   b.konst = c->konst;
   b.alpha = c->alpha;
@@ -295,68 +325,236 @@ int compute_bound(nfhmm_ctx* c, double* out) {
   int n = 0;
   launch_bound(b, c->s_main, &n);
   stage_end(c, NFHMM_STAGE_BOUND, c->s_main, n);
-  CK(cudaMemcpyAsync(c->h_bound, c->bound_dev, sizeof(double), cudaMemcpyDeviceToHost,
-                     c->s_main));
+  CK(cudaMemcpyAsync(c->h_bound, c->bound_dev, (nj + 1) * sizeof(double),
+                     cudaMemcpyDeviceToHost, c->s_main));
   int rc = sync_check(c);
   if (rc) return rc;
-  *out = *c->h_bound;
+  c->bound_ok = true;
   return NFHMM_OK;
 }
 
-int copy_out(void* dst, const void* src, size_t bytes, int on_device, cudaStream_t st) {
-  CK(cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDefault,
-                     st));
-  return NFHMM_OK;
-}
-
-// Copy (V, W, A, pi) into the context's buffers, validate them, refresh the
-// operand copies of beta and set the initial state (z-hat from equal weights,
-// d-hat from init_mode).  Synchronises once.
-int load_and_init(nfhmm_ctx* c, const float* V, const float* W, const float* A, const float* pi,
-                  int on_device) {
+// Copy the model (W, A, pi) into the context, validate it and refresh the
+// layouts and operand copies derived from it.  Queued on s_main.
+int load_model(nfhmm_ctx* c, const float* W, const float* A, const float* pi, int on_device) {
   const nfhmm_dims& d = c->d;
-  const size_t T = d.T, Mp = c->Mp, Fp = c->Fp, S = d.S, N = d.N;
-  int rc = enter(c);
-  if (rc) return rc;
+  const size_t Mp = c->Mp, Fp = c->Fp, S = d.S, N = d.N;
   cudaStream_t st = c->s_main;
-  CK(cudaMemsetAsync(c->err, 0, 4, st));
-  CK(cudaMemsetAsync(c->V, 0, T * Fp * 4, st));
-  CK(cudaMemsetAsync(c->WM, 0, Mp * Fp * 4, st));
-  CK(cudaMemsetAsync(c->c, 0, T * Mp * 4, st));
-  CK(cudaMemsetAsync(c->alpha, 0, T * Mp * 4, st));
-  CK(cudaMemsetAsync(c->bpart, 0, T * c->nbpart * 8, st));
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDefault;
-  CK(cudaMemcpy2DAsync(c->V, Fp * 4, V, (size_t)d.F * 4, (size_t)d.F * 4, T, kind, st));
+  CK(cudaMemsetAsync(c->WM, 0, Mp * Fp * 4, st));
   CK(cudaMemcpy2DAsync(c->WM, Fp * 4, W, (size_t)d.F * 4, (size_t)d.F * 4, (size_t)c->M, kind,
                        st));
   CK(cudaMemcpyAsync(c->A, A, S * N * N * 4, kind, st));
   CK(cudaMemcpyAsync(c->pi, pi, S * N * 4, kind, st));
   stage_begin(c, NFHMM_STAGE_INIT, st);
-  launch_validate(c->V, d.T, d.F, c->Fp, c->WM, c->M, c->A, c->pi, d.S, d.N, c->err, st);
+  launch_validate(c->V, 0, d.F, c->Fp, c->WM, c->M, c->A, c->pi, d.S, d.N, c->err, st);
   launch_transpose(c->WM, c->Mp, c->Fp, c->Fp, c->WF, c->Mp, c->Mp, c->Fp, st);
-  launch_row_sums(c->V, d.T, d.F, c->Fp, c->v, st);
   launch_element_table(c->M, c->Mp, d.K, d.N, d.T, c->ktab, st);
-  int n = 4;
+  int n = 3;
   if (c->use_tc) n += tc_refresh_beta(c->tc, st);
-  // initial state: equal weights (w = 1) through the FP32 contractions
-  launch_fill_rows(c->w32, d.T, c->M, c->Mp, 1.f, st);
-  n += 1;
   stage_end(c, NFHMM_STAGE_INIT, st, n);
-  rc = contract(c, false, true);
+  return NFHMM_OK;
+}
+
+// Copy the spectrogram rows of frames [t0, t0 + T) into the frame store,
+// validate them and set those frames' initial state: z-hat from equal
+// weights (w = 1 through the FP32 contractions) and d-hat from init_mode.
+// The range holds n jobs of frames[0..n) frames (the prior marginals restart
+// at each).  Queued on s_main.
+int load_frames(nfhmm_ctx* c, int t0, int T, const float* V, int on_device, const int* frames,
+                int n) {
+  const nfhmm_dims& d = c->d;
+  const size_t Mp = c->Mp, Fp = c->Fp, N = d.N;
+  cudaStream_t st = c->s_main;
+  if (T <= 0) return NFHMM_OK;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDefault;
+  CK(cudaMemsetAsync(c->V + (size_t)t0 * Fp, 0, (size_t)T * Fp * 4, st));
+  CK(cudaMemsetAsync(c->c + (size_t)t0 * Mp, 0, (size_t)T * Mp * 4, st));
+  CK(cudaMemsetAsync(c->alpha + (size_t)t0 * Mp, 0, (size_t)T * Mp * 4, st));
+  CK(cudaMemsetAsync(c->bpart + (size_t)t0 * c->nbpart, 0, (size_t)T * c->nbpart * 8, st));
+  CK(cudaMemcpy2DAsync(c->V + (size_t)t0 * Fp, Fp * 4, V, (size_t)d.F * 4, (size_t)d.F * 4, T,
+                       kind, st));
+  stage_begin(c, NFHMM_STAGE_INIT, st);
+  launch_validate(c->V + (size_t)t0 * Fp, T, d.F, c->Fp, c->WM, c->M, c->A, c->pi, d.S, d.N,
+                  c->err, st);
+  launch_row_sums(c->V + (size_t)t0 * Fp, T, d.F, c->Fp, c->v + t0, st);
+  launch_fill_rows(c->w32 + (size_t)t0 * Mp, T, c->M, c->Mp, 1.f, st);
+  stage_end(c, NFHMM_STAGE_INIT, st, 3);
+  int rc = contract(c, false, true, t0, T);
   if (rc) return rc;
   stage_begin(c, NFHMM_STAGE_INIT, st);
+  int launches = 0;
   if (d.init_mode == NFHMM_INIT_UNIFORM) {
-    launch_fill(c->dhat, S * T * N, 1.f / (float)d.N, st);
+    for (int s = 0; s < d.S; ++s, ++launches)
+      launch_fill(c->dhat + ((size_t)s * d.T + t0) * N, (size_t)T * N, 1.f / (float)d.N, st);
   } else {
-    launch_prior_marginals(c->A, c->pi, d.S, d.N, d.T, c->dhat, st);
+    int t = t0;
+    for (int j = 0; j < n; ++j, ++launches) {
+      launch_prior_marginals(c->A, c->pi, d.S, d.N, d.T, nullptr, 1, t, t + frames[j], c->dhat,
+                             st);
+      t += frames[j];
+    }
   }
-  stage_end(c, NFHMM_STAGE_INIT, st, 1);
+  stage_end(c, NFHMM_STAGE_INIT, st, launches);
+  return NFHMM_OK;
+}
+
+int fb_chunks(const nfhmm_ctx* c) {
+  int C = 0;
+  for (const Job& j : c->jobs) C += (j.T + c->fb.L - 1) / c->fb.L;
+  return C;
+}
+
+// (Re)allocate the forward-backward scratch and the job tables for chunk
+// length fb.L: room for every job set the frame store and job slots allow.
+int ensure_fb_capacity(nfhmm_ctx* c) {
+  const int need = (c->d.T + c->fb.L - 1) / c->fb.L + c->max_jobs;
+  if (c->fb_scratch && need <= c->Cmax) return NFHMM_OK;
+  CK(cudaStreamSynchronize(c->s_main));
+  CK(cudaStreamSynchronize(c->s_aux));
+  if (c->fb_scratch) {
+    cudaFree(c->fb_scratch);
+    c->device_bytes -= fb_scratch_bytes(c->d.S, c->d.N, c->Cmax);
+    c->fb_scratch = nullptr;
+  }
+  if (c->d_tab) {
+    cudaFree(c->d_tab);
+    c->device_bytes -= (size_t)(3 * c->max_jobs + 2 + c->Cmax) * sizeof(int);
+    c->d_tab = nullptr;
+  }
+  c->Cmax = 0;
+  const size_t sb = fb_scratch_bytes(c->d.S, c->d.N, need);
+  const size_t tb = (size_t)(3 * c->max_jobs + 2 + need) * sizeof(int);
+  CK(dmalloc(c, &c->fb_scratch, sb));
+  CK(dmalloc(c, (void**)&c->d_tab, tb));
+  c->Cmax = need;
+  c->fb.C = need;
+  fb_carve_scratch(c->fb, c->fb_scratch);   // regions sized for Cmax chunks
+  c->fb.chain_c0 = c->d_tab + (c->max_jobs + 1);
+  c->fb.chain_t0 = c->d_tab;
+  c->fb.chain_len = c->d_tab + 2 * (c->max_jobs + 1);
+  c->fb.chunk_chain = c->d_tab + 3 * c->max_jobs + 2;
+  c->fb.C = fb_chunks(c);
+  return NFHMM_OK;
+}
+
+// Upload the job tables for the current job list (queued on s_main; the
+// host copy is staged by the runtime before the call returns).
+int commit_jobs(nfhmm_ctx* c) {
+  const int nj = (int)c->jobs.size(), mj = c->max_jobs;
+  const int C = fb_chunks(c);
+  std::vector<int> tab((size_t)3 * mj + 2 + C, 0);
+  int* job_t0 = tab.data();
+  int* chain_c0 = job_t0 + (mj + 1);
+  int* chain_len = chain_c0 + (mj + 1);
+  int* chunk_chain = chain_len + mj;
+  int cc = 0;
+  for (int j = 0; j < nj; ++j) {
+    job_t0[j] = c->jobs[j].t0;
+    chain_c0[j] = cc;
+    chain_len[j] = c->jobs[j].T;
+    const int nc = (c->jobs[j].T + c->fb.L - 1) / c->fb.L;
+    for (int q = 0; q < nc; ++q) chunk_chain[cc + q] = j;
+    cc += nc;
+  }
+  job_t0[nj] = c->T_active;
+  chain_c0[nj] = cc;
+  CK(cudaMemcpyAsync(c->d_tab, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice,
+                     c->s_main));
+  c->fb.C = C;
+  c->fb.nchains = nj;
+  c->have_alpha = false;
+  c->bpart_ok = false;
+  c->bound_ok = false;
+  return NFHMM_OK;
+}
+
+// Append jobs of the given frame counts, their spectrograms back to back in
+// V.  Validates (synchronises); on failure nothing is added.
+int add_jobs(nfhmm_ctx* c, int n, const int* frames, const float* V, int on_device,
+             long long* ids) {
+  long long total = 0;
+  for (int j = 0; j < n; ++j) {
+    if (frames[j] < 1) return fail(NFHMM_EINVAL, "every job needs at least one frame");
+    total += frames[j];
+  }
+  if ((int)c->jobs.size() + n > c->max_jobs)
+    return fail(NFHMM_EFULL, "the batch holds " + std::to_string(c->jobs.size()) + " of " +
+                                 std::to_string(c->max_jobs) + " jobs");
+  if (c->T_active + total > c->d.T)
+    return fail(NFHMM_EFULL, "the batch has " + std::to_string(c->d.T - c->T_active) +
+                                 " free frames; the jobs need " + std::to_string(total));
+  int rc = enter(c);
+  if (rc) return rc;
+  const int t0 = c->T_active;
+  rc = load_frames(c, t0, (int)total, V, on_device, frames, n);
+  if (rc) return rc;
   rc = sync_check(c);
   if (rc) return rc;
-  c->sweeps_done = 0;
-  c->have_alpha = false;
-  c->inputs_ok = true;
+  int t = t0;
+  for (int j = 0; j < n; ++j) {
+    const long long id = c->next_id++;
+    c->jobs.push_back(Job{id, t, frames[j], 0});
+    if (ids) ids[j] = id;
+    t += frames[j];
+  }
+  c->T_active = t;
+  rc = commit_jobs(c);
+  if (rc) return rc;
   return leave(c);
+}
+
+// Remove job j and move the jobs after it down over its frames (their
+// persistent state: V, counts, d-hat, v; staged through scratch buffers that
+// the next sweep rewrites anyway).
+int remove_job(nfhmm_ctx* c, int j) {
+  const Job gone = c->jobs[j];
+  const nfhmm_dims& d = c->d;
+  const size_t Mp = c->Mp, Fp = c->Fp, N = d.N, S = d.S, Tc = d.T;
+  const int src = gone.t0 + gone.T, tail = c->T_active - src;
+  int rc = enter(c);
+  if (rc) return rc;
+  cudaStream_t st = c->s_main;
+  const cudaMemcpyKind dd = cudaMemcpyDeviceToDevice;
+  if (tail > 0) {
+    const int dst = gone.t0;
+    CK(cudaMemcpyAsync(c->Q, c->V + src * Fp, tail * Fp * 4, dd, st));
+    CK(cudaMemcpyAsync(c->V + dst * Fp, c->Q, tail * Fp * 4, dd, st));
+    CK(cudaMemcpyAsync(c->alpha, c->c + src * Mp, tail * Mp * 4, dd, st));
+    CK(cudaMemcpyAsync(c->c + dst * Mp, c->alpha, tail * Mp * 4, dd, st));
+    CK(cudaMemcpy2DAsync(c->phi, Tc * N * 4, c->dhat + src * N, Tc * N * 4, tail * N * 4, S, dd,
+                         st));
+    CK(cudaMemcpy2DAsync(c->dhat + dst * N, Tc * N * 4, c->phi, Tc * N * 4, tail * N * 4, S, dd,
+                         st));
+    CK(cudaMemcpyAsync(c->frame_terms, c->v + src, tail * 8, dd, st));
+    CK(cudaMemcpyAsync(c->v + dst, c->frame_terms, tail * 8, dd, st));
+  }
+  c->jobs.erase(c->jobs.begin() + j);
+  for (size_t q = j; q < c->jobs.size(); ++q) c->jobs[q].t0 -= gone.T;
+  c->T_active -= gone.T;
+  rc = commit_jobs(c);
+  if (rc) return rc;
+  return leave(c);
+}
+
+int find_job(nfhmm_ctx* c, long long id) {
+  for (size_t j = 0; j < c->jobs.size(); ++j)
+    if (c->jobs[j].id == id) return (int)j;
+  return -1;
+}
+
+// S slices of T_active frames (stride d.T frames) to or from a packed
+// S x T_active x width array.
+int copy_slices(nfhmm_ctx* c, void* dst, const void* src, int width, bool to_packed, int t0,
+                int T, int on_device) {
+  const size_t row = (size_t)T * width * 4, stride = (size_t)c->d.T * width * 4;
+  const size_t off = (size_t)t0 * width * 4;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDefault;
+  if (row == 0) return NFHMM_OK;
+  if (to_packed)
+    CK(cudaMemcpy2DAsync(dst, row, (const char*)src + off, stride, row, c->d.S, kind, c->s_main));
+  else
+    CK(cudaMemcpy2DAsync((char*)dst + off, stride, src, row, row, c->d.S, kind, c->s_main));
+  return NFHMM_OK;
 }
 
 int need_inputs(nfhmm_ctx* c) {
@@ -371,13 +569,20 @@ extern "C" {
 
 const char* nfhmm_last_error(void) { return g_last_error.c_str(); }
 
-int nfhmm_vi_init(nfhmm_ctx** out, const nfhmm_dims* dp, const float* V, const float* W,
-                  const float* A, const float* pi, int inputs_on_device, void* cuda_stream) {
+}  // extern "C"
+
+namespace {
+
+// Allocate a context for a frame store of d.T frames and max_jobs jobs and
+// load the model; no jobs yet.  Synchronises once (model validation).
+int create_ctx(nfhmm_ctx** out, const nfhmm_dims* dp, int max_jobs, const float* W,
+               const float* A, const float* pi, int inputs_on_device, void* cuda_stream) {
   if (out) *out = nullptr;
-  if (!out || !dp || !V || !W || !A || !pi) return fail(NFHMM_EINVAL, "NULL argument");
+  if (!out || !dp || !W || !A || !pi) return fail(NFHMM_EINVAL, "NULL argument");
   const nfhmm_dims d = *dp;
   if (d.S < 1 || d.N < 1 || d.K < 1 || d.F < 1 || d.T < 1)
     return fail(NFHMM_EINVAL, "S, N, K, F, T must all be >= 1");
+  if (max_jobs < 1 || max_jobs > (1 << 20)) return fail(NFHMM_EINVAL, "max_jobs must be in [1, 2^20]");
   const long long M = (long long)d.S * d.N * d.K;
   if (M > (1 << 20) || d.F > (1 << 20) || d.T > (1 << 26))
     return fail(NFHMM_EINVAL, "sizes too large (M, F <= 2^20, T <= 2^26)");
@@ -395,6 +600,7 @@ int nfhmm_vi_init(nfhmm_ctx** out, const nfhmm_dims* dp, const float* V, const f
   c->Mp = (int)round_up(M, 32);
   c->Fp = (int)round_up(d.F, 32);
   c->NK = d.N * d.K;
+  c->max_jobs = max_jobs;
   c->user = reinterpret_cast<cudaStream_t>(cuda_stream);
   c->konst = lgamma((double)M + d.gamma * d.S * d.K) - (double)d.S * d.K * lgamma(1.0 + d.gamma);
   int rc = NFHMM_OK;
@@ -435,26 +641,30 @@ int nfhmm_vi_init(nfhmm_ctx** out, const nfhmm_dims* dp, const float* V, const f
   DMALLOC(c->v, T * 8);
   DMALLOC(c->bpart, T * c->nbpart * 8);
   DMALLOC(c->frame_terms, T * 8);
-  DMALLOC(c->logZ, S * 8);
-  DMALLOC(c->bound_dev, 8);
+  DMALLOC(c->logZ, S * max_jobs * 8);
+  DMALLOC(c->bound_dev, (max_jobs + 1) * 8);
   DMALLOC(c->err, 4);
   DMALLOC(c->ktab, Mp * sizeof(int2));
-  CKI(cudaMallocHost(&c->h_bound, 8));
+  CKI(cudaMallocHost(&c->h_bound, (max_jobs + 1) * 8));
   CKI(cudaMallocHost(&c->h_err, 4));
-  // forward-backward plan and scratch
+  // frames never written by a job are read by the tiles that straddle the
+  // end of the jobs' frames: start them at zero
+  CKI(cudaMemsetAsync(c->V, 0, T * Fp * 4, c->s_main));
+  CKI(cudaMemsetAsync(c->w32, 0, T * Mp * 4, c->s_main));
+  CKI(cudaMemsetAsync(c->err, 0, 4, c->s_main));
+  // forward-backward plan, scratch and job tables
   c->fb.S = d.S;
   c->fb.N = d.N;
-  c->fb.T = d.T;
-  c->fb.L = fb_default_chunk(d.N, d.T);
-  c->fb.C = (d.T + c->fb.L - 1) / c->fb.L;
-  DMALLOC(c->fb_scratch, fb_scratch_bytes(d.S, d.N, d.T, c->fb.L));
-  fb_carve_scratch(c->fb, c->fb_scratch);
+  c->fb.T = d.T;   // frame stride of phi-hat and d-hat
+  c->fb.L = max_jobs == 1 ? fb_default_chunk(d.N, d.T) : fb_default_chunk(d.N, d.T < 4096 ? d.T : 4096);
   c->fb.phi = c->phi;
   c->fb.A = c->A;
   c->fb.pi = c->pi;
   c->fb.dhat = c->dhat;
   c->fb.logZ = c->logZ;
   c->fb.err = c->err;
+  rc = ensure_fb_capacity(c);
+  if (rc) return bail(rc);
 
   // tensor-core plan (operand copies of beta, tensor maps)
   if (d.precision != NFHMM_FP32_SIMT) {
@@ -466,15 +676,177 @@ int nfhmm_vi_init(nfhmm_ctx** out, const nfhmm_dims* dp, const float* V, const f
     c->tc.nbpart = c->nbpart;
     c->use_tc = true;
   }
-  rc = load_and_init(c, V, W, A, pi, inputs_on_device);
+#undef CKI
+#undef DMALLOC
+  rc = enter(c);
+  if (!rc) rc = load_model(c, W, A, pi, inputs_on_device);
+  if (!rc) rc = commit_jobs(c);
+  if (!rc) rc = sync_check(c);
+  if (!rc) rc = leave(c);
   if (rc) return bail(rc);
-  c->sweeps_done = 0;
-  c->have_alpha = false;
+  c->inputs_ok = true;
+  *out = c;
+  return NFHMM_OK;
+}
+
+// Run n sweeps over every job; with want_bound, the bounds of the final
+// state into h_bound (synchronises).
+int sweep_impl(nfhmm_ctx* c, int n_sweeps, bool want_bound) {
+  if (n_sweeps == 0 && want_bound && !c->have_alpha)
+    return fail(NFHMM_ESTATE, "no sweep has run over the current jobs: the bound is defined "
+                              "after a sweep");
+  if (n_sweeps == 0 && want_bound && c->bound_ok) return NFHMM_OK;
+  int rc = enter(c);
+  if (rc) return rc;
+  for (int i = 0; i < n_sweeps; ++i) {
+    const bool last = i == n_sweeps - 1;
+    rc = one_sweep(c, want_bound && last);
+    if (rc) return rc;
+  }
+  if (n_sweeps > 0) {
+    c->sweeps_done += n_sweeps;
+    for (Job& j : c->jobs) j.sweeps += n_sweeps;
+    c->have_alpha = true;
+    c->bpart_ok = want_bound;
+    c->bound_ok = false;
+  }
+  if (want_bound) {
+    if (!c->bpart_ok) {
+      rc = contract(c, true, false, 0, c->T_active);
+      if (rc) return rc;
+      c->bpart_ok = true;
+    }
+    rc = compute_bound(c);
+    if (rc) return rc;
+  }
+  return leave(c);
+}
+
+}  // namespace
+
+extern "C" {
+
+int nfhmm_vi_init(nfhmm_ctx** out, const nfhmm_dims* dp, const float* V, const float* W,
+                  const float* A, const float* pi, int inputs_on_device, void* cuda_stream) {
+  if (out) *out = nullptr;
+  if (!out || !dp || !V) return fail(NFHMM_EINVAL, "NULL argument");
+  nfhmm_ctx* c = nullptr;
+  int rc = create_ctx(&c, dp, 1, W, A, pi, inputs_on_device, cuda_stream);
+  if (rc) return rc;
+  const int T = dp->T;
+  rc = add_jobs(c, 1, &T, V, inputs_on_device, nullptr);
+  if (rc) {
+    free_ctx(c);
+    return rc;
+  }
   *out = c;
   g_last_error.clear();
   return NFHMM_OK;
-#undef CKI
-#undef DMALLOC
+}
+
+int nfhmm_vi_init_batch(nfhmm_ctx** out, const nfhmm_dims* dp, int n_jobs, const int* job_frames,
+                        const float* V, const float* W, const float* A, const float* pi,
+                        int inputs_on_device, void* cuda_stream, long long* job_ids) {
+  if (out) *out = nullptr;
+  if (!out || !dp || !V || !job_frames) return fail(NFHMM_EINVAL, "NULL argument");
+  if (n_jobs < 1) return fail(NFHMM_EINVAL, "n_jobs must be >= 1");
+  long long total = 0;
+  for (int j = 0; j < n_jobs; ++j) {
+    if (job_frames[j] < 1) return fail(NFHMM_EINVAL, "every job needs at least one frame");
+    total += job_frames[j];
+  }
+  if (total != dp->T) return fail(NFHMM_EINVAL, "d->T must equal the sum of job_frames");
+  nfhmm_ctx* c = nullptr;
+  int rc = create_ctx(&c, dp, n_jobs, W, A, pi, inputs_on_device, cuda_stream);
+  if (rc) return rc;
+  rc = add_jobs(c, n_jobs, job_frames, V, inputs_on_device, job_ids);
+  if (rc) {
+    free_ctx(c);
+    return rc;
+  }
+  *out = c;
+  g_last_error.clear();
+  return NFHMM_OK;
+}
+
+int nfhmm_batch_create(nfhmm_ctx** out, const nfhmm_dims* dp, int max_jobs, const float* W,
+                       const float* A, const float* pi, int inputs_on_device, void* cuda_stream) {
+  const int rc = create_ctx(out, dp, max_jobs, W, A, pi, inputs_on_device, cuda_stream);
+  if (!rc) g_last_error.clear();
+  return rc;
+}
+
+int nfhmm_batch_add(nfhmm_ctx* c, int T, const float* V, int on_device, long long* job_id) {
+  if (!c || !V) return fail(NFHMM_EINVAL, "NULL argument");
+  if (need_inputs(c)) return NFHMM_ESTATE;
+  return add_jobs(c, 1, &T, V, on_device, job_id);
+}
+
+int nfhmm_batch_remove(nfhmm_ctx* c, long long job_id) {
+  if (!c) return fail(NFHMM_EINVAL, "NULL context");
+  const int j = find_job(c, job_id);
+  if (j < 0) return fail(NFHMM_EINVAL, "no job " + std::to_string(job_id) + " in the batch");
+  return remove_job(c, j);
+}
+
+int nfhmm_batch_info(nfhmm_ctx* c, int* n_jobs, int* frames_held, long long* ids, int* t0,
+                     int* T, int* sweeps) {
+  if (!c) return fail(NFHMM_EINVAL, "NULL context");
+  if (n_jobs) *n_jobs = (int)c->jobs.size();
+  if (frames_held) *frames_held = c->T_active;
+  for (size_t j = 0; j < c->jobs.size(); ++j) {
+    if (ids) ids[j] = c->jobs[j].id;
+    if (t0) t0[j] = c->jobs[j].t0;
+    if (T) T[j] = c->jobs[j].T;
+    if (sweeps) sweeps[j] = c->jobs[j].sweeps;
+  }
+  return NFHMM_OK;
+}
+
+int nfhmm_job_bounds(nfhmm_ctx* c, double* bounds) {
+  if (!c || !bounds) return fail(NFHMM_EINVAL, "NULL argument");
+  if (need_inputs(c)) return NFHMM_ESTATE;
+  const int rc = sweep_impl(c, 0, true);
+  if (rc) return rc;
+  for (size_t j = 0; j < c->jobs.size(); ++j) bounds[j] = c->h_bound[j];
+  return NFHMM_OK;
+}
+
+int nfhmm_job_posteriors(nfhmm_ctx* c, long long job_id, float* dhat, int on_device) {
+  if (!c || !dhat) return fail(NFHMM_EINVAL, "NULL argument");
+  if (need_inputs(c)) return NFHMM_ESTATE;
+  const int j = find_job(c, job_id);
+  if (j < 0) return fail(NFHMM_EINVAL, "no job " + std::to_string(job_id) + " in the batch");
+  int rc = enter(c);
+  if (rc) return rc;
+  rc = copy_slices(c, dhat, c->dhat, c->d.N, true, c->jobs[j].t0, c->jobs[j].T, on_device);
+  if (rc) return rc;
+  if (!on_device) {
+    rc = sync_check(c);
+    if (rc) return rc;
+  }
+  return leave(c);
+}
+
+int nfhmm_set_option(nfhmm_ctx* c, int key, long long value) {
+  if (!c) return fail(NFHMM_EINVAL, "NULL context");
+  switch (key) {
+    case NFHMM_OPT_FB_CHUNK: {
+      if (value < 1 || value > 128) return fail(NFHMM_EINVAL, "chunk length must be in [1, 128]");
+      const int old = c->fb.L;
+      c->fb.L = (int)value;
+      int rc = ensure_fb_capacity(c);
+      if (rc) {
+        c->fb.L = old;
+        return rc;
+      }
+      rc = enter(c);
+      if (!rc) rc = commit_jobs(c);
+      if (!rc) rc = leave(c);
+      return rc;
+    }
+    default: return fail(NFHMM_EINVAL, "unknown option key");
+  }
 }
 
 int nfhmm_vi_reinit(nfhmm_ctx* c, const float* V, const float* W, const float* A,
@@ -483,34 +855,34 @@ int nfhmm_vi_reinit(nfhmm_ctx* c, const float* V, const float* W, const float* A
   c->inputs_ok = false;
   c->sweeps_done = 0;
   c->have_alpha = false;
-  return load_and_init(c, V, W, A, pi, inputs_on_device);
+  c->bpart_ok = false;
+  c->bound_ok = false;
+  std::vector<int> frames;
+  for (Job& j : c->jobs) {
+    j.sweeps = 0;
+    frames.push_back(j.T);
+  }
+  int rc = enter(c);
+  if (rc) return rc;
+  CK(cudaMemsetAsync(c->err, 0, 4, c->s_main));
+  rc = load_model(c, W, A, pi, inputs_on_device);
+  if (rc) return rc;
+  rc = load_frames(c, 0, c->T_active, V, inputs_on_device, frames.data(), (int)frames.size());
+  if (rc) return rc;
+  rc = sync_check(c);
+  if (rc) return rc;
+  c->inputs_ok = true;
+  return leave(c);
 }
 
 int nfhmm_vi_sweep(nfhmm_ctx* c, int n_sweeps, double* bound_out) {
   if (!c) return fail(NFHMM_EINVAL, "NULL context");
   if (need_inputs(c)) return NFHMM_ESTATE;
   if (n_sweeps < 0) return fail(NFHMM_EINVAL, "n_sweeps must be >= 0");
-  if (n_sweeps == 0 && bound_out && !c->have_alpha)
-    return fail(NFHMM_ESTATE, "no sweep has run: the bound is defined after a sweep");
-  int rc = enter(c);
+  const int rc = sweep_impl(c, n_sweeps, bound_out != nullptr);
   if (rc) return rc;
-  for (int i = 0; i < n_sweeps; ++i) {
-    rc = one_sweep(c, bound_out != nullptr && i == n_sweeps - 1);
-    if (rc) return rc;
-  }
-  if (n_sweeps > 0) {
-    c->sweeps_done += n_sweeps;
-    c->have_alpha = true;
-  }
-  if (bound_out) {
-    if (n_sweeps == 0) {
-      rc = contract(c, true, false);
-      if (rc) return rc;
-    }
-    rc = compute_bound(c, bound_out);
-    if (rc) return rc;
-  }
-  return leave(c);
+  if (bound_out) *bound_out = c->h_bound[c->jobs.size()];
+  return NFHMM_OK;
 }
 
 int nfhmm_bound(nfhmm_ctx* c, double* out) {
@@ -525,21 +897,21 @@ int nfhmm_separate(nfhmm_ctx* c, float* out, int masked, int weights, int out_on
   if (weights != NFHMM_SEP_MEAN && weights != NFHMM_SEP_EXPECTATION)
     return fail(NFHMM_EINVAL, "weights must be NFHMM_SEP_MEAN or NFHMM_SEP_EXPECTATION");
   const nfhmm_dims& d = c->d;
-  const size_t T = d.T, F = d.F, S = d.S;
+  const size_t T = c->T_active, F = d.F, S = d.S;
   int rc = enter(c);
   if (rc) return rc;
   cudaStream_t st = c->s_main;
-  if (!c->wts) CK(cudaMalloc(&c->wts, T * c->Mp * 4));
+  if (!c->wts) CK(dmalloc(c, (void**)&c->wts, (size_t)d.T * c->Mp * 4));
   float* dst = out;
   if (!out_on_device) {
-    if (!c->sep_tmp) CK(cudaMalloc(&c->sep_tmp, S * T * F * 4));
+    if (!c->sep_tmp) CK(dmalloc(c, (void**)&c->sep_tmp, S * (size_t)d.T * F * 4));
     dst = c->sep_tmp;
   }
-  launch_sep_weights(c->alpha, c->v, d.T, c->M, c->Mp, weights, c->wts, st);
+  launch_sep_weights(c->alpha, c->v, (int)T, c->M, c->Mp, weights, c->wts, st);
   c->launches += 1;
   for (int s = 0; s < d.S; ++s) {
     GemmArgs g{};
-    g.rows = d.T;
+    g.rows = (int)T;
     g.cols = d.F;
     g.kdim = c->NK;
     g.A = c->wts + (size_t)s * c->NK;
@@ -553,7 +925,7 @@ int nfhmm_separate(nfhmm_ctx* c, float* out, int masked, int weights, int out_on
     c->launches += 1;
   }
   if (masked) {
-    launch_sep_mask(c->V, c->Fp, dst, d.S, d.T, d.F, st);
+    launch_sep_mask(c->V, c->Fp, dst, d.S, (int)T, d.F, st);
     c->launches += 1;
   }
   if (!out_on_device) {
@@ -569,8 +941,7 @@ int nfhmm_get_posteriors(nfhmm_ctx* c, float* dhat, int on_device) {
   if (need_inputs(c)) return NFHMM_ESTATE;
   int rc = enter(c);
   if (rc) return rc;
-  const size_t n = (size_t)c->d.S * c->d.T * c->d.N;
-  rc = copy_out(dhat, c->dhat, n * 4, on_device, c->s_main);
+  rc = copy_slices(c, dhat, c->dhat, c->d.N, true, 0, c->T_active, on_device);
   if (rc) return rc;
   if (!on_device) {
     rc = sync_check(c);
@@ -582,9 +953,10 @@ int nfhmm_get_posteriors(nfhmm_ctx* c, float* dhat, int on_device) {
 static int get_rows(nfhmm_ctx* c, float* dst, const float* src, int on_device) {
   int rc = enter(c);
   if (rc) return rc;
-  CK(cudaMemcpy2DAsync(dst, (size_t)c->M * 4, src, (size_t)c->Mp * 4, (size_t)c->M * 4,
-                       (size_t)c->d.T, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDefault,
-                       c->s_main));
+  if (c->T_active > 0)
+    CK(cudaMemcpy2DAsync(dst, (size_t)c->M * 4, src, (size_t)c->Mp * 4, (size_t)c->M * 4,
+                         (size_t)c->T_active,
+                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDefault, c->s_main));
   if (!on_device) {
     rc = sync_check(c);
     if (rc) return rc;
@@ -605,8 +977,7 @@ int nfhmm_get_surrogate(nfhmm_ctx* c, float* phi, int on_device) {
   if (!c->have_alpha) return fail(NFHMM_ESTATE, "phi-hat is defined after a sweep");
   int rc = enter(c);
   if (rc) return rc;
-  const size_t n = (size_t)c->d.S * c->d.T * c->d.N;
-  rc = copy_out(phi, c->phi, n * 4, on_device, c->s_main);
+  rc = copy_slices(c, phi, c->phi, c->d.N, true, 0, c->T_active, on_device);
   if (rc) return rc;
   if (!on_device) {
     rc = sync_check(c);
@@ -634,16 +1005,20 @@ int nfhmm_set_state(nfhmm_ctx* c, const float* counts, const float* dhat, int sw
   int rc = enter(c);
   if (rc) return rc;
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDefault;
-  CK(cudaMemcpy2DAsync(c->c, (size_t)c->Mp * 4, counts, (size_t)c->M * 4, (size_t)c->M * 4,
-                       (size_t)c->d.T, kind, c->s_main));
-  const size_t n = (size_t)c->d.S * c->d.T * c->d.N;
-  CK(cudaMemcpyAsync(c->dhat, dhat, n * 4, kind, c->s_main));
+  if (c->T_active > 0)
+    CK(cudaMemcpy2DAsync(c->c, (size_t)c->Mp * 4, counts, (size_t)c->M * 4, (size_t)c->M * 4,
+                         (size_t)c->T_active, kind, c->s_main));
+  rc = copy_slices(c, c->dhat, dhat, c->d.N, false, 0, c->T_active, on_device);
+  if (rc) return rc;
   if (!on_device) {
     rc = sync_check(c);
     if (rc) return rc;
   }
   c->sweeps_done = sweeps_done;
+  for (Job& j : c->jobs) j.sweeps = sweeps_done;
   c->have_alpha = false;
+  c->bpart_ok = false;
+  c->bound_ok = false;
   return leave(c);
 }
 
@@ -664,13 +1039,14 @@ int nfhmm_forward_backward(int S, int N, int T, const float* phi, const float* A
   if (a.L > 128) a.L = 128;
   if (a.L > T) a.L = T;
   a.C = (T + a.L - 1) / a.L;
+  a.nchains = 1;   // one chain over all T frames (null chain tables)
   a.phi = phi;
   a.A = A;
   a.pi = pi;
   a.dhat = dhat;
   a.logZ = logZ;
   void* scratch = nullptr;
-  const size_t bytes = fb_scratch_bytes(S, N, T, a.L) + 256;
+  const size_t bytes = fb_scratch_bytes(S, N, a.C) + 256;
   CK(cudaMallocAsync(&scratch, bytes, st));
   fb_carve_scratch(a, scratch);
   a.err = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(scratch) + bytes - 256);

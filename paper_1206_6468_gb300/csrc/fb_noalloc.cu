@@ -68,7 +68,8 @@ int nfhmm_forward_backward_noalloc(int S, int N, int T, const float* phi, const 
   if (a.L > 128) a.L = 128;
   if (a.L > T) a.L = T;
   a.C = (T + a.L - 1) / a.L;
-  const size_t need = fb_scratch_bytes(S, N, T, a.L) + 256;  // + error word
+  a.nchains = 1;   // one chain over all T frames (null chain tables)
+  const size_t need = fb_scratch_bytes(S, N, a.C) + 256;  // + error word
   if (need > (size_t)NFHMM_NOALLOC_SCRATCH_BYTES)
     return fail(NFHMM_EINVAL, "problem needs " + std::to_string(need) +
                                   " bytes of scratch; the fixed array holds " +

@@ -261,10 +261,15 @@ __global__ void k_bound_frames(BoundArgs a) {
   }
 }
 
+// One block per job: the sum of its frames' terms and its chains' log
+// normalisers.  A one-warp launch then sums the jobs into out[njobs].
 __global__ void k_bound_final(BoundArgs a) {
   __shared__ double red[32];
+  const int j = blockIdx.x;
+  const int t0 = a.job_t0 ? a.job_t0[j] : 0;
+  const int t1 = a.job_t0 ? a.job_t0[j + 1] : a.T;
   double s = 0.0;
-  for (int t = threadIdx.x; t < a.T; t += blockDim.x) s += a.frame_terms[t];
+  for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) s += a.frame_terms[t];
   s = warp_sum_d(s);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
   __syncthreads();
@@ -272,16 +277,24 @@ __global__ void k_bound_final(BoundArgs a) {
     double r = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
     r = warp_sum_d(r);
     if (threadIdx.x == 0) {
-      for (int i = 0; i < a.S; ++i) r += a.logZ[i];
-      a.out[0] = r;
+      for (int i = 0; i < a.S; ++i) r += a.logZ[(size_t)i * a.njobs + j];
+      a.out[j] = r;
     }
   }
 }
 
+__global__ void k_bound_total(BoundArgs a) {
+  double r = 0.0;
+  for (int j = threadIdx.x; j < a.njobs; j += 32) r += a.out[j];
+  r = warp_sum_d(r);
+  if (threadIdx.x == 0) a.out[a.njobs] = r;
+}
+
 void launch_bound(const BoundArgs& a, cudaStream_t st, int* launches) {
   k_bound_frames<<<(a.T + 7) / 8, 256, 0, st>>>(a);
-  k_bound_final<<<1, 1024, 0, st>>>(a);
-  if (launches) *launches += 2;
+  k_bound_final<<<a.njobs, 1024, 0, st>>>(a);
+  k_bound_total<<<1, 32, 0, st>>>(a);
+  if (launches) *launches += 3;
 }
 
 // -------------------------------------------------------------- separation
@@ -344,17 +357,22 @@ void launch_digamma(const float* x, float* psi, float* w, size_t n, cudaStream_t
 }
 
 // --------------------------------------------------------- prior marginals
-// dhat[s][0] = pi_s, dhat[s][t] = dhat[s][t-1] A_s (one block per source).
+// dhat[s][t0] = pi_s, dhat[s][t] = dhat[s][t-1] A_s over each job's frames
+// [t0, t1) (one block per (source, job)).  With a null job table there is one
+// job, frames [t_begin, t_end).  T is the frame stride of dhat.
 __global__ void k_prior_marginals(const float* A, const float* pi, int S, int N, int T,
+                                  const int* job_t0, int njobs, int t_begin, int t_end,
                                   float* dhat) {
   extern __shared__ float sm[];
   float* As = sm;          // N*N
   float* d = sm + N * N;   // N
-  const int s = blockIdx.x;
+  const int s = blockIdx.x / njobs, jb = blockIdx.x - s * njobs;
+  const int t0 = job_t0 ? job_t0[jb] : t_begin;
+  const int t1 = job_t0 ? job_t0[jb + 1] : t_end;
   for (int i = threadIdx.x; i < N * N; i += blockDim.x) As[i] = A[(size_t)s * N * N + i];
   for (int i = threadIdx.x; i < N; i += blockDim.x) d[i] = pi[(size_t)s * N + i];
   __syncthreads();
-  for (int t = 0; t < T; ++t) {
+  for (int t = t0; t < t1; ++t) {
     float nj = 0.f;
     const int j = threadIdx.x;
     if (j < N) {
@@ -366,10 +384,13 @@ __global__ void k_prior_marginals(const float* A, const float* pi, int S, int N,
     __syncthreads();
   }
 }
-void launch_prior_marginals(const float* A, const float* pi, int S, int N, int T, float* dhat,
+void launch_prior_marginals(const float* A, const float* pi, int S, int N, int T,
+                            const int* job_t0, int njobs, int t_begin, int t_end, float* dhat,
                             cudaStream_t st) {
+  if (!job_t0) njobs = 1;
   const int threads = ((N + 31) / 32) * 32;
-  k_prior_marginals<<<S, threads, (N * N + N) * sizeof(float), st>>>(A, pi, S, N, T, dhat);
+  k_prior_marginals<<<S * njobs, threads, (N * N + N) * sizeof(float), st>>>(
+      A, pi, S, N, T, job_t0, njobs, t_begin, t_end, dhat);
 }
 
 }  // namespace nfhmm

@@ -81,6 +81,23 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
 }
+struct ChunkInfo {
+  int t0, len, chain;
+  bool first;
+};
+// frames of global chunk c (null chain tables: one chain over all frames)
+__device__ __forceinline__ ChunkInfo chunk_info(const FBArgs& a, int c) {
+  ChunkInfo ci;
+  const int j = a.chunk_chain ? a.chunk_chain[c] : 0;
+  const int lc = c - (a.chain_c0 ? a.chain_c0[j] : 0);
+  const int ct0 = a.chain_t0 ? a.chain_t0[j] : 0;
+  const int clen = a.chain_len ? a.chain_len[j] : a.T;
+  ci.chain = j;
+  ci.first = lc == 0;
+  ci.t0 = ct0 + lc * a.L;
+  ci.len = min(a.L, clen - lc * a.L);
+  return ci;
+}
 }  // namespace
 
 int fb_max_states() { return FB_MAX_N; }
@@ -165,7 +182,8 @@ __global__ void __launch_bounds__(256, 1) k_fb_products(FBArgs a) {
   for (int q = 0; q < Cfg::RCH; ++q) {
     const int c = cbase + q;
     if (c >= a.C) break;
-    const int t0 = c * L, len = min(a.T, t0 + L) - t0;
+    const ChunkInfo ci = chunk_info(a, c);
+    const int t0 = ci.t0, len = ci.len;
     const float* src = a.phi + ((size_t)s * a.T + t0) * N;
     float* eq = e + q * L * NP;
     for (int i = tid; i < len * N; i += blockDim.x) {
@@ -177,7 +195,7 @@ __global__ void __launch_bounds__(256, 1) k_fb_products(FBArgs a) {
   for (int q = 0; q < Cfg::RCH; ++q) {
     const int c = cbase + q;
     if (c >= a.C) break;
-    const int t0 = c * L, len = min(a.T, t0 + L) - t0;
+    const int len = chunk_info(a, c).len;
     float* eq = e + q * L * NP;
     double ms = 0.0;
     for (int f = warp; f < len; f += 8) {
@@ -211,7 +229,8 @@ __global__ void __launch_bounds__(256, 1) k_fb_products(FBArgs a) {
   const int q = r / NP, i = r - (r / NP) * NP;
   const int c = cbase + q;
   const bool live = q < Cfg::RCH && c < a.C && i < N;
-  const int len = live ? min(a.T, c * L + L) - c * L : 0;
+  const ChunkInfo ci = (q < Cfg::RCH && c < a.C) ? chunk_info(a, c) : ChunkInfo{0, 0, 0, false};
+  const int len = live ? ci.len : 0;
   const float* eq = e + (q < Cfg::RCH ? q : 0) * L * NP;
   float cur[HC];
   ScaleAcc sc;
@@ -220,7 +239,7 @@ __global__ void __launch_bounds__(256, 1) k_fb_products(FBArgs a) {
   for (int u = 0; u < HC; ++u) {
     const int j = j0 + u;
     float v = 0.f;
-    if (live && j < N) v = (c == 0) ? (j == i ? eq[j] : 0.f) : Ag[i * N + j] * eq[j];
+    if (live && j < N) v = ci.first ? (j == i ? eq[j] : 0.f) : Ag[i * N + j] * eq[j];
     cur[u] = v;
   }
   // rescale the row by its maximum (both halves agree through shared memory)
@@ -365,15 +384,17 @@ __global__ void __launch_bounds__(32) k_fb_scan(FBArgs a) {
   constexpr int NN = NP * LD;
   constexpr int CPL = (NP * NP / 4 + 31) / 32;   // 16-byte copies per lane per matrix
   const int N = a.N, C = a.C;
-  const int s = blockIdx.x;
+  const int s = blockIdx.x / a.nchains, chain = blockIdx.x - s * a.nchains;
   const bool fwd = blockIdx.y == 0;
   const int lane = threadIdx.x;
   float* ring = sm;                      // RING x NP x LD
   float* v = ring + RING * NN;           // 64
   const size_t base = (size_t)s * C;
+  const int c0 = a.chain_c0 ? a.chain_c0[chain] : 0;
+  const int c1 = a.chain_c0 ? a.chain_c0[chain + 1] : C;   // the chain's chunks [c0, c1)
   const float* src = fwd ? a.PT : a.P;
-  const int nsteps = fwd ? C : C - 1;
-  auto chunk_of = [&](int q) { return fwd ? q : C - 1 - q; };
+  const int nsteps = fwd ? c1 - c0 : c1 - c0 - 1;
+  auto chunk_of = [&](int q) { return fwd ? c0 + q : c1 - 1 - q; };
   // this lane's 16-byte pieces of a matrix: source and padded destination offsets
   int soff[CPL], doff[CPL];
 #pragma unroll
@@ -404,8 +425,8 @@ __global__ void __launch_bounds__(32) k_fb_scan(FBArgs a) {
   } else {
     r0 = h0 ? 1.f : 0.f;
     r1 = h1 ? 1.f : 0.f;
-    if (h0) a.bwd[(base + C - 1) * N + lane] = 1.f;
-    if (h1) a.bwd[(base + C - 1) * N + lane + 32] = 1.f;
+    if (h0) a.bwd[(base + c1 - 1) * N + lane] = 1.f;
+    if (h1) a.bwd[(base + c1 - 1) * N + lane + 32] = 1.f;
   }
   // u_prev: the previous step's output, not yet normalised; its sum (the
   // previous chunk's normaliser) is reduced while this step's products run.
@@ -471,9 +492,9 @@ __global__ void __launch_bounds__(32) k_fb_scan(FBArgs a) {
     __syncwarp();
     __threadfence_block();
     double lg = 0.0;
-    for (int c = lane; c < C; c += 32) lg += a.Plog[base + c] + log((double)a.lam[base + c]);
+    for (int c = c0 + lane; c < c1; c += 32) lg += a.Plog[base + c] + log((double)a.lam[base + c]);
     lg = warp_sum_d(lg);
-    if (lane == 0) a.logZ[s] = lg;
+    if (lane == 0) a.logZ[(size_t)s * a.nchains + chain] = lg;
   }
 }
 
@@ -498,8 +519,9 @@ __global__ void __launch_bounds__(R_CHUNKS_MAX * 64) k_fb_replay(FBArgs a) {
   float* bv = av + L * NP;               // L x NP backward vectors
   float* x = bv + L * NP + (is_fwd ? 0 : 64);  // 64 per warp
   const bool live = c < a.C;
-  const int t0 = c * L;
-  const int len = live ? min(a.T, t0 + L) - t0 : 0;
+  const ChunkInfo ci = live ? chunk_info(a, c) : ChunkInfo{0, 0, 0, false};
+  const int t0 = ci.t0;
+  const int len = live ? ci.len : 0;
   const float* Ag = a.A + (size_t)s * N * N;
   const bool h0 = lane < N, h1 = lane + 32 < N;
   // forward warp: A[k][j] for j = lane, lane + 32; backward warp: A[j][k]
@@ -541,7 +563,7 @@ __global__ void __launch_bounds__(R_CHUNKS_MAX * 64) k_fb_replay(FBArgs a) {
     float* vec = is_fwd ? av : bv;
     float r0, r1;
     if (is_fwd) {
-      if (c == 0) {
+      if (ci.first) {
         r0 = h0 ? a.pi[(size_t)s * N + lane] * e[lane] : 0.f;
         r1 = h1 ? a.pi[(size_t)s * N + lane + 32] * e[lane + 32] : 0.f;
       } else {
@@ -672,14 +694,19 @@ static cudaError_t launch_np(const FBArgs& a, cudaStream_t st) {
   const int rc = replay_chunks(NP, a.L);
   k_fb_products<NP><<<dim3((a.C + Cfg::RCH - 1) / Cfg::RCH, a.S), 256, smem_products<NP>(a.L),
                       st>>>(a);
-  k_fb_scan<NP><<<dim3(a.S, 2), 32, smem_scan<NP>(), st>>>(a);
+  k_fb_scan<NP><<<dim3(a.S * a.nchains, 2), 32, smem_scan<NP>(), st>>>(a);
   k_fb_replay<NP><<<dim3((a.C + rc - 1) / rc, a.S), rc * 64, rc * smem_replay_chunk(NP, a.L),
                     st>>>(a);
   return cudaGetLastError();
 }
 
-size_t fb_scratch_bytes(int S, int N, int T, int L) {
-  const int C = (T + L - 1) / L;
+int fb_chunk_count(const int* chain_len, int nchains, int L) {
+  int C = 0;
+  for (int j = 0; j < nchains; ++j) C += (chain_len[j] + L - 1) / L;
+  return C;
+}
+
+size_t fb_scratch_bytes(int S, int N, int C) {
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
   size_t b = 0;
   b += al((size_t)S * C * mat_floats(N) * sizeof(float));  // P

@@ -443,9 +443,9 @@ int tc_refresh_beta(TcPlan& p, cudaStream_t st) {
   return 2;
 }
 
-int tc_gemm1(TcPlan& p, double* bpart, cudaStream_t st) {
+int tc_gemm1(TcPlan& p, int rows, double* bpart, cudaStream_t st) {
   TcArgs a{};
-  a.rows = p.T;
+  a.rows = rows;
   a.cols = p.Fp;
   a.kdim = p.Mp;
   a.nbpart = p.nbpart;
@@ -470,9 +470,9 @@ int tc_gemm1(TcPlan& p, double* bpart, cudaStream_t st) {
   return 1;
 }
 
-int tc_gemm2(TcPlan& p, cudaStream_t st) {
+int tc_gemm2(TcPlan& p, int rows, cudaStream_t st) {
   TcArgs a{};
-  a.rows = p.T;
+  a.rows = rows;
   a.cols = p.Mp;
   a.kdim = p.Fp;
   a.w = p.w32;

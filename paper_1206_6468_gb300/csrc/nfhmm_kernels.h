@@ -75,24 +75,34 @@ struct GemmArgs {
 void launch_gemm_simt(const GemmArgs& g, int epi, cudaStream_t st);
 int gemm_simt_col_tiles(int cols);
 
-// Forward-backward, parallel in time over chunks of L frames.
+// Forward-backward, parallel in time over chunks of L frames.  The frames
+// hold one or more independent chains (jobs) back to back; no chunk crosses
+// a chain boundary and each chain's first chunk starts from pi.  With null
+// chain tables there is one chain covering all T frames.
 struct FBArgs {
-  int S, N, T, L, C;
+  int S, N, T, L, C;   // C = total chunks per source over all chains
+  int nchains;
+  const int* chain_c0;     // nchains + 1: first chunk of each chain (chain_c0[nchains] = C)
+  const int* chain_t0;     // nchains: first frame of each chain
+  const int* chain_len;    // nchains: frames of each chain
+  const int* chunk_chain;  // C: chain of each chunk
   const float* phi;  // S x T x N
   const float* A;    // S x N x N row-stochastic
   const float* pi;   // S x N
   float* dhat;       // S x T x N
-  double* logZ;      // S
+  double* logZ;      // S x nchains
   // scratch
-  float* P;          // S x C x nn4(N)   chunk matrices, row-major
-  float* PT;         // S x C x nn4(N)   the same, transposed
+  float* P;          // S x C x NP x NP   chunk matrices, row-major (NP = 8*ceil(N/8))
+  float* PT;         // S x C x NP x NP   the same, transposed
   double* Plog;      // S x C            log of each chunk matrix's scale
   float* fwd;        // S x C x N        forward boundary vectors
   float* lam;        // S x C            forward scan normalisers
   float* bwd;        // S x C x N        backward boundary vectors
   unsigned* err;
 };
-size_t fb_scratch_bytes(int S, int N, int T, int L);
+// chunks of L frames needed by chains of the given lengths
+int fb_chunk_count(const int* chain_len, int nchains, int L);
+size_t fb_scratch_bytes(int S, int N, int C);
 void fb_carve_scratch(FBArgs& a, void* base);
 int fb_default_chunk(int N, int T);
 int fb_max_states();
@@ -101,14 +111,16 @@ cudaError_t launch_fb(const FBArgs& a, cudaStream_t st, int* launches);
 // Bound.
 struct BoundArgs {
   int T, M, Mp, S, K;
+  int njobs;
+  const int* job_t0;       // njobs + 1 frame offsets (device)
   float gamma;
   double konst;            // lnGamma(M + gamma S K) - S K lnGamma(1 + gamma)
   const float* alpha;      // T x Mp
   const double* v;         // T
   const double* bpart; int nbpart;
-  const double* logZ;      // S
+  const double* logZ;      // S x njobs
   double* frame_terms;     // T
-  double* out;             // 1
+  double* out;             // njobs + 1: per-job bounds, then their sum
 };
 void launch_bound(const BoundArgs& a, cudaStream_t st, int* launches);
 
@@ -120,8 +132,11 @@ void launch_sep_mask(const float* V, int Fp, float* out, int S, int T, int F, cu
 // Digamma test entry.
 void launch_digamma(const float* x, float* psi, float* w, size_t n, cudaStream_t st);
 
-// Prior marginals dhat[s][t] = pi A^t (sequential in t, one block per source).
-void launch_prior_marginals(const float* A, const float* pi, int S, int N, int T, float* dhat,
+// Prior marginals dhat[s][t] = pi A^(t - t0(job)) restarted at every job
+// (sequential in t, one block per (source, job)).  job_t0: njobs + 1 device
+// offsets, or null for the single job [t_begin, t_end).  T: frame stride.
+void launch_prior_marginals(const float* A, const float* pi, int S, int N, int T,
+                            const int* job_t0, int njobs, int t_begin, int t_end, float* dhat,
                             cudaStream_t st);
 
 }  // namespace nfhmm

@@ -23,12 +23,29 @@ if not os.path.exists(LIB_PATH):
     raise ImportError(f"libnfhmm.so is not built ({LIB_PATH}); run __graft_entry__.build()")
 _lib = ctypes.CDLL(LIB_PATH)
 
-OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENUMERIC, ESTATE = 0, -1, -2, -3, -4, -5, -6
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENUMERIC, ESTATE, EFULL = 0, -1, -2, -3, -4, -5, -6, -7
 FP32, BF16, FP32_SIMT = 0, 1, 2
 INIT_UNIFORM, INIT_PRIOR = 0, 1
 SEP_MEAN, SEP_EXPECTATION = 0, 1
 STAGES = {"weights": 0, "gemm1": 1, "gemm2": 2, "fb": 3, "bound": 4, "init": 5}
 QUERIES = {"tensor_cores": 0, "fb_chunk": 1, "sweeps_done": 2, "device_bytes": 3}
+OPTIONS = {"fb_chunk": 0}
+PRECISIONS = {"fp32": FP32, "bf16": BF16, "fp32_simt": FP32_SIMT}
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int), ("T", ctypes.c_int), ("V", ctypes.c_void_p),
+                ("arrival_s", ctypes.c_double), ("dhat_out", ctypes.c_void_p)]
+
+
+class ServeOpts(ctypes.Structure):
+    _fields_ = [("rel_tol", ctypes.c_double), ("min_sweeps", ctypes.c_int),
+                ("max_sweeps", ctypes.c_int), ("realtime", ctypes.c_int)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("admit_s", ctypes.c_double), ("done_s", ctypes.c_double),
+                ("sweeps", ctypes.c_int), ("bound", ctypes.c_double), ("status", ctypes.c_int)]
 
 
 class Dims(ctypes.Structure):
@@ -61,6 +78,18 @@ _sigs = {
                                 ctypes.POINTER(ctypes.c_longlong), _i]),
     "nfhmm_query": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_longlong)]),
     "nfhmm_kernel_launches": (ctypes.c_longlong, [_vp]),
+    "nfhmm_vi_init_batch": (_i, [ctypes.POINTER(_vp), ctypes.POINTER(Dims), _i, _vp, _vp, _vp, _vp,
+                                 _vp, _i, _vp, _vp]),
+    "nfhmm_batch_create": (_i, [ctypes.POINTER(_vp), ctypes.POINTER(Dims), _i, _vp, _vp, _vp, _i,
+                                _vp]),
+    "nfhmm_batch_add": (_i, [_vp, _i, _vp, _i, ctypes.POINTER(ctypes.c_longlong)]),
+    "nfhmm_batch_remove": (_i, [_vp, ctypes.c_longlong]),
+    "nfhmm_batch_info": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), _vp, _vp, _vp, _vp]),
+    "nfhmm_job_bounds": (_i, [_vp, _vp]),
+    "nfhmm_job_posteriors": (_i, [_vp, ctypes.c_longlong, _vp, _i]),
+    "nfhmm_set_option": (_i, [_vp, _i, ctypes.c_longlong]),
+    "nfhmm_serve": (_i, [ctypes.POINTER(_vp), _i, ctypes.POINTER(Request), _i,
+                         ctypes.POINTER(ServeOpts), ctypes.POINTER(Result)]),
 }
 for _name, (_res, _args) in _sigs.items():
     _f = getattr(_lib, _name)
@@ -123,34 +152,84 @@ def _f32(x):
     return np.ascontiguousarray(x, dtype=np.float32)
 
 
+def _model_ptrs(W, A, pi):
+    ptrs = [_ptr(x) for x in (W, A, pi)]
+    if len({d for _, d in ptrs}) != 1:
+        raise ValueError("W, A, pi must all be on the host or all on the device")
+    return [p for p, _ in ptrs], ptrs[0][1]
+
+
 class VIContext:
-    """One spectrogram's variational inference state on the GPU.
+    """Variational inference state on the GPU: one spectrogram, or a batch of
+    jobs sharing one model (see Batch).
 
     V (T, F), W (M, F), A (S, N, N), pi (S, N): numpy arrays (host) or torch
     CUDA tensors (device), float32.  precision: "fp32" (split-TF32 tensor
     cores), "bf16" (BF16 tensor cores) or "fp32_simt" (FP32 CUDA cores)."""
 
     def __init__(self, V, W, A, pi, S: int, N: int, K: int, gamma: float = 1.0,
-                 precision: str = "fp32", init_mode: int = INIT_UNIFORM, stream=None):
+                 precision: str = "fp32", init_mode: int = INIT_UNIFORM, stream=None,
+                 job_frames=None):
         V, W, A, pi = _f32(V), _f32(W), _f32(A), _f32(pi)
         T, F = V.shape
-        self.S, self.N, self.K, self.F, self.T = S, N, K, F, T
+        self.S, self.N, self.K, self.F = S, N, K, F
         self.M = S * N * K
         self.gamma = gamma
-        d = Dims(S, N, K, F, T, gamma,
-                 {"fp32": FP32, "bf16": BF16, "fp32_simt": FP32_SIMT}[precision], init_mode)
+        d = Dims(S, N, K, F, T, gamma, PRECISIONS[precision], init_mode)
         pv, dv = _ptr(V)
-        pw, dw = _ptr(W)
-        pa, da = _ptr(A)
-        pp, dp = _ptr(pi)
-        if len({dv, dw, da, dp}) != 1:
+        (pw, pa, pp), dm = _model_ptrs(W, A, pi)
+        if dv != dm:
             raise ValueError("V, W, A, pi must all be on the host or all on the device")
-        self._keep = (V, W, A, pi)
         h = ctypes.c_void_p()
-        _check(_lib.nfhmm_vi_init(ctypes.byref(h), ctypes.byref(d), pv, pw, pa, pp, dv,
-                                  _stream(stream)), "nfhmm_vi_init")
+        if job_frames is None:
+            _check(_lib.nfhmm_vi_init(ctypes.byref(h), ctypes.byref(d), pv, pw, pa, pp, dv,
+                                      _stream(stream)), "nfhmm_vi_init")
+            self.job_ids = [0]
+        else:
+            fr = np.ascontiguousarray(job_frames, dtype=np.int32)
+            ids = np.zeros(len(fr), dtype=np.int64)
+            _check(_lib.nfhmm_vi_init_batch(ctypes.byref(h), ctypes.byref(d), len(fr),
+                                            _vp(fr.ctypes.data), pv, pw, pa, pp, dv,
+                                            _stream(stream), _vp(ids.ctypes.data)),
+                   "nfhmm_vi_init_batch")
+            self.job_ids = ids.tolist()
         self._h = h
-        self._keep = None
+
+    @property
+    def T(self) -> int:
+        """Frames held (all jobs)."""
+        n, t = ctypes.c_int(), ctypes.c_int()
+        _check(_lib.nfhmm_batch_info(self._h, ctypes.byref(n), ctypes.byref(t), None, None, None,
+                                     None), "nfhmm_batch_info")
+        return t.value
+
+    def jobs(self):
+        """List of (id, first frame, frames, sweeps) in frame order."""
+        n, t = ctypes.c_int(), ctypes.c_int()
+        _check(_lib.nfhmm_batch_info(self._h, ctypes.byref(n), ctypes.byref(t), None, None, None,
+                                     None), "nfhmm_batch_info")
+        ids = np.zeros(max(n.value, 1), dtype=np.int64)
+        t0, T, sw = (np.zeros(max(n.value, 1), dtype=np.int32) for _ in range(3))
+        _check(_lib.nfhmm_batch_info(self._h, ctypes.byref(n), ctypes.byref(t),
+                                     _vp(ids.ctypes.data), _vp(t0.ctypes.data),
+                                     _vp(T.ctypes.data), _vp(sw.ctypes.data)), "nfhmm_batch_info")
+        return [(int(ids[j]), int(t0[j]), int(T[j]), int(sw[j])) for j in range(n.value)]
+
+    def job_bounds(self) -> np.ndarray:
+        n = len(self.jobs())
+        out = np.zeros(max(n, 1), dtype=np.float64)
+        _check(_lib.nfhmm_job_bounds(self._h, _vp(out.ctypes.data)), "nfhmm_job_bounds")
+        return out[:n]
+
+    def job_posteriors(self, job_id: int, out=None):
+        T = {j[0]: j[2] for j in self.jobs()}[job_id]
+        out = self._out((self.S, T, self.N), out)
+        p, dev = _ptr(out)
+        _check(_lib.nfhmm_job_posteriors(self._h, job_id, p, dev), "nfhmm_job_posteriors")
+        return out
+
+    def set_option(self, key: str, value: int):
+        _check(_lib.nfhmm_set_option(self._h, OPTIONS[key], int(value)), "nfhmm_set_option")
 
     def reinit(self, V, W, A, pi):
         """Load new inputs of the same sizes and reset to the initial state."""
@@ -259,6 +338,67 @@ class VIContext:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Batch(VIContext):
+    """An empty batch with room for `capacity` frames and `max_jobs` jobs that
+    share one model; jobs are added and removed between sweeps."""
+
+    def __init__(self, W, A, pi, S: int, N: int, K: int, capacity: int, max_jobs: int,
+                 gamma: float = 1.0, precision: str = "fp32", init_mode: int = INIT_UNIFORM,
+                 stream=None):
+        W, A, pi = _f32(W), _f32(A), _f32(pi)
+        F = W.shape[1]
+        self.S, self.N, self.K, self.F = S, N, K, F
+        self.M = S * N * K
+        self.gamma = gamma
+        self.capacity, self.max_jobs = capacity, max_jobs
+        d = Dims(S, N, K, F, capacity, gamma, PRECISIONS[precision], init_mode)
+        (pw, pa, pp), dm = _model_ptrs(W, A, pi)
+        h = ctypes.c_void_p()
+        _check(_lib.nfhmm_batch_create(ctypes.byref(h), ctypes.byref(d), max_jobs, pw, pa, pp, dm,
+                                       _stream(stream)), "nfhmm_batch_create")
+        self._h = h
+        self.job_ids = []
+
+    def add(self, V) -> int:
+        """Append a job (V: (T, F)); returns its id.  Raises NfhmmError with
+        code EFULL when the batch has no room."""
+        V = _f32(V)
+        p, dev = _ptr(V)
+        jid = ctypes.c_longlong()
+        _check(_lib.nfhmm_batch_add(self._h, V.shape[0], p, dev, ctypes.byref(jid)),
+               "nfhmm_batch_add")
+        return jid.value
+
+    def remove(self, job_id: int):
+        _check(_lib.nfhmm_batch_remove(self._h, job_id), "nfhmm_batch_remove")
+
+
+def serve(batches, requests, rel_tol: float = 1e-5, min_sweeps: int = 2,
+          max_sweeps: int = 100, realtime: bool = True, want_posteriors: bool = True):
+    """Run nfhmm_serve.  batches: empty Batch objects (one per model);
+    requests: list of (model index, V (T, F) numpy float32, arrival seconds).
+    Returns (results as a list of dicts, posteriors per request or None)."""
+    n = len(requests)
+    reqs = (Request * max(n, 1))()
+    keep, outs = [], []
+    for r, (m, V, t) in enumerate(requests):
+        V = np.ascontiguousarray(V, dtype=np.float32)
+        b = batches[m]
+        out = np.empty((b.S, V.shape[0], b.N), dtype=np.float32) if want_posteriors else None
+        keep.append(V)
+        outs.append(out)
+        reqs[r] = Request(m, V.shape[0], V.ctypes.data, float(t),
+                          out.ctypes.data if out is not None else None)
+    handles = (_vp * len(batches))(*[b._h.value for b in batches])
+    opts = ServeOpts(rel_tol, min_sweeps, max_sweeps, int(realtime))
+    res = (Result * max(n, 1))()
+    _check(_lib.nfhmm_serve(handles, len(batches), reqs, n, ctypes.byref(opts), res),
+           "nfhmm_serve")
+    results = [dict(admit_s=res[r].admit_s, done_s=res[r].done_s, sweeps=res[r].sweeps,
+                    bound=res[r].bound, status=res[r].status) for r in range(n)]
+    return results, outs
 
 
 def forward_backward(phi, A, pi, chunk_len: int = 0, stream=None):

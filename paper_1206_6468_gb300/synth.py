@@ -68,16 +68,9 @@ def transition_matrix(N: int, self_prob: float) -> np.ndarray:
     return A
 
 
-def make_problem(S: int, N: int, K: int, F: int, T: int, *, self_prob: float = 0.9,
-                 energy_sigma: float = 0.0, quanta_scale: float = 1.0,
-                 gamma: float = 1.0, seed: int = 0) -> Problem:
-    rng = np.random.Generator(np.random.PCG64(seed))
+def _sample_frames(rng, W, A, pi, S, N, K, T, energy_sigma, quanta_scale):
+    """States, weights, energies and quanta of T frames under model (W, A, pi)."""
     M = S * N * K
-    W = rng.dirichlet(0.5 * np.ones(F), size=M)
-    W = np.maximum(W, 1e-12)
-    W /= W.sum(axis=1, keepdims=True)
-    A = np.stack([transition_matrix(N, self_prob) for _ in range(S)])
-    pi = np.full((S, N), 1.0 / N)
     D = np.zeros((S, T), dtype=np.int64)
     for s in range(S):
         if T == 0:
@@ -96,8 +89,100 @@ def make_problem(S: int, N: int, K: int, F: int, T: int, *, self_prob: float = 0
         e = np.ones(T)
     Vbar = e[:, None] * (h @ W)
     V = rng.poisson(1000.0 * quanta_scale * Vbar) / 1000.0
+    return V, D
+
+
+def _sample_frames_vec(rng, W, A, pi, S, N, K, T, energy_sigma, quanta_scale):
+    """The process of _sample_frames with array draws (same distribution,
+    different stream): for long spectrograms."""
+    M = S * N * K
+    D = np.zeros((S, T), dtype=np.int64)
+    u = rng.random((S, T))
+    for s in range(S):
+        if T == 0:
+            continue
+        cum = np.cumsum(A[s], axis=1)
+        cum[:, -1] = 1.0
+        D[s, 0] = min(np.searchsorted(np.cumsum(pi[s]), u[s, 0], side="right"), N - 1)
+        for t in range(1, T):
+            D[s, t] = min(np.searchsorted(cum[D[s, t - 1]], u[s, t], side="right"), N - 1)
+    h = np.zeros((T, M))
+    rows = np.arange(T)
+    for s in range(S):
+        g = rng.gamma(1.0, 1.0, size=(T, K))
+        k0 = (s * N + D[s]) * K
+        for j in range(K):
+            h[rows, k0 + j] = g[:, j]
+    e = np.exp(energy_sigma * rng.standard_normal(T)) if energy_sigma > 0 else np.ones(T)
+    Vbar = e[:, None] * (h @ W)
+    V = rng.poisson(1000.0 * quanta_scale * Vbar) / 1000.0
+    return V, D
+
+
+def _sample_model(rng, S, N, K, F, self_prob):
+    M = S * N * K
+    W = rng.dirichlet(0.5 * np.ones(F), size=M)
+    W = np.maximum(W, 1e-12)
+    W /= W.sum(axis=1, keepdims=True)
+    A = np.stack([transition_matrix(N, self_prob) for _ in range(S)])
+    pi = np.full((S, N), 1.0 / N)
+    return W, A, pi
+
+
+def make_problem(S: int, N: int, K: int, F: int, T: int, *, self_prob: float = 0.9,
+                 energy_sigma: float = 0.0, quanta_scale: float = 1.0,
+                 gamma: float = 1.0, seed: int = 0) -> Problem:
+    rng = np.random.Generator(np.random.PCG64(seed))
+    W, A, pi = _sample_model(rng, S, N, K, F, self_prob)
+    V, D = _sample_frames(rng, W, A, pi, S, N, K, T, energy_sigma, quanta_scale)
     return Problem(S=S, N=N, K=K, F=F, T=T, gamma=gamma, V=V, W=W, A=A, pi=pi,
                    D=D, seed=seed)
+
+
+@dataclasses.dataclass
+class Jobs:
+    """Several spectrograms (jobs) drawn from one model."""
+    S: int
+    N: int
+    K: int
+    F: int
+    gamma: float
+    W: np.ndarray
+    A: np.ndarray
+    pi: np.ndarray
+    V: list              # per job (T_j, F) float64
+    D: list              # per job (S, T_j) int
+    seed: int
+
+    @property
+    def lengths(self) -> np.ndarray:
+        return np.array([v.shape[0] for v in self.V], dtype=np.int64)
+
+    def problem(self, j: int) -> Problem:
+        """Job j as a problem of its own."""
+        return Problem(S=self.S, N=self.N, K=self.K, F=self.F, T=self.V[j].shape[0],
+                       gamma=self.gamma, V=self.V[j], W=self.W, A=self.A, pi=self.pi,
+                       D=self.D[j], seed=self.seed)
+
+    def stacked_V(self) -> np.ndarray:
+        """All jobs' frames back to back, float32."""
+        return np.ascontiguousarray(np.concatenate(self.V, axis=0), dtype=np.float32)
+
+
+def make_jobs(S: int, N: int, K: int, F: int, lengths, *, self_prob: float = 0.9,
+              energy_sigma: float = 0.0, quanta_scale: float = 1.0, gamma: float = 1.0,
+              seed: int = 0) -> Jobs:
+    """One model from `seed` and one spectrogram per entry of `lengths`, job j
+    drawn from its own stream (seed, j)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    W, A, pi = _sample_model(rng, S, N, K, F, self_prob)
+    Vs, Ds = [], []
+    for j, T in enumerate(lengths):
+        r = np.random.Generator(np.random.PCG64([seed, j]))
+        V, D = _sample_frames_vec(r, W, A, pi, S, N, K, int(T), energy_sigma, quanta_scale)
+        Vs.append(V)
+        Ds.append(D)
+    return Jobs(S=S, N=N, K=K, F=F, gamma=gamma, W=W, A=A, pi=pi, V=Vs, D=Ds, seed=seed)
 
 
 # The workloads, by what they are.

@@ -1,0 +1,188 @@
+"""Batches of jobs sharing one model, through the C ABI.
+
+The posterior factorises over independent spectrograms, so a batch must
+give every job exactly the results it gets alone: the kernels treat frames
+independently and chunk each job's chain from its own first frame, so the
+comparison with a one-job context (same forward-backward chunk length) is
+bit for bit.  Against the FP64 oracle the batch is held to the tolerances
+of the single-job parity tests.
+"""
+import numpy as np
+import pytest
+
+from oracle import vi
+from paper_1206_6468_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+D_TOL = 1e-5
+BOUND_RTOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def nf():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1206_6468_gb300 import build
+    build.build()
+    from paper_1206_6468_gb300 import nfhmm
+    return nfhmm
+
+
+def _jobs(lengths, seed=0, S=2, N=4, K=5, F=129, sigma=0.0):
+    return synth.make_jobs(S, N, K, F, lengths, self_prob=0.9, energy_sigma=sigma, seed=seed)
+
+
+def _f32(x):
+    return np.ascontiguousarray(x, dtype=np.float32)
+
+
+def _alone(nf, jobs, j, chunk, precision="fp32", init_mode=0):
+    ctx = nf.VIContext(_f32(jobs.V[j]), _f32(jobs.W), _f32(jobs.A), _f32(jobs.pi), jobs.S,
+                       jobs.N, jobs.K, gamma=jobs.gamma, precision=precision,
+                       init_mode=init_mode)
+    ctx.set_option("fb_chunk", chunk)
+    return ctx
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp32_simt"])
+@pytest.mark.parametrize("init_mode", [0, 1])
+def test_batch_equals_each_job_alone(nf, precision, init_mode):
+    lengths = [1, 5, 130, 777, 64, 300]
+    jobs = _jobs(lengths, seed=11)
+    with nf.VIContext(jobs.stacked_V(), _f32(jobs.W), _f32(jobs.A), _f32(jobs.pi), jobs.S,
+                      jobs.N, jobs.K, precision=precision, init_mode=init_mode,
+                      job_frames=lengths) as b:
+        chunk = b.query("fb_chunk")
+        total = b.sweep(4, bound=True)
+        bounds = b.job_bounds()
+        post = [b.job_posteriors(i) for i in b.job_ids]
+        assert [j[2] for j in b.jobs()] == lengths
+        assert all(j[3] == 4 for j in b.jobs())
+    assert abs(total - bounds.sum()) <= 1e-12 * abs(total)
+    for j in range(len(lengths)):
+        with _alone(nf, jobs, j, chunk, precision, init_mode) as a:
+            L = a.sweep(4, bound=True)
+            d = a.posteriors()
+        assert np.array_equal(post[j], d), f"job {j}"
+        assert L == bounds[j], f"job {j}: {L} vs {bounds[j]}"
+
+
+def test_batch_against_oracle(nf):
+    """A three-job batch against the oracle run job by job: the bound of
+    every job after each of five sweeps (relative 1e-6), d-hat after the
+    first sweep (1e-5, both sides starting from the same initial state) and
+    after the fifth (1e-4: end to end, FP32 rounding at near-tie frames
+    grows by a few times per sweep, as in the single-job trajectory tests),
+    and the batch bound against the sum of the oracle's bounds."""
+    lengths = [200, 37, 129]
+    jobs = _jobs(lengths, seed=5)
+    refs, first = [], []
+    for j in range(len(lengths)):
+        p = jobs.problem(j)
+        V, W, A, pi = (x.astype(np.float32).astype(np.float64) for x in (p.V, p.W, p.A, p.pi))
+        refs.append(vi.run(V, W, A, pi, p.S, p.N, p.K, p.gamma, 5))
+        first.append(vi.run(V, W, A, pi, p.S, p.N, p.K, p.gamma, 1)["dhat"])
+    with nf.VIContext(jobs.stacked_V(), _f32(jobs.W), _f32(jobs.A), _f32(jobs.pi), jobs.S,
+                      jobs.N, jobs.K, job_frames=lengths) as b:
+        Ls = []
+        for i in range(5):
+            b.sweep(1)
+            Ls.append(b.job_bounds())
+            if i == 0:
+                post1 = [b.job_posteriors(k) for k in b.job_ids]
+        post = [b.job_posteriors(k) for k in b.job_ids]
+        L_total = b.bound()
+    for j, ref in enumerate(refs):
+        got = np.array([L[j] for L in Ls])
+        assert np.all(np.abs(got - ref["bounds"]) <= BOUND_RTOL * np.abs(ref["bounds"])), j
+        assert np.max(np.abs(post1[j] - first[j])) <= D_TOL, j
+        assert np.max(np.abs(post[j] - ref["dhat"])) <= 10 * D_TOL, j
+    want = sum(ref["bounds"][-1] for ref in refs)
+    assert abs(L_total - want) <= BOUND_RTOL * abs(want)
+
+
+def test_jobs_come_and_go(nf):
+    """Add, sweep, remove from the middle, add again: every job's state is
+    the one it has alone after the same number of sweeps."""
+    lengths = [90, 250, 33, 400]
+    jobs = _jobs(lengths, seed=8, sigma=1.5)
+    f = {k: _f32(getattr(jobs, k)) for k in ("W", "A", "pi")}
+    with nf.Batch(f["W"], f["A"], f["pi"], jobs.S, jobs.N, jobs.K, capacity=500,
+                  max_jobs=3) as b:
+        chunk = b.query("fb_chunk")
+        ids = [b.add(_f32(jobs.V[j])) for j in range(3)]
+        b.sweep(3)
+        b.remove(ids[1])                       # the frames of the third job move down
+        with pytest.raises(nf.NfhmmError) as e:
+            b.add(_f32(jobs.V[3]))             # 90 + 33 + 400 frames > 500
+        assert e.value.code == nf.EFULL
+        b.sweep(2)
+        ids.append(b.add(np.ascontiguousarray(_f32(jobs.V[3])[:300])))   # 423 frames
+        b.sweep(2)
+        info = {j[0]: j for j in b.jobs()}
+        assert [info[i][3] for i in (ids[0], ids[2], ids[3])] == [7, 7, 2]
+        got = {i: b.job_posteriors(i) for i in (ids[0], ids[2], ids[3])}
+        bounds = dict(zip([j[0] for j in b.jobs()], b.job_bounds()))
+    for j, sweeps, idx in ((0, 7, 0), (2, 7, 2), (3, 2, 3)):
+        V = np.ascontiguousarray(_f32(jobs.V[j])[:300]) if j == 3 else _f32(jobs.V[j])
+        with nf.VIContext(V, f["W"], f["A"], f["pi"], jobs.S, jobs.N, jobs.K) as a:
+            a.set_option("fb_chunk", chunk)
+            L = a.sweep(sweeps, bound=True)
+            d = a.posteriors()
+        assert np.array_equal(got[ids[idx]], d), j
+        assert bounds[ids[idx]] == L, j
+
+
+def test_batch_full_and_invalid_job_leave_batch_unchanged(nf):
+    jobs = _jobs([100, 100], seed=2)
+    f = {k: _f32(getattr(jobs, k)) for k in ("W", "A", "pi")}
+    with nf.Batch(f["W"], f["A"], f["pi"], jobs.S, jobs.N, jobs.K, capacity=150,
+                  max_jobs=4) as b:
+        chunk = b.query("fb_chunk")
+        i0 = b.add(_f32(jobs.V[0]))
+        with pytest.raises(nf.NfhmmError) as e:
+            b.add(_f32(jobs.V[1]))               # 200 frames > capacity 150
+        assert e.value.code == nf.EFULL
+        bad = np.ascontiguousarray(_f32(jobs.V[1])[:20])
+        bad[3, 7] = -1.0
+        with pytest.raises(nf.NfhmmError) as e:
+            b.add(bad)
+        assert e.value.code == nf.EINVAL
+        assert [j[0] for j in b.jobs()] == [i0] and b.T == 100
+        b.sweep(2)
+        d = b.job_posteriors(i0)
+    with nf.VIContext(_f32(jobs.V[0]), f["W"], f["A"], f["pi"], jobs.S, jobs.N, jobs.K) as a:
+        a.set_option("fb_chunk", chunk)
+        a.sweep(2)
+        assert np.array_equal(a.posteriors(), d)
+
+
+def test_empty_batch_sweeps_and_bound(nf):
+    jobs = _jobs([10], seed=3)
+    f = {k: _f32(getattr(jobs, k)) for k in ("W", "A", "pi")}
+    with nf.Batch(f["W"], f["A"], f["pi"], jobs.S, jobs.N, jobs.K, capacity=64,
+                  max_jobs=2) as b:
+        assert b.sweep(2, bound=True) == 0.0
+        i = b.add(_f32(jobs.V[0]))
+        with pytest.raises(nf.NfhmmError) as e:
+            b.bound()                             # no sweep since the job came
+        assert e.value.code == nf.ESTATE
+        b.sweep(1)
+        b.remove(i)
+        assert b.T == 0 and b.jobs() == []
+
+
+def test_fb_chunk_option_changes_only_rounding(nf):
+    p = synth.make_problem(seed=4, **synth.SMALL)
+    f = p.as_f32()
+    out = []
+    for L in (1, 7, 16, 128):
+        with nf.VIContext(f["V"], f["W"], f["A"], f["pi"], p.S, p.N, p.K) as ctx:
+            ctx.set_option("fb_chunk", L)
+            assert ctx.query("fb_chunk") == L
+            out.append((ctx.sweep(3, bound=True), ctx.posteriors()))
+    for L, d in out[1:]:
+        assert abs(L - out[0][0]) <= 1e-7 * abs(out[0][0])
+        assert np.max(np.abs(d - out[0][1])) <= 1e-5
