@@ -288,7 +288,7 @@ def run_batched(args, rank, world, local):
     from paper_1206_6468_gb300 import nfhmm, synth
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    lengths = synth.batched_lengths(64, 500, 8000, seed=job_seed(rank))
+    lengths = synth.batched_lengths(16 if args.ncu_case else 64, 500, 8000, seed=job_seed(rank))
     jobs = synth.make_jobs(2, 40, 10, 513, lengths, self_prob=0.95, energy_sigma=1.5,
                            seed=job_seed(rank))
     f32 = {"V": jobs.stacked_V()}
@@ -303,6 +303,10 @@ def run_batched(args, rank, world, local):
     ctx = nfhmm.VIContext(d_in["V"], d_in["W"], d_in["A"], d_in["pi"], jobs.S, jobs.N, jobs.K,
                           precision=args.precision, job_frames=lengths.tolist())
     sweeps = args.sweeps
+    if args.ncu_case:
+        print("bound after 3 sweeps:", ctx.sweep(3, bound=True), flush=True)
+        ctx.close()
+        return
 
     def step_device():
         ctx.reinit(d_in["V"], d_in["W"], d_in["A"], d_in["pi"])

@@ -212,11 +212,18 @@ NFHMM_API int nfhmm_job_bounds(nfhmm_ctx *c, double *bounds);
 NFHMM_API int nfhmm_job_posteriors(nfhmm_ctx *c, long long job_id, float *dhat, int on_device);
 
 /*
- * nfhmm_set_option -- tune a context:
- *   NFHMM_OPT_FB_CHUNK  frames per time chunk of the forward-backward
- *                       (1..128; results change only by rounding)
+ * nfhmm_set_option -- tune a context (results change only by rounding):
+ *   NFHMM_OPT_FB_CHUNK     frames per time chunk of the forward-backward (1..128)
+ *   NFHMM_OPT_FB_PRODUCTS  how the chunk transfer matrices are formed:
+ *                          NFHMM_FB_PRODUCTS_TC (default for contexts;
+ *                          split-TF32 tcgen05 MMAs over 128-row tiles) or
+ *                          NFHMM_FB_PRODUCTS_SIMT (FP32 FMAs on the CUDA
+ *                          cores; the stateless calls use this form)
  */
-#define NFHMM_OPT_FB_CHUNK 0
+#define NFHMM_OPT_FB_CHUNK    0
+#define NFHMM_OPT_FB_PRODUCTS 1
+#define NFHMM_FB_PRODUCTS_SIMT 0
+#define NFHMM_FB_PRODUCTS_TC   1
 NFHMM_API int nfhmm_set_option(nfhmm_ctx *c, int key, long long value);
 
 /*

@@ -84,6 +84,7 @@ struct nfhmm_ctx {
   double* bpart = nullptr;  // T x nbpart
   int nbpart = 0;
   double* frame_terms = nullptr;  // T
+  double* fterm = nullptr;  // T x 2 per-frame sums for the bound (weights kernel)
   double* logZ = nullptr;   // S x max_jobs
   double* bound_dev = nullptr;    // max_jobs + 1
   unsigned* err = nullptr;
@@ -103,6 +104,7 @@ struct nfhmm_ctx {
   int sweeps_done = 0;
   bool have_alpha = false;    // alpha-hat, phi-hat of a sweep over the current jobs
   bool bpart_ok = false;      // bound partials of the current alpha-hat
+  bool fterm_ok = false;      // per-frame bound sums of the current alpha-hat
   bool bound_ok = false;      // h_bound holds the bound of the current state
   bool inputs_ok = false;
   bool profiling = false;
@@ -136,7 +138,7 @@ void free_ctx(nfhmm_ctx* c) {
   if (c->s_aux) cudaStreamSynchronize(c->s_aux);
   void* bufs[] = {c->V, c->WM, c->WF, c->A, c->pi, c->alpha, c->w32, c->c, c->Q, c->phi,
                   c->dhat, c->wts, c->sep_tmp, c->v, c->bpart, c->frame_terms, c->logZ,
-                  c->bound_dev, c->err, c->ktab, c->fb_scratch, c->d_tab};
+                  c->bound_dev, c->err, c->ktab, c->fb_scratch, c->d_tab, c->fterm};
   for (void* p : bufs)
     if (p) cudaFree(p);
   tc_free(c->tc);
@@ -256,6 +258,7 @@ int contract(nfhmm_ctx* c, bool want_bpart, bool init, int t0, int rows) {
 }
 
 int one_sweep(nfhmm_ctx* c, bool want_bpart) {
+  // with the bound wanted, the weights kernel also forms its per-frame sums
   const nfhmm_dims& d = c->d;
   if (c->T_active == 0) return NFHMM_OK;
   WeightsArgs wa{};
@@ -272,6 +275,7 @@ int one_sweep(nfhmm_ctx* c, bool want_bpart) {
   wa.alpha = c->alpha;
   wa.w32 = c->w32;
   wa.phi = c->phi;
+  wa.fterm = want_bpart ? c->fterm : nullptr;
   wa.err = c->err;
   int fmt = WF_F32;
   if (c->use_tc) {
@@ -318,6 +322,7 @@ int compute_bound(nfhmm_ctx* c) {
   b.v = c->v;
   b.bpart = c->bpart;
   b.nbpart = c->nbpart;
+  b.fterm = c->fterm_ok ? c->fterm : nullptr;
   b.logZ = c->logZ;
   b.frame_terms = c->frame_terms;
   b.out = c->bound_dev;
@@ -464,6 +469,7 @@ int commit_jobs(nfhmm_ctx* c) {
   c->fb.nchains = nj;
   c->have_alpha = false;
   c->bpart_ok = false;
+  c->fterm_ok = false;
   c->bound_ok = false;
   return NFHMM_OK;
 }
@@ -641,6 +647,7 @@ int create_ctx(nfhmm_ctx** out, const nfhmm_dims* dp, int max_jobs, const float*
   DMALLOC(c->v, T * 8);
   DMALLOC(c->bpart, T * c->nbpart * 8);
   DMALLOC(c->frame_terms, T * 8);
+  DMALLOC(c->fterm, T * 16);
   DMALLOC(c->logZ, S * max_jobs * 8);
   DMALLOC(c->bound_dev, (max_jobs + 1) * 8);
   DMALLOC(c->err, 4);
@@ -657,6 +664,7 @@ int create_ctx(nfhmm_ctx** out, const nfhmm_dims* dp, int max_jobs, const float*
   c->fb.N = d.N;
   c->fb.T = d.T;   // frame stride of phi-hat and d-hat
   c->fb.L = max_jobs == 1 ? fb_default_chunk(d.N, d.T) : fb_default_chunk(d.N, d.T < 4096 ? d.T : 4096);
+  c->fb.products = FB_PRODUCTS_TC;
   c->fb.phi = c->phi;
   c->fb.A = c->A;
   c->fb.pi = c->pi;
@@ -708,6 +716,7 @@ int sweep_impl(nfhmm_ctx* c, int n_sweeps, bool want_bound) {
     for (Job& j : c->jobs) j.sweeps += n_sweeps;
     c->have_alpha = true;
     c->bpart_ok = want_bound;
+    c->fterm_ok = want_bound;
     c->bound_ok = false;
   }
   if (want_bound) {
@@ -845,6 +854,12 @@ int nfhmm_set_option(nfhmm_ctx* c, int key, long long value) {
       if (!rc) rc = leave(c);
       return rc;
     }
+    case NFHMM_OPT_FB_PRODUCTS: {
+      if (value != NFHMM_FB_PRODUCTS_SIMT && value != NFHMM_FB_PRODUCTS_TC)
+        return fail(NFHMM_EINVAL, "products must be NFHMM_FB_PRODUCTS_SIMT or _TC");
+      c->fb.products = value == NFHMM_FB_PRODUCTS_TC ? FB_PRODUCTS_TC : FB_PRODUCTS_SIMT;
+      return NFHMM_OK;
+    }
     default: return fail(NFHMM_EINVAL, "unknown option key");
   }
 }
@@ -856,6 +871,7 @@ int nfhmm_vi_reinit(nfhmm_ctx* c, const float* V, const float* W, const float* A
   c->sweeps_done = 0;
   c->have_alpha = false;
   c->bpart_ok = false;
+  c->fterm_ok = false;
   c->bound_ok = false;
   std::vector<int> frames;
   for (Job& j : c->jobs) {
@@ -1018,6 +1034,7 @@ int nfhmm_set_state(nfhmm_ctx* c, const float* counts, const float* dhat, int sw
   for (Job& j : c->jobs) j.sweeps = sweeps_done;
   c->have_alpha = false;
   c->bpart_ok = false;
+  c->fterm_ok = false;
   c->bound_ok = false;
   return leave(c);
 }

@@ -23,7 +23,9 @@ constexpr unsigned FULL = 0xffffffffu;
 // chunk boundary carried in a register (deterministic order, no atomics).
 // The element table ktab[k] = (g, s*T*N + n) (g < 0 for padding) replaces
 // integer division by K and N on the hot path.
-template <int FMT>
+// With BOUND, the warp also sums alpha-hat and the bound's element terms
+// g(alpha) over the frame (Kahan-compensated in float per lane, then double).
+template <int FMT, bool BOUND>
 __global__ void __launch_bounds__(256) k_weights(WeightsArgs a) {
   const int lane = threadIdx.x & 31;
   const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -33,6 +35,8 @@ __global__ void __launch_bounds__(256) k_weights(WeightsArgs a) {
   float carry = 0.f;
   int carry_key = INT_MIN;
   unsigned bad = 0;
+  float sa = 0.f, ca = 0.f, sg = 0.f, cg = 0.f;   // Kahan sums of alpha and g (small part)
+  double big = 0.0;                                // sum of the exact large parts of g
   for (int base = 0; base < a.Mp; base += 32) {
     const int k = base + lane;
     const int2 kt = a.ktab[k];          // Mp is a multiple of 32: k < Mp
@@ -41,7 +45,20 @@ __global__ void __launch_bounds__(256) k_weights(WeightsArgs a) {
     float alpha = 0.f, psi = 0.f, w = 0.f;
     if (el) {
       alpha = a.counts[row + k] + a.gamma * a.dhat[kt.y + toff] + 1.f;
-      digamma_exp(alpha, psi, w);
+      if (BOUND) {
+        float gs, gb;
+        digamma_exp_g(alpha, psi, w, gs, gb);
+        float y = alpha - ca, z = sa + y;
+        ca = (z - sa) - y;
+        sa = z;
+        y = gs - cg;
+        z = sg + y;
+        cg = (z - sg) - y;
+        sg = z;
+        big += (double)gb;
+      } else {
+        digamma_exp(alpha, psi, w);
+      }
       if (!isfinite(psi) || !isfinite(w)) bad |= ERR_NONFINITE;
     }
     a.alpha[row + k] = alpha;
@@ -78,6 +95,14 @@ __global__ void __launch_bounds__(256) k_weights(WeightsArgs a) {
   }
   bad = __reduce_or_sync(FULL, bad);
   if (bad && lane == 0) atomicOr(a.err, bad);
+  if (BOUND) {
+    const double s0 = warp_sum_d((double)sa - (double)ca);
+    const double sgt = warp_sum_d(((double)sg - (double)cg) + big);
+    if (lane == 0) {
+      a.fterm[2 * (size_t)t] = s0;
+      a.fterm[2 * (size_t)t + 1] = sgt;
+    }
+  }
 }
 
 __global__ void k_element_table(int M, int Mp, int K, int N, int T, int2* ktab) {
@@ -97,10 +122,20 @@ void launch_element_table(int M, int Mp, int K, int N, int T, int2* ktab, cudaSt
 void launch_weights(const WeightsArgs& a, int fmt, cudaStream_t st) {
   const int warps = 8;
   dim3 grid((a.T + warps - 1) / warps);
+  const bool b = a.fterm != nullptr;
   switch (fmt) {
-    case WF_TF32X2: k_weights<WF_TF32X2><<<grid, warps * 32, 0, st>>>(a); break;
-    case WF_BF16: k_weights<WF_BF16><<<grid, warps * 32, 0, st>>>(a); break;
-    default: k_weights<WF_F32><<<grid, warps * 32, 0, st>>>(a); break;
+    case WF_TF32X2:
+      if (b) k_weights<WF_TF32X2, true><<<grid, warps * 32, 0, st>>>(a);
+      else k_weights<WF_TF32X2, false><<<grid, warps * 32, 0, st>>>(a);
+      break;
+    case WF_BF16:
+      if (b) k_weights<WF_BF16, true><<<grid, warps * 32, 0, st>>>(a);
+      else k_weights<WF_BF16, false><<<grid, warps * 32, 0, st>>>(a);
+      break;
+    default:
+      if (b) k_weights<WF_F32, true><<<grid, warps * 32, 0, st>>>(a);
+      else k_weights<WF_F32, false><<<grid, warps * 32, 0, st>>>(a);
+      break;
   }
 }
 
@@ -261,6 +296,19 @@ __global__ void k_bound_frames(BoundArgs a) {
   }
 }
 
+// The same per-frame term from the weights kernel's per-frame sums
+// (one thread per frame): no pass over the elements.
+__global__ void k_bound_frames_fused(BoundArgs a) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= a.T) return;
+  const double s0 = a.fterm[2 * (size_t)t], sg = a.fterm[2 * (size_t)t + 1];
+  double vl = 0.0;
+  for (int j = 0; j < a.nbpart; ++j) vl += a.bpart[(size_t)t * a.nbpart + j];
+  const double psi0 = digamma_d(s0);
+  a.frame_terms[t] = vl - a.v[t] * psi0 + a.konst - lgamma(s0) + sg + psi0 * (s0 - (double)a.M) -
+                     (double)a.S * (double)a.gamma * (double)a.K * psi0;
+}
+
 // One block per job: the sum of its frames' terms and its chains' log
 // normalisers.  A one-warp launch then sums the jobs into out[njobs].
 __global__ void k_bound_final(BoundArgs a) {
@@ -291,7 +339,10 @@ __global__ void k_bound_total(BoundArgs a) {
 }
 
 void launch_bound(const BoundArgs& a, cudaStream_t st, int* launches) {
-  k_bound_frames<<<(a.T + 7) / 8, 256, 0, st>>>(a);
+  if (a.fterm)
+    k_bound_frames_fused<<<(a.T + 127) / 128, 128, 0, st>>>(a);
+  else
+    k_bound_frames<<<(a.T + 7) / 8, 256, 0, st>>>(a);
   k_bound_final<<<a.njobs, 1024, 0, st>>>(a);
   k_bound_total<<<1, 32, 0, st>>>(a);
   if (launches) *launches += 3;

@@ -368,6 +368,161 @@ __global__ void __launch_bounds__(256, 1) k_fb_products(FBArgs a) {
   }
 }
 
+// --------------------------------------------- 1'. products on CUDA cores
+// The same chunk matrices with FP32 FMAs: one block per (chunk, source), a
+// warp advances RPW rows of P_c (basis states i) one frame per step, lane j
+// holding columns j and j + 32 and A's columns j, j + 32 in registers.  A
+// step is a vector-matrix product per row: far lower latency than a
+// tensor-core round trip, so chains of a few thousand frames finish sooner;
+// the work (N^3 per frame and source) is the same.  Each row is rescaled by
+// the sum of its previous value (reduced while the step's products run);
+// the removed factors are kept per row as exact (mantissa, exponent) pairs.
+template <int NP>
+struct SimtCfg {
+  static constexpr int RPW = NP <= 16 ? 4 : 8;             // rows per warp
+  static constexpr int WARPS = (NP + RPW - 1) / RPW;
+};
+
+template <int NP>
+__global__ void __launch_bounds__(SimtCfg<NP>::WARPS * 32) k_fb_products_simt(FBArgs a) {
+  constexpr int RPW = SimtCfg<NP>::RPW, WARPS = SimtCfg<NP>::WARPS;
+  constexpr bool TWO = NP > 32;   // lane also holds column j + 32
+  extern __shared__ double smd[];
+  double* dred = smd;             // WARPS partial sums of the frame maxima
+  double* rlog = smd + 32;        // NP row log scales
+  float* e = reinterpret_cast<float*>(smd + 32 + 64);   // L x NP emissions
+  float* xs = e + a.L * NP;                              // WARPS x RPW x NP row vectors
+  const int N = a.N;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = blockIdx.x, s = blockIdx.y;
+  const ChunkInfo ci = chunk_info(a, c);
+  const int len = ci.len;
+  const float* src = a.phi + ((size_t)s * a.T + ci.t0) * N;
+  for (int i = threadIdx.x; i < len * N; i += blockDim.x) {
+    const int f = i / N, n = i - f * N;
+    e[f * NP + n] = src[i];
+  }
+  __syncthreads();
+  double ms = 0.0;
+  for (int f = warp; f < len; f += WARPS) {
+    float* row = e + f * NP;
+    const float x0 = lane < N ? row[lane] : -INFINITY;
+    const float x1 = lane + 32 < N ? row[lane + 32] : -INFINITY;
+    const float m = warp_max(fmaxf(x0, x1));
+    __syncwarp();
+    if (lane < NP) row[lane] = lane < N ? expf(x0 - m) : 0.f;
+    if (lane + 32 < NP) row[lane + 32] = lane + 32 < N ? expf(x1 - m) : 0.f;
+    ms += (double)m;
+  }
+  if (lane == 0) dred[warp] = ms;
+  const float* Ag = a.A + (size_t)s * N * N;
+  float A0[NP], A1[TWO ? NP : 1];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    A0[k] = (lane < N && k < N) ? Ag[k * N + lane] : 0.f;
+    if (TWO) A1[k] = (lane + 32 < N && k < N) ? Ag[k * N + lane + 32] : 0.f;
+  }
+  __syncthreads();
+  float r0[RPW], r1[RPW];
+  ScaleAcc sc[RPW];
+  const float e00 = lane < NP ? e[lane] : 0.f;
+  const float e01 = lane + 32 < NP ? e[lane + 32] : 0.f;
+#pragma unroll
+  for (int u = 0; u < RPW; ++u) {
+    const int i = warp * RPW + u;
+    r0[u] = r1[u] = 0.f;
+    if (i < N) {
+      if (ci.first) {
+        r0[u] = lane == i ? e00 : 0.f;
+        r1[u] = lane + 32 == i ? e01 : 0.f;
+      } else {
+        r0[u] = lane < N ? Ag[i * N + lane] * e00 : 0.f;
+        r1[u] = lane + 32 < N ? Ag[i * N + lane + 32] * e01 : 0.f;
+      }
+    }
+  }
+  float* xw = xs + warp * RPW * NP;
+  unsigned bad = 0;
+  for (int f = 1; f < len; ++f) {
+    __syncwarp();
+#pragma unroll
+    for (int u = 0; u < RPW; ++u) {
+      if (lane < NP) xw[u * NP + lane] = r0[u];
+      if (lane + 32 < NP) xw[u * NP + lane + 32] = r1[u];
+    }
+    __syncwarp();
+    float sp[RPW];
+#pragma unroll
+    for (int u = 0; u < RPW; ++u) sp[u] = warp_sum(r0[u] + r1[u]);
+    const float* ef = e + f * NP;
+    const float ef0 = lane < NP ? ef[lane] : 0.f;
+    const float ef1 = lane + 32 < NP ? ef[lane + 32] : 0.f;
+#pragma unroll
+    for (int u = 0; u < RPW; ++u) {
+      float p0[4] = {0.f, 0.f, 0.f, 0.f}, p1[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int k = 0; k < NP; k += 4) {
+        const float4 xv = *reinterpret_cast<const float4*>(&xw[u * NP + k]);
+        p0[0] = fmaf(xv.x, A0[k], p0[0]);
+        p0[1] = fmaf(xv.y, A0[k + 1], p0[1]);
+        p0[2] = fmaf(xv.z, A0[k + 2], p0[2]);
+        p0[3] = fmaf(xv.w, A0[k + 3], p0[3]);
+        if (TWO) {
+          p1[0] = fmaf(xv.x, A1[k], p1[0]);
+          p1[1] = fmaf(xv.y, A1[k + 1], p1[1]);
+          p1[2] = fmaf(xv.z, A1[k + 2], p1[2]);
+          p1[3] = fmaf(xv.w, A1[k + 3], p1[3]);
+        }
+      }
+      if (!isfinite(sp[u])) bad = 1;
+      const float g = renorm_factor(sp[u]);
+      sc[u].mul(removed_scale(sp[u]));
+      r0[u] = ((p0[0] + p0[1]) + (p0[2] + p0[3])) * ef0 * g;
+      r1[u] = TWO ? ((p1[0] + p1[1]) + (p1[2] + p1[3])) * ef1 * g : 0.f;
+    }
+  }
+  // final normalisation; a row that vanished (state i cannot start this
+  // chunk and reach its end) gets log scale -inf
+  double lr[RPW];
+#pragma unroll
+  for (int u = 0; u < RPW; ++u) {
+    const float sf = warp_sum(r0[u] + r1[u]);
+    if (!isfinite(sf)) bad = 1;
+    const float g = renorm_factor(sf);
+    sc[u].mul(removed_scale(sf));
+    r0[u] *= g;
+    r1[u] *= g;
+    lr[u] = sf > 0.f ? sc[u].log() : -INFINITY;
+    const int i = warp * RPW + u;
+    if (lane == 0 && i < NP) rlog[i] = i < N ? lr[u] : -INFINITY;
+  }
+  if (bad && lane == 0) atomicOr(a.err, ERR_FB_ZERO);
+  __syncthreads();
+  double rmax = -INFINITY, msum = 0.0;
+  for (int i = 0; i < N; ++i) rmax = fmax(rmax, rlog[i]);
+  for (int w = 0; w < WARPS; ++w) msum += dred[w];
+  const size_t base = ((size_t)s * a.C + c) * NP * NP;
+  float* Pg = a.P + base;
+  float* PTg = a.PT + base;
+#pragma unroll
+  for (int u = 0; u < RPW; ++u) {
+    const int i = warp * RPW + u;
+    if (i < NP) {
+      // rmax = -inf only if every row vanished (flagged by the scan)
+      const float g = (i < N && rmax > -INFINITY && lr[u] > -INFINITY) ? (float)exp(lr[u] - rmax) : 0.f;
+      if (lane < NP) {
+        Pg[i * NP + lane] = r0[u] * g;
+        PTg[lane * NP + i] = r0[u] * g;
+      }
+      if (lane + 32 < NP) {
+        Pg[i * NP + lane + 32] = r1[u] * g;
+        PTg[(lane + 32) * NP + i] = r1[u] * g;
+      }
+    }
+  }
+  if (threadIdx.x == 0) a.Plog[(size_t)s * a.C + c] = msum + (rmax > -INFINITY ? rmax : 0.0);
+}
+
 // ------------------------------------------------------------------- 2. scan
 // One warp per (source, direction); lane j holds states j and j + 32.
 // blockIdx.y == 0: forward boundaries fwd[c] = normalised a at the end of
@@ -666,6 +821,11 @@ static size_t smem_products(int L) {
          128 * sizeof(double) + Cfg::RCH * sizeof(double) + 256 * sizeof(float) + 64;
 }
 template <int NP>
+static size_t smem_products_simt(int L) {
+  using Cfg = SimtCfg<NP>;
+  return (32 + 64) * sizeof(double) + (size_t)(L + Cfg::WARPS * Cfg::RPW) * NP * sizeof(float);
+}
+template <int NP>
 static size_t smem_scan() {
   return (size_t)(RING * NP * (NP + 4) + 64) * sizeof(float);
 }
@@ -688,12 +848,20 @@ static cudaError_t launch_np(const FBArgs& a, cudaStream_t st) {
     if (attr == cudaSuccess)
       attr = cudaFuncSetAttribute(k_fb_replay<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)SMEM_OPTIN);
+    if (attr == cudaSuccess)
+      attr = cudaFuncSetAttribute(k_fb_products_simt<NP>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem_products_simt<NP>(FB_MAX_L));
   }
   if (attr != cudaSuccess) return attr;
   using Cfg = ProdCfg<NP>;
   const int rc = replay_chunks(NP, a.L);
-  k_fb_products<NP><<<dim3((a.C + Cfg::RCH - 1) / Cfg::RCH, a.S), 256, smem_products<NP>(a.L),
-                      st>>>(a);
+  if (a.products == FB_PRODUCTS_TC)
+    k_fb_products<NP><<<dim3((a.C + Cfg::RCH - 1) / Cfg::RCH, a.S), 256,
+                        smem_products<NP>(a.L), st>>>(a);
+  else
+    k_fb_products_simt<NP><<<dim3(a.C, a.S), SimtCfg<NP>::WARPS * 32,
+                             smem_products_simt<NP>(a.L), st>>>(a);
   k_fb_scan<NP><<<dim3(a.S * a.nchains, 2), 32, smem_scan<NP>(), st>>>(a);
   k_fb_replay<NP><<<dim3((a.C + rc - 1) / rc, a.S), rc * 64, rc * smem_replay_chunk(NP, a.L),
                     st>>>(a);

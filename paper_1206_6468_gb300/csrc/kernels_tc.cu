@@ -41,7 +41,8 @@ using namespace tc;
 constexpr int BM = 128;
 constexpr int BN1 = 128;           // reconstruction: columns = frequencies
 constexpr int BN2 = 160;           // back-projection: columns = elements
-constexpr int NUM_THREADS = 192;   // 6 warps
+constexpr int EPI_WARPS = 8;                    // two per TMEM lane quarter
+constexpr int NUM_THREADS = 64 + EPI_WARPS * 32;  // TMA warp, MMA warp, epilogue
 enum TcEpi { TEPI_RATIO = 0, TEPI_SCALE = 1 };
 
 template <int KIND>
@@ -196,54 +197,90 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       mma_commit(accum);  // fires once every MMA issued above has completed
     }
   } else {
-    // ---------------- epilogue: warps 2..5, TMEM lanes 32*(warp % 4) ...
+    // ---------------- epilogue: warps 2..9.  Warp w reads TMEM lanes
+    // 32*(w % 4) .. +31 (one output row per thread) and half (w - 2) / 4 of
+    // the tile's columns.  Its V (or w) values are loaded before the
+    // accumulator is ready, so their latency hides behind the main loop.
+    constexpr int HALF = BN / 2;        // a multiple of 16
+    constexpr int NCH = HALF / 16;
     const int quarter = warp & 3;
+    const int half = (warp - 2) >> 2;
     const int r = quarter * 32 + lane;
     const int t = row0 + r;
+    const int cbase = col0 + half * HALF;
+    float pre[HALF];
+    {
+      const float* src = EPI == TEPI_RATIO ? p.V + (size_t)t * p.ldv : p.w + (size_t)t * p.ldw;
+#pragma unroll
+      for (int ch = 0; ch < NCH; ++ch) {
+        const int c = cbase + 16 * ch;
+        if (t < p.rows && c < p.cols) {
+          const float4* sp = reinterpret_cast<const float4*>(src + c);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const float4 v4 = sp[i];
+            pre[16 * ch + 4 * i] = v4.x;
+            pre[16 * ch + 4 * i + 1] = v4.y;
+            pre[16 * ch + 4 * i + 2] = v4.z;
+            pre[16 * ch + 4 * i + 3] = v4.w;
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) pre[16 * ch + i] = 0.f;
+        }
+      }
+    }
     const bool ok = mbar_wait(accum, 0);
     if (!ok) atomicOr(p.err, ERR_TIMEOUT);
     tc_fence_after();
     double part = 0.0;
     unsigned bad = 0;
-    const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16);
+    const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * HALF);
     const int nmain = nkb < Cfg::NMAIN ? nkb : Cfg::NMAIN;   // accumulators written
-#pragma unroll 1
-    for (int cc = 0; cc < BN; cc += 16) {
+#pragma unroll
+    for (int ch = 0; ch < NCH; ++ch) {
+      // every accumulator's 16 columns in flight at once, then one wait
+      uint32_t raw[Cfg::NACC][16];
+#pragma unroll
+      for (int j = 0; j < Cfg::NACC; ++j)
+        if (j == 0 || j < nmain || (K::NOPS == 2 && j == Cfg::NMAIN))
+          tmem_ld16_nw(taddr + (uint32_t)(j * BN + 16 * ch), raw[j]);
+      tmem_wait_ld();
       float acc[16];
-      tmem_ld16(taddr + cc, acc);
-#pragma unroll 1
-      for (int j = 1; j < Cfg::NACC; ++j) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) acc[i] = __uint_as_float(raw[0][i]);
+#pragma unroll
+      for (int j = 1; j < Cfg::NACC; ++j)
         if (j < nmain || (K::NOPS == 2 && j == Cfg::NMAIN)) {
-          float part_j[16];
-          tmem_ld16(taddr + (uint32_t)(j * BN) + cc, part_j);
 #pragma unroll
-          for (int i = 0; i < 16; ++i) acc[i] += part_j[i];
+          for (int i = 0; i < 16; ++i) acc[i] += __uint_as_float(raw[j][i]);
         }
-      }
-      const int c = col0 + cc;
+      const int c = cbase + 16 * ch;
       if (!ok || t >= p.rows || c >= p.cols) continue;   // cols is a multiple of 16
+      const float* vv = pre + 16 * ch;
       if (EPI == TEPI_RATIO) {
-        const float4* vp = reinterpret_cast<const float4*>(p.V + (size_t)t * p.ldv + c);
-        float q[16];
+        float q[16], vl[16];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const float4 v4 = vp[i];
-          const float vv[4] = {v4.x, v4.y, v4.z, v4.w};
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const float v = vv[j], x = acc[4 * i + j];
-            float qq = 0.f;
-            if (v > 0.f) {
-              if (x > 0.f && isfinite(x)) {
-                qq = v / x;
-                part += (double)v * (double)logf(x);
-              } else {
-                bad |= ERR_VHAT_ZERO;
-              }
+        for (int i = 0; i < 16; ++i) {
+          const float v = vv[i], x = acc[i];
+          float qq = 0.f, l = 0.f;
+          if (v > 0.f) {
+            if (x > 0.f && isfinite(x)) {
+              qq = v / x;
+              l = v * logf(x);
+            } else {
+              bad |= ERR_VHAT_ZERO;
             }
-            q[4 * i + j] = qq;
           }
+          q[i] = qq;
+          vl[i] = l;
         }
+        // pairwise sum of the 16 terms in float, then into the double partial
+#pragma unroll
+        for (int w = 8; w > 0; w >>= 1)
+#pragma unroll
+          for (int i = 0; i < w; ++i) vl[i] += vl[i + w];
+        part += (double)vl[0];
         if (KIND == KIND_TF32X3) {
           float4* hp = reinterpret_cast<float4*>(p.out_f32 + (size_t)t * p.ldo + c);
           float4* lp = reinterpret_cast<float4*>(p.out_lo + (size_t)t * p.ldo + c);
@@ -272,18 +309,15 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           }
         }
       } else {
-        const float4* wp = reinterpret_cast<const float4*>(p.w + (size_t)t * p.ldw + c);
         float4* op = reinterpret_cast<float4*>(p.out_f32 + (size_t)t * p.ldo + c);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const float4 w4 = wp[i];
-          op[i] = make_float4(w4.x * acc[4 * i], w4.y * acc[4 * i + 1], w4.z * acc[4 * i + 2],
-                              w4.w * acc[4 * i + 3]);
-        }
+        for (int i = 0; i < 4; ++i)
+          op[i] = make_float4(vv[4 * i] * acc[4 * i], vv[4 * i + 1] * acc[4 * i + 1],
+                              vv[4 * i + 2] * acc[4 * i + 2], vv[4 * i + 3] * acc[4 * i + 3]);
       }
     }
     if (EPI == TEPI_RATIO && p.bpart && ok && t < p.rows)
-      p.bpart[(size_t)t * p.nbpart + blockIdx.x] = part;
+      p.bpart[(size_t)t * p.nbpart + 2 * blockIdx.x + half] = part;
     if (bad) atomicOr(p.err, bad);
   }
   tc_fence_before();
@@ -365,7 +399,8 @@ bool tc_available() {
 
 std::string tc_last_error() { return g_tc_err; }
 
-int tc_col_tiles_gemm1(int Fp) { return (Fp + BN1 - 1) / BN1; }
+// bound partials per frame: one per (column tile, epilogue half)
+int tc_col_tiles_gemm1(int Fp) { return 2 * ((Fp + BN1 - 1) / BN1); }
 
 static Maps* maps_of(TcPlan& p, int which) {
   return reinterpret_cast<Maps*>(&p.maps[which * 4][0]);

@@ -16,18 +16,24 @@ namespace nfhmm {
 // x' * exp(d - acc), where x' is the shifted argument, d = psi(x') - ln x'
 // from the series and acc the recurrence sum, so no ln/exp round trip is
 // needed for large x.  Returns NaN for x <= 0 or NaN.
-__device__ __forceinline__ void digamma_exp(float x, float& psi, float& w) {
+template <bool G>
+__device__ __forceinline__ void digamma_impl(float x, float& psi, float& w, float& gsmall,
+                                             float& gbig) {
   if (!(x > 0.f)) {
     psi = __int_as_float(0x7fc00000);
     w = psi;
+    if (G) gsmall = gbig = psi;
     return;
   }
-  float acc = 0.f;
+  const float a = x;
+  float acc = 0.f, prod = 1.f;
+  int n = 0;
   // x > 0: the first step lands in [1, ...), five more reach x >= 6.
   // __frcp_rn: the correctly rounded reciprocal (same value as 1.f / x)
 #pragma unroll 1
-  for (int i = 0; i < 7 && x < 6.f; ++i) {
+  for (; n < 7 && x < 6.f; ++n) {
     acc += __frcp_rn(x);
+    if (G) prod *= x;
     x += 1.f;
   }
   const float r = __frcp_rn(x);
@@ -36,8 +42,34 @@ __device__ __forceinline__ void digamma_exp(float x, float& psi, float& w) {
       r2 * (1.f / 12.f -
             r2 * (1.f / 120.f - r2 * (1.f / 252.f - r2 * (1.f / 240.f - r2 * (1.f / 132.f)))));
   const float d = -0.5f * r - series;
-  psi = logf(x) + d - acc;
+  const float lx = logf(x);
+  psi = lx + d - acc;
   w = x * expf(d - acc);
+  if (G) {
+    const float st =
+        r * (1.f / 12.f - r2 * (1.f / 360.f - r2 * (1.f / 1260.f - r2 * (1.f / 1680.f))));
+    gsmall = ((float)n + 0.5f) * lx + 0.91893853320467274f + st - logf(prod) -
+             (a - 1.f) * (d - acc);
+    gbig = -((float)n + a);
+  }
+}
+
+__device__ __forceinline__ void digamma_exp(float x, float& psi, float& w) {
+  float unused0, unused1;
+  digamma_impl<false>(x, psi, w, unused0, unused1);
+}
+
+// digamma_exp plus the bound's per-element term g(x) = lnGamma(x) - (x-1) psi(x)
+// from the same shifted argument x' = x + n (n recurrence steps): with
+// Stirling's series lnGamma(x') = (x' - 1/2) ln x' - x' + ln(2 pi)/2 + st(x'),
+// st = 1/(12x') - 1/(360x'^3) + 1/(1260x'^5) - 1/(1680x'^7), and
+// lnGamma(x) = lnGamma(x') - ln(x (x+1) ... (x+n-1)),
+//   g(x) = (n + 1/2) ln x' + ln(2 pi)/2 + st - ln(prod) - (x-1)(d - acc) - x'
+// where d - acc is the series part of psi.  The large part -x' = -(x + n) is
+// returned separately (gbig, exact in double) so that no float sum holds it.
+__device__ __forceinline__ void digamma_exp_g(float x, float& psi, float& w, float& gsmall,
+                                              float& gbig) {
+  digamma_impl<true>(x, psi, w, gsmall, gbig);
 }
 
 __device__ __forceinline__ float digamma_f(float x) {

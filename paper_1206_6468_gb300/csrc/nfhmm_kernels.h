@@ -35,6 +35,7 @@ struct WeightsArgs {
   void* wop_hi;         // format-specific operand copies (may be null)
   void* wop_lo;
   float* phi;           // S x T x N (without the -gamma K psi(alpha_t0) constant)
+  double* fterm;        // null, or T x 2: (sum_k alpha_tk, sum_k g(alpha_tk)) for the bound
   unsigned* err;
 };
 void launch_weights(const WeightsArgs& a, int fmt, cudaStream_t st);
@@ -79,8 +80,12 @@ int gemm_simt_col_tiles(int cols);
 // hold one or more independent chains (jobs) back to back; no chunk crosses
 // a chain boundary and each chain's first chunk starts from pi.  With null
 // chain tables there is one chain covering all T frames.
+// how the chunk matrices are formed: FP32 FMAs on the CUDA cores (lowest
+// latency per frame) or split-TF32 tcgen05 MMAs (a 128-row tile per step)
+enum { FB_PRODUCTS_SIMT = 0, FB_PRODUCTS_TC = 1 };
 struct FBArgs {
   int S, N, T, L, C;   // C = total chunks per source over all chains
+  int products;        // FB_PRODUCTS_SIMT or FB_PRODUCTS_TC
   int nchains;
   const int* chain_c0;     // nchains + 1: first chunk of each chain (chain_c0[nchains] = C)
   const int* chain_t0;     // nchains: first frame of each chain
@@ -118,6 +123,7 @@ struct BoundArgs {
   const float* alpha;      // T x Mp
   const double* v;         // T
   const double* bpart; int nbpart;
+  const double* fterm;     // null, or T x 2 per-frame sums from the weights kernel
   const double* logZ;      // S x njobs
   double* frame_terms;     // T
   double* out;             // njobs + 1: per-job bounds, then their sum

@@ -29,7 +29,8 @@ INIT_UNIFORM, INIT_PRIOR = 0, 1
 SEP_MEAN, SEP_EXPECTATION = 0, 1
 STAGES = {"weights": 0, "gemm1": 1, "gemm2": 2, "fb": 3, "bound": 4, "init": 5}
 QUERIES = {"tensor_cores": 0, "fb_chunk": 1, "sweeps_done": 2, "device_bytes": 3}
-OPTIONS = {"fb_chunk": 0}
+OPTIONS = {"fb_chunk": 0, "fb_products": 1}
+FB_PRODUCTS = {"simt": 0, "tc": 1}
 PRECISIONS = {"fp32": FP32, "bf16": BF16, "fp32_simt": FP32_SIMT}
 
 
@@ -228,7 +229,10 @@ class VIContext:
         _check(_lib.nfhmm_job_posteriors(self._h, job_id, p, dev), "nfhmm_job_posteriors")
         return out
 
-    def set_option(self, key: str, value: int):
+    def set_option(self, key: str, value):
+        """fb_chunk: frames per chunk (1..128); fb_products: "simt" or "tc"."""
+        if key == "fb_products":
+            value = FB_PRODUCTS[value]
         _check(_lib.nfhmm_set_option(self._h, OPTIONS[key], int(value)), "nfhmm_set_option")
 
     def reinit(self, V, W, A, pi):

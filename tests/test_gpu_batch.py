@@ -132,7 +132,10 @@ def test_jobs_come_and_go(nf):
             L = a.sweep(sweeps, bound=True)
             d = a.posteriors()
         assert np.array_equal(got[ids[idx]], d), j
-        assert bounds[ids[idx]] == L, j
+        # the batch's bound comes from a separate pass over alpha-hat after the
+        # sweeps, the lone job's from sums formed during its last sweep: the
+        # same quantity, rounded differently
+        assert abs(bounds[ids[idx]] - L) <= 1e-8 * abs(L), j
 
 
 def test_batch_full_and_invalid_job_leave_batch_unchanged(nf):
@@ -174,13 +177,14 @@ def test_empty_batch_sweeps_and_bound(nf):
         assert b.T == 0 and b.jobs() == []
 
 
-def test_fb_chunk_option_changes_only_rounding(nf):
+def test_fb_options_change_only_rounding(nf):
     p = synth.make_problem(seed=4, **synth.SMALL)
     f = p.as_f32()
     out = []
-    for L in (1, 7, 16, 128):
+    for L, prod in ((1, "simt"), (7, "tc"), (16, "simt"), (16, "tc"), (128, "simt")):
         with nf.VIContext(f["V"], f["W"], f["A"], f["pi"], p.S, p.N, p.K) as ctx:
             ctx.set_option("fb_chunk", L)
+            ctx.set_option("fb_products", prod)
             assert ctx.query("fb_chunk") == L
             out.append((ctx.sweep(3, bound=True), ctx.posteriors()))
     for L, d in out[1:]:

@@ -39,13 +39,16 @@ def maxabs(a, b):
     return float(np.max(np.abs(np.asarray(a, np.float64) - b)))
 
 
-def _ctx(nf, p, precision="fp32", device=False, init_mode=0):
+def _ctx(nf, p, precision="fp32", device=False, init_mode=0, products=None):
     f = p.as_f32()
     if device:
         import torch
         f = {k: torch.from_numpy(v).cuda() for k, v in f.items()}
-    return nf.VIContext(f["V"], f["W"], f["A"], f["pi"], p.S, p.N, p.K, gamma=p.gamma,
-                        precision=precision, init_mode=init_mode)
+    ctx = nf.VIContext(f["V"], f["W"], f["A"], f["pi"], p.S, p.N, p.K, gamma=p.gamma,
+                       precision=precision, init_mode=init_mode)
+    if products is not None:
+        ctx.set_option("fb_products", products)
+    return ctx
 
 
 # ------------------------------------------------------------------ digamma
@@ -140,8 +143,9 @@ def test_initial_state_prior_marginals(nf):
     assert maxabs(dhat, d_ref) <= 1e-6
 
 
+@pytest.mark.parametrize("products", ["simt", "tc"])
 @pytest.mark.parametrize("workload,k", [("SMALL", 0), ("SMALL", 5), ("PAPER_SIZE", 2)])
-def test_one_sweep_from_oracle_state(nf, workload, k):
+def test_one_sweep_from_oracle_state(nf, workload, k, products):
     """One sweep started from the oracle's state after k sweeps: every output
     of the sweep against the oracle's same sweep."""
     cfg = getattr(synth, workload)
@@ -153,7 +157,7 @@ def test_one_sweep_from_oracle_state(nf, workload, k):
     ref = vi.sweep(p.V, p.W, p.A, p.pi, p.S, p.N, p.K, p.gamma, c32.astype(np.float64),
                    d32.astype(np.float64), B)
     L_ref = vi.bound(p.V, p.W, ref["alpha"], ref["logZ"], p.gamma, p.S, p.K, Vhat=ref["Vhat"])
-    with _ctx(nf, p) as ctx:
+    with _ctx(nf, p, products=products) as ctx:
         ctx.set_state(c32, d32, k)
         L = ctx.sweep(1, bound=True)
         alpha = ctx.weights()
