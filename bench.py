@@ -392,7 +392,9 @@ def run_serving(args, rank, world, local):
     pool_n, t_max = 8, 10000
     models = [synth.make_jobs(S, 40, 10, 513, [t_max] * pool_n, self_prob=0.95,
                               energy_sigma=1.5, seed=100 * S + job_seed(rank)) for S in (2, 3)]
-    pools = [[np.ascontiguousarray(v, dtype=np.float32) for v in m.V] for m in models]
+    # request spectrograms arrive in pinned host buffers, as a serving front end would hold them
+    pools = [[torch.from_numpy(np.ascontiguousarray(v, dtype=np.float32)).pin_memory().numpy()
+              for v in m.V] for m in models]
     n_req = int(rng.poisson(args.serve_rate * args.serve_seconds))
     arrivals = np.sort(rng.uniform(0.0, args.serve_seconds, size=n_req))
     Ts = np.exp(rng.uniform(np.log(200), np.log(t_max), size=n_req)).astype(int)

@@ -117,6 +117,14 @@ NFHMM_API int nfhmm_vi_reinit(nfhmm_ctx *c, const float *V, const float *W, cons
 NFHMM_API int nfhmm_vi_sweep(nfhmm_ctx *c, int n_sweeps, double *bound_out);
 
 /*
+ * nfhmm_vi_sweep_async -- queue n_sweeps >= 1 sweeps without waiting.  With
+ * prepare_bound = 1 the last sweep also forms the bound's per-frame terms, so
+ * that a following nfhmm_bound or nfhmm_job_bounds only reduces them.  Lets
+ * a caller keep several contexts' sweeps in flight at once.
+ */
+NFHMM_API int nfhmm_vi_sweep_async(nfhmm_ctx *c, int n_sweeps, int prepare_bound);
+
+/*
  * nfhmm_bound -- the variational lower bound of the current state
  * (alpha-hat of the last sweep with its optimal z-hat and d-hat), reduced in
  * FP64.  The paper prints no bound; it follows from Eq. 1 and the factorised
@@ -195,8 +203,18 @@ NFHMM_API int nfhmm_batch_create(nfhmm_ctx **out, const nfhmm_dims *d, int max_j
 NFHMM_API int nfhmm_batch_add(nfhmm_ctx *c, int T, const float *V, int on_device,
                               long long *job_id);
 
+/* nfhmm_batch_add_many -- append n jobs at once (job j: T[j] frames from
+ * V[j]), validated together (one synchronisation); all or none are added.
+ * job_ids: NULL or n ids. */
+NFHMM_API int nfhmm_batch_add_many(nfhmm_ctx *c, int n, const int *T, const float *const *V,
+                                   int on_device, long long *job_ids);
+
 /* nfhmm_batch_remove -- drop a job and free its frames (asynchronous). */
 NFHMM_API int nfhmm_batch_remove(nfhmm_ctx *c, long long job_id);
+
+/* nfhmm_batch_remove_many -- drop n jobs and close the gaps in one pass
+ * (asynchronous). */
+NFHMM_API int nfhmm_batch_remove_many(nfhmm_ctx *c, int n, const long long *job_ids);
 
 /* nfhmm_batch_info -- number of jobs, frames held, and per job (arrays of at
  * least n_jobs entries, each may be NULL): id, first frame, frames, sweeps
@@ -219,9 +237,13 @@ NFHMM_API int nfhmm_job_posteriors(nfhmm_ctx *c, long long job_id, float *dhat, 
  *                          split-TF32 tcgen05 MMAs over 128-row tiles) or
  *                          NFHMM_FB_PRODUCTS_SIMT (FP32 FMAs on the CUDA
  *                          cores; the stateless calls use this form)
+ *   NFHMM_OPT_GRAPHS       1 (default): with profiling off, a sweep whose
+ *                          launch configuration has run before is replayed
+ *                          from a captured CUDA graph; 0: launch by launch
  */
 #define NFHMM_OPT_FB_CHUNK    0
 #define NFHMM_OPT_FB_PRODUCTS 1
+#define NFHMM_OPT_GRAPHS      2
 #define NFHMM_FB_PRODUCTS_SIMT 0
 #define NFHMM_FB_PRODUCTS_TC   1
 NFHMM_API int nfhmm_set_option(nfhmm_ctx *c, int key, long long value);
@@ -340,11 +362,14 @@ NFHMM_API long long nfhmm_kernel_launches(nfhmm_ctx *c);
  *   NFHMM_Q_FB_CHUNK      frames per time chunk of the forward-backward
  *   NFHMM_Q_SWEEPS_DONE   sweeps run since the initial state
  *   NFHMM_Q_DEVICE_BYTES  device memory the context holds
+ *   NFHMM_Q_FRAME_CAPACITY, NFHMM_Q_MAX_JOBS  the batch's room
  */
 #define NFHMM_Q_TENSOR_CORES 0
 #define NFHMM_Q_FB_CHUNK     1
 #define NFHMM_Q_SWEEPS_DONE  2
 #define NFHMM_Q_DEVICE_BYTES 3
+#define NFHMM_Q_FRAME_CAPACITY 4   /* frames the context's frame store holds */
+#define NFHMM_Q_MAX_JOBS       5   /* jobs the context can hold            */
 NFHMM_API int nfhmm_query(nfhmm_ctx *c, int key, long long *value);
 
 #ifdef __cplusplus

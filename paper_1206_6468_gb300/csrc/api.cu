@@ -92,6 +92,7 @@ struct nfhmm_ctx {
   // job tables on the device: job_t0[max_jobs + 1] | chain_c0[max_jobs + 1] |
   // chain_len[max_jobs] | chunk_chain[Cmax]
   int* d_tab = nullptr;
+  int* fb_seg = nullptr;     // 3 * max_jobs ints: segment table of a compaction
   int Cmax = 0;              // chunk capacity of the forward-backward scratch
   void* fb_scratch = nullptr;
   FBArgs fb{};
@@ -108,6 +109,13 @@ struct nfhmm_ctx {
   bool bound_ok = false;      // h_bound holds the bound of the current state
   bool inputs_ok = false;
   bool profiling = false;
+  // one sweep captured as a CUDA graph, per variant (without / with the
+  // bound's terms); valid while the launch configuration stays the same
+  bool use_graphs = true;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  long long graph_key[2] = {-1, -1};
+  int graph_seen[2] = {0, 0};       // sweeps run uncaptured with the current key
+  long long graph_launches[2] = {0, 0};
   StageEvents stages[NFHMM_NUM_STAGES];
   long long launches = 0;
   size_t device_bytes = 0;
@@ -138,10 +146,13 @@ void free_ctx(nfhmm_ctx* c) {
   if (c->s_aux) cudaStreamSynchronize(c->s_aux);
   void* bufs[] = {c->V, c->WM, c->WF, c->A, c->pi, c->alpha, c->w32, c->c, c->Q, c->phi,
                   c->dhat, c->wts, c->sep_tmp, c->v, c->bpart, c->frame_terms, c->logZ,
-                  c->bound_dev, c->err, c->ktab, c->fb_scratch, c->d_tab, c->fterm};
+                  c->bound_dev, c->err, c->ktab, c->fb_scratch, c->d_tab, c->fterm,
+                  c->fb_seg};
   for (void* p : bufs)
     if (p) cudaFree(p);
   tc_free(c->tc);
+  for (auto& g : c->graph)
+    if (g) cudaGraphExecDestroy(g);
   if (c->h_bound) cudaFreeHost(c->h_bound);
   if (c->h_err) cudaFreeHost(c->h_err);
   for (auto& s : c->stages) {
@@ -360,13 +371,13 @@ int load_model(nfhmm_ctx* c, const float* W, const float* A, const float* pi, in
   return NFHMM_OK;
 }
 
-// Copy the spectrogram rows of frames [t0, t0 + T) into the frame store,
-// validate them and set those frames' initial state: z-hat from equal
-// weights (w = 1 through the FP32 contractions) and d-hat from init_mode.
-// The range holds n jobs of frames[0..n) frames (the prior marginals restart
-// at each).  Queued on s_main.
-int load_frames(nfhmm_ctx* c, int t0, int T, const float* V, int on_device, const int* frames,
-                int n) {
+// Copy the spectrograms of n jobs (frames[j] rows from Vs[j]) into frames
+// [t0, t0 + T) of the frame store, back to back, validate them and set those
+// frames' initial state: z-hat from equal weights (w = 1 through the FP32
+// contractions) and d-hat from init_mode (the prior marginals restart at
+// every job).  Queued on s_main.
+int load_frames(nfhmm_ctx* c, int t0, int T, const float* const* Vs, int on_device,
+                const int* frames, int n) {
   const nfhmm_dims& d = c->d;
   const size_t Mp = c->Mp, Fp = c->Fp, N = d.N;
   cudaStream_t st = c->s_main;
@@ -376,8 +387,9 @@ int load_frames(nfhmm_ctx* c, int t0, int T, const float* V, int on_device, cons
   CK(cudaMemsetAsync(c->c + (size_t)t0 * Mp, 0, (size_t)T * Mp * 4, st));
   CK(cudaMemsetAsync(c->alpha + (size_t)t0 * Mp, 0, (size_t)T * Mp * 4, st));
   CK(cudaMemsetAsync(c->bpart + (size_t)t0 * c->nbpart, 0, (size_t)T * c->nbpart * 8, st));
-  CK(cudaMemcpy2DAsync(c->V + (size_t)t0 * Fp, Fp * 4, V, (size_t)d.F * 4, (size_t)d.F * 4, T,
-                       kind, st));
+  for (int j = 0, t = t0; j < n; t += frames[j], ++j)
+    CK(cudaMemcpy2DAsync(c->V + (size_t)t * Fp, Fp * 4, Vs[j], (size_t)d.F * 4, (size_t)d.F * 4,
+                         frames[j], kind, st));
   stage_begin(c, NFHMM_STAGE_INIT, st);
   launch_validate(c->V + (size_t)t0 * Fp, T, d.F, c->Fp, c->WM, c->M, c->A, c->pi, d.S, d.N,
                   c->err, st);
@@ -474,9 +486,9 @@ int commit_jobs(nfhmm_ctx* c) {
   return NFHMM_OK;
 }
 
-// Append jobs of the given frame counts, their spectrograms back to back in
-// V.  Validates (synchronises); on failure nothing is added.
-int add_jobs(nfhmm_ctx* c, int n, const int* frames, const float* V, int on_device,
+// Append n jobs (frames[j] frames, spectrogram Vs[j]).  Validates
+// (synchronises once); on failure nothing is added.
+int add_jobs(nfhmm_ctx* c, int n, const int* frames, const float* const* Vs, int on_device,
              long long* ids) {
   long long total = 0;
   for (int j = 0; j < n; ++j) {
@@ -492,7 +504,7 @@ int add_jobs(nfhmm_ctx* c, int n, const int* frames, const float* V, int on_devi
   int rc = enter(c);
   if (rc) return rc;
   const int t0 = c->T_active;
-  rc = load_frames(c, t0, (int)total, V, on_device, frames, n);
+  rc = load_frames(c, t0, (int)total, Vs, on_device, frames, n);
   if (rc) return rc;
   rc = sync_check(c);
   if (rc) return rc;
@@ -509,34 +521,68 @@ int add_jobs(nfhmm_ctx* c, int n, const int* frames, const float* V, int on_devi
   return leave(c);
 }
 
-// Remove job j and move the jobs after it down over its frames (their
-// persistent state: V, counts, d-hat, v; staged through scratch buffers that
-// the next sweep rewrites anyway).
-int remove_job(nfhmm_ctx* c, int j) {
-  const Job gone = c->jobs[j];
+// Remove the jobs whose flags are set and move the others down over the
+// freed frames (their persistent state: V, counts, d-hat, v).  The frames
+// from the first removed job on are copied to scratch buffers that the next
+// sweep rewrites anyway (Q, alpha-hat, phi-hat, the bound's frame terms) and
+// gathered back by one kernel.
+int remove_jobs(nfhmm_ctx* c, const std::vector<char>& gone) {
   const nfhmm_dims& d = c->d;
   const size_t Mp = c->Mp, Fp = c->Fp, N = d.N, S = d.S, Tc = d.T;
-  const int src = gone.t0 + gone.T, tail = c->T_active - src;
+  size_t first = 0;
+  while (first < c->jobs.size() && !gone[first]) ++first;
+  if (first == c->jobs.size()) return NFHMM_OK;
+  const int base = c->jobs[first].t0, span = c->T_active - base;
+  std::vector<int> seg;   // (destination first frame, source offset in the copy, frames)
+  std::vector<Job> kept(c->jobs.begin(), c->jobs.begin() + first);
+  int t = base;
+  for (size_t j = first; j < c->jobs.size(); ++j) {
+    if (gone[j]) continue;
+    Job q = c->jobs[j];
+    seg.push_back(t);
+    seg.push_back(q.t0 - base);
+    seg.push_back(q.T);
+    q.t0 = t;
+    t += q.T;
+    kept.push_back(q);
+  }
   int rc = enter(c);
   if (rc) return rc;
   cudaStream_t st = c->s_main;
-  const cudaMemcpyKind dd = cudaMemcpyDeviceToDevice;
-  if (tail > 0) {
-    const int dst = gone.t0;
-    CK(cudaMemcpyAsync(c->Q, c->V + src * Fp, tail * Fp * 4, dd, st));
-    CK(cudaMemcpyAsync(c->V + dst * Fp, c->Q, tail * Fp * 4, dd, st));
-    CK(cudaMemcpyAsync(c->alpha, c->c + src * Mp, tail * Mp * 4, dd, st));
-    CK(cudaMemcpyAsync(c->c + dst * Mp, c->alpha, tail * Mp * 4, dd, st));
-    CK(cudaMemcpy2DAsync(c->phi, Tc * N * 4, c->dhat + src * N, Tc * N * 4, tail * N * 4, S, dd,
+  if (!seg.empty()) {
+    const cudaMemcpyKind dd = cudaMemcpyDeviceToDevice;
+    CK(cudaMemcpyAsync(c->Q, c->V + base * Fp, span * Fp * 4, dd, st));
+    CK(cudaMemcpyAsync(c->alpha, c->c + base * Mp, span * Mp * 4, dd, st));
+    CK(cudaMemcpy2DAsync(c->phi, Tc * N * 4, c->dhat + base * N, Tc * N * 4, span * N * 4, S, dd,
                          st));
-    CK(cudaMemcpy2DAsync(c->dhat + dst * N, Tc * N * 4, c->phi, Tc * N * 4, tail * N * 4, S, dd,
-                         st));
-    CK(cudaMemcpyAsync(c->frame_terms, c->v + src, tail * 8, dd, st));
-    CK(cudaMemcpyAsync(c->v + dst, c->frame_terms, tail * 8, dd, st));
+    CK(cudaMemcpyAsync(c->frame_terms, c->v + base, span * 8, dd, st));
+    // the segment table rides in the chunk-table region, rewritten below
+    CK(cudaMemcpyAsync(c->fb_seg, seg.data(), seg.size() * sizeof(int), cudaMemcpyHostToDevice,
+                       st));
+    FrameMove m{};
+    m.nseg = (int)seg.size() / 3;
+    m.seg = c->fb_seg;
+    m.frames = t - base;
+    m.base = base;
+    m.Tc = d.T;
+    m.Fp = c->Fp;
+    m.Mp = c->Mp;
+    m.SN = d.S * d.N;
+    m.N = d.N;
+    m.S = d.S;
+    m.V = c->V;
+    m.Vs = c->Q;
+    m.c = c->c;
+    m.cs = c->alpha;
+    m.dhat = c->dhat;
+    m.ds = c->phi;
+    m.v = c->v;
+    m.vs = c->frame_terms;
+    launch_move_frames(m, st);
+    c->launches += 1;
   }
-  c->jobs.erase(c->jobs.begin() + j);
-  for (size_t q = j; q < c->jobs.size(); ++q) c->jobs[q].t0 -= gone.T;
-  c->T_active -= gone.T;
+  c->jobs.swap(kept);
+  c->T_active = t;
   rc = commit_jobs(c);
   if (rc) return rc;
   return leave(c);
@@ -648,6 +694,7 @@ int create_ctx(nfhmm_ctx** out, const nfhmm_dims* dp, int max_jobs, const float*
   DMALLOC(c->bpart, T * c->nbpart * 8);
   DMALLOC(c->frame_terms, T * 8);
   DMALLOC(c->fterm, T * 16);
+  DMALLOC(c->fb_seg, (size_t)3 * max_jobs * sizeof(int));
   DMALLOC(c->logZ, S * max_jobs * 8);
   DMALLOC(c->bound_dev, (max_jobs + 1) * 8);
   DMALLOC(c->err, 4);
@@ -697,9 +744,62 @@ int create_ctx(nfhmm_ctx** out, const nfhmm_dims* dp, int max_jobs, const float*
   return NFHMM_OK;
 }
 
-// Run n sweeps over every job; with want_bound, the bounds of the final
-// state into h_bound (synchronises).
-int sweep_impl(nfhmm_ctx* c, int n_sweeps, bool want_bound) {
+// The launch configuration a captured sweep depends on.
+long long graph_key_of(const nfhmm_ctx* c) {
+  long long k = c->T_active;
+  k = k * 1000003 + c->fb.C;
+  k = k * 1048583 + c->fb.nchains;
+  k = k * 131 + c->fb.L;
+  k = k * 3 + c->fb.products;
+  return k;
+}
+
+// One sweep: from a captured CUDA graph once the same configuration has run
+// uncaptured once (profiling off), else launch by launch.
+int sweep_once(nfhmm_ctx* c, bool want_bpart) {
+  const int v = want_bpart ? 1 : 0;
+  if (!c->use_graphs || c->profiling || c->T_active == 0) return one_sweep(c, want_bpart);
+  const long long key = graph_key_of(c);
+  if (c->graph_key[v] != key) {
+    if (c->graph[v]) cudaGraphExecDestroy(c->graph[v]);
+    c->graph[v] = nullptr;
+    c->graph_key[v] = key;
+    c->graph_seen[v] = 0;
+  }
+  if (!c->graph[v]) {
+    if (c->graph_seen[v]++ == 0) return one_sweep(c, want_bpart);   // warm: first launches
+    const long long l0 = c->launches;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(c->s_main, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      c->use_graphs = false;
+      return one_sweep(c, want_bpart);
+    }
+    const int rc = one_sweep(c, want_bpart);
+    const cudaError_t e = cudaStreamEndCapture(c->s_main, &g);
+    if (rc || e != cudaSuccess || !g ||
+        cudaGraphInstantiate(&c->graph[v], g, 0) != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      c->graph[v] = nullptr;
+      c->use_graphs = false;
+      c->launches = l0;
+      if (rc) return rc;
+      return one_sweep(c, want_bpart);   // capture unavailable: launch directly
+    }
+    cudaGraphDestroy(g);
+    c->graph_launches[v] = c->launches - l0;
+    c->launches = l0;
+  }
+  CK(cudaGraphLaunch(c->graph[v], c->s_main));
+  c->launches += c->graph_launches[v];
+  return NFHMM_OK;
+}
+
+// Run n sweeps over every job; with want_bound, the last one also forms the
+// bound's per-frame terms, and with finish the bounds of the final state go
+// into h_bound (synchronises).
+int sweep_impl(nfhmm_ctx* c, int n_sweeps, bool want_bound, bool finish = true) {
   if (n_sweeps == 0 && want_bound && !c->have_alpha)
     return fail(NFHMM_ESTATE, "no sweep has run over the current jobs: the bound is defined "
                               "after a sweep");
@@ -708,7 +808,7 @@ int sweep_impl(nfhmm_ctx* c, int n_sweeps, bool want_bound) {
   if (rc) return rc;
   for (int i = 0; i < n_sweeps; ++i) {
     const bool last = i == n_sweeps - 1;
-    rc = one_sweep(c, want_bound && last);
+    rc = sweep_once(c, want_bound && last);
     if (rc) return rc;
   }
   if (n_sweeps > 0) {
@@ -719,7 +819,7 @@ int sweep_impl(nfhmm_ctx* c, int n_sweeps, bool want_bound) {
     c->fterm_ok = want_bound;
     c->bound_ok = false;
   }
-  if (want_bound) {
+  if (want_bound && finish) {
     if (!c->bpart_ok) {
       rc = contract(c, true, false, 0, c->T_active);
       if (rc) return rc;
@@ -743,7 +843,7 @@ int nfhmm_vi_init(nfhmm_ctx** out, const nfhmm_dims* dp, const float* V, const f
   int rc = create_ctx(&c, dp, 1, W, A, pi, inputs_on_device, cuda_stream);
   if (rc) return rc;
   const int T = dp->T;
-  rc = add_jobs(c, 1, &T, V, inputs_on_device, nullptr);
+  rc = add_jobs(c, 1, &T, &V, inputs_on_device, nullptr);
   if (rc) {
     free_ctx(c);
     return rc;
@@ -768,7 +868,9 @@ int nfhmm_vi_init_batch(nfhmm_ctx** out, const nfhmm_dims* dp, int n_jobs, const
   nfhmm_ctx* c = nullptr;
   int rc = create_ctx(&c, dp, n_jobs, W, A, pi, inputs_on_device, cuda_stream);
   if (rc) return rc;
-  rc = add_jobs(c, n_jobs, job_frames, V, inputs_on_device, job_ids);
+  std::vector<const float*> Vs(n_jobs);
+  for (int j = 0, t = 0; j < n_jobs; t += job_frames[j], ++j) Vs[j] = V + (size_t)t * dp->F;
+  rc = add_jobs(c, n_jobs, job_frames, Vs.data(), inputs_on_device, job_ids);
   if (rc) {
     free_ctx(c);
     return rc;
@@ -788,14 +890,32 @@ int nfhmm_batch_create(nfhmm_ctx** out, const nfhmm_dims* dp, int max_jobs, cons
 int nfhmm_batch_add(nfhmm_ctx* c, int T, const float* V, int on_device, long long* job_id) {
   if (!c || !V) return fail(NFHMM_EINVAL, "NULL argument");
   if (need_inputs(c)) return NFHMM_ESTATE;
-  return add_jobs(c, 1, &T, V, on_device, job_id);
+  return add_jobs(c, 1, &T, &V, on_device, job_id);
+}
+
+int nfhmm_batch_add_many(nfhmm_ctx* c, int n, const int* T, const float* const* V, int on_device,
+                         long long* job_ids) {
+  if (!c || !T || !V || n < 0) return fail(NFHMM_EINVAL, "NULL argument or n < 0");
+  if (need_inputs(c)) return NFHMM_ESTATE;
+  for (int j = 0; j < n; ++j)
+    if (!V[j]) return fail(NFHMM_EINVAL, "NULL spectrogram");
+  if (n == 0) return NFHMM_OK;
+  return add_jobs(c, n, T, V, on_device, job_ids);
 }
 
 int nfhmm_batch_remove(nfhmm_ctx* c, long long job_id) {
-  if (!c) return fail(NFHMM_EINVAL, "NULL context");
-  const int j = find_job(c, job_id);
-  if (j < 0) return fail(NFHMM_EINVAL, "no job " + std::to_string(job_id) + " in the batch");
-  return remove_job(c, j);
+  return nfhmm_batch_remove_many(c, 1, &job_id);
+}
+
+int nfhmm_batch_remove_many(nfhmm_ctx* c, int n, const long long* job_ids) {
+  if (!c || (n > 0 && !job_ids) || n < 0) return fail(NFHMM_EINVAL, "NULL argument or n < 0");
+  std::vector<char> gone(c->jobs.size(), 0);
+  for (int i = 0; i < n; ++i) {
+    const int j = find_job(c, job_ids[i]);
+    if (j < 0) return fail(NFHMM_EINVAL, "no job " + std::to_string(job_ids[i]) + " in the batch");
+    gone[j] = 1;
+  }
+  return remove_jobs(c, gone);
 }
 
 int nfhmm_batch_info(nfhmm_ctx* c, int* n_jobs, int* frames_held, long long* ids, int* t0,
@@ -860,6 +980,10 @@ int nfhmm_set_option(nfhmm_ctx* c, int key, long long value) {
       c->fb.products = value == NFHMM_FB_PRODUCTS_TC ? FB_PRODUCTS_TC : FB_PRODUCTS_SIMT;
       return NFHMM_OK;
     }
+    case NFHMM_OPT_GRAPHS: {
+      c->use_graphs = value != 0;
+      return NFHMM_OK;
+    }
     default: return fail(NFHMM_EINVAL, "unknown option key");
   }
 }
@@ -883,7 +1007,10 @@ int nfhmm_vi_reinit(nfhmm_ctx* c, const float* V, const float* W, const float* A
   CK(cudaMemsetAsync(c->err, 0, 4, c->s_main));
   rc = load_model(c, W, A, pi, inputs_on_device);
   if (rc) return rc;
-  rc = load_frames(c, 0, c->T_active, V, inputs_on_device, frames.data(), (int)frames.size());
+  std::vector<const float*> Vs(frames.size());
+  for (size_t j = 0, t = 0; j < frames.size(); t += frames[j], ++j) Vs[j] = V + t * c->d.F;
+  rc = load_frames(c, 0, c->T_active, Vs.data(), inputs_on_device, frames.data(),
+                   (int)frames.size());
   if (rc) return rc;
   rc = sync_check(c);
   if (rc) return rc;
@@ -899,6 +1026,13 @@ int nfhmm_vi_sweep(nfhmm_ctx* c, int n_sweeps, double* bound_out) {
   if (rc) return rc;
   if (bound_out) *bound_out = c->h_bound[c->jobs.size()];
   return NFHMM_OK;
+}
+
+int nfhmm_vi_sweep_async(nfhmm_ctx* c, int n_sweeps, int prepare_bound) {
+  if (!c) return fail(NFHMM_EINVAL, "NULL context");
+  if (need_inputs(c)) return NFHMM_ESTATE;
+  if (n_sweeps < 1) return fail(NFHMM_EINVAL, "n_sweeps must be >= 1");
+  return sweep_impl(c, n_sweeps, prepare_bound != 0, false);
 }
 
 int nfhmm_bound(nfhmm_ctx* c, double* out) {
@@ -1123,6 +1257,8 @@ int nfhmm_query(nfhmm_ctx* c, int key, long long* value) {
     case NFHMM_Q_FB_CHUNK: *value = c->fb.L; return NFHMM_OK;
     case NFHMM_Q_SWEEPS_DONE: *value = c->sweeps_done; return NFHMM_OK;
     case NFHMM_Q_DEVICE_BYTES: *value = (long long)c->device_bytes; return NFHMM_OK;
+    case NFHMM_Q_FRAME_CAPACITY: *value = c->d.T; return NFHMM_OK;
+    case NFHMM_Q_MAX_JOBS: *value = c->max_jobs; return NFHMM_OK;
     default: return fail(NFHMM_EINVAL, "unknown query key");
   }
 }

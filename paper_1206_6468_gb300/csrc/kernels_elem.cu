@@ -407,6 +407,37 @@ void launch_digamma(const float* x, float* psi, float* w, size_t n, cudaStream_t
   k_digamma<<<512, 256, 0, st>>>(x, psi, w, n);
 }
 
+// ------------------------------------------------------ frame compaction
+// One warp per destination frame: find its segment (binary search over the
+// segment table), then copy the frame's V, counts, d-hat and v rows.
+__global__ void k_move_frames(FrameMove m) {
+  const int lane = threadIdx.x & 31;
+  const int f = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (f >= m.frames) return;
+  const int t = m.base + f;
+  int lo = 0, hi = m.nseg - 1;
+  while (lo < hi) {   // last segment with dst first frame <= t
+    const int mid = (lo + hi + 1) >> 1;
+    if (m.seg[3 * mid] <= t) lo = mid; else hi = mid - 1;
+  }
+  const int src = m.seg[3 * lo + 1] + (t - m.seg[3 * lo]);   // offset in the copy
+  const float4* vs = reinterpret_cast<const float4*>(m.Vs + (size_t)src * m.Fp);
+  float4* vd = reinterpret_cast<float4*>(m.V + (size_t)t * m.Fp);
+  for (int i = lane; i < m.Fp / 4; i += 32) vd[i] = vs[i];
+  const float4* cs = reinterpret_cast<const float4*>(m.cs + (size_t)src * m.Mp);
+  float4* cd = reinterpret_cast<float4*>(m.c + (size_t)t * m.Mp);
+  for (int i = lane; i < m.Mp / 4; i += 32) cd[i] = cs[i];
+  for (int i = lane; i < m.SN; i += 32) {
+    const int s = i / m.N, n = i - s * m.N;
+    m.dhat[((size_t)s * m.Tc + t) * m.N + n] = m.ds[((size_t)s * m.Tc + src) * m.N + n];
+  }
+  if (lane == 0) m.v[t] = m.vs[src];
+}
+void launch_move_frames(const FrameMove& m, cudaStream_t st) {
+  if (m.frames <= 0 || m.nseg <= 0) return;
+  k_move_frames<<<(m.frames + 7) / 8, 256, 0, st>>>(m);
+}
+
 // --------------------------------------------------------- prior marginals
 // dhat[s][t0] = pi_s, dhat[s][t] = dhat[s][t-1] A_s over each job's frames
 // [t0, t1) (one block per (source, job)).  With a null job table there is one

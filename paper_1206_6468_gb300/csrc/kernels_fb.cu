@@ -137,11 +137,10 @@ __device__ __forceinline__ uint32_t sw128_off(int r, int k, int atom_bytes) {
 }
 
 template <int NP>
-__global__ void __launch_bounds__(256, 1) k_fb_products(FBArgs a) {
+__global__ void __launch_bounds__(128, 1) k_fb_products(FBArgs a) {
   using namespace tc;
   using Cfg = ProdCfg<NP>;
-  constexpr int NOUT = Cfg::NOUT;
-  constexpr int HC = NOUT / 2;   // columns per thread: two warps share each TMEM lane quarter
+  constexpr int NOUT = Cfg::NOUT;   // columns per row, a multiple of 16
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -152,8 +151,7 @@ __global__ void __launch_bounds__(256, 1) k_fb_products(FBArgs a) {
   float* e = reinterpret_cast<float*>(b_lo + Cfg::B_BYTES);   // RCH x L x NP
   double* rhod = reinterpret_cast<double*>(e + Cfg::RCH * a.L * NP);  // 128
   double* msum = rhod + 128;                                   // RCH
-  float* pmax = reinterpret_cast<float*>(msum + Cfg::RCH);     // 2 x 128
-  uint64_t* bar = reinterpret_cast<uint64_t*>(pmax + 256);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(msum + Cfg::RCH);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
 
   const int N = a.N, L = a.L, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -178,15 +176,14 @@ __global__ void __launch_bounds__(256, 1) k_fb_products(FBArgs a) {
     *reinterpret_cast<float*>(b_hi + off) = h;
     *reinterpret_cast<float*>(b_lo + off) = tf32_hi(v - h);
   }
-  // emissions of the tile's chunks
+  // emissions of the tile's chunks: exp(phi - max over states), per frame
   for (int q = 0; q < Cfg::RCH; ++q) {
     const int c = cbase + q;
     if (c >= a.C) break;
     const ChunkInfo ci = chunk_info(a, c);
-    const int t0 = ci.t0, len = ci.len;
-    const float* src = a.phi + ((size_t)s * a.T + t0) * N;
+    const float* src = a.phi + ((size_t)s * a.T + ci.t0) * N;
     float* eq = e + q * L * NP;
-    for (int i = tid; i < len * N; i += blockDim.x) {
+    for (int i = tid; i < ci.len * N; i += blockDim.x) {
       const int f = i / N, n = i - f * N;
       eq[f * NP + n] = src[i];
     }
@@ -198,7 +195,7 @@ __global__ void __launch_bounds__(256, 1) k_fb_products(FBArgs a) {
     const int len = chunk_info(a, c).len;
     float* eq = e + q * L * NP;
     double ms = 0.0;
-    for (int f = warp; f < len; f += 8) {
+    for (int f = warp; f < len; f += 4) {
       float* row = eq + f * NP;
       const float x0 = lane < N ? row[lane] : -INFINITY;
       const float x1 = lane + 32 < N ? row[lane + 32] : -INFINITY;
@@ -210,11 +207,7 @@ __global__ void __launch_bounds__(256, 1) k_fb_products(FBArgs a) {
     }
     if (lane == 0) rhod[warp] = ms;
     __syncthreads();
-    if (tid == 0) {
-      double t = 0.0;
-      for (int w = 0; w < 8; ++w) t += rhod[w];
-      msum[q] = t;
-    }
+    if (tid == 0) msum[q] = rhod[0] + rhod[1] + rhod[2] + rhod[3];
     __syncthreads();
   }
   tc_fence_before();
@@ -222,57 +215,52 @@ __global__ void __launch_bounds__(256, 1) k_fb_products(FBArgs a) {
   tc_fence_after();
   const uint32_t tmem = *tslot;
 
-  // this thread: row r (chunk q, basis state i), columns [j0, j0 + HC)
-  const int half = warp >> 2;
-  const int r = (warp & 3) * 32 + lane;
-  const int j0 = half * HC;
+  // this thread: row r of the tile = TMEM lane r (chunk q, basis state i)
+  const int r = tid;
   const int q = r / NP, i = r - (r / NP) * NP;
   const int c = cbase + q;
   const bool live = q < Cfg::RCH && c < a.C && i < N;
   const ChunkInfo ci = (q < Cfg::RCH && c < a.C) ? chunk_info(a, c) : ChunkInfo{0, 0, 0, false};
   const int len = live ? ci.len : 0;
   const float* eq = e + (q < Cfg::RCH ? q : 0) * L * NP;
-  float cur[HC];
+  float cur[NOUT];
   ScaleAcc sc;
   bool zero_row = false;   // once zero, a row stays zero: its scale is then -inf
+  unsigned bad = 0;
 #pragma unroll
-  for (int u = 0; u < HC; ++u) {
-    const int j = j0 + u;
+  for (int j = 0; j < NOUT; ++j) {
     float v = 0.f;
     if (live && j < N) v = ci.first ? (j == i ? eq[j] : 0.f) : Ag[i * N + j] * eq[j];
-    cur[u] = v;
+    cur[j] = v;
   }
-  // rescale the row by its maximum (both halves agree through shared memory)
-  // and write it, split into tf32 hi/lo, into the swizzled operand tile
+  // rescale the row by its maximum and write it, split into tf32 hi/lo,
+  // into the swizzled operand tile (the thread owns the whole row)
   auto normalise_and_store = [&]() {
     float m = 0.f;
 #pragma unroll
-    for (int u = 0; u < HC; ++u) m = fmaxf(m, cur[u]);
-    pmax[half * 128 + r] = m;
-    __syncthreads();
-    m = fmaxf(pmax[r], pmax[128 + r]);
+    for (int j = 0; j < NOUT; ++j) m = fmaxf(m, cur[j]);
     if (live) {
       // an all-zero row is legitimate (state i cannot start this chunk)
       if (!isfinite(m)) {
-        if (half == 0) atomicOr(a.err, ERR_FB_ZERO);
+        bad = 1;
         m = 0.f;
       }
       if (m == 0.f) zero_row = true;
-      const float f = renorm_factor(m);
+      const float g = renorm_factor(m);
 #pragma unroll
-      for (int u = 0; u < HC; ++u) cur[u] *= f;
+      for (int j = 0; j < NOUT; ++j) cur[j] *= g;
       sc.mul(removed_scale(m));
     }
 #pragma unroll
-    for (int cc = 0; cc < HC / 4; ++cc) {
-      if (j0 + 4 * cc < NP) {
+    for (int cc = 0; cc < NOUT / 4; ++cc) {
+      if (4 * cc < NP) {
         float h[4], l[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           h[u] = tf32_hi(cur[4 * cc + u]);
           l[u] = tf32_hi(cur[4 * cc + u] - h[u]);
         }
-        const uint32_t off = sw128_off(r, j0 + 4 * cc, 128 * 128);
+        const uint32_t off = sw128_off(r, 4 * cc, 128 * 128);
         *reinterpret_cast<float4*>(rows_hi + off) = make_float4(h[0], h[1], h[2], h[3]);
         *reinterpret_cast<float4*>(rows_lo + off) = make_float4(l[0], l[1], l[2], l[3]);
       }
@@ -283,12 +271,13 @@ __global__ void __launch_bounds__(256, 1) k_fb_products(FBArgs a) {
   constexpr uint32_t ID = idesc<KIND_TF32X3>(128, NOUT);
   const uint32_t rh = smem_u32(rows_hi), rl = smem_u32(rows_lo);
   const uint32_t bh = smem_u32(b_hi), bl = smem_u32(b_lo);
-  const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)j0;
+  const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
   bool ok = true;
   for (int f = 1; f < L; ++f) {
     fence_proxy_async_smem();   // the operand rows written above, to the tensor core
     tc_fence_before();
-    __syncthreads();
+    // every row written; and the decision to stop is the same in every thread
+    if (__syncthreads_or(!ok)) break;
     if (tid == 0) {
       tc_fence_after();
 #pragma unroll
@@ -304,61 +293,55 @@ __global__ void __launch_bounds__(256, 1) k_fb_products(FBArgs a) {
     if (!mbar_wait(bar, (f - 1) & 1)) {
       ok = false;
       if (lane == 0) atomicOr(a.err, ERR_TIMEOUT);
+      continue;   // the next barrier stops every thread
     }
-    // the decision to stop must be the same in every thread (barriers follow)
-    ok = !__syncthreads_or(!ok);
     tc_fence_after();
-    float y[HC], x[HC];
+    uint32_t yr[NOUT / 16][16], xr[NOUT / 16][16];
 #pragma unroll
-    for (int cc = 0; cc + 16 <= HC; cc += 16) {
-      tmem_ld16(taddr + cc, *reinterpret_cast<float(*)[16]>(&y[cc]));
-      tmem_ld16(taddr + NOUT + cc, *reinterpret_cast<float(*)[16]>(&x[cc]));
+    for (int cc = 0; cc < NOUT / 16; ++cc) {
+      tmem_ld16_nw(taddr + 16 * cc, yr[cc]);
+      tmem_ld16_nw(taddr + NOUT + 16 * cc, xr[cc]);
     }
-    if (HC % 16 == 8) {
-      tmem_ld8(taddr + (HC - 8), &y[HC - 8]);
-      tmem_ld8(taddr + NOUT + (HC - 8), &x[HC - 8]);
-    }
+    tmem_wait_ld();
     if (live && f < len) {
-      const float* ef = eq + f * NP + j0;
+      const float* ef = eq + f * NP;
 #pragma unroll
-      for (int u = 0; u < HC; u += 4) {
-        if (j0 + u < NP) {
-          const float4 e4 = *reinterpret_cast<const float4*>(ef + u);
-          cur[u] = (y[u] + x[u]) * e4.x;
-          cur[u + 1] = (y[u + 1] + x[u + 1]) * e4.y;
-          cur[u + 2] = (y[u + 2] + x[u + 2]) * e4.z;
-          cur[u + 3] = (y[u + 3] + x[u + 3]) * e4.w;
+      for (int j = 0; j < NOUT; j += 4) {
+        if (j < NP) {
+          const float4 e4 = *reinterpret_cast<const float4*>(ef + j);
+          const float ev[4] = {e4.x, e4.y, e4.z, e4.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            cur[j + u] = (__uint_as_float(yr[(j + u) >> 4][(j + u) & 15]) +
+                          __uint_as_float(xr[(j + u) >> 4][(j + u) & 15])) * ev[u];
         } else {
-          cur[u] = cur[u + 1] = cur[u + 2] = cur[u + 3] = 0.f;
+          cur[j] = cur[j + 1] = cur[j + 2] = cur[j + 3] = 0.f;
         }
       }
     }
     normalise_and_store();
-    if (!ok) break;
   }
+  if (bad) atomicOr(a.err, ERR_FB_ZERO);
   // common scale for the chunk: P_c = exp(rho_max) * (rows scaled to it)
   const double lr = zero_row ? -INFINITY : sc.log();
-  if (half == 0) rhod[r] = live ? lr : -INFINITY;
+  rhod[r] = live ? lr : -INFINITY;
   __syncthreads();
   if (q < Cfg::RCH && c < a.C && i < NP) {
     double rmax = -INFINITY;
     for (int ii = 0; ii < N; ++ii) rmax = fmax(rmax, rhod[q * NP + ii]);
     // rmax = -inf only if every row of the chunk vanished (flagged by the scan)
-    const float f = (live && rmax > -INFINITY) ? (float)exp(lr - rmax) : 0.f;
+    const float g = (live && rmax > -INFINITY) ? (float)exp(lr - rmax) : 0.f;
     if (rmax == -INFINITY) rmax = 0.0;
     const size_t base = ((size_t)s * a.C + c) * NP * NP;
     float* Pg = a.P + base;
     float* PTg = a.PT + base;
 #pragma unroll
-    for (int u = 0; u < HC; ++u) {
-      const int j = j0 + u;
-      if (j < NP) {
-        const float v = live ? cur[u] * f : 0.f;
-        Pg[i * NP + j] = v;
-        PTg[j * NP + i] = v;
-      }
+    for (int j = 0; j < NP; ++j) {
+      const float v = live ? cur[j] * g : 0.f;
+      Pg[i * NP + j] = v;
+      PTg[j * NP + i] = v;
     }
-    if (i == 0 && half == 0) a.Plog[(size_t)s * a.C + c] = msum[q] + rmax;
+    if (i == 0) a.Plog[(size_t)s * a.C + c] = msum[q] + rmax;
   }
   tc_fence_before();
   __syncthreads();
@@ -857,7 +840,7 @@ static cudaError_t launch_np(const FBArgs& a, cudaStream_t st) {
   using Cfg = ProdCfg<NP>;
   const int rc = replay_chunks(NP, a.L);
   if (a.products == FB_PRODUCTS_TC)
-    k_fb_products<NP><<<dim3((a.C + Cfg::RCH - 1) / Cfg::RCH, a.S), 256,
+    k_fb_products<NP><<<dim3((a.C + Cfg::RCH - 1) / Cfg::RCH, a.S), 128,
                         smem_products<NP>(a.L), st>>>(a);
   else
     k_fb_products_simt<NP><<<dim3(a.C, a.S), SimtCfg<NP>::WARPS * 32,

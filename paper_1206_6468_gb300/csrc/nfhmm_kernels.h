@@ -138,6 +138,20 @@ void launch_sep_mask(const float* V, int Fp, float* out, int S, int T, int F, cu
 // Digamma test entry.
 void launch_digamma(const float* x, float* psi, float* w, size_t n, cudaStream_t st);
 
+// Compaction of a batch's frame store: destination frames [base, base +
+// frames) come from segments (dst first frame, source offset, length) of a
+// copy of the old frames [base, ...) held in the *s buffers.
+struct FrameMove {
+  int nseg;
+  const int* seg;   // 3 * nseg
+  int frames, base, Tc, Fp, Mp, SN, N, S;
+  float* V; const float* Vs;        // Fp per frame
+  float* c; const float* cs;        // Mp per frame
+  float* dhat; const float* ds;     // S x (Tc frames x N)
+  double* v; const double* vs;
+};
+void launch_move_frames(const FrameMove& m, cudaStream_t st);
+
 // Prior marginals dhat[s][t] = pi A^(t - t0(job)) restarted at every job
 // (sequential in t, one block per (source, job)).  job_t0: njobs + 1 device
 // offsets, or null for the single job [t_begin, t_end).  T: frame stride.

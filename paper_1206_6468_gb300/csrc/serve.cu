@@ -64,6 +64,15 @@ int nfhmm_serve(nfhmm_ctx** batches, int n_batches, const nfhmm_request* reqs, i
   std::vector<std::deque<int>> queue(n_batches);
   for (int r : order) queue[reqs[r].model].push_back(r);
   std::vector<std::vector<Active>> active(n_batches);
+  std::vector<int> capacity_of(n_batches), max_jobs_of(n_batches);
+  for (int b = 0; b < n_batches; ++b) {
+    long long cap = 0, mj = 0;
+    int rc = nfhmm_query(batches[b], NFHMM_Q_FRAME_CAPACITY, &cap);
+    if (!rc) rc = nfhmm_query(batches[b], NFHMM_Q_MAX_JOBS, &mj);
+    if (rc) return rc;
+    capacity_of[b] = (int)cap;
+    max_jobs_of[b] = (int)mj;
+  }
 
   using clk = std::chrono::steady_clock;
   const auto t_start = clk::now();
@@ -72,31 +81,57 @@ int nfhmm_serve(nfhmm_ctx** batches, int n_batches, const nfhmm_request* reqs, i
   int done = 0;
   std::vector<double> bounds;
   while (done < n_reqs) {
-    // admission: in arrival order while the batch has room
+    // admission: in arrival order while the batch has room, all of a
+    // batch's newcomers in one call
     for (int b = 0; b < n_batches; ++b) {
+      int nj = 0, held = 0;
+      int rc = nfhmm_batch_info(batches[b], &nj, &held, nullptr, nullptr, nullptr, nullptr);
+      if (rc) return rc;
+      const int cap_jobs = max_jobs_of[b], cap_frames = capacity_of[b];
+      std::vector<int> take;
+      std::vector<int> fr;
+      std::vector<const float*> vs;
       while (!queue[b].empty() && arrived(queue[b].front())) {
         const int r = queue[b].front();
-        long long id = -1;
-        const int rc = nfhmm_batch_add(batches[b], reqs[r].T, reqs[r].V, 0, &id);
-        if (rc == NFHMM_EFULL) {
-          if (active[b].empty()) {   // can never fit: fail the request
-            results[r].status = rc;
-            results[r].done_s = now();
-            queue[b].pop_front();
-            ++done;
-            continue;
-          }
-          break;
-        }
-        queue[b].pop_front();
-        if (rc) {
-          results[r].status = rc;
+        if (reqs[r].T > cap_frames) {   // can never fit
+          results[r].status = NFHMM_EFULL;
           results[r].done_s = now();
+          queue[b].pop_front();
           ++done;
           continue;
         }
-        results[r].admit_s = now();
-        active[b].push_back(Active{r, id, 0.0, 0});
+        if (nj + (int)take.size() + 1 > cap_jobs || held + reqs[r].T > cap_frames) break;
+        held += reqs[r].T;
+        take.push_back(r);
+        fr.push_back(reqs[r].T);
+        vs.push_back(reqs[r].V);
+        queue[b].pop_front();
+      }
+      if (take.empty()) continue;
+      std::vector<long long> ids(take.size());
+      rc = nfhmm_batch_add_many(batches[b], (int)take.size(), fr.data(), vs.data(), 0, ids.data());
+      if (rc == NFHMM_EINVAL) {
+        // a bad spectrogram among them: add one by one to find it
+        for (size_t i = 0; i < take.size(); ++i) {
+          const int r = take[i];
+          long long id = -1;
+          const int rc1 = nfhmm_batch_add(batches[b], reqs[r].T, reqs[r].V, 0, &id);
+          if (rc1) {
+            results[r].status = rc1;
+            results[r].done_s = now();
+            ++done;
+            continue;
+          }
+          results[r].admit_s = now();
+          active[b].push_back(Active{r, id, 0.0, 0});
+        }
+        continue;
+      }
+      if (rc) return rc;
+      const double ta = now();
+      for (size_t i = 0; i < take.size(); ++i) {
+        results[take[i]].admit_s = ta;
+        active[b].push_back(Active{take[i], ids[i], 0.0, 0});
       }
     }
     bool any = false;
@@ -111,17 +146,21 @@ int nfhmm_serve(nfhmm_ctx** batches, int n_batches, const nfhmm_request* reqs, i
       if (wait > 0) std::this_thread::sleep_for(std::chrono::duration<double>(wait));
       continue;
     }
-    // one sweep of every non-empty batch, with per-job bounds
+    // one sweep of every non-empty batch, all in flight together, then the
+    // per-job bounds of each
     for (int b = 0; b < n_batches; ++b) {
       if (active[b].empty()) continue;
-      double total = 0.0;
-      int rc = nfhmm_vi_sweep(batches[b], 1, &total);
+      const int rc = nfhmm_vi_sweep_async(batches[b], 1, 1);
       if (rc) return rc;
+    }
+    for (int b = 0; b < n_batches; ++b) {
+      if (active[b].empty()) continue;
       bounds.assign(active[b].size(), 0.0);
-      rc = nfhmm_job_bounds(batches[b], bounds.data());
+      int rc = nfhmm_job_bounds(batches[b], bounds.data());
       if (rc) return rc;
       // job order in the batch is admission order, as in active[b]
       std::vector<Active> keep;
+      std::vector<long long> leaving;
       for (size_t j = 0; j < active[b].size(); ++j) {
         Active& a = active[b][j];
         a.sweeps += 1;
@@ -141,11 +180,14 @@ int nfhmm_serve(nfhmm_ctx** batches, int n_batches, const nfhmm_request* reqs, i
           res.status = NFHMM_OK;
           res.done_s = now();
           ++done;
-          rc = nfhmm_batch_remove(batches[b], a.id);
-          if (rc) return rc;
+          leaving.push_back(a.id);
         } else {
           keep.push_back(a);
         }
+      }
+      if (!leaving.empty()) {
+        rc = nfhmm_batch_remove_many(batches[b], (int)leaving.size(), leaving.data());
+        if (rc) return rc;
       }
       active[b].swap(keep);
     }

@@ -28,8 +28,9 @@ FP32, BF16, FP32_SIMT = 0, 1, 2
 INIT_UNIFORM, INIT_PRIOR = 0, 1
 SEP_MEAN, SEP_EXPECTATION = 0, 1
 STAGES = {"weights": 0, "gemm1": 1, "gemm2": 2, "fb": 3, "bound": 4, "init": 5}
-QUERIES = {"tensor_cores": 0, "fb_chunk": 1, "sweeps_done": 2, "device_bytes": 3}
-OPTIONS = {"fb_chunk": 0, "fb_products": 1}
+QUERIES = {"tensor_cores": 0, "fb_chunk": 1, "sweeps_done": 2, "device_bytes": 3,
+           "frame_capacity": 4, "max_jobs": 5}
+OPTIONS = {"fb_chunk": 0, "fb_products": 1, "graphs": 2}
 FB_PRODUCTS = {"simt": 0, "tc": 1}
 PRECISIONS = {"fp32": FP32, "bf16": BF16, "fp32_simt": FP32_SIMT}
 
@@ -85,6 +86,9 @@ _sigs = {
                                 _vp]),
     "nfhmm_batch_add": (_i, [_vp, _i, _vp, _i, ctypes.POINTER(ctypes.c_longlong)]),
     "nfhmm_batch_remove": (_i, [_vp, ctypes.c_longlong]),
+    "nfhmm_batch_add_many": (_i, [_vp, _i, _vp, _vp, _i, _vp]),
+    "nfhmm_batch_remove_many": (_i, [_vp, _i, _vp]),
+    "nfhmm_vi_sweep_async": (_i, [_vp, _i, _i]),
     "nfhmm_batch_info": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), _vp, _vp, _vp, _vp]),
     "nfhmm_job_bounds": (_i, [_vp, _vp]),
     "nfhmm_job_posteriors": (_i, [_vp, ctypes.c_longlong, _vp, _i]),
@@ -253,6 +257,10 @@ class VIContext:
         _check(_lib.nfhmm_vi_sweep(self._h, n, None), "nfhmm_vi_sweep")
         return None
 
+    def sweep_async(self, n: int = 1, prepare_bound: bool = False):
+        """Queue n sweeps without waiting (see nfhmm_vi_sweep_async)."""
+        _check(_lib.nfhmm_vi_sweep_async(self._h, n, int(prepare_bound)), "nfhmm_vi_sweep_async")
+
     def bound(self) -> float:
         out = ctypes.c_double()
         _check(_lib.nfhmm_bound(self._h, ctypes.byref(out)), "nfhmm_bound")
@@ -377,6 +385,26 @@ class Batch(VIContext):
 
     def remove(self, job_id: int):
         _check(_lib.nfhmm_batch_remove(self._h, job_id), "nfhmm_batch_remove")
+
+    def add_many(self, Vs) -> list:
+        """Append several jobs at once (validated together); returns their ids."""
+        Vs = [_f32(V) for V in Vs]
+        ptrs = [_ptr(V) for V in Vs]
+        if len({d for _, d in ptrs}) > 1:
+            raise ValueError("all spectrograms on the host or all on the device")
+        n = len(Vs)
+        T = np.array([V.shape[0] for V in Vs], dtype=np.int32)
+        arr = (_vp * max(n, 1))(*[p.value for p, _ in ptrs])
+        ids = np.zeros(max(n, 1), dtype=np.int64)
+        _check(_lib.nfhmm_batch_add_many(self._h, n, _vp(T.ctypes.data), arr,
+                                         ptrs[0][1] if n else 0, _vp(ids.ctypes.data)),
+               "nfhmm_batch_add_many")
+        return ids[:n].tolist()
+
+    def remove_many(self, job_ids):
+        ids = np.ascontiguousarray(job_ids, dtype=np.int64)
+        _check(_lib.nfhmm_batch_remove_many(self._h, len(ids), _vp(ids.ctypes.data)),
+               "nfhmm_batch_remove_many")
 
 
 def serve(batches, requests, rel_tol: float = 1e-5, min_sweeps: int = 2,

@@ -138,6 +138,33 @@ def test_jobs_come_and_go(nf):
         assert abs(bounds[ids[idx]] - L) <= 1e-8 * abs(L), j
 
 
+def test_many_jobs_in_and_out_at_once(nf):
+    """add_many, then remove_many of non-adjacent jobs (the survivors move
+    down in one gather) and queued sweeps: each survivor and each newcomer
+    equals its lone run bit for bit."""
+    lengths = [40, 7, 130, 64, 1, 90, 55]
+    jobs = _jobs(lengths, seed=13, sigma=1.0)
+    f = {k: _f32(getattr(jobs, k)) for k in ("W", "A", "pi")}
+    with nf.Batch(f["W"], f["A"], f["pi"], jobs.S, jobs.N, jobs.K, capacity=400,
+                  max_jobs=6) as b:
+        chunk = b.query("fb_chunk")
+        assert b.query("frame_capacity") == 400 and b.query("max_jobs") == 6
+        ids = b.add_many([_f32(jobs.V[j]) for j in range(5)])
+        b.sweep_async(2)
+        b.remove_many([ids[1], ids[3]])
+        ids += b.add_many([_f32(jobs.V[5]), _f32(jobs.V[6])])
+        b.sweep_async(3, prepare_bound=True)
+        bounds = dict(zip([j[0] for j in b.jobs()], b.job_bounds()))
+        got = {i: b.job_posteriors(i) for i in bounds}
+        assert [j[2] for j in b.jobs()] == [40, 130, 1, 90, 55]
+    for j, sweeps in ((0, 5), (2, 5), (4, 5), (5, 3), (6, 3)):
+        with _alone(nf, jobs, j, chunk) as a:
+            L = a.sweep(sweeps, bound=True)
+            d = a.posteriors()
+        assert np.array_equal(got[ids[j]], d), j
+        assert bounds[ids[j]] == L, j
+
+
 def test_batch_full_and_invalid_job_leave_batch_unchanged(nf):
     jobs = _jobs([100, 100], seed=2)
     f = {k: _f32(getattr(jobs, k)) for k in ("W", "A", "pi")}
@@ -190,3 +217,27 @@ def test_fb_options_change_only_rounding(nf):
     for L, d in out[1:]:
         assert abs(L - out[0][0]) <= 1e-7 * abs(out[0][0])
         assert np.max(np.abs(d - out[0][1])) <= 1e-5
+
+
+def test_graph_replay_matches_direct_launches(nf):
+    """Sweeps replayed from captured CUDA graphs equal sweeps launched one
+    by one, also across job changes that invalidate the captured graph."""
+    lengths = [120, 33, 260]
+    jobs = _jobs(lengths, seed=17, sigma=1.0)
+    f = {k: _f32(getattr(jobs, k)) for k in ("W", "A", "pi")}
+    out = []
+    for graphs in (1, 0):
+        with nf.Batch(f["W"], f["A"], f["pi"], jobs.S, jobs.N, jobs.K, capacity=500,
+                      max_jobs=3) as b:
+            b.set_option("graphs", graphs)
+            ids = b.add_many([_f32(v) for v in jobs.V[:2]])
+            b.sweep(4)
+            L1 = b.sweep(3, bound=True)
+            b.remove(ids[0])
+            ids.append(b.add(_f32(jobs.V[2])))
+            b.sweep(4)
+            L2 = b.sweep(2, bound=True)
+            out.append((L1, L2, b.posteriors(), b.kernel_launches()))
+    assert out[0][0] == out[1][0] and out[0][1] == out[1][1]
+    assert np.array_equal(out[0][2], out[1][2])
+    assert out[0][3] == out[1][3]
