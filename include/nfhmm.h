@@ -233,13 +233,15 @@ NFHMM_API int nfhmm_job_posteriors(nfhmm_ctx *c, long long job_id, float *dhat, 
  * nfhmm_set_option -- tune a context (results change only by rounding):
  *   NFHMM_OPT_FB_CHUNK     frames per time chunk of the forward-backward (1..128)
  *   NFHMM_OPT_FB_PRODUCTS  how the chunk transfer matrices are formed:
- *                          NFHMM_FB_PRODUCTS_TC (default for contexts;
- *                          split-TF32 tcgen05 MMAs over 128-row tiles) or
- *                          NFHMM_FB_PRODUCTS_SIMT (FP32 FMAs on the CUDA
- *                          cores; the stateless calls use this form)
- *   NFHMM_OPT_GRAPHS       1 (default): with profiling off, a sweep whose
- *                          launch configuration has run before is replayed
- *                          from a captured CUDA graph; 0: launch by launch
+ *                          NFHMM_FB_PRODUCTS_TC (default, and the form of
+ *                          the stateless calls: split-TF32 tcgen05 MMAs over
+ *                          128-row tiles) or NFHMM_FB_PRODUCTS_SIMT (FP32
+ *                          FMAs on the CUDA cores, one thread per row)
+ *   NFHMM_OPT_GRAPHS       1 (default): a run of sweeps whose launch
+ *                          configuration (frames, chunks, sweep count, bound)
+ *                          has run before is replayed from a captured CUDA
+ *                          graph, profiling events included; 0: launch by
+ *                          launch
  */
 #define NFHMM_OPT_FB_CHUNK    0
 #define NFHMM_OPT_FB_PRODUCTS 1

@@ -42,9 +42,28 @@ namespace {
 size_t round_up(size_t x, size_t m) { return (x + m - 1) / m * m; }
 
 struct StageEvents {
-  std::vector<cudaEvent_t> begin, end;
+  std::vector<cudaEvent_t> begin, end;   // launches made one by one
   long long launches = 0;
-  size_t device_bytes = 0;
+  double ms_acc = 0.0;                   // harvested from graph replays
+  long long inv_acc = 0;
+};
+
+// A run of sweeps captured as a CUDA graph.  With profiling on, the stage
+// events are part of the graph (event record nodes) and are read after each
+// replay, before the next one records them again.
+struct SweepGraph {
+  long long key = -1;
+  cudaGraphExec_t exec = nullptr;
+  int seen = 0;                          // runs made uncaptured with this key
+  unsigned long long last_use = 0;
+  long long launches = 0;                // kernels per replay
+  long long stage_launches[NFHMM_NUM_STAGES] = {};
+  struct Ev {
+    int stage;
+    cudaEvent_t begin, end;
+  };
+  std::vector<Ev> events;
+  bool pending = false;                  // a replay whose events are unread
 };
 
 }  // namespace
@@ -109,13 +128,11 @@ struct nfhmm_ctx {
   bool bound_ok = false;      // h_bound holds the bound of the current state
   bool inputs_ok = false;
   bool profiling = false;
-  // one sweep captured as a CUDA graph, per variant (without / with the
-  // bound's terms); valid while the launch configuration stays the same
+  // runs of sweeps captured as CUDA graphs, by launch configuration
   bool use_graphs = true;
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
-  long long graph_key[2] = {-1, -1};
-  int graph_seen[2] = {0, 0};       // sweeps run uncaptured with the current key
-  long long graph_launches[2] = {0, 0};
+  SweepGraph graphs[4];
+  unsigned long long graph_clock = 0;
+  SweepGraph* capturing = nullptr;
   StageEvents stages[NFHMM_NUM_STAGES];
   long long launches = 0;
   size_t device_bytes = 0;
@@ -127,6 +144,11 @@ void stage_begin(nfhmm_ctx* c, int stage, cudaStream_t st) {
   if (!c->profiling) return;
   cudaEvent_t e;
   cudaEventCreate(&e);
+  if (c->capturing) {   // an event record node of the graph being captured
+    cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+    c->capturing->events.push_back(SweepGraph::Ev{stage, e, nullptr});
+    return;
+  }
   cudaEventRecord(e, st);
   c->stages[stage].begin.push_back(e);
 }
@@ -136,8 +158,43 @@ void stage_end(nfhmm_ctx* c, int stage, cudaStream_t st, int launches) {
   if (!c->profiling) return;
   cudaEvent_t e;
   cudaEventCreate(&e);
+  if (c->capturing) {
+    cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+    auto& ev = c->capturing->events;
+    for (auto it = ev.rbegin(); it != ev.rend(); ++it)
+      if (it->stage == stage && !it->end) {
+        it->end = e;
+        break;
+      }
+    return;
+  }
   cudaEventRecord(e, st);
   c->stages[stage].end.push_back(e);
+}
+
+// Add the stage times of a graph's last replay to the stage totals.
+void harvest(nfhmm_ctx* c, SweepGraph& g) {
+  if (!g.pending) return;
+  g.pending = false;
+  for (auto& ev : g.events) {
+    if (!ev.end) continue;
+    float ms = 0.f;
+    if (cudaEventSynchronize(ev.end) == cudaSuccess &&
+        cudaEventElapsedTime(&ms, ev.begin, ev.end) == cudaSuccess) {
+      c->stages[ev.stage].ms_acc += ms;
+      c->stages[ev.stage].inv_acc += 1;
+    }
+  }
+}
+
+void drop_graph(nfhmm_ctx* c, SweepGraph& g) {
+  harvest(c, g);
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  for (auto& ev : g.events) {
+    if (ev.begin) cudaEventDestroy(ev.begin);
+    if (ev.end) cudaEventDestroy(ev.end);
+  }
+  g = SweepGraph();
 }
 
 void free_ctx(nfhmm_ctx* c) {
@@ -151,8 +208,7 @@ void free_ctx(nfhmm_ctx* c) {
   for (void* p : bufs)
     if (p) cudaFree(p);
   tc_free(c->tc);
-  for (auto& g : c->graph)
-    if (g) cudaGraphExecDestroy(g);
+  for (auto& g : c->graphs) drop_graph(c, g);
   if (c->h_bound) cudaFreeHost(c->h_bound);
   if (c->h_err) cudaFreeHost(c->h_err);
   for (auto& s : c->stages) {
@@ -744,55 +800,94 @@ int create_ctx(nfhmm_ctx** out, const nfhmm_dims* dp, int max_jobs, const float*
   return NFHMM_OK;
 }
 
-// The launch configuration a captured sweep depends on.
-long long graph_key_of(const nfhmm_ctx* c) {
+// The launch configuration a captured run of sweeps depends on.
+long long graph_key_of(const nfhmm_ctx* c, int n, bool want_bpart) {
   long long k = c->T_active;
   k = k * 1000003 + c->fb.C;
   k = k * 1048583 + c->fb.nchains;
   k = k * 131 + c->fb.L;
   k = k * 3 + c->fb.products;
+  k = k * 1009 + n;
+  k = k * 2 + (want_bpart ? 1 : 0);
+  k = k * 2 + (c->profiling ? 1 : 0);
   return k;
 }
 
-// One sweep: from a captured CUDA graph once the same configuration has run
-// uncaptured once (profiling off), else launch by launch.
-int sweep_once(nfhmm_ctx* c, bool want_bpart) {
-  const int v = want_bpart ? 1 : 0;
-  if (!c->use_graphs || c->profiling || c->T_active == 0) return one_sweep(c, want_bpart);
-  const long long key = graph_key_of(c);
-  if (c->graph_key[v] != key) {
-    if (c->graph[v]) cudaGraphExecDestroy(c->graph[v]);
-    c->graph[v] = nullptr;
-    c->graph_key[v] = key;
-    c->graph_seen[v] = 0;
+int sweeps_direct(nfhmm_ctx* c, int n, bool want_bpart) {
+  for (int i = 0; i < n; ++i) {
+    const int rc = one_sweep(c, want_bpart && i == n - 1);
+    if (rc) return rc;
   }
-  if (!c->graph[v]) {
-    if (c->graph_seen[v]++ == 0) return one_sweep(c, want_bpart);   // warm: first launches
+  return NFHMM_OK;
+}
+
+// n sweeps (the last with the bound's terms if want_bpart), replayed from
+// captured CUDA graphs once the same launch configuration has run uncaptured
+// once, else launched one by one.  Without profiling, graphs of one sweep
+// are replayed n times (any n); with profiling, the run of n sweeps is one
+// graph, so that every sweep's stage events are distinct nodes.
+int run_graph(nfhmm_ctx* c, int n, bool want_bpart);
+int run_sweeps(nfhmm_ctx* c, int n, bool want_bpart) {
+  if (!c->use_graphs || c->T_active == 0 || n < 1) return sweeps_direct(c, n, want_bpart);
+  if (c->profiling) return run_graph(c, n, want_bpart);
+  for (int i = 0; i < n; ++i) {
+    const int rc = run_graph(c, 1, want_bpart && i == n - 1);
+    if (rc) return rc;
+  }
+  return NFHMM_OK;
+}
+
+int run_graph(nfhmm_ctx* c, int n, bool want_bpart) {
+  if (!c->use_graphs) return sweeps_direct(c, n, want_bpart);
+  const long long key = graph_key_of(c, n, want_bpart);
+  SweepGraph* g = nullptr;
+  for (auto& x : c->graphs)
+    if (x.key == key) g = &x;
+  if (!g) {   // reuse the least recently used slot
+    g = &c->graphs[0];
+    for (auto& x : c->graphs)
+      if (x.last_use < g->last_use) g = &x;
+    drop_graph(c, *g);
+    g->key = key;
+  }
+  g->last_use = ++c->graph_clock;
+  if (!g->exec) {
+    if (g->seen++ == 0) return sweeps_direct(c, n, want_bpart);   // first launches uncaptured
     const long long l0 = c->launches;
-    cudaGraph_t g = nullptr;
+    long long s0[NFHMM_NUM_STAGES];
+    for (int i = 0; i < NFHMM_NUM_STAGES; ++i) s0[i] = c->stages[i].launches;
+    cudaGraph_t graph = nullptr;
     if (cudaStreamBeginCapture(c->s_main, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
       cudaGetLastError();
       c->use_graphs = false;
-      return one_sweep(c, want_bpart);
+      return sweeps_direct(c, n, want_bpart);
     }
-    const int rc = one_sweep(c, want_bpart);
-    const cudaError_t e = cudaStreamEndCapture(c->s_main, &g);
-    if (rc || e != cudaSuccess || !g ||
-        cudaGraphInstantiate(&c->graph[v], g, 0) != cudaSuccess) {
-      if (g) cudaGraphDestroy(g);
-      cudaGetLastError();
-      c->graph[v] = nullptr;
-      c->use_graphs = false;
-      c->launches = l0;
-      if (rc) return rc;
-      return one_sweep(c, want_bpart);   // capture unavailable: launch directly
-    }
-    cudaGraphDestroy(g);
-    c->graph_launches[v] = c->launches - l0;
+    c->capturing = g;
+    const int rc = sweeps_direct(c, n, want_bpart);
+    c->capturing = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->s_main, &graph);
+    const bool good = !rc && e == cudaSuccess && graph &&
+                      cudaGraphInstantiate(&g->exec, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    g->launches = c->launches - l0;
     c->launches = l0;
+    for (int i = 0; i < NFHMM_NUM_STAGES; ++i) {
+      g->stage_launches[i] = c->stages[i].launches - s0[i];
+      c->stages[i].launches = s0[i];
+    }
+    if (!good) {
+      cudaGetLastError();
+      drop_graph(c, *g);
+      c->use_graphs = false;
+      if (rc) return rc;
+      return sweeps_direct(c, n, want_bpart);   // capture unavailable: launch directly
+    }
   }
-  CK(cudaGraphLaunch(c->graph[v], c->s_main));
-  c->launches += c->graph_launches[v];
+  harvest(c, *g);   // its events are about to be recorded again
+  CK(cudaGraphLaunch(g->exec, c->s_main));
+  c->launches += g->launches;
+  for (int i = 0; i < NFHMM_NUM_STAGES; ++i) c->stages[i].launches += g->stage_launches[i];
+  g->pending = c->profiling && !g->events.empty();
   return NFHMM_OK;
 }
 
@@ -806,11 +901,8 @@ int sweep_impl(nfhmm_ctx* c, int n_sweeps, bool want_bound, bool finish = true) 
   if (n_sweeps == 0 && want_bound && c->bound_ok) return NFHMM_OK;
   int rc = enter(c);
   if (rc) return rc;
-  for (int i = 0; i < n_sweeps; ++i) {
-    const bool last = i == n_sweeps - 1;
-    rc = sweep_once(c, want_bound && last);
-    if (rc) return rc;
-  }
+  rc = run_sweeps(c, n_sweeps, want_bound);
+  if (rc) return rc;
   if (n_sweeps > 0) {
     c->sweeps_done += n_sweeps;
     for (Job& j : c->jobs) j.sweeps += n_sweeps;
@@ -1191,6 +1283,7 @@ int nfhmm_forward_backward(int S, int N, int T, const float* phi, const float* A
   if (a.L > T) a.L = T;
   a.C = (T + a.L - 1) / a.L;
   a.nchains = 1;   // one chain over all T frames (null chain tables)
+  a.products = FB_PRODUCTS_TC;
   a.phi = phi;
   a.A = A;
   a.pi = pi;
@@ -1227,8 +1320,9 @@ int nfhmm_profile_read(nfhmm_ctx* c, int stage, double* ms_total, long long* inv
   if (!c || stage < 0 || stage >= NFHMM_NUM_STAGES) return fail(NFHMM_EINVAL, "bad argument");
   CK(cudaStreamSynchronize(c->s_main));
   CK(cudaStreamSynchronize(c->s_aux));
+  for (auto& g : c->graphs) harvest(c, g);
   StageEvents& s = c->stages[stage];
-  double tot = 0.0;
+  double tot = s.ms_acc;
   const size_t n = s.begin.size() < s.end.size() ? s.begin.size() : s.end.size();
   for (size_t i = 0; i < n; ++i) {
     float ms = 0.f;
@@ -1236,7 +1330,7 @@ int nfhmm_profile_read(nfhmm_ctx* c, int stage, double* ms_total, long long* inv
     tot += ms;
   }
   if (ms_total) *ms_total = tot;
-  if (invocations) *invocations = (long long)n;
+  if (invocations) *invocations = (long long)n + s.inv_acc;
   if (launches) *launches = s.launches;
   if (reset) {
     for (auto e : s.begin) cudaEventDestroy(e);
@@ -1244,6 +1338,8 @@ int nfhmm_profile_read(nfhmm_ctx* c, int stage, double* ms_total, long long* inv
     s.begin.clear();
     s.end.clear();
     s.launches = 0;
+    s.ms_acc = 0.0;
+    s.inv_acc = 0;
   }
   return NFHMM_OK;
 }

@@ -352,158 +352,148 @@ __global__ void __launch_bounds__(128, 1) k_fb_products(FBArgs a) {
 }
 
 // --------------------------------------------- 1'. products on CUDA cores
-// The same chunk matrices with FP32 FMAs: one block per (chunk, source), a
-// warp advances RPW rows of P_c (basis states i) one frame per step, lane j
-// holding columns j and j + 32 and A's columns j, j + 32 in registers.  A
-// step is a vector-matrix product per row: far lower latency than a
-// tensor-core round trip, so chains of a few thousand frames finish sooner;
-// the work (N^3 per frame and source) is the same.  Each row is rescaled by
-// the sum of its previous value (reduced while the step's products run);
-// the removed factors are kept per row as exact (mantissa, exponent) pairs.
+// The same chunk matrices with FP32 FMAs: one thread per row of P_c (chunk
+// q, basis state i), 128 threads holding the rows of floor(128/NP) chunks
+// as in the tensor-core form.  A step is the row times A (read from shared
+// memory, the same address in every lane: a broadcast) times the frame's
+// emissions, then a rescale by the row's maximum: all thread-local, no
+// barrier inside the frame loop.
 template <int NP>
-struct SimtCfg {
-  static constexpr int RPW = NP <= 16 ? 4 : 8;             // rows per warp
-  static constexpr int WARPS = (NP + RPW - 1) / RPW;
-};
-
-template <int NP>
-__global__ void __launch_bounds__(SimtCfg<NP>::WARPS * 32) k_fb_products_simt(FBArgs a) {
-  constexpr int RPW = SimtCfg<NP>::RPW, WARPS = SimtCfg<NP>::WARPS;
-  constexpr bool TWO = NP > 32;   // lane also holds column j + 32
+__global__ void __launch_bounds__(128) k_fb_products_simt(FBArgs a) {
+  constexpr int RCH = 128 / NP;
+  constexpr int XS = NP + 1;   // padded row stride: rows of neighbouring threads in different banks
   extern __shared__ double smd[];
-  double* dred = smd;             // WARPS partial sums of the frame maxima
-  double* rlog = smd + 32;        // NP row log scales
-  float* e = reinterpret_cast<float*>(smd + 32 + 64);   // L x NP emissions
-  float* xs = e + a.L * NP;                              // WARPS x RPW x NP row vectors
-  const int N = a.N;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int c = blockIdx.x, s = blockIdx.y;
-  const ChunkInfo ci = chunk_info(a, c);
-  const int len = ci.len;
-  const float* src = a.phi + ((size_t)s * a.T + ci.t0) * N;
-  for (int i = threadIdx.x; i < len * N; i += blockDim.x) {
-    const int f = i / N, n = i - f * N;
-    e[f * NP + n] = src[i];
-  }
-  __syncthreads();
-  double ms = 0.0;
-  for (int f = warp; f < len; f += WARPS) {
-    float* row = e + f * NP;
-    const float x0 = lane < N ? row[lane] : -INFINITY;
-    const float x1 = lane + 32 < N ? row[lane + 32] : -INFINITY;
-    const float m = warp_max(fmaxf(x0, x1));
-    __syncwarp();
-    if (lane < NP) row[lane] = lane < N ? expf(x0 - m) : 0.f;
-    if (lane + 32 < NP) row[lane + 32] = lane + 32 < N ? expf(x1 - m) : 0.f;
-    ms += (double)m;
-  }
-  if (lane == 0) dred[warp] = ms;
+  double* rhod = smd;                                      // 128
+  double* msum = smd + 128;                                // RCH (<= 16)
+  float* As = reinterpret_cast<float*>(smd + 128 + 16);    // NP x NP, A[k][j]
+  float* xs = As + NP * NP;                                // 128 x XS current rows
+  float* e = xs + 128 * XS + 3;                            // RCH x L x NP (16-byte aligned)
+  e = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(e) + 15) & ~(uintptr_t)15);
+  const int N = a.N, L = a.L, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int s = blockIdx.y;
+  const int cbase = blockIdx.x * RCH;
   const float* Ag = a.A + (size_t)s * N * N;
-  float A0[NP], A1[TWO ? NP : 1];
-#pragma unroll
-  for (int k = 0; k < NP; ++k) {
-    A0[k] = (lane < N && k < N) ? Ag[k * N + lane] : 0.f;
-    if (TWO) A1[k] = (lane + 32 < N && k < N) ? Ag[k * N + lane + 32] : 0.f;
+  for (int idx = tid; idx < NP * NP; idx += 128) {
+    const int k = idx / NP, j = idx - k * NP;
+    As[idx] = (k < N && j < N) ? Ag[k * N + j] : 0.f;
   }
-  __syncthreads();
-  float r0[RPW], r1[RPW];
-  ScaleAcc sc[RPW];
-  const float e00 = lane < NP ? e[lane] : 0.f;
-  const float e01 = lane + 32 < NP ? e[lane + 32] : 0.f;
-#pragma unroll
-  for (int u = 0; u < RPW; ++u) {
-    const int i = warp * RPW + u;
-    r0[u] = r1[u] = 0.f;
-    if (i < N) {
-      if (ci.first) {
-        r0[u] = lane == i ? e00 : 0.f;
-        r1[u] = lane + 32 == i ? e01 : 0.f;
-      } else {
-        r0[u] = lane < N ? Ag[i * N + lane] * e00 : 0.f;
-        r1[u] = lane + 32 < N ? Ag[i * N + lane + 32] * e01 : 0.f;
-      }
+  for (int q = 0; q < RCH; ++q) {
+    const int c = cbase + q;
+    if (c >= a.C) break;
+    const ChunkInfo ci = chunk_info(a, c);
+    const float* src = a.phi + ((size_t)s * a.T + ci.t0) * N;
+    float* eq = e + q * L * NP;
+    for (int i = tid; i < ci.len * N; i += 128) {
+      const int f = i / N, n = i - f * N;
+      eq[f * NP + n] = src[i];
     }
   }
-  float* xw = xs + warp * RPW * NP;
+  __syncthreads();
+  for (int q = 0; q < RCH; ++q) {
+    const int c = cbase + q;
+    if (c >= a.C) break;
+    const int len = chunk_info(a, c).len;
+    float* eq = e + q * L * NP;
+    double ms = 0.0;
+    for (int f = warp; f < len; f += 4) {
+      float* row = eq + f * NP;
+      const float x0 = lane < N ? row[lane] : -INFINITY;
+      const float x1 = lane + 32 < N ? row[lane + 32] : -INFINITY;
+      const float m = warp_max(fmaxf(x0, x1));
+      __syncwarp();
+      if (lane < NP) row[lane] = lane < N ? expf(x0 - m) : 0.f;
+      if (lane + 32 < NP) row[lane + 32] = lane + 32 < N ? expf(x1 - m) : 0.f;
+      ms += (double)m;
+    }
+    if (lane == 0) rhod[warp] = ms;
+    __syncthreads();
+    if (tid == 0) msum[q] = rhod[0] + rhod[1] + rhod[2] + rhod[3];
+    __syncthreads();
+  }
+  const int q = tid / NP, i = tid - q * NP;
+  const int c = cbase + q;
+  const bool live = q < RCH && c < a.C && i < N;
+  const ChunkInfo ci = (q < RCH && c < a.C) ? chunk_info(a, c) : ChunkInfo{0, 0, 0, false};
+  const int len = live ? ci.len : 0;
+  const float* eq = e + (q < RCH ? q : 0) * L * NP;
+  float* xr = xs + tid * XS;   // this thread's row
+  float y[NP];
+  ScaleAcc sc;
+  bool zero_row = false;
   unsigned bad = 0;
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    float v = 0.f;
+    if (live && j < N) v = ci.first ? (j == i ? eq[j] : 0.f) : As[i * NP + j] * eq[j];
+    y[j] = v;
+  }
+  // rescale y by its maximum into this thread's row in shared memory
+  auto normalise_store = [&]() {
+    float m = 0.f;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) m = fmaxf(m, y[j]);
+    if (!isfinite(m)) {
+      bad = 1;
+      m = 0.f;
+    }
+    if (m == 0.f) zero_row = true;
+    const float g = renorm_factor(m);
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      y[j] *= g;
+      xr[j] = y[j];
+    }
+    sc.mul(removed_scale(m));
+  };
+  if (live) normalise_store();
   for (int f = 1; f < len; ++f) {
-    __syncwarp();
 #pragma unroll
-    for (int u = 0; u < RPW; ++u) {
-      if (lane < NP) xw[u * NP + lane] = r0[u];
-      if (lane + 32 < NP) xw[u * NP + lane + 32] = r1[u];
-    }
-    __syncwarp();
-    float sp[RPW];
+    for (int j = 0; j < NP; ++j) y[j] = 0.f;
+#pragma unroll 2
+    for (int k = 0; k < NP; ++k) {
+      const float xk = xr[k];
+      const float* ak = As + k * NP;
 #pragma unroll
-    for (int u = 0; u < RPW; ++u) sp[u] = warp_sum(r0[u] + r1[u]);
-    const float* ef = e + f * NP;
-    const float ef0 = lane < NP ? ef[lane] : 0.f;
-    const float ef1 = lane + 32 < NP ? ef[lane + 32] : 0.f;
-#pragma unroll
-    for (int u = 0; u < RPW; ++u) {
-      float p0[4] = {0.f, 0.f, 0.f, 0.f}, p1[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-      for (int k = 0; k < NP; k += 4) {
-        const float4 xv = *reinterpret_cast<const float4*>(&xw[u * NP + k]);
-        p0[0] = fmaf(xv.x, A0[k], p0[0]);
-        p0[1] = fmaf(xv.y, A0[k + 1], p0[1]);
-        p0[2] = fmaf(xv.z, A0[k + 2], p0[2]);
-        p0[3] = fmaf(xv.w, A0[k + 3], p0[3]);
-        if (TWO) {
-          p1[0] = fmaf(xv.x, A1[k], p1[0]);
-          p1[1] = fmaf(xv.y, A1[k + 1], p1[1]);
-          p1[2] = fmaf(xv.z, A1[k + 2], p1[2]);
-          p1[3] = fmaf(xv.w, A1[k + 3], p1[3]);
-        }
+      for (int j = 0; j < NP; j += 4) {
+        const float4 a4 = *reinterpret_cast<const float4*>(ak + j);
+        y[j] = fmaf(xk, a4.x, y[j]);
+        y[j + 1] = fmaf(xk, a4.y, y[j + 1]);
+        y[j + 2] = fmaf(xk, a4.z, y[j + 2]);
+        y[j + 3] = fmaf(xk, a4.w, y[j + 3]);
       }
-      if (!isfinite(sp[u])) bad = 1;
-      const float g = renorm_factor(sp[u]);
-      sc[u].mul(removed_scale(sp[u]));
-      r0[u] = ((p0[0] + p0[1]) + (p0[2] + p0[3])) * ef0 * g;
-      r1[u] = TWO ? ((p1[0] + p1[1]) + (p1[2] + p1[3])) * ef1 * g : 0.f;
     }
-  }
-  // final normalisation; a row that vanished (state i cannot start this
-  // chunk and reach its end) gets log scale -inf
-  double lr[RPW];
+    const float* ef = eq + f * NP;
 #pragma unroll
-  for (int u = 0; u < RPW; ++u) {
-    const float sf = warp_sum(r0[u] + r1[u]);
-    if (!isfinite(sf)) bad = 1;
-    const float g = renorm_factor(sf);
-    sc[u].mul(removed_scale(sf));
-    r0[u] *= g;
-    r1[u] *= g;
-    lr[u] = sf > 0.f ? sc[u].log() : -INFINITY;
-    const int i = warp * RPW + u;
-    if (lane == 0 && i < NP) rlog[i] = i < N ? lr[u] : -INFINITY;
+    for (int j = 0; j < NP; j += 4) {
+      const float4 e4 = *reinterpret_cast<const float4*>(ef + j);
+      y[j] *= e4.x;
+      y[j + 1] *= e4.y;
+      y[j + 2] *= e4.z;
+      y[j + 3] *= e4.w;
+    }
+    normalise_store();
   }
-  if (bad && lane == 0) atomicOr(a.err, ERR_FB_ZERO);
+  if (bad) atomicOr(a.err, ERR_FB_ZERO);
+  const double lr = zero_row ? -INFINITY : sc.log();
+  rhod[tid] = live ? lr : -INFINITY;
   __syncthreads();
-  double rmax = -INFINITY, msum = 0.0;
-  for (int i = 0; i < N; ++i) rmax = fmax(rmax, rlog[i]);
-  for (int w = 0; w < WARPS; ++w) msum += dred[w];
-  const size_t base = ((size_t)s * a.C + c) * NP * NP;
-  float* Pg = a.P + base;
-  float* PTg = a.PT + base;
+  if (q < RCH && c < a.C && i < NP) {
+    double rmax = -INFINITY;
+    for (int ii = 0; ii < N; ++ii) rmax = fmax(rmax, rhod[q * NP + ii]);
+    // rmax = -inf only if every row of the chunk vanished (flagged by the scan)
+    const float g = (live && rmax > -INFINITY) ? (float)exp(lr - rmax) : 0.f;
+    if (rmax == -INFINITY) rmax = 0.0;
+    const size_t base = ((size_t)s * a.C + c) * NP * NP;
+    float* Pg = a.P + base;
+    float* PTg = a.PT + base;
 #pragma unroll
-  for (int u = 0; u < RPW; ++u) {
-    const int i = warp * RPW + u;
-    if (i < NP) {
-      // rmax = -inf only if every row vanished (flagged by the scan)
-      const float g = (i < N && rmax > -INFINITY && lr[u] > -INFINITY) ? (float)exp(lr[u] - rmax) : 0.f;
-      if (lane < NP) {
-        Pg[i * NP + lane] = r0[u] * g;
-        PTg[lane * NP + i] = r0[u] * g;
-      }
-      if (lane + 32 < NP) {
-        Pg[i * NP + lane + 32] = r1[u] * g;
-        PTg[(lane + 32) * NP + i] = r1[u] * g;
-      }
+    for (int j = 0; j < NP; ++j) {
+      const float v = live ? y[j] * g : 0.f;
+      Pg[i * NP + j] = v;
+      PTg[j * NP + i] = v;
     }
+    if (i == 0) a.Plog[(size_t)s * a.C + c] = msum[q] + rmax;
   }
-  if (threadIdx.x == 0) a.Plog[(size_t)s * a.C + c] = msum + (rmax > -INFINITY ? rmax : 0.0);
 }
 
 // ------------------------------------------------------------------- 2. scan
@@ -805,8 +795,8 @@ static size_t smem_products(int L) {
 }
 template <int NP>
 static size_t smem_products_simt(int L) {
-  using Cfg = SimtCfg<NP>;
-  return (32 + 64) * sizeof(double) + (size_t)(L + Cfg::WARPS * Cfg::RPW) * NP * sizeof(float);
+  return (128 + 16) * sizeof(double) +
+         (size_t)(NP * NP + 128 * (NP + 1) + 8 + (128 / NP) * L * NP) * sizeof(float);
 }
 template <int NP>
 static size_t smem_scan() {
@@ -843,7 +833,7 @@ static cudaError_t launch_np(const FBArgs& a, cudaStream_t st) {
     k_fb_products<NP><<<dim3((a.C + Cfg::RCH - 1) / Cfg::RCH, a.S), 128,
                         smem_products<NP>(a.L), st>>>(a);
   else
-    k_fb_products_simt<NP><<<dim3(a.C, a.S), SimtCfg<NP>::WARPS * 32,
+    k_fb_products_simt<NP><<<dim3((a.C + Cfg::RCH - 1) / Cfg::RCH, a.S), 128,
                              smem_products_simt<NP>(a.L), st>>>(a);
   k_fb_scan<NP><<<dim3(a.S * a.nchains, 2), 32, smem_scan<NP>(), st>>>(a);
   k_fb_replay<NP><<<dim3((a.C + rc - 1) / rc, a.S), rc * 64, rc * smem_replay_chunk(NP, a.L),

@@ -11,7 +11,7 @@ namespace nfhmm {
 
 // psi(x) and w = exp(psi(x)) for x > 0, float.
 // psi: recurrence psi(x) = psi(x + 1) - 1/x (Abramowitz & Stegun 6.3.5) up to
-// x >= 6, then the asymptotic series psi(x) ~ ln x - 1/(2x) - sum_k
+// x >= 6 (the reciprocals summed as one fraction), then the asymptotic series psi(x) ~ ln x - 1/(2x) - sum_k
 // B_2k / (2k x^2k) (A&S 6.3.18) through the x^-10 term.  w is formed as
 // x' * exp(d - acc), where x' is the shifted argument, d = psi(x') - ln x'
 // from the series and acc the recurrence sum, so no ln/exp round trip is
@@ -26,16 +26,20 @@ __device__ __forceinline__ void digamma_impl(float x, float& psi, float& w, floa
     return;
   }
   const float a = x;
-  float acc = 0.f, prod = 1.f;
+  // x > 0: the first step lands in [1, ...), five more reach x >= 6.  The
+  // recurrence sum acc = sum_i 1/(x+i) is kept as one fraction num/den
+  // (num' = num (x+i) + den, den' = den (x+i)), so the shift costs one
+  // division instead of one reciprocal per step; den is also the product
+  // (x)(x+1)...(x+n-1) of the lnGamma shift.
+  float num = 0.f, prod = 1.f;
   int n = 0;
-  // x > 0: the first step lands in [1, ...), five more reach x >= 6.
-  // __frcp_rn: the correctly rounded reciprocal (same value as 1.f / x)
 #pragma unroll 1
   for (; n < 7 && x < 6.f; ++n) {
-    acc += __frcp_rn(x);
-    if (G) prod *= x;
+    num = fmaf(num, x, prod);
+    prod *= x;
     x += 1.f;
   }
+  const float acc = n > 0 ? num / prod : 0.f;
   const float r = __frcp_rn(x);
   const float r2 = r * r;
   const float series =

@@ -241,3 +241,26 @@ def test_graph_replay_matches_direct_launches(nf):
     assert out[0][0] == out[1][0] and out[0][1] == out[1][1]
     assert np.array_equal(out[0][2], out[1][2])
     assert out[0][3] == out[1][3]
+
+
+def test_profiling_through_graphs_counts_every_launch(nf):
+    """With profiling on, sweeps replayed from a graph report the same stage
+    invocations and launches as sweeps launched one by one."""
+    p = synth.make_problem(seed=6, **synth.SMALL)
+    f = p.as_f32()
+    res = []
+    for graphs in (1, 0):
+        with nf.VIContext(f["V"], f["W"], f["A"], f["pi"], p.S, p.N, p.K) as ctx:
+            ctx.set_option("graphs", graphs)
+            ctx.profile_enable(True)
+            for _ in range(4):
+                ctx.sweep(5, bound=True)
+            prof = {st: ctx.profile_read(st) for st in ("weights", "gemm1", "gemm2", "fb",
+                                                         "bound")}
+            res.append((prof, ctx.posteriors()))
+    for st in res[0][0]:
+        ms_g, inv_g, l_g = res[0][0][st]
+        ms_d, inv_d, l_d = res[1][0][st]
+        assert inv_g == inv_d and l_g == l_d, st
+        assert ms_g > 0 and ms_d > 0, st
+    assert np.array_equal(res[0][1], res[1][1])
