@@ -237,6 +237,9 @@ NFHMM_API int nfhmm_job_posteriors(nfhmm_ctx *c, long long job_id, float *dhat, 
  *                          the stateless calls: split-TF32 tcgen05 MMAs over
  *                          128-row tiles) or NFHMM_FB_PRODUCTS_SIMT (FP32
  *                          FMAs on the CUDA cores, one thread per row)
+ *   NFHMM_OPT_FB_GROUP     chunks per group of the two-level scan across
+ *                          chunks (2..4096), 0 for a single-level scan, -1
+ *                          (default) for a size that follows the chunk length
  *   NFHMM_OPT_GRAPHS       1 (default): a run of sweeps whose launch
  *                          configuration (frames, chunks, sweep count, bound)
  *                          has run before is replayed from a captured CUDA
@@ -246,6 +249,7 @@ NFHMM_API int nfhmm_job_posteriors(nfhmm_ctx *c, long long job_id, float *dhat, 
 #define NFHMM_OPT_FB_CHUNK    0
 #define NFHMM_OPT_FB_PRODUCTS 1
 #define NFHMM_OPT_GRAPHS      2
+#define NFHMM_OPT_FB_GROUP    3
 #define NFHMM_FB_PRODUCTS_SIMT 0
 #define NFHMM_FB_PRODUCTS_TC   1
 NFHMM_API int nfhmm_set_option(nfhmm_ctx *c, int key, long long value);
@@ -317,9 +321,10 @@ NFHMM_API int nfhmm_forward_backward(int S, int N, int T, const float *phi, cons
  * The call allocates nothing: its scratch is one fixed device array of
  * NFHMM_NOALLOC_SCRATCH_BYTES compiled into the library, which every GPU that
  * loads the library holds until the process exits.  A problem needs about
- * 8*S*C*(P*P + N) + 12*S*C bytes, C = ceil(T/L), P = 8*ceil(N/8) (L = chunk
- * length, at most 128; by default ceil(sqrt(T)/2) clamped to [16, 64]), plus
- * alignment; larger problems are rejected with NFHMM_EINVAL and a message
+ * 8*S*(C + C')*(P*P + N) + 12*S*(C + C') bytes, C = ceil(T/L) chunks of L frames
+ * (L at most 128; by default ceil(sqrt(T)/2) clamped to [16, 64]), C' =
+ * ceil(C/G) groups of G = ceil(sqrt(C/2)) chunks (none below 24 chunks),
+ * P = 8*ceil(N/8), plus alignment; larger problems are rejected with NFHMM_EINVAL and a message
  * giving both sizes.
  * The first call on a device looks up the array's device address (with that
  * device current) and should be made before any stream capture.  All calls
@@ -372,6 +377,7 @@ NFHMM_API long long nfhmm_kernel_launches(nfhmm_ctx *c);
 #define NFHMM_Q_DEVICE_BYTES 3
 #define NFHMM_Q_FRAME_CAPACITY 4   /* frames the context's frame store holds */
 #define NFHMM_Q_MAX_JOBS       5   /* jobs the context can hold            */
+#define NFHMM_Q_FB_GROUP       6   /* chunks per group of the scan (0: none) */
 NFHMM_API int nfhmm_query(nfhmm_ctx *c, int key, long long *value);
 
 #ifdef __cplusplus

@@ -113,6 +113,8 @@ struct nfhmm_ctx {
   int* d_tab = nullptr;
   int* fb_seg = nullptr;     // 3 * max_jobs ints: segment table of a compaction
   int Cmax = 0;              // chunk capacity of the forward-backward scratch
+  int NGmax = 0;             // group capacity
+  bool group_auto = true;    // group size follows the chunk length
   void* fb_scratch = nullptr;
   FBArgs fb{};
   TcPlan tc{};
@@ -479,34 +481,51 @@ int fb_chunks(const nfhmm_ctx* c) {
 
 // (Re)allocate the forward-backward scratch and the job tables for chunk
 // length fb.L: room for every job set the frame store and job slots allow.
+// Table layout (ints): job_t0[mj+1] | chain_c0[mj+1] | chain_len[mj] |
+// chunk_chain[Cmax] | grp_c0[NGmax+1] | chain_g0[mj+1].
+size_t tab_ints(const nfhmm_ctx* c) {
+  return (size_t)3 * c->max_jobs + 2 + c->Cmax + c->NGmax + 1 + c->max_jobs + 1;
+}
+
+int groups_for(const nfhmm_ctx* c, int chunks) {
+  return c->fb.G >= 2 ? (chunks + c->fb.G - 1) / c->fb.G : 0;
+}
+
+// (Re)allocate the forward-backward scratch and the job tables for chunk
+// length fb.L and group size fb.G: room for every job set the frame store
+// and job slots allow.
 int ensure_fb_capacity(nfhmm_ctx* c) {
   const int need = (c->d.T + c->fb.L - 1) / c->fb.L + c->max_jobs;
-  if (c->fb_scratch && need <= c->Cmax) return NFHMM_OK;
+  const int gneed = c->fb.G >= 2 ? need / c->fb.G + 1 + c->max_jobs : 0;
+  if (c->fb_scratch && need <= c->Cmax && gneed <= c->NGmax) return NFHMM_OK;
   CK(cudaStreamSynchronize(c->s_main));
   CK(cudaStreamSynchronize(c->s_aux));
   if (c->fb_scratch) {
     cudaFree(c->fb_scratch);
-    c->device_bytes -= fb_scratch_bytes(c->d.S, c->d.N, c->Cmax);
+    c->device_bytes -= fb_scratch_bytes(c->d.S, c->d.N, c->Cmax, c->NGmax);
     c->fb_scratch = nullptr;
   }
   if (c->d_tab) {
     cudaFree(c->d_tab);
-    c->device_bytes -= (size_t)(3 * c->max_jobs + 2 + c->Cmax) * sizeof(int);
+    c->device_bytes -= tab_ints(c) * sizeof(int);
     c->d_tab = nullptr;
   }
-  c->Cmax = 0;
-  const size_t sb = fb_scratch_bytes(c->d.S, c->d.N, need);
-  const size_t tb = (size_t)(3 * c->max_jobs + 2 + need) * sizeof(int);
-  CK(dmalloc(c, &c->fb_scratch, sb));
-  CK(dmalloc(c, (void**)&c->d_tab, tb));
   c->Cmax = need;
-  c->fb.C = need;
-  fb_carve_scratch(c->fb, c->fb_scratch);   // regions sized for Cmax chunks
-  c->fb.chain_c0 = c->d_tab + (c->max_jobs + 1);
+  c->NGmax = gneed;
+  CK(dmalloc(c, &c->fb_scratch, fb_scratch_bytes(c->d.S, c->d.N, c->Cmax, c->NGmax)));
+  CK(dmalloc(c, (void**)&c->d_tab, tab_ints(c) * sizeof(int)));
+  c->fb.C = c->Cmax;
+  c->fb.NG = c->NGmax;
+  fb_carve_scratch(c->fb, c->fb_scratch);   // regions sized for Cmax chunks, NGmax groups
+  const int mj = c->max_jobs;
   c->fb.chain_t0 = c->d_tab;
-  c->fb.chain_len = c->d_tab + 2 * (c->max_jobs + 1);
-  c->fb.chunk_chain = c->d_tab + 3 * c->max_jobs + 2;
+  c->fb.chain_c0 = c->d_tab + (mj + 1);
+  c->fb.chain_len = c->d_tab + 2 * (mj + 1);
+  c->fb.chunk_chain = c->d_tab + 3 * mj + 2;
+  c->fb.grp_c0 = c->d_tab + 3 * mj + 2 + c->Cmax;
+  c->fb.chain_g0 = c->fb.grp_c0 + c->NGmax + 1;
   c->fb.C = fb_chunks(c);
+  c->fb.NG = 0;
   return NFHMM_OK;
 }
 
@@ -515,25 +534,32 @@ int ensure_fb_capacity(nfhmm_ctx* c) {
 int commit_jobs(nfhmm_ctx* c) {
   const int nj = (int)c->jobs.size(), mj = c->max_jobs;
   const int C = fb_chunks(c);
-  std::vector<int> tab((size_t)3 * mj + 2 + C, 0);
+  std::vector<int> tab(tab_ints(c), 0);
   int* job_t0 = tab.data();
   int* chain_c0 = job_t0 + (mj + 1);
   int* chain_len = chain_c0 + (mj + 1);
   int* chunk_chain = chain_len + mj;
-  int cc = 0;
+  int* grp_c0 = chunk_chain + c->Cmax;
+  int* chain_g0 = grp_c0 + c->NGmax + 1;
+  int cc = 0, ng = 0;
   for (int j = 0; j < nj; ++j) {
     job_t0[j] = c->jobs[j].t0;
     chain_c0[j] = cc;
+    chain_g0[j] = ng;
     chain_len[j] = c->jobs[j].T;
     const int nc = (c->jobs[j].T + c->fb.L - 1) / c->fb.L;
     for (int q = 0; q < nc; ++q) chunk_chain[cc + q] = j;
+    for (int k = 0; k < groups_for(c, nc); ++k) grp_c0[ng++] = cc + k * c->fb.G;
     cc += nc;
   }
   job_t0[nj] = c->T_active;
   chain_c0[nj] = cc;
+  chain_g0[nj] = ng;
+  if (c->NGmax > 0) grp_c0[ng] = cc;
   CK(cudaMemcpyAsync(c->d_tab, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice,
                      c->s_main));
   c->fb.C = C;
+  c->fb.NG = ng;
   c->fb.nchains = nj;
   c->have_alpha = false;
   c->bpart_ok = false;
@@ -768,6 +794,10 @@ int create_ctx(nfhmm_ctx** out, const nfhmm_dims* dp, int max_jobs, const float*
   c->fb.T = d.T;   // frame stride of phi-hat and d-hat
   c->fb.L = max_jobs == 1 ? fb_default_chunk(d.N, d.T) : fb_default_chunk(d.N, d.T < 4096 ? d.T : 4096);
   c->fb.products = FB_PRODUCTS_TC;
+  {
+    const int tref = max_jobs == 1 ? d.T : (d.T < 4096 ? d.T : 4096);
+    c->fb.G = fb_default_group((tref + c->fb.L - 1) / c->fb.L);
+  }
   c->fb.phi = c->phi;
   c->fb.A = c->A;
   c->fb.pi = c->pi;
@@ -806,6 +836,8 @@ long long graph_key_of(const nfhmm_ctx* c, int n, bool want_bpart) {
   k = k * 1000003 + c->fb.C;
   k = k * 1048583 + c->fb.nchains;
   k = k * 131 + c->fb.L;
+  k = k * 4099 + c->fb.G;
+  k = k * 1000033 + c->fb.NG;
   k = k * 3 + c->fb.products;
   k = k * 1009 + n;
   k = k * 2 + (want_bpart ? 1 : 0);
@@ -1052,13 +1084,27 @@ int nfhmm_job_posteriors(nfhmm_ctx* c, long long job_id, float* dhat, int on_dev
 int nfhmm_set_option(nfhmm_ctx* c, int key, long long value) {
   if (!c) return fail(NFHMM_EINVAL, "NULL context");
   switch (key) {
-    case NFHMM_OPT_FB_CHUNK: {
-      if (value < 1 || value > 128) return fail(NFHMM_EINVAL, "chunk length must be in [1, 128]");
-      const int old = c->fb.L;
-      c->fb.L = (int)value;
+    case NFHMM_OPT_FB_CHUNK:
+    case NFHMM_OPT_FB_GROUP: {
+      if (key == NFHMM_OPT_FB_CHUNK && (value < 1 || value > 128))
+        return fail(NFHMM_EINVAL, "chunk length must be in [1, 128]");
+      if (key == NFHMM_OPT_FB_GROUP && (value < -1 || value == 1 || value > 4096))
+        return fail(NFHMM_EINVAL, "group size must be -1 (automatic), 0 (none) or 2..4096");
+      const int oldL = c->fb.L, oldG = c->fb.G;
+      const bool old_auto = c->group_auto;
+      if (key == NFHMM_OPT_FB_CHUNK) c->fb.L = (int)value;
+      if (key == NFHMM_OPT_FB_GROUP) c->group_auto = value < 0;
+      if (c->group_auto) {
+        const int tref = c->max_jobs == 1 ? c->d.T : (c->d.T < 4096 ? c->d.T : 4096);
+        c->fb.G = fb_default_group((tref + c->fb.L - 1) / c->fb.L);
+      } else if (key == NFHMM_OPT_FB_GROUP) {
+        c->fb.G = (int)value;
+      }
       int rc = ensure_fb_capacity(c);
       if (rc) {
-        c->fb.L = old;
+        c->fb.L = oldL;
+        c->fb.G = oldG;
+        c->group_auto = old_auto;
         return rc;
       }
       rc = enter(c);
@@ -1284,13 +1330,15 @@ int nfhmm_forward_backward(int S, int N, int T, const float* phi, const float* A
   a.C = (T + a.L - 1) / a.L;
   a.nchains = 1;   // one chain over all T frames (null chain tables)
   a.products = FB_PRODUCTS_TC;
+  a.G = fb_default_group(a.C);
+  a.NG = a.G >= 2 ? (a.C + a.G - 1) / a.G : 0;
   a.phi = phi;
   a.A = A;
   a.pi = pi;
   a.dhat = dhat;
   a.logZ = logZ;
   void* scratch = nullptr;
-  const size_t bytes = fb_scratch_bytes(S, N, a.C) + 256;
+  const size_t bytes = fb_scratch_bytes(S, N, a.C, a.NG) + 256;
   CK(cudaMallocAsync(&scratch, bytes, st));
   fb_carve_scratch(a, scratch);
   a.err = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(scratch) + bytes - 256);
@@ -1351,6 +1399,7 @@ int nfhmm_query(nfhmm_ctx* c, int key, long long* value) {
   switch (key) {
     case NFHMM_Q_TENSOR_CORES: *value = c->use_tc ? 1 : 0; return NFHMM_OK;
     case NFHMM_Q_FB_CHUNK: *value = c->fb.L; return NFHMM_OK;
+    case NFHMM_Q_FB_GROUP: *value = c->fb.G; return NFHMM_OK;
     case NFHMM_Q_SWEEPS_DONE: *value = c->sweeps_done; return NFHMM_OK;
     case NFHMM_Q_DEVICE_BYTES: *value = (long long)c->device_bytes; return NFHMM_OK;
     case NFHMM_Q_FRAME_CAPACITY: *value = c->d.T; return NFHMM_OK;

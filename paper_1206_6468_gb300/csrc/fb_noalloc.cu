@@ -70,7 +70,9 @@ int nfhmm_forward_backward_noalloc(int S, int N, int T, const float* phi, const 
   a.C = (T + a.L - 1) / a.L;
   a.nchains = 1;   // one chain over all T frames (null chain tables)
   a.products = FB_PRODUCTS_TC;
-  const size_t need = fb_scratch_bytes(S, N, a.C) + 256;  // + error word
+  a.G = fb_default_group(a.C);
+  a.NG = a.G >= 2 ? (a.C + a.G - 1) / a.G : 0;
+  const size_t need = fb_scratch_bytes(S, N, a.C, a.NG) + 256;  // + error word
   if (need > (size_t)NFHMM_NOALLOC_SCRATCH_BYTES)
     return fail(NFHMM_EINVAL, "problem needs " + std::to_string(need) +
                                   " bytes of scratch; the fixed array holds " +

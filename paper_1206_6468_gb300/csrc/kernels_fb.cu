@@ -505,21 +505,42 @@ __global__ void __launch_bounds__(128) k_fb_products_simt(FBArgs a) {
 // chunk c (bwd[C-1] = 1); y_i = sum_j P[i][j] v_j reads row i of P.
 // Matrices are staged with rows padded to NP + 4 floats (conflict-free
 // float4 reads).  The vector is rescaled by the previous step's sum.
-template <int NP>
+// MODE_CHAINS: one warp per (chain, direction) over the chain's units (the
+// chunks, or the groups when called with the group arrays in place of the
+// chunk arrays), as above.
+// MODE_GROUP_REPLAY: one warp per (group, direction) over the group's chunks,
+// started from the group-level boundary vectors (pi / ones at a chain's
+// ends); writes the chunk boundary vectors only.
+enum { MODE_CHAINS = 0, MODE_GROUP_REPLAY = 1 };
+template <int NP, int MODE>
 __global__ void __launch_bounds__(32) k_fb_scan(FBArgs a) {
   extern __shared__ float sm[];
   constexpr int LD = NP + 4;
   constexpr int NN = NP * LD;
   constexpr int CPL = (NP * NP / 4 + 31) / 32;   // 16-byte copies per lane per matrix
   const int N = a.N, C = a.C;
-  const int s = blockIdx.x / a.nchains, chain = blockIdx.x - s * a.nchains;
   const bool fwd = blockIdx.y == 0;
   const int lane = threadIdx.x;
   float* ring = sm;                      // RING x NP x LD
   float* v = ring + RING * NN;           // 64
+  int s, chain = 0, c0, c1;
+  bool first = true, last = true;        // group replay: the group opens / closes its chain
+  if (MODE == MODE_CHAINS) {
+    s = blockIdx.x / a.nchains;
+    chain = blockIdx.x - s * a.nchains;
+    c0 = a.chain_c0 ? a.chain_c0[chain] : 0;
+    c1 = a.chain_c0 ? a.chain_c0[chain + 1] : C;   // the chain's units [c0, c1)
+  } else {
+    s = blockIdx.x / a.NG;
+    const int g = blockIdx.x - s * a.NG;
+    c0 = a.grp_c0 ? a.grp_c0[g] : g * a.G;
+    c1 = a.grp_c0 ? a.grp_c0[g + 1] : min((g + 1) * a.G, C);
+    const int j = a.chunk_chain ? a.chunk_chain[c0] : 0;
+    first = c0 == (a.chain_c0 ? a.chain_c0[j] : 0);
+    last = c1 == (a.chain_c0 ? a.chain_c0[j + 1] : C);
+    chain = g;   // for the start vectors below
+  }
   const size_t base = (size_t)s * C;
-  const int c0 = a.chain_c0 ? a.chain_c0[chain] : 0;
-  const int c1 = a.chain_c0 ? a.chain_c0[chain + 1] : C;   // the chain's chunks [c0, c1)
   const float* src = fwd ? a.PT : a.P;
   const int nsteps = fwd ? c1 - c0 : c1 - c0 - 1;
   auto chunk_of = [&](int q) { return fwd ? c0 + q : c1 - 1 - q; };
@@ -548,13 +569,22 @@ __global__ void __launch_bounds__(32) k_fb_scan(FBArgs a) {
   const int j0 = lane < NP ? lane : 0, j1 = lane + 32 < NP ? lane + 32 : 0;
   float r0 = 0.f, r1 = 0.f;
   if (fwd) {
-    if (h0) r0 = a.pi[(size_t)s * N + lane];
-    if (h1) r1 = a.pi[(size_t)s * N + lane + 32];
+    const float* st = (MODE == MODE_CHAINS || first)
+                          ? a.pi + (size_t)s * N
+                          : a.gfwd + ((size_t)s * a.NG + chain - 1) * N;
+    if (h0) r0 = st[lane];
+    if (h1) r1 = st[lane + 32];
   } else {
-    r0 = h0 ? 1.f : 0.f;
-    r1 = h1 ? 1.f : 0.f;
-    if (h0) a.bwd[(base + c1 - 1) * N + lane] = 1.f;
-    if (h1) a.bwd[(base + c1 - 1) * N + lane + 32] = 1.f;
+    if (MODE == MODE_CHAINS || last) {
+      r0 = h0 ? 1.f : 0.f;
+      r1 = h1 ? 1.f : 0.f;
+    } else {
+      const float* st = a.gbwd + ((size_t)s * a.NG + chain) * N;
+      if (h0) r0 = st[lane];
+      if (h1) r1 = st[lane + 32];
+    }
+    if (h0) a.bwd[(base + c1 - 1) * N + lane] = r0;
+    if (h1) a.bwd[(base + c1 - 1) * N + lane + 32] = r1;
   }
   // u_prev: the previous step's output, not yet normalised; its sum (the
   // previous chunk's normaliser) is reduced while this step's products run.
@@ -565,7 +595,7 @@ __global__ void __launch_bounds__(32) k_fb_scan(FBArgs a) {
     if (fwd) {
       if (h0) a.fwd[(base + c) * N + lane] = w0 * il;
       if (h1) a.fwd[(base + c) * N + lane + 32] = w1 * il;
-      if (lane == 0) a.lam[base + c] = removed_scale(lam_q);
+      if (MODE == MODE_CHAINS && lane == 0) a.lam[base + c] = removed_scale(lam_q);
     } else {
       if (h0) a.bwd[(base + c - 1) * N + lane] = w0 * il;
       if (h1) a.bwd[(base + c - 1) * N + lane + 32] = w1 * il;
@@ -616,13 +646,166 @@ __global__ void __launch_bounds__(32) k_fb_scan(FBArgs a) {
     emit(nsteps - 1, lam, u0, u1);
   }
   cp_async_wait<0>();
-  if (fwd) {
+  if (MODE == MODE_CHAINS && fwd) {
     __syncwarp();
     __threadfence_block();
     double lg = 0.0;
     for (int c = c0 + lane; c < c1; c += 32) lg += a.Plog[base + c] + log((double)a.lam[base + c]);
     lg = warp_sum_d(lg);
     if (lane == 0) a.logZ[(size_t)s * a.nchains + chain] = lg;
+  }
+}
+
+// ------------------------------------------------------ 2'. group products
+// Q_g = P_c0 P_c0+1 ... P_c1-1 for each group of chunks, row by row: row i is
+// the forward chain started from the basis vector e_i, one warp advancing
+// two rows over the group's chunk matrices (staged once per block with
+// cp.async and shared by its four warps).  Each row is rescaled by the sum
+// of its previous value; the removed factors are kept per row and the rows
+// brought to a common scale by k_fb_group_flatten.
+constexpr int GRING = 4;
+template <int NP>
+__global__ void __launch_bounds__(128) k_fb_group_products(FBArgs a) {
+  constexpr int LD = NP + 4;
+  constexpr int NN = NP * LD;
+  constexpr int CPT = (NP * NP / 4 + 127) / 128;   // 16-byte copies per thread per matrix
+  extern __shared__ float sm[];
+  float* ring = sm;                     // GRING x NP x LD
+  float* vbuf = ring + GRING * NN;      // 4 warps x 2 rows x 64
+  const int N = a.N, C = a.C;
+  const int s = blockIdx.z, g = blockIdx.y;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int c0 = a.grp_c0 ? a.grp_c0[g] : g * a.G;
+  const int c1 = a.grp_c0 ? a.grp_c0[g + 1] : min((g + 1) * a.G, C);
+  const int nsteps = c1 - c0;
+  const size_t cbase = (size_t)s * C;
+  int soff[CPT], doff[CPT];
+#pragma unroll
+  for (int m = 0; m < CPT; ++m) {
+    const int i = (tid + 128 * m) * 4;
+    soff[m] = i < NP * NP ? i : -1;
+    doff[m] = (i / NP) * LD + (i % NP);
+  }
+  auto prefetch = [&](int q) {
+    if (q < nsteps) {
+      const float* gsrc = a.PT + (cbase + c0 + q) * NP * NP;
+      float* d = ring + (q % GRING) * NN;
+#pragma unroll
+      for (int m = 0; m < CPT; ++m)
+        if (soff[m] >= 0) cp_async16(d + doff[m], gsrc + soff[m]);
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int q = 0; q < GRING - 1; ++q) prefetch(q);
+
+  const int ia = blockIdx.x * 8 + warp * 2, ib = ia + 1;
+  const bool la = ia < N, lb = ib < N;
+  const bool h0 = lane < N, h1 = lane + 32 < N;
+  const int j0 = lane < NP ? lane : 0, j1 = lane + 32 < NP ? lane + 32 : 0;
+  float ua0 = (la && lane == ia) ? 1.f : 0.f, ua1 = (la && lane + 32 == ia) ? 1.f : 0.f;
+  float ub0 = (lb && lane == ib) ? 1.f : 0.f, ub1 = (lb && lane + 32 == ib) ? 1.f : 0.f;
+  ScaleAcc sca, scb;
+  float* va = vbuf + warp * 128;
+  float* vb = va + 64;
+  unsigned bad = 0;
+  for (int q = 0; q < nsteps; ++q) {
+    cp_async_wait<GRING - 2>();
+    __syncthreads();              // matrix q landed; every warp is past step q - 1
+    prefetch(q + GRING - 1);      // into the slot step q - 1 read
+    va[lane] = ua0;
+    va[lane + 32] = ua1;
+    vb[lane] = ub0;
+    vb[lane + 32] = ub1;
+    __syncwarp();
+    float lama = warp_sum(ua0 + ua1), lamb = warp_sum(ub0 + ub1);
+    if (q > 0) {
+      if (!isfinite(lama) || !isfinite(lamb)) bad = 1;
+      sca.mul(removed_scale(lama));
+      scb.mul(removed_scale(lamb));
+    }
+    const float* P = ring + (q % GRING) * NN;
+    float ya0[4] = {0.f, 0.f, 0.f, 0.f}, ya1[4] = {0.f, 0.f, 0.f, 0.f};
+    float yb0[4] = {0.f, 0.f, 0.f, 0.f}, yb1[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int i = 0; i < NP; i += 4) {
+      const float4 xa = *reinterpret_cast<const float4*>(&va[i]);
+      const float4 xb = *reinterpret_cast<const float4*>(&vb[i]);
+      const float4 p0 = *reinterpret_cast<const float4*>(&P[j0 * LD + i]);
+      ya0[0] = fmaf(xa.x, p0.x, ya0[0]);
+      ya0[1] = fmaf(xa.y, p0.y, ya0[1]);
+      ya0[2] = fmaf(xa.z, p0.z, ya0[2]);
+      ya0[3] = fmaf(xa.w, p0.w, ya0[3]);
+      yb0[0] = fmaf(xb.x, p0.x, yb0[0]);
+      yb0[1] = fmaf(xb.y, p0.y, yb0[1]);
+      yb0[2] = fmaf(xb.z, p0.z, yb0[2]);
+      yb0[3] = fmaf(xb.w, p0.w, yb0[3]);
+      if (NP > 32) {
+        const float4 p1 = *reinterpret_cast<const float4*>(&P[j1 * LD + i]);
+        ya1[0] = fmaf(xa.x, p1.x, ya1[0]);
+        ya1[1] = fmaf(xa.y, p1.y, ya1[1]);
+        ya1[2] = fmaf(xa.z, p1.z, ya1[2]);
+        ya1[3] = fmaf(xa.w, p1.w, ya1[3]);
+        yb1[0] = fmaf(xb.x, p1.x, yb1[0]);
+        yb1[1] = fmaf(xb.y, p1.y, yb1[1]);
+        yb1[2] = fmaf(xb.z, p1.z, yb1[2]);
+        yb1[3] = fmaf(xb.w, p1.w, yb1[3]);
+      }
+    }
+    const float fa = q > 0 ? renorm_factor(lama) : 1.f;
+    const float fb = q > 0 ? renorm_factor(lamb) : 1.f;
+    ua0 = h0 ? ((ya0[0] + ya0[1]) + (ya0[2] + ya0[3])) * fa : 0.f;
+    ua1 = h1 ? ((ya1[0] + ya1[1]) + (ya1[2] + ya1[3])) * fa : 0.f;
+    ub0 = h0 ? ((yb0[0] + yb0[1]) + (yb0[2] + yb0[3])) * fb : 0.f;
+    ub1 = h1 ? ((yb1[0] + yb1[1]) + (yb1[2] + yb1[3])) * fb : 0.f;
+  }
+  cp_async_wait<0>();
+  // final normalisation; rows of this group's product, and their log scales
+  const float sa = warp_sum(ua0 + ua1), sb = warp_sum(ub0 + ub1);
+  if (!isfinite(sa) || !isfinite(sb)) bad = 1;
+  const float fa = renorm_factor(sa), fb = renorm_factor(sb);
+  sca.mul(removed_scale(sa));
+  scb.mul(removed_scale(sb));
+  const size_t qb = ((size_t)s * a.NG + g) * NP * NP;
+  const size_t rb = ((size_t)s * a.NG + g) * NP;
+  if (ia < NP) {
+    if (lane < NP) a.Q[qb + (size_t)ia * NP + lane] = la ? ua0 * fa : 0.f;
+    if (lane + 32 < NP) a.Q[qb + (size_t)ia * NP + lane + 32] = la ? ua1 * fa : 0.f;
+    if (lane == 0) a.rowlog[rb + ia] = (la && sa > 0.f) ? sca.log() : -INFINITY;
+  }
+  if (ib < NP) {
+    if (lane < NP) a.Q[qb + (size_t)ib * NP + lane] = lb ? ub0 * fb : 0.f;
+    if (lane + 32 < NP) a.Q[qb + (size_t)ib * NP + lane + 32] = lb ? ub1 * fb : 0.f;
+    if (lane == 0) a.rowlog[rb + ib] = (lb && sb > 0.f) ? scb.log() : -INFINITY;
+  }
+  if (bad && lane == 0) atomicOr(a.err, ERR_FB_ZERO);
+}
+
+// Bring each group product's rows to a common scale (the largest row scale)
+// and write Q, its transpose and its log scale (sum of the chunks' scales).
+template <int NP>
+__global__ void __launch_bounds__(64) k_fb_group_flatten(FBArgs a) {
+  const int g = blockIdx.x, s = blockIdx.y, i = threadIdx.x;
+  const int N = a.N;
+  const size_t qb = ((size_t)s * a.NG + g) * NP * NP;
+  const size_t rb = ((size_t)s * a.NG + g) * NP;
+  double rmax = -INFINITY;
+  for (int k = 0; k < N; ++k) rmax = fmax(rmax, a.rowlog[rb + k]);
+  if (i < NP) {
+    const double lr = a.rowlog[rb + i];
+    const float f = (i < N && rmax > -INFINITY && lr > -INFINITY) ? (float)exp(lr - rmax) : 0.f;
+    for (int j = 0; j < NP; ++j) {
+      const float v = a.Q[qb + (size_t)i * NP + j] * f;
+      a.Q[qb + (size_t)i * NP + j] = v;
+      a.QT[qb + (size_t)j * NP + i] = v;
+    }
+  }
+  if (i == 0) {
+    const int c0 = a.grp_c0 ? a.grp_c0[g] : g * a.G;
+    const int c1 = a.grp_c0 ? a.grp_c0[g + 1] : min((g + 1) * a.G, a.C);
+    double lg = rmax > -INFINITY ? rmax : 0.0;
+    for (int c = c0; c < c1; ++c) lg += a.Plog[(size_t)s * a.C + c];
+    a.Qlog[(size_t)s * a.NG + g] = lg;
   }
 }
 
@@ -799,6 +982,10 @@ static size_t smem_products_simt(int L) {
          (size_t)(NP * NP + 128 * (NP + 1) + 8 + (128 / NP) * L * NP) * sizeof(float);
 }
 template <int NP>
+static size_t smem_group() {
+  return (size_t)(GRING * NP * (NP + 4) + 4 * 128) * sizeof(float);
+}
+template <int NP>
 static size_t smem_scan() {
   return (size_t)(RING * NP * (NP + 4) + 64) * sizeof(float);
 }
@@ -816,8 +1003,17 @@ static cudaError_t launch_np(const FBArgs& a, cudaStream_t st) {
     attr = cudaFuncSetAttribute(k_fb_products<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem_products<NP>(FB_MAX_L));
     if (attr == cudaSuccess)
-      attr = cudaFuncSetAttribute(k_fb_scan<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      attr = cudaFuncSetAttribute(k_fb_scan<NP, MODE_CHAINS>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem_scan<NP>());
+    if (attr == cudaSuccess)
+      attr = cudaFuncSetAttribute(k_fb_scan<NP, MODE_GROUP_REPLAY>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem_scan<NP>());
+    if (attr == cudaSuccess)
+      attr = cudaFuncSetAttribute(k_fb_group_products<NP>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem_group<NP>());
     if (attr == cudaSuccess)
       attr = cudaFuncSetAttribute(k_fb_replay<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)SMEM_OPTIN);
@@ -835,7 +1031,25 @@ static cudaError_t launch_np(const FBArgs& a, cudaStream_t st) {
   else
     k_fb_products_simt<NP><<<dim3((a.C + Cfg::RCH - 1) / Cfg::RCH, a.S), 128,
                              smem_products_simt<NP>(a.L), st>>>(a);
-  k_fb_scan<NP><<<dim3(a.S * a.nchains, 2), 32, smem_scan<NP>(), st>>>(a);
+  if (a.G >= 2) {
+    // group products, the scan across groups (the chain scan over the group
+    // arrays), then each group's chunk boundaries
+    k_fb_group_products<NP><<<dim3(NP / 8, a.NG, a.S), 128, smem_group<NP>(), st>>>(a);
+    k_fb_group_flatten<NP><<<dim3(a.NG, a.S), 64, 0, st>>>(a);
+    FBArgs b = a;
+    b.C = a.NG;
+    b.chain_c0 = a.chain_g0;
+    b.P = a.Q;
+    b.PT = a.QT;
+    b.Plog = a.Qlog;
+    b.fwd = a.gfwd;
+    b.bwd = a.gbwd;
+    b.lam = a.glam;
+    k_fb_scan<NP, MODE_CHAINS><<<dim3(a.S * a.nchains, 2), 32, smem_scan<NP>(), st>>>(b);
+    k_fb_scan<NP, MODE_GROUP_REPLAY><<<dim3(a.S * a.NG, 2), 32, smem_scan<NP>(), st>>>(a);
+  } else {
+    k_fb_scan<NP, MODE_CHAINS><<<dim3(a.S * a.nchains, 2), 32, smem_scan<NP>(), st>>>(a);
+  }
   k_fb_replay<NP><<<dim3((a.C + rc - 1) / rc, a.S), rc * 64, rc * smem_replay_chunk(NP, a.L),
                     st>>>(a);
   return cudaGetLastError();
@@ -847,8 +1061,9 @@ int fb_chunk_count(const int* chain_len, int nchains, int L) {
   return C;
 }
 
-size_t fb_scratch_bytes(int S, int N, int C) {
+size_t fb_scratch_bytes(int S, int N, int C, int NG) {
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t P = pad8(N);
   size_t b = 0;
   b += al((size_t)S * C * mat_floats(N) * sizeof(float));  // P
   b += al((size_t)S * C * mat_floats(N) * sizeof(float));  // P^T
@@ -856,12 +1071,19 @@ size_t fb_scratch_bytes(int S, int N, int C) {
   b += al((size_t)S * C * N * sizeof(float));              // fwd
   b += al((size_t)S * C * sizeof(float));                  // lam
   b += al((size_t)S * C * N * sizeof(float));              // bwd
+  b += al((size_t)S * NG * mat_floats(N) * sizeof(float)); // Q
+  b += al((size_t)S * NG * mat_floats(N) * sizeof(float)); // Q^T
+  b += al((size_t)S * NG * sizeof(double));                // Qlog
+  b += al((size_t)S * NG * P * sizeof(double));            // rowlog
+  b += al((size_t)S * NG * N * sizeof(float));             // gfwd
+  b += al((size_t)S * NG * N * sizeof(float));             // gbwd
+  b += al((size_t)S * NG * sizeof(float));                 // glam
   return b;
 }
 
 void fb_carve_scratch(FBArgs& a, void* base) {
   char* p = reinterpret_cast<char*>(base);
-  const size_t S = a.S, C = a.C, N = a.N;
+  const size_t S = a.S, C = a.C, N = a.N, NG = a.NG, P = pad8(a.N);
   auto take = [&](size_t bytes) {
     char* r = p;
     p += (bytes + 255) & ~(size_t)255;
@@ -873,10 +1095,25 @@ void fb_carve_scratch(FBArgs& a, void* base) {
   a.fwd = reinterpret_cast<float*>(take(S * C * N * sizeof(float)));
   a.lam = reinterpret_cast<float*>(take(S * C * sizeof(float)));
   a.bwd = reinterpret_cast<float*>(take(S * C * N * sizeof(float)));
+  a.Q = reinterpret_cast<float*>(take(S * NG * mat_floats((int)N) * sizeof(float)));
+  a.QT = reinterpret_cast<float*>(take(S * NG * mat_floats((int)N) * sizeof(float)));
+  a.Qlog = reinterpret_cast<double*>(take(S * NG * sizeof(double)));
+  a.rowlog = reinterpret_cast<double*>(take(S * NG * P * sizeof(double)));
+  a.gfwd = reinterpret_cast<float*>(take(S * NG * N * sizeof(float)));
+  a.gbwd = reinterpret_cast<float*>(take(S * NG * N * sizeof(float)));
+  a.glam = reinterpret_cast<float*>(take(S * NG * sizeof(float)));
+}
+
+int fb_default_group(int C) {
+  // the grouped scan costs ~2G + C/G serial steps: G = sqrt(C/2); below
+  // ~24 chunks a plain scan is as short
+  if (C < 24) return 0;
+  int G = (int)ceil(sqrt(0.5 * (double)C));
+  return G < 2 ? 2 : G;
 }
 
 cudaError_t launch_fb(const FBArgs& a, cudaStream_t st, int* launches) {
-  if (launches) *launches += 3;
+  if (launches) *launches += a.G >= 2 ? 6 : 3;
   switch (pad8(a.N)) {
     case 8: return launch_np<8>(a, st);
     case 16: return launch_np<16>(a, st);

@@ -103,13 +103,29 @@ struct FBArgs {
   float* fwd;        // S x C x N        forward boundary vectors
   float* lam;        // S x C            forward scan normalisers
   float* bwd;        // S x C x N        backward boundary vectors
+  // Groups of G consecutive chunks of a chain (G >= 2; 0 = no groups): the
+  // scan across chunks becomes group products, a scan across groups and a
+  // replay of each group's chunk boundaries.  Group g covers chunks
+  // [grp_c0[g], grp_c0[g+1]); null tables: one chain, groups of G.
+  int G, NG;
+  const int* grp_c0;    // NG + 1
+  const int* chain_g0;  // nchains + 1: first group of each chain
+  float* Q;             // S x NG x NP x NP  group products (rows scaled to a common scale)
+  float* QT;            // S x NG x NP x NP  the same, transposed
+  double* Qlog;         // S x NG            log of each group product's scale
+  double* rowlog;       // S x NG x NP       per-row log scales before the common scale
+  float* gfwd;          // S x NG x N        forward vectors at group ends
+  float* gbwd;          // S x NG x N        backward vectors at group ends
+  float* glam;          // S x NG            group scan normalisers
   unsigned* err;
 };
 // chunks of L frames needed by chains of the given lengths
 int fb_chunk_count(const int* chain_len, int nchains, int L);
-size_t fb_scratch_bytes(int S, int N, int C);
-void fb_carve_scratch(FBArgs& a, void* base);
+size_t fb_scratch_bytes(int S, int N, int C, int NG);
+void fb_carve_scratch(FBArgs& a, void* base);   // regions for a.C chunks and a.NG groups
 int fb_default_chunk(int N, int T);
+// group size for chains of about C chunks (0: no groups)
+int fb_default_group(int C);
 int fb_max_states();
 cudaError_t launch_fb(const FBArgs& a, cudaStream_t st, int* launches);
 

@@ -29,8 +29,8 @@ INIT_UNIFORM, INIT_PRIOR = 0, 1
 SEP_MEAN, SEP_EXPECTATION = 0, 1
 STAGES = {"weights": 0, "gemm1": 1, "gemm2": 2, "fb": 3, "bound": 4, "init": 5}
 QUERIES = {"tensor_cores": 0, "fb_chunk": 1, "sweeps_done": 2, "device_bytes": 3,
-           "frame_capacity": 4, "max_jobs": 5}
-OPTIONS = {"fb_chunk": 0, "fb_products": 1, "graphs": 2}
+           "frame_capacity": 4, "max_jobs": 5, "fb_group": 6}
+OPTIONS = {"fb_chunk": 0, "fb_products": 1, "graphs": 2, "fb_group": 3}
 FB_PRODUCTS = {"simt": 0, "tc": 1}
 PRECISIONS = {"fp32": FP32, "bf16": BF16, "fp32_simt": FP32_SIMT}
 

@@ -38,12 +38,19 @@ def _f32(x):
     return np.ascontiguousarray(x, dtype=np.float32)
 
 
-def _alone(nf, jobs, j, chunk, precision="fp32", init_mode=0):
-    ctx = nf.VIContext(_f32(jobs.V[j]), _f32(jobs.W), _f32(jobs.A), _f32(jobs.pi), jobs.S,
-                       jobs.N, jobs.K, gamma=jobs.gamma, precision=precision,
-                       init_mode=init_mode)
-    ctx.set_option("fb_chunk", chunk)
+def _alone(nf, jobs, j, chunk, precision="fp32", init_mode=0, V=None):
+    """Job j in a context of its own, with the batch's forward-backward
+    geometry (chunk, group): the same kernels' arithmetic for its frames."""
+    V = _f32(jobs.V[j]) if V is None else V
+    ctx = nf.VIContext(V, _f32(jobs.W), _f32(jobs.A), _f32(jobs.pi), jobs.S, jobs.N, jobs.K,
+                       gamma=jobs.gamma, precision=precision, init_mode=init_mode)
+    ctx.set_option("fb_chunk", chunk[0])
+    ctx.set_option("fb_group", chunk[1])
     return ctx
+
+
+def _geometry(ctx):
+    return ctx.query("fb_chunk"), ctx.query("fb_group")
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16", "fp32_simt"])
@@ -54,7 +61,7 @@ def test_batch_equals_each_job_alone(nf, precision, init_mode):
     with nf.VIContext(jobs.stacked_V(), _f32(jobs.W), _f32(jobs.A), _f32(jobs.pi), jobs.S,
                       jobs.N, jobs.K, precision=precision, init_mode=init_mode,
                       job_frames=lengths) as b:
-        chunk = b.query("fb_chunk")
+        chunk = _geometry(b)
         total = b.sweep(4, bound=True)
         bounds = b.job_bounds()
         post = [b.job_posteriors(i) for i in b.job_ids]
@@ -111,7 +118,7 @@ def test_jobs_come_and_go(nf):
     f = {k: _f32(getattr(jobs, k)) for k in ("W", "A", "pi")}
     with nf.Batch(f["W"], f["A"], f["pi"], jobs.S, jobs.N, jobs.K, capacity=500,
                   max_jobs=3) as b:
-        chunk = b.query("fb_chunk")
+        chunk = _geometry(b)
         ids = [b.add(_f32(jobs.V[j])) for j in range(3)]
         b.sweep(3)
         b.remove(ids[1])                       # the frames of the third job move down
@@ -127,8 +134,7 @@ def test_jobs_come_and_go(nf):
         bounds = dict(zip([j[0] for j in b.jobs()], b.job_bounds()))
     for j, sweeps, idx in ((0, 7, 0), (2, 7, 2), (3, 2, 3)):
         V = np.ascontiguousarray(_f32(jobs.V[j])[:300]) if j == 3 else _f32(jobs.V[j])
-        with nf.VIContext(V, f["W"], f["A"], f["pi"], jobs.S, jobs.N, jobs.K) as a:
-            a.set_option("fb_chunk", chunk)
+        with _alone(nf, jobs, j, chunk, V=V) as a:
             L = a.sweep(sweeps, bound=True)
             d = a.posteriors()
         assert np.array_equal(got[ids[idx]], d), j
@@ -147,7 +153,7 @@ def test_many_jobs_in_and_out_at_once(nf):
     f = {k: _f32(getattr(jobs, k)) for k in ("W", "A", "pi")}
     with nf.Batch(f["W"], f["A"], f["pi"], jobs.S, jobs.N, jobs.K, capacity=400,
                   max_jobs=6) as b:
-        chunk = b.query("fb_chunk")
+        chunk = _geometry(b)
         assert b.query("frame_capacity") == 400 and b.query("max_jobs") == 6
         ids = b.add_many([_f32(jobs.V[j]) for j in range(5)])
         b.sweep_async(2)
@@ -170,7 +176,7 @@ def test_batch_full_and_invalid_job_leave_batch_unchanged(nf):
     f = {k: _f32(getattr(jobs, k)) for k in ("W", "A", "pi")}
     with nf.Batch(f["W"], f["A"], f["pi"], jobs.S, jobs.N, jobs.K, capacity=150,
                   max_jobs=4) as b:
-        chunk = b.query("fb_chunk")
+        chunk = _geometry(b)
         i0 = b.add(_f32(jobs.V[0]))
         with pytest.raises(nf.NfhmmError) as e:
             b.add(_f32(jobs.V[1]))               # 200 frames > capacity 150
@@ -183,8 +189,7 @@ def test_batch_full_and_invalid_job_leave_batch_unchanged(nf):
         assert [j[0] for j in b.jobs()] == [i0] and b.T == 100
         b.sweep(2)
         d = b.job_posteriors(i0)
-    with nf.VIContext(_f32(jobs.V[0]), f["W"], f["A"], f["pi"], jobs.S, jobs.N, jobs.K) as a:
-        a.set_option("fb_chunk", chunk)
+    with _alone(nf, jobs, 0, chunk) as a:
         a.sweep(2)
         assert np.array_equal(a.posteriors(), d)
 

@@ -79,6 +79,8 @@ def test_digamma_and_weights(nf):
     (1, 16, 3000, 0, 20.0),   # tiles exactly full of chunk rows; emissions underflow
     (2, 24, 2000, 0, 80.0),   # very sharp emissions: rows vanish, sums go subnormal
     (1, 8, 777, 0, 20.0),     # many chunks per tile, ragged tail
+    (2, 40, 3000, 10, 20.0),  # two-level scan whose last group holds one chunk
+    (1, 40, 3000, 2, 20.0),   # 1500 chunks: groups of 28
 ])
 def test_forward_backward(nf, S, N, T, L, scale):
     import torch
