@@ -39,7 +39,12 @@ namespace nfhmm {
 namespace {
 constexpr int FB_MAX_N = 64;
 constexpr int FB_MAX_L = 128;
-constexpr int RING = 8;             // scan: prefetch depth
+// scan: prefetch depth (a step waits on a copy issued RING - 1 steps
+// earlier), as deep as the shared memory allows
+template <int NP>
+struct ScanRing {
+  static constexpr int R = NP <= 48 ? 16 : 8;
+};
 constexpr int R_CHUNKS_MAX = 4;     // replay: chunks per block (2 warps each)
 constexpr size_t SMEM_OPTIN = 227 * 1024;
 
@@ -72,6 +77,12 @@ struct ScaleAcc {
   __device__ __forceinline__ double log() const { return (double)e * 0.6931471805599453 + ::log((double)m); }
 };
 
+// 4-byte asynchronous copy (cp.async.ca): many in flight per thread, so a
+// scattered gather into shared memory pays the global latency once
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem));
+}
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
@@ -81,6 +92,26 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
 }
+// The row with the largest scale among n (mantissa m in [0.5, 1), or 0 for a
+// row that vanished, and binary exponent e), or -1 if every row vanished.  A
+// row's factor relative to it is then ldexpf(m / m_max, e - e_max), one
+// rounding, and no double-precision work per row.
+__device__ __forceinline__ int scale_argmax(const float* m, const int* e, int n) {
+  int best = -1;
+  float bk = -INFINITY;
+  for (int i = 0; i < n; ++i) {
+    if (m[i] > 0.f) {
+      const float k = (float)e[i] + log2f(m[i]);
+      if (k > bk) {
+        bk = k;
+        best = i;
+      }
+    }
+  }
+  return best;
+}
+constexpr double LN2 = 0.69314718055994530942;
+
 struct ChunkInfo {
   int t0, len, chain;
   bool first;
@@ -103,10 +134,11 @@ __device__ __forceinline__ ChunkInfo chunk_info(const FBArgs& a, int c) {
 int fb_max_states() { return FB_MAX_N; }
 
 int fb_default_chunk(int N, int T) {
-  // products cost ~L serial tensor-core steps, the scan ~T/L warp steps:
-  // chunks of ~sqrt(T)/2 frames balance them (16..64).
-  int L = (int)ceil(0.5 * sqrt((double)T));
-  if (L < 16) L = 16;
+  // products and replay cost ~L serial frame steps, the two-level scan
+  // ~2 sqrt(T/(2L)) chunk steps: chunks of ~0.3 sqrt(T) frames (8..64)
+  // balance them (measured optimum 16 at T = 3000).
+  int L = (int)lround(0.3 * sqrt((double)T));
+  if (L < 8) L = 8;
   if (L > 64) L = 64;
   if (L > T) L = T;
   (void)N;
@@ -166,17 +198,8 @@ __global__ void __launch_bounds__(128, 1) k_fb_products(FBArgs a) {
     tmem_alloc(tslot, Cfg::TMEM_COLS);
     tmem_relinquish();
   }
-  // B operand: B[j][k] = A[k][j] (zero outside N x N), split into tf32 hi/lo
-  const float* Ag = a.A + (size_t)s * N * N;
-  for (int idx = tid; idx < NOUT * Cfg::KATOMS * 32; idx += blockDim.x) {
-    const int j = idx / (Cfg::KATOMS * 32), k = idx - j * (Cfg::KATOMS * 32);
-    const float v = (j < N && k < N) ? Ag[k * N + j] : 0.f;
-    const float h = tf32_hi(v);
-    const uint32_t off = sw128_off(j, k, NOUT * 128);
-    *reinterpret_cast<float*>(b_hi + off) = h;
-    *reinterpret_cast<float*>(b_lo + off) = tf32_hi(v - h);
-  }
-  // emissions of the tile's chunks: exp(phi - max over states), per frame
+  // emissions of the tile's chunks (gathered with asynchronous copies while
+  // the B operand is formed)
   for (int q = 0; q < Cfg::RCH; ++q) {
     const int c = cbase + q;
     if (c >= a.C) break;
@@ -185,9 +208,33 @@ __global__ void __launch_bounds__(128, 1) k_fb_products(FBArgs a) {
     float* eq = e + q * L * NP;
     for (int i = tid; i < ci.len * N; i += blockDim.x) {
       const int f = i / N, n = i - f * N;
-      eq[f * NP + n] = src[i];
+      cp_async4(eq + f * NP + n, src + i);
     }
   }
+  cp_async_commit();
+  // B operand: B[j][k] = A[k][j] (zero outside N x N), split into tf32 hi/lo;
+  // this thread's values are loaded first, all in flight together
+  const float* Ag = a.A + (size_t)s * N * N;
+  constexpr int BPT = (NOUT * Cfg::KATOMS * 32 + 127) / 128;
+  float bv[BPT];
+#pragma unroll
+  for (int u = 0; u < BPT; ++u) {
+    const int idx = tid + 128 * u;
+    const int j = idx / (Cfg::KATOMS * 32), k = idx - j * (Cfg::KATOMS * 32);
+    bv[u] = (idx < NOUT * Cfg::KATOMS * 32 && j < N && k < N) ? __ldg(Ag + k * N + j) : 0.f;
+  }
+#pragma unroll
+  for (int u = 0; u < BPT; ++u) {
+    const int idx = tid + 128 * u;
+    if (idx < NOUT * Cfg::KATOMS * 32) {
+      const int j = idx / (Cfg::KATOMS * 32), k = idx - j * (Cfg::KATOMS * 32);
+      const float h = tf32_hi(bv[u]);
+      const uint32_t off = sw128_off(j, k, NOUT * 128);
+      *reinterpret_cast<float*>(b_hi + off) = h;
+      *reinterpret_cast<float*>(b_lo + off) = tf32_hi(bv[u] - h);
+    }
+  }
+  cp_async_wait<0>();
   __syncthreads();
   for (int q = 0; q < Cfg::RCH; ++q) {
     const int c = cbase + q;
@@ -322,16 +369,19 @@ __global__ void __launch_bounds__(128, 1) k_fb_products(FBArgs a) {
     normalise_and_store();
   }
   if (bad) atomicOr(a.err, ERR_FB_ZERO);
-  // common scale for the chunk: P_c = exp(rho_max) * (rows scaled to it)
-  const double lr = zero_row ? -INFINITY : sc.log();
-  rhod[r] = live ? lr : -INFINITY;
+  // common scale for the chunk: P_c = (scale of its largest row) * (rows
+  // scaled to it); the row scales sit where the frame maxima were summed
+  float* rm = reinterpret_cast<float*>(rhod);
+  int* re = reinterpret_cast<int*>(rm + 128);
+  rm[r] = (live && !zero_row) ? sc.m : 0.f;
+  re[r] = sc.e;
   __syncthreads();
   if (q < Cfg::RCH && c < a.C && i < NP) {
-    double rmax = -INFINITY;
-    for (int ii = 0; ii < N; ++ii) rmax = fmax(rmax, rhod[q * NP + ii]);
-    // rmax = -inf only if every row of the chunk vanished (flagged by the scan)
-    const float g = (live && rmax > -INFINITY) ? (float)exp(lr - rmax) : 0.f;
-    if (rmax == -INFINITY) rmax = 0.0;
+    // best < 0 only if every row of the chunk vanished (flagged by the scan)
+    const int best = scale_argmax(rm + q * NP, re + q * NP, N);
+    const float g = (live && best >= 0 && rm[r] > 0.f)
+                        ? ldexpf(rm[r] / rm[q * NP + best], re[r] - re[q * NP + best])
+                        : 0.f;
     const size_t base = ((size_t)s * a.C + c) * NP * NP;
     float* Pg = a.P + base;
     float* PTg = a.PT + base;
@@ -341,7 +391,10 @@ __global__ void __launch_bounds__(128, 1) k_fb_products(FBArgs a) {
       Pg[i * NP + j] = v;
       PTg[j * NP + i] = v;
     }
-    if (i == 0) a.Plog[(size_t)s * a.C + c] = msum[q] + rmax;
+    if (i == 0)
+      a.Plog[(size_t)s * a.C + c] =
+          msum[q] + (best >= 0 ? (double)re[q * NP + best] * LN2 + log((double)rm[q * NP + best])
+                               : 0.0);
   }
   tc_fence_before();
   __syncthreads();
@@ -375,7 +428,8 @@ __global__ void __launch_bounds__(128) k_fb_products_simt(FBArgs a) {
   const float* Ag = a.A + (size_t)s * N * N;
   for (int idx = tid; idx < NP * NP; idx += 128) {
     const int k = idx / NP, j = idx - k * NP;
-    As[idx] = (k < N && j < N) ? Ag[k * N + j] : 0.f;
+    if (k < N && j < N) cp_async4(As + idx, Ag + k * N + j);
+    else As[idx] = 0.f;
   }
   for (int q = 0; q < RCH; ++q) {
     const int c = cbase + q;
@@ -385,9 +439,11 @@ __global__ void __launch_bounds__(128) k_fb_products_simt(FBArgs a) {
     float* eq = e + q * L * NP;
     for (int i = tid; i < ci.len * N; i += 128) {
       const int f = i / N, n = i - f * N;
-      eq[f * NP + n] = src[i];
+      cp_async4(eq + f * NP + n, src + i);
     }
   }
+  cp_async_commit();
+  cp_async_wait<0>();
   __syncthreads();
   for (int q = 0; q < RCH; ++q) {
     const int c = cbase + q;
@@ -474,15 +530,17 @@ __global__ void __launch_bounds__(128) k_fb_products_simt(FBArgs a) {
     normalise_store();
   }
   if (bad) atomicOr(a.err, ERR_FB_ZERO);
-  const double lr = zero_row ? -INFINITY : sc.log();
-  rhod[tid] = live ? lr : -INFINITY;
+  float* rm = reinterpret_cast<float*>(rhod);
+  int* re = reinterpret_cast<int*>(rm + 128);
+  rm[tid] = (live && !zero_row) ? sc.m : 0.f;
+  re[tid] = sc.e;
   __syncthreads();
   if (q < RCH && c < a.C && i < NP) {
-    double rmax = -INFINITY;
-    for (int ii = 0; ii < N; ++ii) rmax = fmax(rmax, rhod[q * NP + ii]);
-    // rmax = -inf only if every row of the chunk vanished (flagged by the scan)
-    const float g = (live && rmax > -INFINITY) ? (float)exp(lr - rmax) : 0.f;
-    if (rmax == -INFINITY) rmax = 0.0;
+    // best < 0 only if every row of the chunk vanished (flagged by the scan)
+    const int best = scale_argmax(rm + q * NP, re + q * NP, N);
+    const float g = (live && best >= 0 && rm[tid] > 0.f)
+                        ? ldexpf(rm[tid] / rm[q * NP + best], re[tid] - re[q * NP + best])
+                        : 0.f;
     const size_t base = ((size_t)s * a.C + c) * NP * NP;
     float* Pg = a.P + base;
     float* PTg = a.PT + base;
@@ -492,7 +550,10 @@ __global__ void __launch_bounds__(128) k_fb_products_simt(FBArgs a) {
       Pg[i * NP + j] = v;
       PTg[j * NP + i] = v;
     }
-    if (i == 0) a.Plog[(size_t)s * a.C + c] = msum[q] + rmax;
+    if (i == 0)
+      a.Plog[(size_t)s * a.C + c] =
+          msum[q] + (best >= 0 ? (double)re[q * NP + best] * LN2 + log((double)rm[q * NP + best])
+                               : 0.0);
   }
 }
 
@@ -515,6 +576,7 @@ enum { MODE_CHAINS = 0, MODE_GROUP_REPLAY = 1 };
 template <int NP, int MODE>
 __global__ void __launch_bounds__(32) k_fb_scan(FBArgs a) {
   extern __shared__ float sm[];
+  constexpr int RING = ScanRing<NP>::R;
   constexpr int LD = NP + 4;
   constexpr int NN = NP * LD;
   constexpr int CPL = (NP * NP / 4 + 31) / 32;   // 16-byte copies per lane per matrix
@@ -658,22 +720,25 @@ __global__ void __launch_bounds__(32) k_fb_scan(FBArgs a) {
 
 // ------------------------------------------------------ 2'. group products
 // Q_g = P_c0 P_c0+1 ... P_c1-1 for each group of chunks, row by row: row i is
-// the forward chain started from the basis vector e_i, one warp advancing
-// two rows over the group's chunk matrices (staged once per block with
-// cp.async and shared by its four warps).  Each row is rescaled by the sum
-// of its previous value; the removed factors are kept per row and the rows
-// brought to a common scale by k_fb_group_flatten.
-constexpr int GRING = 4;
+// the forward chain started from the basis vector e_i.  One block per group:
+// warp w advances rows 2w and 2w+1 over the group's chunk matrices, staged
+// once per step with cp.async and shared by all warps.  Each row is rescaled
+// by the sum of its previous value, the removed factors kept per row; at the
+// end the rows are brought to the common scale of the largest and written
+// with the transpose and the group's log scale (plus its chunks' scales).
+constexpr int GRING = 8;
 template <int NP>
-__global__ void __launch_bounds__(128) k_fb_group_products(FBArgs a) {
+__global__ void __launch_bounds__(NP * 16) k_fb_group_products(FBArgs a) {
   constexpr int LD = NP + 4;
   constexpr int NN = NP * LD;
-  constexpr int CPT = (NP * NP / 4 + 127) / 128;   // 16-byte copies per thread per matrix
+  constexpr int NT = NP * 16;                       // threads: NP/2 warps
+  constexpr int CPT = (NP * NP / 4 + NT - 1) / NT;  // 16-byte copies per thread per matrix
   extern __shared__ float sm[];
-  float* ring = sm;                     // GRING x NP x LD
-  float* vbuf = ring + GRING * NN;      // 4 warps x 2 rows x 64
+  double* rl = reinterpret_cast<double*>(sm);       // NP row log scales
+  float* ring = sm + 2 * NP;                        // GRING x NP x LD
+  float* vbuf = ring + GRING * NN;                  // NP/2 warps x 2 rows x 64
   const int N = a.N, C = a.C;
-  const int s = blockIdx.z, g = blockIdx.y;
+  const int g = blockIdx.x, s = blockIdx.y;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int c0 = a.grp_c0 ? a.grp_c0[g] : g * a.G;
   const int c1 = a.grp_c0 ? a.grp_c0[g + 1] : min((g + 1) * a.G, C);
@@ -682,7 +747,7 @@ __global__ void __launch_bounds__(128) k_fb_group_products(FBArgs a) {
   int soff[CPT], doff[CPT];
 #pragma unroll
   for (int m = 0; m < CPT; ++m) {
-    const int i = (tid + 128 * m) * 4;
+    const int i = (tid + NT * m) * 4;
     soff[m] = i < NP * NP ? i : -1;
     doff[m] = (i / NP) * LD + (i % NP);
   }
@@ -699,7 +764,7 @@ __global__ void __launch_bounds__(128) k_fb_group_products(FBArgs a) {
 #pragma unroll
   for (int q = 0; q < GRING - 1; ++q) prefetch(q);
 
-  const int ia = blockIdx.x * 8 + warp * 2, ib = ia + 1;
+  const int ia = warp * 2, ib = ia + 1;
   const bool la = ia < N, lb = ib < N;
   const bool h0 = lane < N, h1 = lane + 32 < N;
   const int j0 = lane < NP ? lane : 0, j1 = lane + 32 < NP ? lane + 32 : 0;
@@ -718,7 +783,7 @@ __global__ void __launch_bounds__(128) k_fb_group_products(FBArgs a) {
     vb[lane] = ub0;
     vb[lane + 32] = ub1;
     __syncwarp();
-    float lama = warp_sum(ua0 + ua1), lamb = warp_sum(ub0 + ub1);
+    const float lama = warp_sum(ua0 + ua1), lamb = warp_sum(ub0 + ub1);
     if (q > 0) {
       if (!isfinite(lama) || !isfinite(lamb)) bad = 1;
       sca.mul(removed_scale(lama));
@@ -760,53 +825,50 @@ __global__ void __launch_bounds__(128) k_fb_group_products(FBArgs a) {
     ub1 = h1 ? ((yb1[0] + yb1[1]) + (yb1[2] + yb1[3])) * fb : 0.f;
   }
   cp_async_wait<0>();
-  // final normalisation; rows of this group's product, and their log scales
+  // final normalisation of each row, then the common scale
   const float sa = warp_sum(ua0 + ua1), sb = warp_sum(ub0 + ub1);
   if (!isfinite(sa) || !isfinite(sb)) bad = 1;
   const float fa = renorm_factor(sa), fb = renorm_factor(sb);
   sca.mul(removed_scale(sa));
   scb.mul(removed_scale(sb));
-  const size_t qb = ((size_t)s * a.NG + g) * NP * NP;
-  const size_t rb = ((size_t)s * a.NG + g) * NP;
-  if (ia < NP) {
-    if (lane < NP) a.Q[qb + (size_t)ia * NP + lane] = la ? ua0 * fa : 0.f;
-    if (lane + 32 < NP) a.Q[qb + (size_t)ia * NP + lane + 32] = la ? ua1 * fa : 0.f;
-    if (lane == 0) a.rowlog[rb + ia] = (la && sa > 0.f) ? sca.log() : -INFINITY;
+  float* rm = reinterpret_cast<float*>(rl);
+  int* re = reinterpret_cast<int*>(rm + NP);
+  __shared__ int best_row;
+  if (lane == 0) {
+    rm[ia] = (la && sa > 0.f) ? sca.m : 0.f;
+    re[ia] = sca.e;
+    rm[ib] = (lb && sb > 0.f) ? scb.m : 0.f;
+    re[ib] = scb.e;
   }
-  if (ib < NP) {
-    if (lane < NP) a.Q[qb + (size_t)ib * NP + lane] = lb ? ub0 * fb : 0.f;
-    if (lane + 32 < NP) a.Q[qb + (size_t)ib * NP + lane + 32] = lb ? ub1 * fb : 0.f;
-    if (lane == 0) a.rowlog[rb + ib] = (lb && sb > 0.f) ? scb.log() : -INFINITY;
+  __syncthreads();
+  if (tid == 0) best_row = scale_argmax(rm, re, N);
+  __syncthreads();
+  const int best = best_row;
+  const float ga = (best >= 0 && rm[ia] > 0.f)
+                       ? ldexpf(rm[ia] / rm[best], re[ia] - re[best]) * fa : 0.f;
+  const float gb = (best >= 0 && rm[ib] > 0.f)
+                       ? ldexpf(rm[ib] / rm[best], re[ib] - re[best]) * fb : 0.f;
+  const double rmax = best >= 0 ? (double)re[best] * LN2 + log((double)rm[best]) : -INFINITY;
+  const size_t qb = ((size_t)s * a.NG + g) * NP * NP;
+  if (lane < NP) {
+    a.Q[qb + (size_t)ia * NP + lane] = ua0 * ga;
+    a.Q[qb + (size_t)ib * NP + lane] = ub0 * gb;
+    a.QT[qb + (size_t)lane * NP + ia] = ua0 * ga;
+    a.QT[qb + (size_t)lane * NP + ib] = ub0 * gb;
+  }
+  if (lane + 32 < NP) {
+    a.Q[qb + (size_t)ia * NP + lane + 32] = ua1 * ga;
+    a.Q[qb + (size_t)ib * NP + lane + 32] = ub1 * gb;
+    a.QT[qb + (size_t)(lane + 32) * NP + ia] = ua1 * ga;
+    a.QT[qb + (size_t)(lane + 32) * NP + ib] = ub1 * gb;
+  }
+  if (warp == 0) {   // the group's scale: its chunks' scales (loaded in parallel) and rmax
+    double lg = 0.0;
+    for (int c = c0 + lane; c < c1; c += 32) lg += a.Plog[cbase + c];
+    lg = warp_sum_d(lg);
+    if (lane == 0) a.Qlog[(size_t)s * a.NG + g] = lg + (rmax > -INFINITY ? rmax : 0.0);
   }
   if (bad && lane == 0) atomicOr(a.err, ERR_FB_ZERO);
-}
-
-// Bring each group product's rows to a common scale (the largest row scale)
-// and write Q, its transpose and its log scale (sum of the chunks' scales).
-template <int NP>
-__global__ void __launch_bounds__(64) k_fb_group_flatten(FBArgs a) {
-  const int g = blockIdx.x, s = blockIdx.y, i = threadIdx.x;
-  const int N = a.N;
-  const size_t qb = ((size_t)s * a.NG + g) * NP * NP;
-  const size_t rb = ((size_t)s * a.NG + g) * NP;
-  double rmax = -INFINITY;
-  for (int k = 0; k < N; ++k) rmax = fmax(rmax, a.rowlog[rb + k]);
-  if (i < NP) {
-    const double lr = a.rowlog[rb + i];
-    const float f = (i < N && rmax > -INFINITY && lr > -INFINITY) ? (float)exp(lr - rmax) : 0.f;
-    for (int j = 0; j < NP; ++j) {
-      const float v = a.Q[qb + (size_t)i * NP + j] * f;
-      a.Q[qb + (size_t)i * NP + j] = v;
-      a.QT[qb + (size_t)j * NP + i] = v;
-    }
-  }
-  if (i == 0) {
-    const int c0 = a.grp_c0 ? a.grp_c0[g] : g * a.G;
-    const int c1 = a.grp_c0 ? a.grp_c0[g + 1] : min((g + 1) * a.G, a.C);
-    double lg = rmax > -INFINITY ? rmax : 0.0;
-    for (int c = c0; c < c1; ++c) lg += a.Plog[(size_t)s * a.C + c];
-    a.Qlog[(size_t)s * a.NG + g] = lg;
-  }
 }
 
 // ----------------------------------------------------------------- 3. replay
@@ -848,14 +910,17 @@ __global__ void __launch_bounds__(R_CHUNKS_MAX * 64) k_fb_replay(FBArgs a) {
     }
   }
   if (live) {
-    // the chunk's two warps copy its phi rows (contiguous) with coalesced loads
+    // the chunk's two warps gather its phi rows (contiguous) with
+    // asynchronous copies, all in flight together
     const float* src = a.phi + (size_t)s * a.T * N + (size_t)t0 * N;
     const int tot = len * N;
     for (int i = (int)threadIdx.x - q * 64; i < tot; i += 64) {
       const int f = i / N, n = i - f * N;
-      e[f * NP + n] = src[i];
+      cp_async4(e + f * NP + n, src + i);
     }
   }
+  cp_async_commit();
+  cp_async_wait<0>();
   __syncthreads();
   if (live) {
     for (int f = is_fwd ? 0 : 1; f < len; f += 2) {
@@ -983,11 +1048,11 @@ static size_t smem_products_simt(int L) {
 }
 template <int NP>
 static size_t smem_group() {
-  return (size_t)(GRING * NP * (NP + 4) + 4 * 128) * sizeof(float);
+  return (size_t)(2 * NP + GRING * NP * (NP + 4) + (NP / 2) * 128) * sizeof(float);
 }
 template <int NP>
 static size_t smem_scan() {
-  return (size_t)(RING * NP * (NP + 4) + 64) * sizeof(float);
+  return (size_t)(ScanRing<NP>::R * NP * (NP + 4) + 64) * sizeof(float);
 }
 static size_t smem_replay_chunk(int NP, int L) { return (size_t)(3 * L * NP + 128) * sizeof(float); }
 static int replay_chunks(int NP, int L) {
@@ -1034,8 +1099,7 @@ static cudaError_t launch_np(const FBArgs& a, cudaStream_t st) {
   if (a.G >= 2) {
     // group products, the scan across groups (the chain scan over the group
     // arrays), then each group's chunk boundaries
-    k_fb_group_products<NP><<<dim3(NP / 8, a.NG, a.S), 128, smem_group<NP>(), st>>>(a);
-    k_fb_group_flatten<NP><<<dim3(a.NG, a.S), 64, 0, st>>>(a);
+    k_fb_group_products<NP><<<dim3(a.NG, a.S), NP * 16, smem_group<NP>(), st>>>(a);
     FBArgs b = a;
     b.C = a.NG;
     b.chain_c0 = a.chain_g0;
@@ -1063,7 +1127,6 @@ int fb_chunk_count(const int* chain_len, int nchains, int L) {
 
 size_t fb_scratch_bytes(int S, int N, int C, int NG) {
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
-  const size_t P = pad8(N);
   size_t b = 0;
   b += al((size_t)S * C * mat_floats(N) * sizeof(float));  // P
   b += al((size_t)S * C * mat_floats(N) * sizeof(float));  // P^T
@@ -1074,7 +1137,6 @@ size_t fb_scratch_bytes(int S, int N, int C, int NG) {
   b += al((size_t)S * NG * mat_floats(N) * sizeof(float)); // Q
   b += al((size_t)S * NG * mat_floats(N) * sizeof(float)); // Q^T
   b += al((size_t)S * NG * sizeof(double));                // Qlog
-  b += al((size_t)S * NG * P * sizeof(double));            // rowlog
   b += al((size_t)S * NG * N * sizeof(float));             // gfwd
   b += al((size_t)S * NG * N * sizeof(float));             // gbwd
   b += al((size_t)S * NG * sizeof(float));                 // glam
@@ -1083,7 +1145,7 @@ size_t fb_scratch_bytes(int S, int N, int C, int NG) {
 
 void fb_carve_scratch(FBArgs& a, void* base) {
   char* p = reinterpret_cast<char*>(base);
-  const size_t S = a.S, C = a.C, N = a.N, NG = a.NG, P = pad8(a.N);
+  const size_t S = a.S, C = a.C, N = a.N, NG = a.NG;
   auto take = [&](size_t bytes) {
     char* r = p;
     p += (bytes + 255) & ~(size_t)255;
@@ -1098,7 +1160,6 @@ void fb_carve_scratch(FBArgs& a, void* base) {
   a.Q = reinterpret_cast<float*>(take(S * NG * mat_floats((int)N) * sizeof(float)));
   a.QT = reinterpret_cast<float*>(take(S * NG * mat_floats((int)N) * sizeof(float)));
   a.Qlog = reinterpret_cast<double*>(take(S * NG * sizeof(double)));
-  a.rowlog = reinterpret_cast<double*>(take(S * NG * P * sizeof(double)));
   a.gfwd = reinterpret_cast<float*>(take(S * NG * N * sizeof(float)));
   a.gbwd = reinterpret_cast<float*>(take(S * NG * N * sizeof(float)));
   a.glam = reinterpret_cast<float*>(take(S * NG * sizeof(float)));
@@ -1113,7 +1174,7 @@ int fb_default_group(int C) {
 }
 
 cudaError_t launch_fb(const FBArgs& a, cudaStream_t st, int* launches) {
-  if (launches) *launches += a.G >= 2 ? 6 : 3;
+  if (launches) *launches += a.G >= 2 ? 5 : 3;
   switch (pad8(a.N)) {
     case 8: return launch_np<8>(a, st);
     case 16: return launch_np<16>(a, st);

@@ -41,6 +41,7 @@ using namespace tc;
 constexpr int BM = 128;
 constexpr int BN1 = 128;           // reconstruction: columns = frequencies
 constexpr int BN2 = 160;           // back-projection: columns = elements
+constexpr int BNX = 64;            // exact inference back-projection: the S*K elements of a joint state
 constexpr int EPI_WARPS = 8;                    // two per TMEM lane quarter
 constexpr int NUM_THREADS = 64 + EPI_WARPS * 32;  // TMA warp, MMA warp, epilogue
 enum TcEpi { TEPI_RATIO = 0, TEPI_SCALE = 1 };
@@ -93,6 +94,10 @@ struct TcArgs {
   int ldo;
   double* bpart;                  // RATIO: bound partial per (row, column tile), may be null
   unsigned* err;
+  // batched form: the rows are items of brows rows each (a multiple of BM),
+  // of which the first bvalid are real; item b reads B rows from b * bstride
+  // on, and V (RATIO) is shared by the items.  brows = 0: one item.
+  int brows, bvalid, bstride;
 };
 
 // ------------------------------------------------------------------ kernel
@@ -113,6 +118,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int col0 = blockIdx.x * BN, row0 = blockIdx.y * BM;
+  const int bitem = p.brows ? row0 / p.brows : 0;   // batch item of this row tile
+  const int bcol0 = col0 + bitem * p.bstride;         // its first B row
   const int nkb = (p.kdim + K::BK - 1) / K::BK;
 
   if (threadIdx.x == 0) {
@@ -154,10 +161,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         mbar_expect_tx(&full[s], Cfg::STAGE_BYTES);
         const int kx = kb * K::BK;
         tma_load_2d(stage_ptr(s, 0), &maps.a_hi, &full[s], kx, row0);
-        tma_load_2d(stage_ptr(s, 2), &maps.b_hi, &full[s], kx, col0);
+        tma_load_2d(stage_ptr(s, 2), &maps.b_hi, &full[s], kx, bcol0);
         if (K::NOPS == 2) {
           tma_load_2d(stage_ptr(s, 1), &maps.a_lo, &full[s], kx, row0);
-          tma_load_2d(stage_ptr(s, 3), &maps.b_lo, &full[s], kx, col0);
+          tma_load_2d(stage_ptr(s, 3), &maps.b_lo, &full[s], kx, bcol0);
         }
         issued = kb + 1;
       }
@@ -207,14 +214,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     const int half = (warp - 2) >> 2;
     const int r = quarter * 32 + lane;
     const int t = row0 + r;
+    const int tl = t - bitem * p.brows;               // row within its batch item
+    const bool rv = p.brows ? tl < p.bvalid : t < p.rows;
     const int cbase = col0 + half * HALF;
     float pre[HALF];
     {
-      const float* src = EPI == TEPI_RATIO ? p.V + (size_t)t * p.ldv : p.w + (size_t)t * p.ldw;
+      const float* src = EPI == TEPI_RATIO ? p.V + (size_t)tl * p.ldv : p.w + (size_t)t * p.ldw;
 #pragma unroll
       for (int ch = 0; ch < NCH; ++ch) {
         const int c = cbase + 16 * ch;
-        if (t < p.rows && c < p.cols) {
+        if (rv && c < p.cols) {
           const float4* sp = reinterpret_cast<const float4*>(src + c);
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
@@ -256,7 +265,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           for (int i = 0; i < 16; ++i) acc[i] += __uint_as_float(raw[j][i]);
         }
       const int c = cbase + 16 * ch;
-      if (!ok || t >= p.rows || c >= p.cols) continue;   // cols is a multiple of 16
+      if (!ok || !rv || c >= p.cols) continue;   // cols is a multiple of 16
       const float* vv = pre + 16 * ch;
       if (EPI == TEPI_RATIO) {
         float q[16], vl[16];
@@ -316,7 +325,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                               vv[4 * i + 2] * acc[4 * i + 2], vv[4 * i + 3] * acc[4 * i + 3]);
       }
     }
-    if (EPI == TEPI_RATIO && p.bpart && ok && t < p.rows)
+    if (EPI == TEPI_RATIO && p.bpart && ok && rv)
       p.bpart[(size_t)t * p.nbpart + 2 * blockIdx.x + half] = part;
     if (bad) atomicOr(p.err, bad);
   }
@@ -525,6 +534,117 @@ int tc_gemm2(TcPlan& p, int rows, cudaStream_t st) {
     return -1;
   }
   return 1;
+}
+
+int tc_exact_plan(ExactTc& p) {
+  const bool bf = p.precision == 1;
+  p.w_format = bf ? WF_BF16 : WF_TF32X2;
+  const int es = bf ? 2 : 4;
+  const int bk = bf ? KindCfg<KIND_BF16>::BK : KindCfg<KIND_TF32X3>::BK;
+  auto alloc = [&](void** ptr, size_t bytes) {
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+      g_tc_err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+      return false;
+    }
+    cudaMemset(*ptr, 0, bytes);
+    return true;
+  };
+  const size_t rows = (size_t)p.NC * p.Tp;
+  const size_t th = rows * p.SKp * es, q = rows * p.Fp * es, b = (size_t)p.NC * p.Fp * p.SKp * es;
+  if (!alloc(&p.th_hi, th) || !alloc(&p.q_hi, q) || !alloc(&p.b1_hi, b) || !alloc(&p.b2_hi, b))
+    return -1;
+  if (!bf && (!alloc(&p.th_lo, th) || !alloc(&p.q_lo, q) || !alloc(&p.b1_lo, b) ||
+              !alloc(&p.b2_lo, b)))
+    return -1;
+  if (rows > (size_t)INT32_MAX || (size_t)p.NC * p.Fp > (size_t)INT32_MAX) {
+    g_tc_err = "exact inference: too many rows for one tensor map";
+    return -1;
+  }
+  Maps* m1 = reinterpret_cast<Maps*>(&p.maps[0][0]);
+  Maps* m2 = reinterpret_cast<Maps*>(&p.maps[4][0]);
+  bool ok = make_map(&m1->a_hi, p.th_hi, es, p.SKp, (int)rows, p.SKp, bk, BM) &&
+            make_map(&m1->b_hi, p.b1_hi, es, p.SKp, p.NC * p.Fp, p.SKp, bk, BN1) &&
+            make_map(&m2->a_hi, p.q_hi, es, p.Fp, (int)rows, p.Fp, bk, BM) &&
+            make_map(&m2->b_hi, p.b2_hi, es, p.Fp, p.NC * p.SKp, p.Fp, bk, BNX);
+  if (ok && !bf)
+    ok = make_map(&m1->a_lo, p.th_lo, es, p.SKp, (int)rows, p.SKp, bk, BM) &&
+         make_map(&m1->b_lo, p.b1_lo, es, p.SKp, p.NC * p.Fp, p.SKp, bk, BN1) &&
+         make_map(&m2->a_lo, p.q_lo, es, p.Fp, (int)rows, p.Fp, bk, BM) &&
+         make_map(&m2->b_lo, p.b2_lo, es, p.Fp, p.NC * p.SKp, p.Fp, bk, BNX);
+  if (!ok) return -1;
+  if (bf) {
+    m1->a_lo = m1->a_hi;
+    m1->b_lo = m1->b_hi;
+    m2->a_lo = m2->a_hi;
+    m2->b_lo = m2->b_hi;
+  }
+  p.nbpart = tc_col_tiles_gemm1(p.Fp);
+  return 0;
+}
+
+int tc_exact_gemm1(ExactTc& p, cudaStream_t st) {
+  TcArgs a{};
+  a.rows = p.NC * p.Tp;
+  a.cols = p.Fp;
+  a.kdim = p.SKp;
+  a.nbpart = p.nbpart;
+  a.V = p.V;
+  a.ldv = p.Fp;
+  a.ldo = p.Fp;
+  a.bpart = p.bpart;
+  a.err = p.err;
+  a.brows = p.Tp;
+  a.bvalid = p.T;
+  a.bstride = p.Fp;
+  const Maps& m = *reinterpret_cast<const Maps*>(&p.maps[0][0]);
+  cudaError_t e;
+  if (p.precision == 1) {
+    a.out_bf16 = reinterpret_cast<__nv_bfloat16*>(p.q_hi);
+    e = launch_gemm<KIND_BF16, BN1, TEPI_RATIO>(m, a, st);
+  } else {
+    a.out_f32 = reinterpret_cast<float*>(p.q_hi);
+    a.out_lo = reinterpret_cast<float*>(p.q_lo);
+    e = launch_gemm<KIND_TF32X3, BN1, TEPI_RATIO>(m, a, st);
+  }
+  if (e != cudaSuccess) {
+    g_tc_err = cudaGetErrorString(e);
+    return -1;
+  }
+  return 1;
+}
+
+int tc_exact_gemm2(ExactTc& p, cudaStream_t st) {
+  TcArgs a{};
+  a.rows = p.NC * p.Tp;
+  a.cols = p.SKp;
+  a.kdim = p.Fp;
+  a.w = p.th32;
+  a.ldw = p.SKp;
+  a.out_f32 = p.out;
+  a.ldo = p.SKp;
+  a.err = p.err;
+  a.brows = p.Tp;
+  a.bvalid = p.T;
+  a.bstride = p.SKp;
+  const Maps& m = *reinterpret_cast<const Maps*>(&p.maps[4][0]);
+  cudaError_t e;
+  if (p.precision == 1)
+    e = launch_gemm<KIND_BF16, BNX, TEPI_SCALE>(m, a, st);
+  else
+    e = launch_gemm<KIND_TF32X3, BNX, TEPI_SCALE>(m, a, st);
+  if (e != cudaSuccess) {
+    g_tc_err = cudaGetErrorString(e);
+    return -1;
+  }
+  return 1;
+}
+
+void tc_exact_free(ExactTc& p) {
+  void* bufs[] = {p.th_hi, p.th_lo, p.q_hi, p.q_lo, p.b1_hi, p.b1_lo, p.b2_hi, p.b2_lo};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  p.th_hi = p.th_lo = p.q_hi = p.q_lo = p.b1_hi = p.b1_lo = p.b2_hi = p.b2_lo = nullptr;
 }
 
 void tc_free(TcPlan& p) {

@@ -113,7 +113,6 @@ struct FBArgs {
   float* Q;             // S x NG x NP x NP  group products (rows scaled to a common scale)
   float* QT;            // S x NG x NP x NP  the same, transposed
   double* Qlog;         // S x NG            log of each group product's scale
-  double* rowlog;       // S x NG x NP       per-row log scales before the common scale
   float* gfwd;          // S x NG x N        forward vectors at group ends
   float* gbwd;          // S x NG x N        backward vectors at group ends
   float* glam;          // S x NG            group scan normalisers

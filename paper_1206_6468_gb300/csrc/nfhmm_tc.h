@@ -33,6 +33,34 @@ struct TcPlan {
   alignas(64) unsigned char maps[8][128];
 };
 
+// Batched contractions of exact inference in the original N-FHMM: one item
+// per joint state c, each with its own B rows (the S*K elements c selects):
+//   gemm1: Vhat[c][t][f] = sum_k theta[c][t][k] beta_ck(f) -> Q = V / Vhat, log-lik partials
+//   gemm2: out[c][t][k]  = theta[c][t][k] * sum_f Q[c][t][f] beta_ck(f)
+struct ExactTc {
+  int precision = 0, w_format = 0;
+  int NC = 0, T = 0, Tp = 0, SKp = 0, F = 0, Fp = 0;
+  void* th_hi = nullptr;  // NC*Tp x SKp  theta operand (tf32 hi as float, or bf16)
+  void* th_lo = nullptr;
+  void* q_hi = nullptr;   // NC*Tp x Fp   Q operand
+  void* q_lo = nullptr;
+  void* b1_hi = nullptr;  // NC*Fp x SKp  B1[c][f][k] = beta_ck(f)
+  void* b1_lo = nullptr;
+  void* b2_hi = nullptr;  // NC*SKp x Fp  B2[c][k][f] = beta_ck(f)
+  void* b2_lo = nullptr;
+  const float* V = nullptr;     // T x Fp (shared by the items)
+  const float* th32 = nullptr;  // NC*Tp x SKp theta in float
+  float* out = nullptr;         // NC*Tp x SKp
+  double* bpart = nullptr;      // NC*Tp x nbpart
+  int nbpart = 0;
+  unsigned* err = nullptr;
+  alignas(64) unsigned char maps[8][128];
+};
+int tc_exact_plan(ExactTc& p);   // allocates the operand arrays, builds the tensor maps
+int tc_exact_gemm1(ExactTc& p, cudaStream_t st);
+int tc_exact_gemm2(ExactTc& p, cudaStream_t st);
+void tc_exact_free(ExactTc& p);
+
 bool tc_available();
 std::string tc_last_error();
 int tc_col_tiles_gemm1(int Fp);
