@@ -59,10 +59,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-case", action="store_true",
                     help="run one context for 3 sweeps and exit (a small case for ncu)")
-    ap.add_argument("--workload", default="single", choices=["single", "batched", "serving"],
+    ap.add_argument("--workload", default="single",
+                    choices=["single", "batched", "serving", "exact"],
                     help="single: one S2 N40 K10 F513 T3000 job per step (the headline); "
                          "batched: 64 jobs, T ~ U[500, 8000], in one batch per step; "
-                         "serving: Poisson arrivals served by continuous batching")
+                         "serving: Poisson arrivals served by continuous batching; "
+                         "exact: exact-inference EM iteration against a variational sweep")
+    ap.add_argument("--exact-frames", type=int, default=3000)
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-saturate", action="store_true",
@@ -495,6 +498,68 @@ def run_serving(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def run_exact(args, rank, world, local):
+    """Per-iteration time of exact inference in the original N-FHMM (EM over
+    the N^S joint states) against a variational sweep on the same
+    spectrogram, at the configurations of Section 5's comparison: S=2 sources
+    of N=20 dictionaries with K=30 elements (exact inference's best) and
+    K=20 (the variational method's best); F=513, T frames."""
+    import torch
+
+    from paper_1206_6468_gb300 import nfhmm, synth
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    T = args.exact_frames
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, n):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    res = {}
+    sampler = ClockSampler(local)
+    sampler.start()
+    for K in (30, 20):
+        p = synth.make_problem(S=2, N=20, K=K, F=513, T=T, self_prob=0.95, energy_sigma=1.5,
+                               seed=job_seed(rank))
+        f = {k: torch.from_numpy(v).to(dev) for k, v in p.as_f32().items()}
+        ctx = nfhmm.VIContext(f["V"], f["W"], f["A"], f["pi"], p.S, p.N, p.K,
+                              precision=args.precision)
+        ctx.sweep(5)
+        vi_ms = timed(lambda: ctx.sweep(1), 50)
+        ctx.close()
+        x = nfhmm.ExactNFHMM(f["V"], f["W"], f["A"], f["pi"], p.S, p.N, p.K,
+                             precision=args.precision)
+        x.iterate(2, loglik=False)
+        ex_ms = timed(lambda: x.iterate(1, loglik=False), 5)
+        ll = x.iterate(1)
+        x.close()
+        res[K] = {"vi_ms_per_sweep": vi_ms, "exact_ms_per_iteration": ex_ms,
+                  "exact_over_vi": ex_ms / vi_ms, "exact_loglik": ll}
+    clocks = sampler.stop()
+    line = {
+        "metric": "exact N-FHMM EM iteration time / variational sweep time", "value":
+            res[30]["exact_ms_per_iteration"] / res[20]["vi_ms_per_sweep"],
+        "unit": "x", "n_gpus": world, "steps": 5, "warmup": 2,
+        "ms_per_step": res[30]["exact_ms_per_iteration"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else "bf16", "data": "synthetic",
+        "config": {"workload": f"exact vs variational, S2 N20 F513 T{T}; exact K30, "
+                               "variational K20 (each method's best configuration in Section 5)",
+                   "joint_states": 400, "precision": args.precision},
+        "by_config": {f"K{K}": v for K, v in res.items()},
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_setup()
@@ -506,6 +571,9 @@ def main():
         return
     if args.workload == "serving":
         run_serving(args, rank, world, local)
+        return
+    if args.workload == "exact":
+        run_exact(args, rank, world, local)
         return
     import torch
 

@@ -239,7 +239,9 @@ NFHMM_API int nfhmm_job_posteriors(nfhmm_ctx *c, long long job_id, float *dhat, 
  *                          FMAs on the CUDA cores, one thread per row)
  *   NFHMM_OPT_FB_GROUP     chunks per group of the two-level scan across
  *                          chunks (2..4096), 0 for a single-level scan, -1
- *                          (default) for a size that follows the chunk length
+ *                          for a size that follows the chunk length (the
+ *                          default of one-job contexts; batches default to 0
+ *                          and chunks of 32 frames)
  *   NFHMM_OPT_GRAPHS       1 (default): a run of sweeps whose launch
  *                          configuration (frames, chunks, sweep count, bound)
  *                          has run before is replayed from a captured CUDA
@@ -291,6 +293,36 @@ typedef struct {
 } nfhmm_result;
 NFHMM_API int nfhmm_serve(nfhmm_ctx **batches, int n_batches, const nfhmm_request *reqs,
                           int n_reqs, const nfhmm_serve_opts *opts, nfhmm_result *results);
+
+/*
+ * Exact inference in the original N-FHMM -- the comparison system of
+ * Section 5, whose model opens Section 2.2: each frame t and joint state
+ * c = (d^(1), ..., d^(S)) has its own maximum-likelihood mixture weights
+ * theta_t(c) over the S*K elements that c selects (element index
+ * (s*N + d^(s))*K + j).  One EM iteration: the frame log-likelihoods
+ * l_t(c) = sum_f V_tf log sum_k theta_t(c)_k beta_k(f) for all N^S joint
+ * states, forward-backward over the joint chain (transitions prod_s A^(s),
+ * initial prod_s pi^(s)) for the posteriors gamma_t(c) and log P(V | theta),
+ * then theta_t(c)_k <- theta_t(c)_k sum_f beta_k(f) V_tf / Vhat_tc(f),
+ * normalised.  Weights start uniform.  Its cost grows as N^S: it is the
+ * yardstick of the paper's per-iteration comparison, not a separation path.
+ * Same V, W, A, pi layouts as nfhmm_vi_init; d->precision NFHMM_FP32 or
+ * NFHMM_BF16 (the contractions); gamma and init_mode are not used.
+ * Limits: S*K <= 64, N^S <= 4096.  Joint states are numbered with the last
+ * source's state varying fastest.
+ */
+typedef struct nfhmm_exact nfhmm_exact;
+NFHMM_API int nfhmm_exact_create(nfhmm_exact **out, const nfhmm_dims *d, const float *V,
+                                 const float *W, const float *A, const float *pi,
+                                 int inputs_on_device, void *cuda_stream);
+/* n_iter >= 1 EM iterations; loglik_out: NULL, or log P(V | theta) of the
+ * weights the last iteration started from (synchronises). */
+NFHMM_API int nfhmm_exact_iterate(nfhmm_exact *x, int n_iter, double *loglik_out);
+/* gamma: T x N^S posteriors of the last iteration's E-step. */
+NFHMM_API int nfhmm_exact_posteriors(nfhmm_exact *x, float *gamma, int on_device);
+/* theta: T x N^S x (S*K) current weights. */
+NFHMM_API int nfhmm_exact_weights(nfhmm_exact *x, float *theta, int on_device);
+NFHMM_API void nfhmm_exact_destroy(nfhmm_exact *x);
 
 /* nfhmm_destroy -- free the context and its device memory (waits for its work). */
 NFHMM_API void nfhmm_destroy(nfhmm_ctx *c);

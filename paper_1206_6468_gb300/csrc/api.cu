@@ -792,12 +792,13 @@ int create_ctx(nfhmm_ctx** out, const nfhmm_dims* dp, int max_jobs, const float*
   c->fb.S = d.S;
   c->fb.N = d.N;
   c->fb.T = d.T;   // frame stride of phi-hat and d-hat
-  c->fb.L = max_jobs == 1 ? fb_default_chunk(d.N, d.T) : fb_default_chunk(d.N, d.T < 4096 ? d.T : 4096);
+  // one job: the chain's latency sets the sweep (chunks of 0.3 sqrt(T) frames
+  // and the two-level scan); batches: many chains run side by side and the
+  // total work sets it (chunks of 32 frames, one-level scan)
+  c->fb.L = max_jobs == 1 ? fb_default_chunk(d.N, d.T) : (d.T < 32 ? d.T : 32);
   c->fb.products = FB_PRODUCTS_TC;
-  {
-    const int tref = max_jobs == 1 ? d.T : (d.T < 4096 ? d.T : 4096);
-    c->fb.G = fb_default_group((tref + c->fb.L - 1) / c->fb.L);
-  }
+  c->fb.G = max_jobs == 1 ? fb_default_group((d.T + c->fb.L - 1) / c->fb.L) : 0;
+  c->group_auto = max_jobs == 1;
   c->fb.phi = c->phi;
   c->fb.A = c->A;
   c->fb.pi = c->pi;
@@ -1095,8 +1096,7 @@ int nfhmm_set_option(nfhmm_ctx* c, int key, long long value) {
       if (key == NFHMM_OPT_FB_CHUNK) c->fb.L = (int)value;
       if (key == NFHMM_OPT_FB_GROUP) c->group_auto = value < 0;
       if (c->group_auto) {
-        const int tref = c->max_jobs == 1 ? c->d.T : (c->d.T < 4096 ? c->d.T : 4096);
-        c->fb.G = fb_default_group((tref + c->fb.L - 1) / c->fb.L);
+        c->fb.G = fb_default_group((c->d.T + c->fb.L - 1) / c->fb.L);
       } else if (key == NFHMM_OPT_FB_GROUP) {
         c->fb.G = (int)value;
       }

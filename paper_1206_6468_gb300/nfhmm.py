@@ -95,6 +95,12 @@ _sigs = {
     "nfhmm_set_option": (_i, [_vp, _i, ctypes.c_longlong]),
     "nfhmm_serve": (_i, [ctypes.POINTER(_vp), _i, ctypes.POINTER(Request), _i,
                          ctypes.POINTER(ServeOpts), ctypes.POINTER(Result)]),
+    "nfhmm_exact_create": (_i, [ctypes.POINTER(_vp), ctypes.POINTER(Dims), _vp, _vp, _vp, _vp, _i,
+                                _vp]),
+    "nfhmm_exact_iterate": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_double)]),
+    "nfhmm_exact_posteriors": (_i, [_vp, _vp, _i]),
+    "nfhmm_exact_weights": (_i, [_vp, _vp, _i]),
+    "nfhmm_exact_destroy": (None, [_vp]),
 }
 for _name, (_res, _args) in _sigs.items():
     _f = getattr(_lib, _name)
@@ -405,6 +411,61 @@ class Batch(VIContext):
         ids = np.ascontiguousarray(job_ids, dtype=np.int64)
         _check(_lib.nfhmm_batch_remove_many(self._h, len(ids), _vp(ids.ctypes.data)),
                "nfhmm_batch_remove_many")
+
+
+class ExactNFHMM:
+    """Exact inference in the original N-FHMM (the comparison system):
+    per-(frame, joint state) weights, EM with forward-backward over the N^S
+    joint states.  Same input conventions as VIContext."""
+
+    def __init__(self, V, W, A, pi, S: int, N: int, K: int, precision: str = "fp32",
+                 stream=None):
+        V, W, A, pi = _f32(V), _f32(W), _f32(A), _f32(pi)
+        T, F = V.shape
+        self.S, self.N, self.K, self.F, self.T = S, N, K, F, T
+        self.NC = N ** S
+        d = Dims(S, N, K, F, T, 1.0, PRECISIONS[precision], 0)
+        ptrs = [_ptr(x) for x in (V, W, A, pi)]
+        if len({dv for _, dv in ptrs}) != 1:
+            raise ValueError("V, W, A, pi must all be on the host or all on the device")
+        h = ctypes.c_void_p()
+        _check(_lib.nfhmm_exact_create(ctypes.byref(h), ctypes.byref(d), *[p for p, _ in ptrs],
+                                       ptrs[0][1], _stream(stream)), "nfhmm_exact_create")
+        self._h = h
+
+    def iterate(self, n: int = 1, loglik: bool = True) -> Optional[float]:
+        if loglik:
+            out = ctypes.c_double()
+            _check(_lib.nfhmm_exact_iterate(self._h, n, ctypes.byref(out)), "nfhmm_exact_iterate")
+            return out.value
+        _check(_lib.nfhmm_exact_iterate(self._h, n, None), "nfhmm_exact_iterate")
+        return None
+
+    def posteriors(self, out=None):
+        out = np.empty((self.T, self.NC), dtype=np.float32) if out is None else out
+        p, dev = _ptr(out)
+        _check(_lib.nfhmm_exact_posteriors(self._h, p, dev), "nfhmm_exact_posteriors")
+        return out
+
+    def weights(self, out=None):
+        out = np.empty((self.T, self.NC, self.S * self.K), dtype=np.float32) if out is None else out
+        p, dev = _ptr(out)
+        _check(_lib.nfhmm_exact_weights(self._h, p, dev), "nfhmm_exact_weights")
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.nfhmm_exact_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def serve(batches, requests, rel_tol: float = 1e-5, min_sweeps: int = 2,
