@@ -46,6 +46,10 @@ UNIT = "frame·iterations/s"
 SWEEPS = 50
 FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
 TF32_OVER_BF16 = 1.1 / 2.25                              # nominal dense ratio
+# stage events bracket every PROFILE_STRIDE-th sweep of the timed region
+# (the rest replay the same one-sweep graph without events)
+PROFILE_STRIDE = 5
+TIMED_NOTE = f"stages of every {PROFILE_STRIDE}th sweep bracketed by CUDA events"
 
 
 def parse():
@@ -288,7 +292,7 @@ def measured_traffic(stage, workload):
     return val
 
 
-def roofline_of(prof, steps, T, S, N, K, F, precision, tc, peaks):
+def roofline_of(prof, steps, T, S, N, K, F, precision, tc, peaks, sweeps_run):
     """Roofline object of the stage with the largest summed event time."""
     class _P:
         pass
@@ -312,8 +316,10 @@ def roofline_of(prof, steps, T, S, N, K, F, precision, tc, peaks):
         note = f"{peaks['source']} HBM copy bandwidth"
     return {"bound": bound_kind, "kernel": dom, "achieved": achieved, "peak": peak, "unit": unit,
             "frac": achieved / peak, "traffic": None, "peak_source": note,
-            "launch_ms": 1e3 * avg_s, "launches_per_invocation": dom_launches / max(dom_inv, 1),
-            "stage_ms_per_step": {s: round(prof[s][0] / steps, 4) for s in prof}}
+            "launch_ms": 1e3 * avg_s, "launches_per_invocation": dom_launches / max(sweeps_run, 1),
+            "stage_ms_per_invocation": {s: round(prof[s][0] / max(prof[s][1], 1), 4)
+                                        for s in prof},
+            "timed_sweeps": TIMED_NOTE}
 
 
 def run_batched(args, rank, world, local):
@@ -354,6 +360,7 @@ def run_batched(args, rank, world, local):
         ctx.posteriors(out=h_dhat)
         return L
 
+    ctx.set_option("profile_stride", PROFILE_STRIDE)
     ctx.profile_enable(True)
     for _ in range(args.warmup):
         step_device()
@@ -404,7 +411,7 @@ def run_batched(args, rank, world, local):
                    "l2": "inputs larger than L2; flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{world}"},
         "roofline": dict(roofline_of(prof, args.steps, T, 2, 40, 10, 513, args.precision, tc,
-                                     peaks), fb_chunk=ctx.query("fb_chunk")),
+                                     peaks, args.steps * sweeps), fb_chunk=ctx.query("fb_chunk")),
         "e2e": {"value": aggregate(fit, args.steps, world, tot_e2e), "unit": UNIT,
                 "h2d_bytes_per_step": int(sum(v.numel() * 4 for v in h_in.values())),
                 "d2h_bytes_per_step": int(h_dhat.numel() * 4 + 8)},
@@ -608,7 +615,8 @@ def main():
         return L
 
     # warm-up with profiling on, as in the timed region (the sweeps' CUDA
-    # graph, profiling events included, is captured here)
+    # graphs, with and without stage events, are captured here)
+    ctx.set_option("profile_stride", PROFILE_STRIDE)
     ctx.profile_enable(True)
     for _ in range(args.warmup):
         step_device()
@@ -668,7 +676,7 @@ def main():
         achieved = amount / avg_s / 1e9
         peak = peaks["hbm_gbs"]
         peak_note = f"{peaks['source']} HBM copy bandwidth"
-    stage_ms = {s: round(prof[s][0] / args.steps, 4) for s in prof}
+    stage_ms = {s: round(prof[s][0] / max(prof[s][1], 1), 4) for s in prof}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -684,8 +692,9 @@ def main():
                      "unit": unit, "frac": achieved / peak,
                      "traffic": measured_traffic(dom, f"paper_size_{args.precision}"),
                      "peak_source": peak_note, "launch_ms": 1e3 * avg_s,
-                     "launches_per_invocation": dom_launches / max(dom_inv, 1),
-                     "stage_ms_per_step": stage_ms, "fb_chunk": ctx.query("fb_chunk")},
+                     "launches_per_invocation": dom_launches / max(args.steps * sweeps, 1),
+                     "stage_ms_per_invocation": stage_ms, "timed_sweeps": TIMED_NOTE,
+                     "fb_chunk": ctx.query("fb_chunk")},
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": int(sum(v.numel() * 4 for v in h_in.values())),
                 "d2h_bytes_per_step": int(h_dhat.numel() * 4 + 8)},

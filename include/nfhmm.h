@@ -242,16 +242,22 @@ NFHMM_API int nfhmm_job_posteriors(nfhmm_ctx *c, long long job_id, float *dhat, 
  *                          for a size that follows the chunk length (the
  *                          default of one-job contexts; batches default to 0
  *                          and chunks of 32 frames)
- *   NFHMM_OPT_GRAPHS       1 (default): a run of sweeps whose launch
- *                          configuration (frames, chunks, sweep count, bound)
- *                          has run before is replayed from a captured CUDA
- *                          graph, profiling events included; 0: launch by
- *                          launch
+ *   NFHMM_OPT_GRAPHS       1 (default): a sweep whose launch configuration
+ *                          (frames, chunks, bound terms, timed by profiling
+ *                          or not) has run before is replayed from a captured
+ *                          one-sweep CUDA graph, profiling events included;
+ *                          0: launch by launch
+ *   NFHMM_OPT_PROFILE_STRIDE  k >= 1 (default 1): with profiling on, the
+ *                          stages of every k-th sweep of a run (the 1st,
+ *                          k+1-th, ...) are bracketed by events, the others
+ *                          run without them; stage launches are counted
+ *                          for every sweep
  */
 #define NFHMM_OPT_FB_CHUNK    0
 #define NFHMM_OPT_FB_PRODUCTS 1
 #define NFHMM_OPT_GRAPHS      2
 #define NFHMM_OPT_FB_GROUP    3
+#define NFHMM_OPT_PROFILE_STRIDE 4
 #define NFHMM_FB_PRODUCTS_SIMT 0
 #define NFHMM_FB_PRODUCTS_TC   1
 NFHMM_API int nfhmm_set_option(nfhmm_ctx *c, int key, long long value);
@@ -356,7 +362,9 @@ NFHMM_API int nfhmm_forward_backward(int S, int N, int T, const float *phi, cons
  * 8*S*(C + C')*(P*P + N) + 12*S*(C + C') bytes, C = ceil(T/L) chunks of L frames
  * (L at most 128; by default 0.3*sqrt(T) rounded, clamped to [8, 64]), C' =
  * ceil(C/G) groups of G = ceil(sqrt(C/2)) chunks (none below 24 chunks),
- * P = 8*ceil(N/8), plus alignment; larger problems are rejected with NFHMM_EINVAL and a message
+ * P = 8*ceil(N/8), plus, when there are groups, 256*S*C*ceil(P/32)*P16 bytes
+ * of tensor-core operand images (P16 = P rounded up to a multiple of 16), plus
+ * alignment; larger problems are rejected with NFHMM_EINVAL and a message
  * giving both sizes.
  * The first call on a device looks up the array's device address (with that
  * device current) and should be made before any stream capture.  All calls
@@ -364,7 +372,7 @@ NFHMM_API int nfhmm_forward_backward(int S, int N, int T, const float *phi, cons
  * overlaps on the GPU (different streams, or different host threads without
  * ordering) race on it.  Asynchronous; inputs and outputs on the device.
  */
-#define NFHMM_NOALLOC_SCRATCH_BYTES (8u << 20)
+#define NFHMM_NOALLOC_SCRATCH_BYTES (32u << 20)
 NFHMM_API int nfhmm_forward_backward_noalloc(int S, int N, int T, const float *phi,
                                              const float *A, const float *pi, float *dhat,
                                              double *logZ, int chunk_len, void *cuda_stream);
@@ -376,7 +384,8 @@ NFHMM_API int nfhmm_forward_backward_noalloc(int S, int N, int T, const float *p
 NFHMM_API int nfhmm_digamma(const float *x, float *psi_out, float *w_out, size_t n, void *cuda_stream);
 
 /*
- * Profiling: with profiling on, every kernel stage a context runs is
+ * Profiling: with profiling on, every kernel stage a context runs (of every
+ * k-th sweep, NFHMM_OPT_PROFILE_STRIDE) is
  * bracketed by CUDA events on the stream it runs on.  nfhmm_profile_read
  * synchronises and returns, for one stage since the last reset, the summed
  * event time (ms), the number of stage invocations and of kernel launches.

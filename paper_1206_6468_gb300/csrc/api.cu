@@ -48,7 +48,7 @@ struct StageEvents {
   long long inv_acc = 0;
 };
 
-// A run of sweeps captured as a CUDA graph.  With profiling on, the stage
+// A sweep captured as a CUDA graph.  With profiling on, the stage
 // events are part of the graph (event record nodes) and are read after each
 // replay, before the next one records them again.
 struct SweepGraph {
@@ -130,9 +130,11 @@ struct nfhmm_ctx {
   bool bound_ok = false;      // h_bound holds the bound of the current state
   bool inputs_ok = false;
   bool profiling = false;
+  int prof_stride = 1;        // events around every prof_stride-th sweep of a run
+  bool prof_gate = true;      // this sweep's stages are timed
   // runs of sweeps captured as CUDA graphs, by launch configuration
   bool use_graphs = true;
-  SweepGraph graphs[4];
+  SweepGraph graphs[8];
   unsigned long long graph_clock = 0;
   SweepGraph* capturing = nullptr;
   StageEvents stages[NFHMM_NUM_STAGES];
@@ -143,7 +145,7 @@ struct nfhmm_ctx {
 namespace {
 
 void stage_begin(nfhmm_ctx* c, int stage, cudaStream_t st) {
-  if (!c->profiling) return;
+  if (!c->profiling || !c->prof_gate) return;
   cudaEvent_t e;
   cudaEventCreate(&e);
   if (c->capturing) {   // an event record node of the graph being captured
@@ -157,7 +159,7 @@ void stage_begin(nfhmm_ctx* c, int stage, cudaStream_t st) {
 void stage_end(nfhmm_ctx* c, int stage, cudaStream_t st, int launches) {
   c->launches += launches;
   c->stages[stage].launches += launches;
-  if (!c->profiling) return;
+  if (!c->profiling || !c->prof_gate) return;
   cudaEvent_t e;
   cudaEventCreate(&e);
   if (c->capturing) {
@@ -392,6 +394,7 @@ int compute_bound(nfhmm_ctx* c) {
   b.bpart = c->bpart;
   b.nbpart = c->nbpart;
   b.fterm = c->fterm_ok ? c->fterm : nullptr;
+  b.funits = weights_units(c->d.S, c->d.N);
   b.logZ = c->logZ;
   b.frame_terms = c->frame_terms;
   b.out = c->bound_dev;
@@ -500,6 +503,8 @@ int ensure_fb_capacity(nfhmm_ctx* c) {
   if (c->fb_scratch && need <= c->Cmax && gneed <= c->NGmax) return NFHMM_OK;
   CK(cudaStreamSynchronize(c->s_main));
   CK(cudaStreamSynchronize(c->s_aux));
+  // captured sweeps hold pointers into the buffers about to be replaced
+  for (auto& g : c->graphs) drop_graph(c, g);
   if (c->fb_scratch) {
     cudaFree(c->fb_scratch);
     c->device_bytes -= fb_scratch_bytes(c->d.S, c->d.N, c->Cmax, c->NGmax);
@@ -775,7 +780,7 @@ int create_ctx(nfhmm_ctx** out, const nfhmm_dims* dp, int max_jobs, const float*
   DMALLOC(c->v, T * 8);
   DMALLOC(c->bpart, T * c->nbpart * 8);
   DMALLOC(c->frame_terms, T * 8);
-  DMALLOC(c->fterm, T * 16);
+  DMALLOC(c->fterm, T * 16 * weights_units(d.S, d.N));
   DMALLOC(c->fb_seg, (size_t)3 * max_jobs * sizeof(int));
   DMALLOC(c->logZ, S * max_jobs * 8);
   DMALLOC(c->bound_dev, (max_jobs + 1) * 8);
@@ -831,8 +836,10 @@ int create_ctx(nfhmm_ctx** out, const nfhmm_dims* dp, int max_jobs, const float*
   return NFHMM_OK;
 }
 
-// The launch configuration a captured run of sweeps depends on.
-long long graph_key_of(const nfhmm_ctx* c, int n, bool want_bpart) {
+// The launch configuration a captured sweep depends on; timed: its stages
+// are bracketed by events (then slot alternates between two instances, so
+// that one may still be in flight while the other is launched).
+long long graph_key_of(const nfhmm_ctx* c, bool want_bpart, bool timed, int slot) {
   long long k = c->T_active;
   k = k * 1000003 + c->fb.C;
   k = k * 1048583 + c->fb.nchains;
@@ -840,39 +847,44 @@ long long graph_key_of(const nfhmm_ctx* c, int n, bool want_bpart) {
   k = k * 4099 + c->fb.G;
   k = k * 1000033 + c->fb.NG;
   k = k * 3 + c->fb.products;
-  k = k * 1009 + n;
   k = k * 2 + (want_bpart ? 1 : 0);
-  k = k * 2 + (c->profiling ? 1 : 0);
+  k = k * 3 + (timed ? 1 + slot : 0);
   return k;
 }
 
-int sweeps_direct(nfhmm_ctx* c, int n, bool want_bpart) {
+// n sweeps launched one by one; with profiling, the stages of sweep i are
+// timed when (first + i) is a multiple of the profiling stride.
+int sweeps_direct(nfhmm_ctx* c, int n, bool want_bpart, long long first = 0) {
   for (int i = 0; i < n; ++i) {
+    c->prof_gate = (first + i) % c->prof_stride == 0;
     const int rc = one_sweep(c, want_bpart && i == n - 1);
+    c->prof_gate = true;
     if (rc) return rc;
   }
   return NFHMM_OK;
 }
 
-// n sweeps (the last with the bound's terms if want_bpart), replayed from
-// captured CUDA graphs once the same launch configuration has run uncaptured
-// once, else launched one by one.  Without profiling, graphs of one sweep
-// are replayed n times (any n); with profiling, the run of n sweeps is one
-// graph, so that every sweep's stage events are distinct nodes.
-int run_graph(nfhmm_ctx* c, int n, bool want_bpart);
+// n sweeps (the last with the bound's terms if want_bpart), each replayed
+// from a captured one-sweep CUDA graph once the same launch configuration has
+// run uncaptured once, else launched one by one.  With profiling, every
+// prof_stride-th sweep replays a graph with stage events (two instances in
+// turn; an instance's previous events are read before it is launched again).
+int run_graph(nfhmm_ctx* c, bool want_bpart, long long index);
 int run_sweeps(nfhmm_ctx* c, int n, bool want_bpart) {
   if (!c->use_graphs || c->T_active == 0 || n < 1) return sweeps_direct(c, n, want_bpart);
-  if (c->profiling) return run_graph(c, n, want_bpart);
   for (int i = 0; i < n; ++i) {
-    const int rc = run_graph(c, 1, want_bpart && i == n - 1);
+    const int rc = run_graph(c, want_bpart && i == n - 1, i);
     if (rc) return rc;
   }
   return NFHMM_OK;
 }
 
-int run_graph(nfhmm_ctx* c, int n, bool want_bpart) {
-  if (!c->use_graphs) return sweeps_direct(c, n, want_bpart);
-  const long long key = graph_key_of(c, n, want_bpart);
+int run_graph(nfhmm_ctx* c, bool want_bpart, long long index) {
+  const bool timed = c->profiling && index % c->prof_stride == 0;
+  const int slot = (int)((index / c->prof_stride) & 1);
+  // the index the sweep is captured with: one that gives it the same gate
+  const long long cap_index = timed || c->prof_stride == 1 ? 0 : 1;
+  const long long key = graph_key_of(c, want_bpart, timed, slot);
   SweepGraph* g = nullptr;
   for (auto& x : c->graphs)
     if (x.key == key) g = &x;
@@ -885,7 +897,7 @@ int run_graph(nfhmm_ctx* c, int n, bool want_bpart) {
   }
   g->last_use = ++c->graph_clock;
   if (!g->exec) {
-    if (g->seen++ == 0) return sweeps_direct(c, n, want_bpart);   // first launches uncaptured
+    if (g->seen++ == 0) return sweeps_direct(c, 1, want_bpart, index);   // first uncaptured
     const long long l0 = c->launches;
     long long s0[NFHMM_NUM_STAGES];
     for (int i = 0; i < NFHMM_NUM_STAGES; ++i) s0[i] = c->stages[i].launches;
@@ -893,10 +905,10 @@ int run_graph(nfhmm_ctx* c, int n, bool want_bpart) {
     if (cudaStreamBeginCapture(c->s_main, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
       cudaGetLastError();
       c->use_graphs = false;
-      return sweeps_direct(c, n, want_bpart);
+      return sweeps_direct(c, 1, want_bpart, index);
     }
     c->capturing = g;
-    const int rc = sweeps_direct(c, n, want_bpart);
+    const int rc = sweeps_direct(c, 1, want_bpart, cap_index);
     c->capturing = nullptr;
     const cudaError_t e = cudaStreamEndCapture(c->s_main, &graph);
     const bool good = !rc && e == cudaSuccess && graph &&
@@ -913,7 +925,7 @@ int run_graph(nfhmm_ctx* c, int n, bool want_bpart) {
       drop_graph(c, *g);
       c->use_graphs = false;
       if (rc) return rc;
-      return sweeps_direct(c, n, want_bpart);   // capture unavailable: launch directly
+      return sweeps_direct(c, 1, want_bpart, index);   // capture unavailable: launch directly
     }
   }
   harvest(c, *g);   // its events are about to be recorded again
@@ -1120,6 +1132,11 @@ int nfhmm_set_option(nfhmm_ctx* c, int key, long long value) {
     }
     case NFHMM_OPT_GRAPHS: {
       c->use_graphs = value != 0;
+      return NFHMM_OK;
+    }
+    case NFHMM_OPT_PROFILE_STRIDE: {
+      if (value < 1 || value > 1000000) return fail(NFHMM_EINVAL, "profile stride must be >= 1");
+      c->prof_stride = (int)value;
       return NFHMM_OK;
     }
     default: return fail(NFHMM_EINVAL, "unknown option key");

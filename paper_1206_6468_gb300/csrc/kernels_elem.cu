@@ -17,50 +17,54 @@ namespace nfhmm {
 constexpr unsigned FULL = 0xffffffffu;
 
 // ------------------------------------------------------------ weights (Eq. 6, 8)
-// One warp per frame t.  Elements are visited in chunks of 32 consecutive k;
-// phi-hat for block g = k / K is the inclusive segmented scan of psi at the
-// block's last element, with the partial sum of a block that straddles a
-// chunk boundary carried in a register (deterministic order, no atomics).
-// The element table ktab[k] = (g, s*T*N + n) (g < 0 for padding) replaces
-// integer division by K and N on the hot path.
+// One warp per unit of WB consecutive blocks g = (s, n) of one frame t (WB*K
+// consecutive elements): each lane takes every 32nd element of the unit
+// (coalesced loads and stores), forms alpha-hat (Eq. 6), psi and
+// w = exp(psi), and parks psi in shared memory; then lane b sums the K values
+// of the unit's block b in element order, which is Eq. 8's sum over the
+// block (deterministic, no shuffles or atomics).  Padding elements k >= M are
+// never touched (zero since the frame was loaded).  The element table
+// ktab[k] = (g, s*T*N + n) replaces integer division on the hot path.
 // With BOUND, the warp also sums alpha-hat and the bound's element terms
-// g(alpha) over the frame (Kahan-compensated in float per lane, then double).
+// g(alpha) over its unit (Kahan-compensated in float per lane, then double)
+// into fterm[t][h] for unit h of the frame.
+constexpr int WB = 16;
 template <int FMT, bool BOUND>
 __global__ void __launch_bounds__(256) k_weights(WeightsArgs a) {
-  const int lane = threadIdx.x & 31;
-  const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (t >= a.T) return;
+  extern __shared__ float wsm[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int NB = a.S * a.N;                 // blocks per frame
+  const int NH = (NB + WB - 1) / WB;        // units per frame
+  const long long u = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (u >= (long long)a.T * NH) return;     // whole warps
+  const int t = (int)(u / NH), h = (int)(u - (long long)t * NH);
+  const int UE = WB * a.K;
+  const int k0 = h * UE, k1 = min(k0 + UE, a.M);
+  float* ps = wsm + warp * UE;
   const size_t row = (size_t)t * a.Mp;
   const size_t toff = (size_t)t * a.N;
-  float carry = 0.f;
-  int carry_key = INT_MIN;
   unsigned bad = 0;
   float sa = 0.f, ca = 0.f, sg = 0.f, cg = 0.f;   // Kahan sums of alpha and g (small part)
   double big = 0.0;                                // sum of the exact large parts of g
-  for (int base = 0; base < a.Mp; base += 32) {
-    const int k = base + lane;
-    const int2 kt = a.ktab[k];          // Mp is a multiple of 32: k < Mp
-    const int g = kt.x;
-    const bool el = g >= 0;
-    float alpha = 0.f, psi = 0.f, w = 0.f;
-    if (el) {
-      alpha = a.counts[row + k] + a.gamma * a.dhat[kt.y + toff] + 1.f;
-      if (BOUND) {
-        float gs, gb;
-        digamma_exp_g(alpha, psi, w, gs, gb);
-        float y = alpha - ca, z = sa + y;
-        ca = (z - sa) - y;
-        sa = z;
-        y = gs - cg;
-        z = sg + y;
-        cg = (z - sg) - y;
-        sg = z;
-        big += (double)gb;
-      } else {
-        digamma_exp(alpha, psi, w);
-      }
-      if (!isfinite(psi) || !isfinite(w)) bad |= ERR_NONFINITE;
+  for (int k = k0 + lane; k < k1; k += 32) {
+    const int dy = a.ktab[k].y;
+    const float alpha = a.counts[row + k] + a.gamma * a.dhat[dy + toff] + 1.f;
+    float psi, w;
+    if (BOUND) {
+      float gs, gb;
+      digamma_exp_g(alpha, psi, w, gs, gb);
+      float y = alpha - ca, z = sa + y;
+      ca = (z - sa) - y;
+      sa = z;
+      y = gs - cg;
+      z = sg + y;
+      cg = (z - sg) - y;
+      sg = z;
+      big += (double)gb;
+    } else {
+      digamma_exp(alpha, psi, w);
     }
+    if (!isfinite(psi) || !isfinite(w)) bad |= ERR_NONFINITE;
     a.alpha[row + k] = alpha;
     a.w32[row + k] = w;
     if (FMT == WF_TF32X2) {
@@ -70,28 +74,15 @@ __global__ void __launch_bounds__(256) k_weights(WeightsArgs a) {
     } else if (FMT == WF_BF16) {
       reinterpret_cast<__nv_bfloat16*>(a.wop_hi)[row + k] = __float2bfloat16_rn(w);
     }
-    // inclusive segmented scan of psi keyed by block g
-    float x = psi;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const float y = __shfl_up_sync(FULL, x, d);
-      const int gy = __shfl_up_sync(FULL, g, d);
-      if (lane >= d && gy == g) x += y;
-    }
-    if (g == carry_key) x += carry;
-    int gnext = __shfl_down_sync(FULL, g, 1);
-    if (lane == 31) gnext = (k + 1 < a.Mp) ? a.ktab[k + 1].x : INT_MIN;
-    if (el && gnext != g) a.phi[kt.y + toff] = a.gamma * x;   // last element of block g
-    const float x31 = __shfl_sync(FULL, x, 31);
-    const int g31 = __shfl_sync(FULL, g, 31);
-    const int gn31 = __shfl_sync(FULL, gnext, 31);
-    if (g31 >= 0 && gn31 == g31) {
-      carry = x31;
-      carry_key = g31;
-    } else {
-      carry = 0.f;
-      carry_key = INT_MIN;
-    }
+    ps[k - k0] = psi;
+  }
+  __syncwarp();
+  const int b = h * WB + lane;
+  if (lane < WB && b < NB) {
+    const float* pb = ps + lane * a.K;
+    float x = 0.f;
+    for (int j = 0; j < a.K; ++j) x += pb[j];
+    a.phi[a.ktab[b * a.K].y + toff] = a.gamma * x;
   }
   bad = __reduce_or_sync(FULL, bad);
   if (bad && lane == 0) atomicOr(a.err, bad);
@@ -99,11 +90,12 @@ __global__ void __launch_bounds__(256) k_weights(WeightsArgs a) {
     const double s0 = warp_sum_d((double)sa - (double)ca);
     const double sgt = warp_sum_d(((double)sg - (double)cg) + big);
     if (lane == 0) {
-      a.fterm[2 * (size_t)t] = s0;
-      a.fterm[2 * (size_t)t + 1] = sgt;
+      a.fterm[2 * (size_t)u] = s0;
+      a.fterm[2 * (size_t)u + 1] = sgt;
     }
   }
 }
+int weights_units(int S, int N) { return (S * N + WB - 1) / WB; }
 
 __global__ void k_element_table(int M, int Mp, int K, int N, int T, int2* ktab) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -121,20 +113,22 @@ void launch_element_table(int M, int Mp, int K, int N, int T, int2* ktab, cudaSt
 
 void launch_weights(const WeightsArgs& a, int fmt, cudaStream_t st) {
   const int warps = 8;
-  dim3 grid((a.T + warps - 1) / warps);
+  const long long units = (long long)a.T * weights_units(a.S, a.N);
+  dim3 grid((unsigned)((units + warps - 1) / warps));
+  const size_t smem = (size_t)warps * WB * a.K * sizeof(float);
   const bool b = a.fterm != nullptr;
   switch (fmt) {
     case WF_TF32X2:
-      if (b) k_weights<WF_TF32X2, true><<<grid, warps * 32, 0, st>>>(a);
-      else k_weights<WF_TF32X2, false><<<grid, warps * 32, 0, st>>>(a);
+      if (b) k_weights<WF_TF32X2, true><<<grid, warps * 32, smem, st>>>(a);
+      else k_weights<WF_TF32X2, false><<<grid, warps * 32, smem, st>>>(a);
       break;
     case WF_BF16:
-      if (b) k_weights<WF_BF16, true><<<grid, warps * 32, 0, st>>>(a);
-      else k_weights<WF_BF16, false><<<grid, warps * 32, 0, st>>>(a);
+      if (b) k_weights<WF_BF16, true><<<grid, warps * 32, smem, st>>>(a);
+      else k_weights<WF_BF16, false><<<grid, warps * 32, smem, st>>>(a);
       break;
     default:
-      if (b) k_weights<WF_F32, true><<<grid, warps * 32, 0, st>>>(a);
-      else k_weights<WF_F32, false><<<grid, warps * 32, 0, st>>>(a);
+      if (b) k_weights<WF_F32, true><<<grid, warps * 32, smem, st>>>(a);
+      else k_weights<WF_F32, false><<<grid, warps * 32, smem, st>>>(a);
       break;
   }
 }
@@ -301,7 +295,11 @@ __global__ void k_bound_frames(BoundArgs a) {
 __global__ void k_bound_frames_fused(BoundArgs a) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= a.T) return;
-  const double s0 = a.fterm[2 * (size_t)t], sg = a.fterm[2 * (size_t)t + 1];
+  double s0 = 0.0, sg = 0.0;
+  for (int h = 0; h < a.funits; ++h) {
+    s0 += a.fterm[2 * ((size_t)t * a.funits + h)];
+    sg += a.fterm[2 * ((size_t)t * a.funits + h) + 1];
+  }
   double vl = 0.0;
   for (int j = 0; j < a.nbpart; ++j) vl += a.bpart[(size_t)t * a.nbpart + j];
   const double psi0 = digamma_d(s0);

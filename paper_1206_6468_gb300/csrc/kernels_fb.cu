@@ -28,6 +28,7 @@
 // emissions and zero initial probability, so padded states never carry mass;
 // every kernel is instantiated per NP and its loops unroll fully.
 // Limits: chunk length 1 <= L <= FB_MAX_L, states N <= FB_MAX_N.
+#include <limits.h>
 #include <math.h>
 
 #include "nfhmm_device.cuh"
@@ -147,17 +148,45 @@ int fb_default_chunk(int N, int T) {
 
 static inline size_t mat_floats(int N) { return (size_t)pad8(N) * pad8(N); }
 
-// --------------------------------------------------------------- 1. products
+// ------------------------------------------------- 1. chain products (tensor cores)
+// One 128-row tile of product rows advanced through a run of factors, one
+// split-TF32 tcgen05.mma of the tile per factor.  Row i of a product of
+// factors F_1 ... F_n is the forward recursion started from basis state i, so
+// every row evolves on its own (one TMEM lane per row):
+//   CHAIN_CHUNK: the rows of floor(128/NP) chunks; the factor of frame t is
+//                G_t = A diag(e_t): B operand A (fixed), the emissions applied
+//                to the product rows after each step;
+//   CHAIN_GROUP: the rows of one group of chunks; the factors are its chunk
+//                matrices, whose split operand images the chunk pass wrote,
+//                brought in by bulk copies a few steps ahead.
+// Eight warps: warp w reads TMEM lanes 32(w%4).. (one row per thread) and
+// half w/4 of the columns; the two halves of a row exchange their maxima
+// through shared memory (a 64-thread named barrier).  Rows are rescaled by
+// powers of two (exact), the removed exponents summed per row; at the end
+// the rows of a chunk (group) are brought to the exponent of its largest row.
+enum { CHAIN_CHUNK = 0, CHAIN_GROUP = 1 };
 template <int NP>
-struct ProdCfg {
-  static constexpr int RCH = 128 / NP;              // chunks per 128-row tile
+struct ChainCfg {
+  static constexpr int RCH = 128 / NP;              // chunks per tile (chunk pass)
   static constexpr int NOUT = (NP + 15) & ~15;      // MMA N (multiple of 16)
+  static constexpr int HC = NOUT / 2;               // columns per epilogue half (multiple of 8)
   static constexpr int KSTEPS = NP / 8;             // tf32 MMA K = 8
   static constexpr int KATOMS = (NP + 31) / 32;     // 128-byte swizzle atoms along K
   static constexpr int ROWS_BYTES = KATOMS * 128 * 128;
   static constexpr int B_BYTES = KATOMS * NOUT * 128;
+  static constexpr int IMG_BYTES = 2 * B_BYTES;     // tf32 hi and lo copies of one B operand
+  static constexpr int RING = 4;                    // group pass: chunk images in flight
   static constexpr int TMEM_COLS = 2 * NOUT <= 32 ? 32 : 2 * NOUT <= 64 ? 64 : 128;
-  static constexpr int SMEM_FIXED = 2 * ROWS_BYTES + 2 * B_BYTES;
+};
+struct ChainMisc {
+  double msum[16];       // chunk pass: summed frame maxima per chunk; group pass: [0] = chunk logs
+  double part[8];        // per-warp partial sums
+  float pmax[2][128];    // row maxima of the two column halves
+  int pe[128];           // row exponents for the common scale
+  int best[16];          // exponent of the largest row per chunk
+  uint64_t mma_bar;
+  uint64_t full[ChainCfg<8>::RING];
+  uint32_t tslot;
 };
 
 // byte offset of element (row r, k) in a K-major tile of 128-byte rows with
@@ -167,147 +196,219 @@ __device__ __forceinline__ uint32_t sw128_off(int r, int k, int atom_bytes) {
   return atom * atom_bytes + (r >> 3) * 1024 + (r & 7) * 128 + ((((kk >> 2) ^ (r & 7))) << 4) +
          ((kk & 3) << 2);
 }
+__device__ __forceinline__ void named_bar(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+__device__ __forceinline__ void tmem_ld8_nw(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr));
+}
+// exact power of two 2^k for -126 <= k <= 127
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }
 
-template <int NP>
-__global__ void __launch_bounds__(128, 1) k_fb_products(FBArgs a) {
+template <int NP, int MODE>
+__global__ void __launch_bounds__(256, MODE == CHAIN_CHUNK ? 2 : 1) k_fb_chain(FBArgs a) {
   using namespace tc;
-  using Cfg = ProdCfg<NP>;
-  constexpr int NOUT = Cfg::NOUT;   // columns per row, a multiple of 16
+  using Cfg = ChainCfg<NP>;
+  constexpr int NOUT = Cfg::NOUT, HC = Cfg::HC, RING = Cfg::RING;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint8_t* rows_hi = smem;
   uint8_t* rows_lo = rows_hi + Cfg::ROWS_BYTES;
-  uint8_t* b_hi = rows_lo + Cfg::ROWS_BYTES;
-  uint8_t* b_lo = b_hi + Cfg::B_BYTES;
-  float* e = reinterpret_cast<float*>(b_lo + Cfg::B_BYTES);   // RCH x L x NP
-  double* rhod = reinterpret_cast<double*>(e + Cfg::RCH * a.L * NP);  // 128
-  double* msum = rhod + 128;                                   // RCH
-  uint64_t* bar = reinterpret_cast<uint64_t*>(msum + Cfg::RCH);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+  uint8_t* bbuf = rows_lo + Cfg::ROWS_BYTES;   // chunk pass: A split; group pass: image ring
+  constexpr int BBUF = MODE == CHAIN_CHUNK ? Cfg::IMG_BYTES : RING * Cfg::IMG_BYTES;
+  float* e = reinterpret_cast<float*>(bbuf + BBUF);   // chunk pass: RCH x L x NP emissions
+  const int ne = MODE == CHAIN_CHUNK ? Cfg::RCH * a.L * NP : 0;
+  ChainMisc* ms = reinterpret_cast<ChainMisc*>(e + ne);
 
-  const int N = a.N, L = a.L, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int N = a.N, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int quarter = warp & 3, half = warp >> 2;
+  const int r = quarter * 32 + lane;           // tile row = TMEM lane
+  const int j0 = half * HC;                    // first column of this thread
   const int s = blockIdx.y;
-  const int cbase = blockIdx.x * Cfg::RCH;
+  const size_t cb = (size_t)s * a.C;
+
+  // rows of this thread: chunk pass (chunk q of the tile, state i); group pass (state i)
+  int q = 0, i = r, c = 0, c0 = 0, nst = 0;
+  bool live = false, first = false;
+  int len = 0, cbase = 0;
+  if (MODE == CHAIN_CHUNK) {
+    cbase = blockIdx.x * Cfg::RCH;
+    q = r / NP;
+    i = r - q * NP;
+    c = cbase + q;
+    const bool inchunk = q < Cfg::RCH && c < a.C;
+    ChunkInfo ci = inchunk ? chunk_info(a, c) : ChunkInfo{0, 0, 0, false};
+    live = inchunk && i < N;
+    len = live ? ci.len : 0;
+    first = ci.first;
+    nst = a.L - 1;
+  } else {
+    const int g = blockIdx.x;
+    c0 = a.grp_c0 ? a.grp_c0[g] : g * a.G;
+    const int c1 = a.grp_c0 ? a.grp_c0[g + 1] : min((g + 1) * a.G, a.C);
+    live = i < N;
+    nst = c1 - c0 - 1;
+  }
 
   if (tid == 0) {
-    mbar_init(bar, 1);
+    mbar_init(&ms->mma_bar, 1);
+    if (MODE == CHAIN_GROUP)
+      for (int u = 0; u < RING; ++u) mbar_init(&ms->full[u], 1);
     fence_barrier_init();
   }
   if (warp == 0) {
-    tmem_alloc(tslot, Cfg::TMEM_COLS);
+    tmem_alloc(&ms->tslot, Cfg::TMEM_COLS);
     tmem_relinquish();
   }
-  // emissions of the tile's chunks (gathered with asynchronous copies while
-  // the B operand is formed)
-  for (int q = 0; q < Cfg::RCH; ++q) {
-    const int c = cbase + q;
-    if (c >= a.C) break;
-    const ChunkInfo ci = chunk_info(a, c);
-    const float* src = a.phi + ((size_t)s * a.T + ci.t0) * N;
-    float* eq = e + q * L * NP;
-    for (int i = tid; i < ci.len * N; i += blockDim.x) {
-      const int f = i / N, n = i - f * N;
-      cp_async4(eq + f * NP + n, src + i);
-    }
-  }
-  cp_async_commit();
-  // B operand: B[j][k] = A[k][j] (zero outside N x N), split into tf32 hi/lo;
-  // this thread's values are loaded first, all in flight together
   const float* Ag = a.A + (size_t)s * N * N;
-  constexpr int BPT = (NOUT * Cfg::KATOMS * 32 + 127) / 128;
-  float bv[BPT];
+  if (MODE == CHAIN_CHUNK) {
+    // emissions of the tile's chunks (asynchronous gathers while B is formed)
+    for (int qq = 0; qq < Cfg::RCH; ++qq) {
+      const int cc = cbase + qq;
+      if (cc >= a.C) break;
+      const ChunkInfo ci = chunk_info(a, cc);
+      const float* src = a.phi + ((size_t)s * a.T + ci.t0) * N;
+      float* eq = e + qq * a.L * NP;
+      for (int u = tid; u < ci.len * N; u += 256) {
+        const int f = u / N, n = u - f * N;
+        cp_async4(eq + f * NP + n, src + u);
+      }
+    }
+    cp_async_commit();
+    // B operand: B[j][k] = A[k][j] (zero outside N x N), split into tf32 hi/lo
+    constexpr int BW = NOUT * Cfg::KATOMS * 32;
+    constexpr int BPT = (BW + 255) / 256;
+    float bv[BPT];
 #pragma unroll
-  for (int u = 0; u < BPT; ++u) {
-    const int idx = tid + 128 * u;
-    const int j = idx / (Cfg::KATOMS * 32), k = idx - j * (Cfg::KATOMS * 32);
-    bv[u] = (idx < NOUT * Cfg::KATOMS * 32 && j < N && k < N) ? __ldg(Ag + k * N + j) : 0.f;
-  }
-#pragma unroll
-  for (int u = 0; u < BPT; ++u) {
-    const int idx = tid + 128 * u;
-    if (idx < NOUT * Cfg::KATOMS * 32) {
+    for (int u = 0; u < BPT; ++u) {
+      const int idx = tid + 256 * u;
       const int j = idx / (Cfg::KATOMS * 32), k = idx - j * (Cfg::KATOMS * 32);
-      const float h = tf32_hi(bv[u]);
-      const uint32_t off = sw128_off(j, k, NOUT * 128);
-      *reinterpret_cast<float*>(b_hi + off) = h;
-      *reinterpret_cast<float*>(b_lo + off) = tf32_hi(bv[u] - h);
+      bv[u] = (idx < BW && j < N && k < N) ? __ldg(Ag + k * N + j) : 0.f;
     }
-  }
-  cp_async_wait<0>();
-  __syncthreads();
-  for (int q = 0; q < Cfg::RCH; ++q) {
-    const int c = cbase + q;
-    if (c >= a.C) break;
-    const int len = chunk_info(a, c).len;
-    float* eq = e + q * L * NP;
-    double ms = 0.0;
-    for (int f = warp; f < len; f += 4) {
-      float* row = eq + f * NP;
-      const float x0 = lane < N ? row[lane] : -INFINITY;
-      const float x1 = lane + 32 < N ? row[lane + 32] : -INFINITY;
-      const float m = warp_max(fmaxf(x0, x1));
-      __syncwarp();
-      if (lane < NP) row[lane] = lane < N ? expf(x0 - m) : 0.f;
-      if (lane + 32 < NP) row[lane + 32] = lane + 32 < N ? expf(x1 - m) : 0.f;
-      ms += (double)m;
+#pragma unroll
+    for (int u = 0; u < BPT; ++u) {
+      const int idx = tid + 256 * u;
+      if (idx < BW) {
+        const int j = idx / (Cfg::KATOMS * 32), k = idx - j * (Cfg::KATOMS * 32);
+        const float h = tf32_hi(bv[u]);
+        const uint32_t off = sw128_off(j, k, NOUT * 128);
+        *reinterpret_cast<float*>(bbuf + off) = h;
+        *reinterpret_cast<float*>(bbuf + Cfg::B_BYTES + off) = tf32_hi(bv[u] - h);
+      }
     }
-    if (lane == 0) rhod[warp] = ms;
+    cp_async_wait<0>();
     __syncthreads();
-    if (tid == 0) msum[q] = rhod[0] + rhod[1] + rhod[2] + rhod[3];
-    __syncthreads();
+    // e_t = exp(phi_t - max phi_t), the maxima summed per chunk
+    for (int qq = 0; qq < Cfg::RCH; ++qq) {
+      const int cc = cbase + qq;
+      if (cc >= a.C) break;
+      const int ln = chunk_info(a, cc).len;
+      float* eq = e + qq * a.L * NP;
+      double sm = 0.0;
+      for (int f = warp; f < ln; f += 8) {
+        float* row = eq + f * NP;
+        const float x0 = lane < N ? row[lane] : -INFINITY;
+        const float x1 = lane + 32 < N ? row[lane + 32] : -INFINITY;
+        const float m = warp_max(fmaxf(x0, x1));
+        __syncwarp();
+        if (lane < NP) row[lane] = lane < N ? expf(x0 - m) : 0.f;
+        if (lane + 32 < NP) row[lane + 32] = lane + 32 < N ? expf(x1 - m) : 0.f;
+        sm += (double)m;
+      }
+      if (lane == 0) ms->part[warp] = sm;
+      __syncthreads();
+      if (tid == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += ms->part[w];
+        ms->msum[qq] = t;
+      }
+      __syncthreads();
+    }
+  } else {
+    __syncthreads();   // barriers initialised
+    if (tid == 0) {
+      for (int u = 0; u < RING && u < nst; ++u) {
+        mbar_expect_tx(&ms->full[u], Cfg::IMG_BYTES);
+        bulk_g2s(bbuf + u * Cfg::IMG_BYTES, a.Pimg + (cb + c0 + 1 + u) * Cfg::IMG_BYTES,
+                 Cfg::IMG_BYTES, &ms->full[u]);
+      }
+    }
+    if (warp == 7) {   // the group's scale starts as the sum of its chunks' scales
+      double lg = 0.0;
+      for (int cc = c0 + lane; cc <= c0 + nst; cc += 32) lg += a.Plog[cb + cc];
+      lg = warp_sum_d(lg);
+      if (lane == 0) ms->msum[0] = lg;
+    }
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem = *tslot;
+  const uint32_t tmem = ms->tslot;
 
-  // this thread: row r of the tile = TMEM lane r (chunk q, basis state i)
-  const int r = tid;
-  const int q = r / NP, i = r - (r / NP) * NP;
-  const int c = cbase + q;
-  const bool live = q < Cfg::RCH && c < a.C && i < N;
-  const ChunkInfo ci = (q < Cfg::RCH && c < a.C) ? chunk_info(a, c) : ChunkInfo{0, 0, 0, false};
-  const int len = live ? ci.len : 0;
-  const float* eq = e + (q < Cfg::RCH ? q : 0) * L * NP;
-  float cur[NOUT];
-  ScaleAcc sc;
-  bool zero_row = false;   // once zero, a row stays zero: its scale is then -inf
+  const float* eq = e + (MODE == CHAIN_CHUNK && q < Cfg::RCH ? q : 0) * a.L * NP;
+  float cur[HC];
+  int ex_row = 0;          // the row's true value = stored value * 2^ex_row
+  bool zero_row = false;   // once zero, a row stays zero
   unsigned bad = 0;
+  if (MODE == CHAIN_CHUNK) {
 #pragma unroll
-  for (int j = 0; j < NOUT; ++j) {
-    float v = 0.f;
-    if (live && j < N) v = ci.first ? (j == i ? eq[j] : 0.f) : Ag[i * N + j] * eq[j];
-    cur[j] = v;
+    for (int jj = 0; jj < HC; ++jj) {
+      const int j = j0 + jj;
+      float v = 0.f;
+      if (live && j < N) v = first ? (j == i ? eq[j] : 0.f) : Ag[i * N + j] * eq[j];
+      cur[jj] = v;
+    }
+  } else {
+    const float* Pr = a.P + (cb + c0) * NP * NP + (size_t)i * NP;
+#pragma unroll
+    for (int jj = 0; jj < HC; ++jj) {
+      const int j = j0 + jj;
+      cur[jj] = (live && j < NP) ? Pr[j] : 0.f;
+    }
   }
-  // rescale the row by its maximum and write it, split into tf32 hi/lo,
-  // into the swizzled operand tile (the thread owns the whole row)
+  // rescale the row by a power of two that brings its maximum into [0.5, 1)
+  // and write this thread's columns, split into tf32 hi/lo, into the
+  // swizzled operand tile
   auto normalise_and_store = [&]() {
     float m = 0.f;
 #pragma unroll
-    for (int j = 0; j < NOUT; ++j) m = fmaxf(m, cur[j]);
+    for (int jj = 0; jj < HC; ++jj) m = fmaxf(m, cur[jj]);
+    ms->pmax[half][r] = m;
+    named_bar(1 + quarter, 64);
+    m = fmaxf(m, ms->pmax[half ^ 1][r]);
     if (live) {
       // an all-zero row is legitimate (state i cannot start this chunk)
       if (!isfinite(m)) {
         bad = 1;
         m = 0.f;
       }
-      if (m == 0.f) zero_row = true;
-      const float g = renorm_factor(m);
+      if (m == 0.f) {
+        zero_row = true;
+      } else {
+        int ex;
+        frexpf(m, &ex);
+        const int k = -ex > 126 ? 126 : -ex;
+        const float g = pow2f(k);
 #pragma unroll
-      for (int j = 0; j < NOUT; ++j) cur[j] *= g;
-      sc.mul(removed_scale(m));
+        for (int jj = 0; jj < HC; ++jj) cur[jj] *= g;
+        ex_row -= k;
+      }
     }
 #pragma unroll
-    for (int cc = 0; cc < NOUT / 4; ++cc) {
-      if (4 * cc < NP) {
+    for (int cc = 0; cc < HC / 4; ++cc) {
+      if (j0 + 4 * cc < NP) {
         float h[4], l[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           h[u] = tf32_hi(cur[4 * cc + u]);
           l[u] = tf32_hi(cur[4 * cc + u] - h[u]);
         }
-        const uint32_t off = sw128_off(r, 4 * cc, 128 * 128);
+        const uint32_t off = sw128_off(r, j0 + 4 * cc, 128 * 128);
         *reinterpret_cast<float4*>(rows_hi + off) = make_float4(h[0], h[1], h[2], h[3]);
         *reinterpret_cast<float4*>(rows_lo + off) = make_float4(l[0], l[1], l[2], l[3]);
       }
@@ -317,14 +418,33 @@ __global__ void __launch_bounds__(128, 1) k_fb_products(FBArgs a) {
 
   constexpr uint32_t ID = idesc<KIND_TF32X3>(128, NOUT);
   const uint32_t rh = smem_u32(rows_hi), rl = smem_u32(rows_lo);
-  const uint32_t bh = smem_u32(b_hi), bl = smem_u32(b_lo);
-  const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+  const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)j0;
   bool ok = true;
-  for (int f = 1; f < L; ++f) {
+  int issued = MODE == CHAIN_GROUP ? min(RING, nst) : 0;   // group pass: images requested
+  int consumed = 0;                                          // and waited for
+  for (int f = 1; f <= nst; ++f) {
+    bool okf = ok;
+    uint32_t bh = smem_u32(bbuf);
+    if (MODE == CHAIN_GROUP) {
+      const int slot = (f - 1) % RING;
+      bh = smem_u32(bbuf + slot * Cfg::IMG_BYTES);
+      if (tid == 0) {
+        if (!mbar_wait(&ms->full[slot], ((f - 1) / RING) & 1)) {
+          okf = false;
+          atomicOr(a.err, ERR_TIMEOUT);
+        } else {
+          consumed = f;
+        }
+      }
+    }
+    const uint32_t bl = bh + Cfg::B_BYTES;
     fence_proxy_async_smem();   // the operand rows written above, to the tensor core
     tc_fence_before();
     // every row written; and the decision to stop is the same in every thread
-    if (__syncthreads_or(!ok)) break;
+    if (__syncthreads_or(!okf)) {
+      ok = false;
+      break;
+    }
     if (tid == 0) {
       tc_fence_after();
 #pragma unroll
@@ -335,66 +455,109 @@ __global__ void __launch_bounds__(128, 1) k_fb_products(FBArgs a) {
         mma<KIND_TF32X3>(tmem + NOUT, sdesc(rh + ao), sdesc(bl + bo), ID, kk > 0 ? 1u : 0u);
         mma<KIND_TF32X3>(tmem + NOUT, sdesc(rl + ao), sdesc(bh + bo), ID, 1u);
       }
-      mma_commit(bar);
+      mma_commit(&ms->mma_bar);
     }
-    if (!mbar_wait(bar, (f - 1) & 1)) {
-      ok = false;
+    const bool done = mbar_wait(&ms->mma_bar, (f - 1) & 1);
+    if (!done) {
+      ok = false;   // the next step's barrier stops every thread
       if (lane == 0) atomicOr(a.err, ERR_TIMEOUT);
-      continue;   // the next barrier stops every thread
     }
     tc_fence_after();
-    uint32_t yr[NOUT / 16][16], xr[NOUT / 16][16];
-#pragma unroll
-    for (int cc = 0; cc < NOUT / 16; ++cc) {
-      tmem_ld16_nw(taddr + 16 * cc, yr[cc]);
-      tmem_ld16_nw(taddr + NOUT + 16 * cc, xr[cc]);
+    if (MODE == CHAIN_GROUP && tid == 0 && done && f + RING <= nst) {
+      // the step's MMAs have completed: its slot takes the image RING steps ahead
+      const int slot = (f - 1) % RING;
+      mbar_expect_tx(&ms->full[slot], Cfg::IMG_BYTES);
+      bulk_g2s(bbuf + slot * Cfg::IMG_BYTES, a.Pimg + (cb + c0 + f + RING) * Cfg::IMG_BYTES,
+               Cfg::IMG_BYTES, &ms->full[slot]);
+      issued = f + RING;
     }
-    tmem_wait_ld();
-    if (live && f < len) {
-      const float* ef = eq + f * NP;
+    if (done) {
+      uint32_t yr[HC], xr[HC];
 #pragma unroll
-      for (int j = 0; j < NOUT; j += 4) {
-        if (j < NP) {
-          const float4 e4 = *reinterpret_cast<const float4*>(ef + j);
-          const float ev[4] = {e4.x, e4.y, e4.z, e4.w};
+      for (int cc = 0; cc < HC / 8; ++cc) {
+        tmem_ld8_nw(taddr + 8 * cc, yr + 8 * cc);
+        tmem_ld8_nw(taddr + NOUT + 8 * cc, xr + 8 * cc);
+      }
+      tmem_wait_ld();
+      if (MODE == CHAIN_CHUNK) {
+        if (live && f < len) {
+          const float* ef = eq + f * NP + j0;
 #pragma unroll
-          for (int u = 0; u < 4; ++u)
-            cur[j + u] = (__uint_as_float(yr[(j + u) >> 4][(j + u) & 15]) +
-                          __uint_as_float(xr[(j + u) >> 4][(j + u) & 15])) * ev[u];
-        } else {
-          cur[j] = cur[j + 1] = cur[j + 2] = cur[j + 3] = 0.f;
+          for (int jj = 0; jj < HC; jj += 4) {
+            if (j0 + jj < NP) {
+              const float4 e4 = *reinterpret_cast<const float4*>(ef + jj);
+              const float ev[4] = {e4.x, e4.y, e4.z, e4.w};
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+                cur[jj + u] = (__uint_as_float(yr[jj + u]) + __uint_as_float(xr[jj + u])) * ev[u];
+            } else {
+              cur[jj] = cur[jj + 1] = cur[jj + 2] = cur[jj + 3] = 0.f;
+            }
+          }
         }
+      } else if (live) {
+#pragma unroll
+        for (int jj = 0; jj < HC; ++jj)
+          cur[jj] = j0 + jj < NP ? __uint_as_float(yr[jj]) + __uint_as_float(xr[jj]) : 0.f;
       }
     }
     normalise_and_store();
   }
+  if (MODE == CHAIN_GROUP && tid == 0) {
+    // every copy issued must have landed before the block may exit
+    for (int f = consumed + 1; f <= issued; ++f)
+      if (!mbar_wait(&ms->full[(f - 1) % RING], ((f - 1) / RING) & 1)) atomicOr(a.err, ERR_TIMEOUT);
+  }
   if (bad) atomicOr(a.err, ERR_FB_ZERO);
-  // common scale for the chunk: P_c = (scale of its largest row) * (rows
-  // scaled to it); the row scales sit where the frame maxima were summed
-  float* rm = reinterpret_cast<float*>(rhod);
-  int* re = reinterpret_cast<int*>(rm + 128);
-  rm[r] = (live && !zero_row) ? sc.m : 0.f;
-  re[r] = sc.e;
+
+  // common scale: the rows of a chunk (group) relative to its largest row
+  if (half == 0) ms->pe[r] = (live && !zero_row) ? ex_row : INT_MIN;
   __syncthreads();
-  if (q < Cfg::RCH && c < a.C && i < NP) {
-    // best < 0 only if every row of the chunk vanished (flagged by the scan)
-    const int best = scale_argmax(rm + q * NP, re + q * NP, N);
-    const float g = (live && best >= 0 && rm[r] > 0.f)
-                        ? ldexpf(rm[r] / rm[q * NP + best], re[r] - re[q * NP + best])
-                        : 0.f;
-    const size_t base = ((size_t)s * a.C + c) * NP * NP;
-    float* Pg = a.P + base;
-    float* PTg = a.PT + base;
+  const int nq = MODE == CHAIN_CHUNK ? Cfg::RCH : 1;
+  if (tid < nq) {
+    int b = INT_MIN;
+    for (int u = 0; u < N; ++u) b = max(b, ms->pe[tid * NP + u]);
+    ms->best[tid] = b;
+  }
+  __syncthreads();
+  const bool owner = MODE == CHAIN_CHUNK ? (q < Cfg::RCH && c < a.C && i < NP) : i < NP;
+  if (owner) {
+    // best == INT_MIN only if every row vanished (flagged by the scan)
+    const int best = ms->best[MODE == CHAIN_CHUNK ? q : 0];
+    const bool nz = live && !zero_row && best != INT_MIN;
+    const float g = nz ? ldexpf(1.f, ex_row - best) : 0.f;
+    const size_t base = (MODE == CHAIN_CHUNK ? cb + c : ((size_t)s * a.NG + blockIdx.x)) * NP * NP;
+    float* Pg = (MODE == CHAIN_CHUNK ? a.P : a.Q) + base;
+    float* PTg = (MODE == CHAIN_CHUNK ? a.PT : a.QT) + base;
+    float v[HC];
 #pragma unroll
-    for (int j = 0; j < NP; ++j) {
-      const float v = live ? cur[j] * g : 0.f;
-      Pg[i * NP + j] = v;
-      PTg[j * NP + i] = v;
+    for (int jj = 0; jj < HC; ++jj) v[jj] = nz ? cur[jj] * g : 0.f;
+#pragma unroll
+    for (int jj = 0; jj < HC; jj += 4)
+      if (j0 + jj < NP)
+        *reinterpret_cast<float4*>(Pg + (size_t)i * NP + j0 + jj) =
+            make_float4(v[jj], v[jj + 1], v[jj + 2], v[jj + 3]);
+#pragma unroll
+    for (int jj = 0; jj < HC; ++jj)
+      if (j0 + jj < NP) PTg[(size_t)(j0 + jj) * NP + i] = v[jj];
+    if (MODE == CHAIN_CHUNK && a.Pimg) {
+      // the chunk matrix as the group pass's B operand: B[j][k = i] = P[i][j]
+      uint8_t* img = a.Pimg + (cb + c) * Cfg::IMG_BYTES;
+#pragma unroll
+      for (int jj = 0; jj < HC; ++jj) {
+        const uint32_t off = sw128_off(j0 + jj, i, NOUT * 128);
+        const float h = tf32_hi(v[jj]);
+        *reinterpret_cast<float*>(img + off) = h;
+        *reinterpret_cast<float*>(img + Cfg::B_BYTES + off) = tf32_hi(v[jj] - h);
+      }
     }
-    if (i == 0)
-      a.Plog[(size_t)s * a.C + c] =
-          msum[q] + (best >= 0 ? (double)re[q * NP + best] * LN2 + log((double)rm[q * NP + best])
-                               : 0.0);
+    if (i == 0 && half == 0) {
+      const double lb = best != INT_MIN ? (double)best * LN2 : 0.0;
+      if (MODE == CHAIN_CHUNK)
+        a.Plog[cb + c] = ms->msum[q] + lb;
+      else
+        a.Qlog[(size_t)s * a.NG + blockIdx.x] = ms->msum[0] + lb;
+    }
   }
   tc_fence_before();
   __syncthreads();
@@ -1036,10 +1199,11 @@ __global__ void __launch_bounds__(R_CHUNKS_MAX * 64) k_fb_replay(FBArgs a) {
 
 // ------------------------------------------------------------------ launch
 template <int NP>
-static size_t smem_products(int L) {
-  using Cfg = ProdCfg<NP>;
-  return 1024 + Cfg::SMEM_FIXED + (size_t)Cfg::RCH * L * NP * sizeof(float) +
-         128 * sizeof(double) + Cfg::RCH * sizeof(double) + 256 * sizeof(float) + 64;
+static size_t smem_chain(int mode, int L) {
+  using Cfg = ChainCfg<NP>;
+  const size_t bb = mode == CHAIN_CHUNK ? Cfg::IMG_BYTES : Cfg::RING * Cfg::IMG_BYTES;
+  const size_t ee = mode == CHAIN_CHUNK ? (size_t)Cfg::RCH * L * NP * sizeof(float) : 0;
+  return 1024 + 2 * (size_t)Cfg::ROWS_BYTES + bb + ee + sizeof(ChainMisc);
 }
 template <int NP>
 static size_t smem_products_simt(int L) {
@@ -1065,8 +1229,13 @@ template <int NP>
 static cudaError_t launch_np(const FBArgs& a, cudaStream_t st) {
   static cudaError_t attr = cudaErrorNotReady;
   if (attr == cudaErrorNotReady) {
-    attr = cudaFuncSetAttribute(k_fb_products<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem_products<NP>(FB_MAX_L));
+    attr = cudaFuncSetAttribute(k_fb_chain<NP, CHAIN_CHUNK>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_chain<NP>(CHAIN_CHUNK, FB_MAX_L));
+    if (attr == cudaSuccess)
+      attr = cudaFuncSetAttribute(k_fb_chain<NP, CHAIN_GROUP>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem_chain<NP>(CHAIN_GROUP, 0));
     if (attr == cudaSuccess)
       attr = cudaFuncSetAttribute(k_fb_scan<NP, MODE_CHAINS>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1088,18 +1257,24 @@ static cudaError_t launch_np(const FBArgs& a, cudaStream_t st) {
                                   (int)smem_products_simt<NP>(FB_MAX_L));
   }
   if (attr != cudaSuccess) return attr;
-  using Cfg = ProdCfg<NP>;
+  using Cfg = ChainCfg<NP>;
   const int rc = replay_chunks(NP, a.L);
-  if (a.products == FB_PRODUCTS_TC)
-    k_fb_products<NP><<<dim3((a.C + Cfg::RCH - 1) / Cfg::RCH, a.S), 128,
-                        smem_products<NP>(a.L), st>>>(a);
-  else
-    k_fb_products_simt<NP><<<dim3((a.C + Cfg::RCH - 1) / Cfg::RCH, a.S), 128,
-                             smem_products_simt<NP>(a.L), st>>>(a);
+  const bool tc = a.products == FB_PRODUCTS_TC;
+  const dim3 pgrid((a.C + Cfg::RCH - 1) / Cfg::RCH, a.S);
+  if (tc) {
+    FBArgs p = a;   // the chunk pass writes the group pass's operand images
+    if (a.G < 2) p.Pimg = nullptr;
+    k_fb_chain<NP, CHAIN_CHUNK><<<pgrid, 256, smem_chain<NP>(CHAIN_CHUNK, a.L), st>>>(p);
+  } else {
+    k_fb_products_simt<NP><<<pgrid, 128, smem_products_simt<NP>(a.L), st>>>(a);
+  }
   if (a.G >= 2) {
     // group products, the scan across groups (the chain scan over the group
     // arrays), then each group's chunk boundaries
-    k_fb_group_products<NP><<<dim3(a.NG, a.S), NP * 16, smem_group<NP>(), st>>>(a);
+    if (tc)
+      k_fb_chain<NP, CHAIN_GROUP><<<dim3(a.NG, a.S), 256, smem_chain<NP>(CHAIN_GROUP, 0), st>>>(a);
+    else
+      k_fb_group_products<NP><<<dim3(a.NG, a.S), NP * 16, smem_group<NP>(), st>>>(a);
     FBArgs b = a;
     b.C = a.NG;
     b.chain_c0 = a.chain_g0;
@@ -1140,7 +1315,13 @@ size_t fb_scratch_bytes(int S, int N, int C, int NG) {
   b += al((size_t)S * NG * N * sizeof(float));             // gfwd
   b += al((size_t)S * NG * N * sizeof(float));             // gbwd
   b += al((size_t)S * NG * sizeof(float));                 // glam
+  if (NG > 0) b += al((size_t)S * C * fb_image_bytes(N));  // chunk operand images
   return b;
+}
+
+size_t fb_image_bytes(int N) {
+  const int NP = pad8(N), katoms = (NP + 31) / 32, nout = (NP + 15) & ~15;
+  return 2 * (size_t)katoms * nout * 128;
 }
 
 void fb_carve_scratch(FBArgs& a, void* base) {
@@ -1163,6 +1344,7 @@ void fb_carve_scratch(FBArgs& a, void* base) {
   a.gfwd = reinterpret_cast<float*>(take(S * NG * N * sizeof(float)));
   a.gbwd = reinterpret_cast<float*>(take(S * NG * N * sizeof(float)));
   a.glam = reinterpret_cast<float*>(take(S * NG * sizeof(float)));
+  a.Pimg = NG > 0 ? reinterpret_cast<uint8_t*>(take(S * C * fb_image_bytes((int)N))) : nullptr;
 }
 
 int fb_default_group(int C) {

@@ -35,10 +35,12 @@ struct WeightsArgs {
   void* wop_hi;         // format-specific operand copies (may be null)
   void* wop_lo;
   float* phi;           // S x T x N (without the -gamma K psi(alpha_t0) constant)
-  double* fterm;        // null, or T x 2: (sum_k alpha_tk, sum_k g(alpha_tk)) for the bound
+  double* fterm;        // null, or T x weights_units(S, N) x 2: per unit of the frame,
+                        // (sum_k alpha_tk, sum_k g(alpha_tk)) for the bound
   unsigned* err;
 };
 void launch_weights(const WeightsArgs& a, int fmt, cudaStream_t st);
+int weights_units(int S, int N);   // units (of 16 blocks) per frame of the weights kernel
 void launch_element_table(int M, int Mp, int K, int N, int T, int2* ktab, cudaStream_t st);
 
 // Fill buf[t*ld + k] = (k < M) ? value : 0 for t < T, k < ld.
@@ -116,11 +118,13 @@ struct FBArgs {
   float* gfwd;          // S x NG x N        forward vectors at group ends
   float* gbwd;          // S x NG x N        backward vectors at group ends
   float* glam;          // S x NG            group scan normalisers
+  uint8_t* Pimg;        // S x C chunk matrices as split tf32 operand images (groups only)
   unsigned* err;
 };
 // chunks of L frames needed by chains of the given lengths
 int fb_chunk_count(const int* chain_len, int nchains, int L);
 size_t fb_scratch_bytes(int S, int N, int C, int NG);
+size_t fb_image_bytes(int N);   // bytes of one chunk's operand image
 void fb_carve_scratch(FBArgs& a, void* base);   // regions for a.C chunks and a.NG groups
 int fb_default_chunk(int N, int T);
 // group size for chains of about C chunks (0: no groups)
@@ -138,7 +142,8 @@ struct BoundArgs {
   const float* alpha;      // T x Mp
   const double* v;         // T
   const double* bpart; int nbpart;
-  const double* fterm;     // null, or T x 2 per-frame sums from the weights kernel
+  const double* fterm;     // null, or T x funits x 2 per-unit sums from the weights kernel
+  int funits;
   const double* logZ;      // S x njobs
   double* frame_terms;     // T
   double* out;             // njobs + 1: per-job bounds, then their sum

@@ -30,7 +30,7 @@ SEP_MEAN, SEP_EXPECTATION = 0, 1
 STAGES = {"weights": 0, "gemm1": 1, "gemm2": 2, "fb": 3, "bound": 4, "init": 5}
 QUERIES = {"tensor_cores": 0, "fb_chunk": 1, "sweeps_done": 2, "device_bytes": 3,
            "frame_capacity": 4, "max_jobs": 5, "fb_group": 6}
-OPTIONS = {"fb_chunk": 0, "fb_products": 1, "graphs": 2, "fb_group": 3}
+OPTIONS = {"fb_chunk": 0, "fb_products": 1, "graphs": 2, "fb_group": 3, "profile_stride": 4}
 FB_PRODUCTS = {"simt": 0, "tc": 1}
 PRECISIONS = {"fp32": FP32, "bf16": BF16, "fp32_simt": FP32_SIMT}
 
@@ -240,7 +240,9 @@ class VIContext:
         return out
 
     def set_option(self, key: str, value):
-        """fb_chunk: frames per chunk (1..128); fb_products: "simt" or "tc"."""
+        """fb_chunk: frames per chunk (1..128); fb_products: "simt" or "tc";
+        fb_group: chunks per group (-1 automatic, 0 none); graphs: 0/1;
+        profile_stride: time the stages of every k-th sweep of a run."""
         if key == "fb_products":
             value = FB_PRODUCTS[value]
         _check(_lib.nfhmm_set_option(self._h, OPTIONS[key], int(value)), "nfhmm_set_option")

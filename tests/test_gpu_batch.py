@@ -269,3 +269,46 @@ def test_profiling_through_graphs_counts_every_launch(nf):
         assert inv_g == inv_d and l_g == l_d, st
         assert ms_g > 0 and ms_d > 0, st
     assert np.array_equal(res[0][1], res[1][1])
+
+
+def test_graphs_dropped_when_scratch_is_reallocated(nf):
+    """A chunk length that needs more forward-backward scratch reallocates it;
+    sweeps captured before then must not be replayed afterwards.  Going back
+    to the first geometry (the same launch configuration as the first graphs)
+    must give what launching one by one gives."""
+    p = synth.make_problem(seed=9, **synth.SMALL)
+    f = p.as_f32()
+    out = []
+    for graphs in (1, 0):
+        with nf.VIContext(f["V"], f["W"], f["A"], f["pi"], p.S, p.N, p.K) as ctx:
+            ctx.set_option("graphs", graphs)
+            L0 = ctx.query("fb_chunk")
+            ctx.sweep(4)
+            ctx.set_option("fb_chunk", 2)          # more chunks: new scratch
+            ctx.sweep(3)
+            ctx.set_option("fb_chunk", L0)
+            out.append((ctx.sweep(4, bound=True), ctx.posteriors()))
+    assert out[0][0] == out[1][0]
+    assert np.array_equal(out[0][1], out[1][1])
+
+
+@pytest.mark.parametrize("stride", [2, 3])
+def test_profile_stride_times_every_kth_sweep(nf, stride):
+    """With a profiling stride k, the stages of sweeps 0, k, 2k, ... of each
+    run are timed, every launch is still counted, and results do not change."""
+    p = synth.make_problem(seed=6, **synth.SMALL)
+    f = p.as_f32()
+    res = []
+    for k in (1, stride):
+        with nf.VIContext(f["V"], f["W"], f["A"], f["pi"], p.S, p.N, p.K) as ctx:
+            ctx.set_option("profile_stride", k)
+            ctx.profile_enable(True)
+            for _ in range(3):
+                ctx.sweep(7, bound=True)
+            prof = {st: ctx.profile_read(st) for st in ("weights", "fb")}
+            res.append((prof, ctx.posteriors()))
+    for st in ("weights", "fb"):
+        assert res[0][0][st][1] == 3 * 7
+        assert res[1][0][st][1] == 3 * len(range(0, 7, stride))
+        assert res[0][0][st][2] == res[1][0][st][2]
+    assert np.array_equal(res[0][1], res[1][1])
