@@ -159,6 +159,12 @@ static inline size_t mat_floats(int N) { return (size_t)pad8(N) * pad8(N); }
 //   CHAIN_GROUP: the rows of one group of chunks; the factors are its chunk
 //                matrices, whose split operand images the chunk pass wrote,
 //                brought in by bulk copies a few steps ahead.
+// The B operand holds the factor's tf32 hi and lo parts stacked along N
+// (rows [0, NOUT) and [NOUT, 2 NOUT) of each swizzle atom), so one MMA of
+// N = 2 NOUT gives rows_hi*B_hi and rows_hi*B_lo, and a second (N = NOUT)
+// adds rows_lo*B_hi to the cross terms: two MMAs per K step instead of three
+// (the issue of tcgen05.mma by one thread, not the tensor core, bounds a
+// step of these small tiles).
 // Eight warps: warp w reads TMEM lanes 32(w%4).. (one row per thread) and
 // half w/4 of the columns; the two halves of a row exchange their maxima
 // through shared memory (a 64-thread named barrier).  Rows are rescaled by
@@ -173,17 +179,16 @@ struct ChainCfg {
   static constexpr int KSTEPS = NP / 8;             // tf32 MMA K = 8
   static constexpr int KATOMS = (NP + 31) / 32;     // 128-byte swizzle atoms along K
   static constexpr int ROWS_BYTES = KATOMS * 128 * 128;
-  static constexpr int B_BYTES = KATOMS * NOUT * 128;
-  static constexpr int IMG_BYTES = 2 * B_BYTES;     // tf32 hi and lo copies of one B operand
+  static constexpr int BATOM = 2 * NOUT * 128;      // one swizzle atom of B: hi rows, lo rows
+  static constexpr int IMG_BYTES = KATOMS * BATOM;  // the stacked B operand of one factor
   static constexpr int RING = 4;                    // group pass: chunk images in flight
   static constexpr int TMEM_COLS = 2 * NOUT <= 32 ? 32 : 2 * NOUT <= 64 ? 64 : 128;
 };
 struct ChainMisc {
   double msum[16];       // chunk pass: summed frame maxima per chunk; group pass: [0] = chunk logs
-  double part[8];        // per-warp partial sums
   float pmax[2][128];    // row maxima of the two column halves
-  int pe[128];           // row exponents for the common scale
   int best[16];          // exponent of the largest row per chunk
+  int clen[16];          // chunk pass: frames of each chunk of the tile
   uint64_t mma_bar;
   uint64_t full[ChainCfg<8>::RING];
   uint32_t tslot;
@@ -221,9 +226,13 @@ __global__ void __launch_bounds__(256, MODE == CHAIN_CHUNK ? 2 : 1) k_fb_chain(F
   uint8_t* rows_lo = rows_hi + Cfg::ROWS_BYTES;
   uint8_t* bbuf = rows_lo + Cfg::ROWS_BYTES;   // chunk pass: A split; group pass: image ring
   constexpr int BBUF = MODE == CHAIN_CHUNK ? Cfg::IMG_BYTES : RING * Cfg::IMG_BYTES;
-  float* e = reinterpret_cast<float*>(bbuf + BBUF);   // chunk pass: RCH x L x NP emissions
+  // chunk pass: RCH x L x NP emissions, RCH x L frame maxima, A (N x N)
+  float* e = reinterpret_cast<float*>(bbuf + BBUF);
   const int ne = MODE == CHAIN_CHUNK ? Cfg::RCH * a.L * NP : 0;
-  ChainMisc* ms = reinterpret_cast<ChainMisc*>(e + ne);
+  float* rmax = e + ne;
+  float* As = rmax + (MODE == CHAIN_CHUNK ? ((Cfg::RCH * a.L + 1) & ~1) : 0);
+  const int na = MODE == CHAIN_CHUNK ? ((a.N * a.N + 1) & ~1) : 0;
+  ChainMisc* ms = reinterpret_cast<ChainMisc*>(As + na);
 
   const int N = a.N, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int quarter = warp & 3, half = warp >> 2;
@@ -261,13 +270,15 @@ __global__ void __launch_bounds__(256, MODE == CHAIN_CHUNK ? 2 : 1) k_fb_chain(F
       for (int u = 0; u < RING; ++u) mbar_init(&ms->full[u], 1);
     fence_barrier_init();
   }
+  if (tid < 16) ms->best[tid] = INT_MIN;
   if (warp == 0) {
     tmem_alloc(&ms->tslot, Cfg::TMEM_COLS);
     tmem_relinquish();
   }
   const float* Ag = a.A + (size_t)s * N * N;
   if (MODE == CHAIN_CHUNK) {
-    // emissions of the tile's chunks (asynchronous gathers while B is formed)
+    // emissions of the tile's chunks and A, by asynchronous gathers
+    for (int u = tid; u < N * N; u += 256) cp_async4(As + u, Ag + u);
     for (int qq = 0; qq < Cfg::RCH; ++qq) {
       const int cc = cbase + qq;
       if (cc >= a.C) break;
@@ -280,56 +291,54 @@ __global__ void __launch_bounds__(256, MODE == CHAIN_CHUNK ? 2 : 1) k_fb_chain(F
       }
     }
     cp_async_commit();
-    // B operand: B[j][k] = A[k][j] (zero outside N x N), split into tf32 hi/lo
-    constexpr int BW = NOUT * Cfg::KATOMS * 32;
-    constexpr int BPT = (BW + 255) / 256;
-    float bv[BPT];
-#pragma unroll
-    for (int u = 0; u < BPT; ++u) {
-      const int idx = tid + 256 * u;
-      const int j = idx / (Cfg::KATOMS * 32), k = idx - j * (Cfg::KATOMS * 32);
-      bv[u] = (idx < BW && j < N && k < N) ? __ldg(Ag + k * N + j) : 0.f;
-    }
-#pragma unroll
-    for (int u = 0; u < BPT; ++u) {
-      const int idx = tid + 256 * u;
-      if (idx < BW) {
-        const int j = idx / (Cfg::KATOMS * 32), k = idx - j * (Cfg::KATOMS * 32);
-        const float h = tf32_hi(bv[u]);
-        const uint32_t off = sw128_off(j, k, NOUT * 128);
-        *reinterpret_cast<float*>(bbuf + off) = h;
-        *reinterpret_cast<float*>(bbuf + Cfg::B_BYTES + off) = tf32_hi(bv[u] - h);
-      }
-    }
+    if (tid < Cfg::RCH) ms->clen[tid] = cbase + tid < a.C ? chunk_info(a, cbase + tid).len : 0;
     cp_async_wait<0>();
     __syncthreads();
-    // e_t = exp(phi_t - max phi_t), the maxima summed per chunk
-    for (int qq = 0; qq < Cfg::RCH; ++qq) {
-      const int cc = cbase + qq;
-      if (cc >= a.C) break;
-      const int ln = chunk_info(a, cc).len;
-      float* eq = e + qq * a.L * NP;
-      double sm = 0.0;
-      for (int f = warp; f < ln; f += 8) {
-        float* row = eq + f * NP;
-        const float x0 = lane < N ? row[lane] : -INFINITY;
-        const float x1 = lane + 32 < N ? row[lane + 32] : -INFINITY;
-        const float m = warp_max(fmaxf(x0, x1));
-        __syncwarp();
-        if (lane < NP) row[lane] = lane < N ? expf(x0 - m) : 0.f;
-        if (lane + 32 < NP) row[lane + 32] = lane + 32 < N ? expf(x1 - m) : 0.f;
-        sm += (double)m;
+    // B operand: B[j][k] = A[k][j] (zero outside N x N), split into tf32 hi
+    // (rows j) and lo (rows NOUT + j) of each swizzle atom; only the K < NP
+    // columns the MMAs read
+    for (int idx = tid; idx < NOUT * NP; idx += 256) {
+      const int j = idx / NP, k = idx - j * NP;
+      const float v = (j < N && k < N) ? As[k * N + j] : 0.f;
+      const float h = tf32_hi(v);
+      *reinterpret_cast<float*>(bbuf + sw128_off(j, k, Cfg::BATOM)) = h;
+      *reinterpret_cast<float*>(bbuf + sw128_off(j + NOUT, k, Cfg::BATOM)) = tf32_hi(v - h);
+    }
+    // e_t = exp(phi_t - max phi_t) for every frame of the tile: four
+    // threads per frame (a quarter of the states each), the maxima kept per
+    // frame and summed per chunk in double by one warp (fixed order)
+    constexpr int QS = NP / 4;   // states per thread (NP is a multiple of 8)
+    for (int base = warp * 8; base < Cfg::RCH * a.L; base += 64) {   // warp-uniform trips
+      const int rho = base + (lane >> 2);
+      const int qq = rho / a.L, f = rho - qq * a.L;
+      // uniform across the row's 4 threads; every lane takes part in the shuffles
+      const bool ok_row = rho < Cfg::RCH * a.L && f < ms->clen[qq];
+      float* row = e + (ok_row ? rho : 0) * NP + (tid & 3) * QS;
+      const int n0 = (tid & 3) * QS;
+      float x[QS];
+      float m = -INFINITY;
+#pragma unroll
+      for (int u = 0; u < QS; ++u) {
+        x[u] = (ok_row && n0 + u < N) ? row[u] : -INFINITY;
+        m = fmaxf(m, x[u]);
       }
-      if (lane == 0) ms->part[warp] = sm;
-      __syncthreads();
-      if (tid == 0) {
-        double t = 0.0;
-        for (int w = 0; w < 8; ++w) t += ms->part[w];
-        ms->msum[qq] = t;
+      m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+      m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
+      if (ok_row) {
+#pragma unroll
+        for (int u = 0; u < QS; ++u) row[u] = n0 + u < N ? expf(x[u] - m) : 0.f;
+        if ((tid & 3) == 0) rmax[rho] = m;
       }
-      __syncthreads();
+    }
+    __syncthreads();
+    for (int qq = warp; qq < Cfg::RCH; qq += 8) {
+      double t = 0.0;
+      for (int f = lane; f < ms->clen[qq]; f += 32) t += (double)rmax[qq * a.L + f];
+      t = warp_sum_d(t);
+      if (lane == 0) ms->msum[qq] = t;
     }
   } else {
+    griddep_wait();    // the chunk pass's matrices, images and scales
     __syncthreads();   // barriers initialised
     if (tid == 0) {
       for (int u = 0; u < RING && u < nst; ++u) {
@@ -360,7 +369,7 @@ __global__ void __launch_bounds__(256, MODE == CHAIN_CHUNK ? 2 : 1) k_fb_chain(F
     for (int jj = 0; jj < HC; ++jj) {
       const int j = j0 + jj;
       float v = 0.f;
-      if (live && j < N) v = first ? (j == i ? eq[j] : 0.f) : Ag[i * N + j] * eq[j];
+      if (live && j < N) v = first ? (j == i ? eq[j] : 0.f) : As[i * N + j] * eq[j];
       cur[jj] = v;
     }
   } else {
@@ -375,9 +384,10 @@ __global__ void __launch_bounds__(256, MODE == CHAIN_CHUNK ? 2 : 1) k_fb_chain(F
   // and write this thread's columns, split into tf32 hi/lo, into the
   // swizzled operand tile
   auto normalise_and_store = [&]() {
-    float m = 0.f;
+    float m4[4] = {0.f, 0.f, 0.f, 0.f};   // four independent chains
 #pragma unroll
-    for (int jj = 0; jj < HC; ++jj) m = fmaxf(m, cur[jj]);
+    for (int jj = 0; jj < HC; ++jj) m4[jj & 3] = fmaxf(m4[jj & 3], cur[jj]);
+    float m = fmaxf(fmaxf(m4[0], m4[1]), fmaxf(m4[2], m4[3]));
     ms->pmax[half][r] = m;
     named_bar(1 + quarter, 64);
     m = fmaxf(m, ms->pmax[half ^ 1][r]);
@@ -391,7 +401,10 @@ __global__ void __launch_bounds__(256, MODE == CHAIN_CHUNK ? 2 : 1) k_fb_chain(F
         zero_row = true;
       } else {
         int ex;
-        frexpf(m, &ex);
+        if (m >= 0x1p-126f)
+          ex = ((__float_as_int(m) >> 23) & 0xff) - 126;   // m = f 2^ex, f in [0.5, 1)
+        else
+          frexpf(m, &ex);
         const int k = -ex > 126 ? 126 : -ex;
         const float g = pow2f(k);
 #pragma unroll
@@ -416,7 +429,8 @@ __global__ void __launch_bounds__(256, MODE == CHAIN_CHUNK ? 2 : 1) k_fb_chain(F
   };
   normalise_and_store();
 
-  constexpr uint32_t ID = idesc<KIND_TF32X3>(128, NOUT);
+  constexpr uint32_t ID2 = idesc<KIND_TF32X3>(128, 2 * NOUT);
+  constexpr uint32_t ID1 = idesc<KIND_TF32X3>(128, NOUT);
   const uint32_t rh = smem_u32(rows_hi), rl = smem_u32(rows_lo);
   const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)j0;
   bool ok = true;
@@ -437,7 +451,6 @@ __global__ void __launch_bounds__(256, MODE == CHAIN_CHUNK ? 2 : 1) k_fb_chain(F
         }
       }
     }
-    const uint32_t bl = bh + Cfg::B_BYTES;
     fence_proxy_async_smem();   // the operand rows written above, to the tensor core
     tc_fence_before();
     // every row written; and the decision to stop is the same in every thread
@@ -450,10 +463,10 @@ __global__ void __launch_bounds__(256, MODE == CHAIN_CHUNK ? 2 : 1) k_fb_chain(F
 #pragma unroll
       for (int kk = 0; kk < Cfg::KSTEPS; ++kk) {
         const uint32_t ao = (kk >> 2) * (128 * 128) + (kk & 3) * 32;
-        const uint32_t bo = (kk >> 2) * (NOUT * 128) + (kk & 3) * 32;
-        mma<KIND_TF32X3>(tmem, sdesc(rh + ao), sdesc(bh + bo), ID, kk > 0 ? 1u : 0u);
-        mma<KIND_TF32X3>(tmem + NOUT, sdesc(rh + ao), sdesc(bl + bo), ID, kk > 0 ? 1u : 0u);
-        mma<KIND_TF32X3>(tmem + NOUT, sdesc(rl + ao), sdesc(bh + bo), ID, 1u);
+        const uint32_t bo = (kk >> 2) * Cfg::BATOM + (kk & 3) * 32;
+        // [main | cross] (+)= rows_hi [B_hi | B_lo];  cross += rows_lo B_hi
+        mma<KIND_TF32X3>(tmem, sdesc(rh + ao), sdesc(bh + bo), ID2, kk > 0 ? 1u : 0u);
+        mma<KIND_TF32X3>(tmem + NOUT, sdesc(rl + ao), sdesc(bh + bo), ID1, 1u);
       }
       mma_commit(&ms->mma_bar);
     }
@@ -472,37 +485,41 @@ __global__ void __launch_bounds__(256, MODE == CHAIN_CHUNK ? 2 : 1) k_fb_chain(F
       issued = f + RING;
     }
     if (done) {
-      uint32_t yr[HC], xr[HC];
+      // 8 columns of both accumulators at a time (bounded register use)
 #pragma unroll
       for (int cc = 0; cc < HC / 8; ++cc) {
-        tmem_ld8_nw(taddr + 8 * cc, yr + 8 * cc);
-        tmem_ld8_nw(taddr + NOUT + 8 * cc, xr + 8 * cc);
-      }
-      tmem_wait_ld();
-      if (MODE == CHAIN_CHUNK) {
-        if (live && f < len) {
-          const float* ef = eq + f * NP + j0;
+        uint32_t yr[8], xr[8];
+        tmem_ld8_nw(taddr + 8 * cc, yr);
+        tmem_ld8_nw(taddr + NOUT + 8 * cc, xr);
+        tmem_wait_ld();
+        if (MODE == CHAIN_CHUNK) {
+          if (live && f < len) {
+            const float* ef = eq + f * NP + j0 + 8 * cc;
 #pragma unroll
-          for (int jj = 0; jj < HC; jj += 4) {
-            if (j0 + jj < NP) {
-              const float4 e4 = *reinterpret_cast<const float4*>(ef + jj);
-              const float ev[4] = {e4.x, e4.y, e4.z, e4.w};
+            for (int h4 = 0; h4 < 8; h4 += 4) {
+              const int jj = 8 * cc + h4;
+              if (j0 + jj < NP) {
+                const float4 e4 = *reinterpret_cast<const float4*>(ef + h4);
+                const float ev[4] = {e4.x, e4.y, e4.z, e4.w};
 #pragma unroll
-              for (int u = 0; u < 4; ++u)
-                cur[jj + u] = (__uint_as_float(yr[jj + u]) + __uint_as_float(xr[jj + u])) * ev[u];
-            } else {
-              cur[jj] = cur[jj + 1] = cur[jj + 2] = cur[jj + 3] = 0.f;
+                for (int u = 0; u < 4; ++u)
+                  cur[jj + u] = (__uint_as_float(yr[h4 + u]) + __uint_as_float(xr[h4 + u])) * ev[u];
+              } else {
+                cur[jj] = cur[jj + 1] = cur[jj + 2] = cur[jj + 3] = 0.f;
+              }
             }
           }
-        }
-      } else if (live) {
+        } else if (live) {
 #pragma unroll
-        for (int jj = 0; jj < HC; ++jj)
-          cur[jj] = j0 + jj < NP ? __uint_as_float(yr[jj]) + __uint_as_float(xr[jj]) : 0.f;
+          for (int u = 0; u < 8; ++u)
+            cur[8 * cc + u] =
+                j0 + 8 * cc + u < NP ? __uint_as_float(yr[u]) + __uint_as_float(xr[u]) : 0.f;
+        }
       }
     }
     normalise_and_store();
   }
+  griddep_launch_dependents();   // the next pass may start its launch and setup
   if (MODE == CHAIN_GROUP && tid == 0) {
     // every copy issued must have landed before the block may exit
     for (int f = consumed + 1; f <= issued; ++f)
@@ -511,14 +528,7 @@ __global__ void __launch_bounds__(256, MODE == CHAIN_CHUNK ? 2 : 1) k_fb_chain(F
   if (bad) atomicOr(a.err, ERR_FB_ZERO);
 
   // common scale: the rows of a chunk (group) relative to its largest row
-  if (half == 0) ms->pe[r] = (live && !zero_row) ? ex_row : INT_MIN;
-  __syncthreads();
-  const int nq = MODE == CHAIN_CHUNK ? Cfg::RCH : 1;
-  if (tid < nq) {
-    int b = INT_MIN;
-    for (int u = 0; u < N; ++u) b = max(b, ms->pe[tid * NP + u]);
-    ms->best[tid] = b;
-  }
+  if (half == 0 && live && !zero_row) atomicMax(&ms->best[MODE == CHAIN_CHUNK ? q : 0], ex_row);
   __syncthreads();
   const bool owner = MODE == CHAIN_CHUNK ? (q < Cfg::RCH && c < a.C && i < NP) : i < NP;
   if (owner) {
@@ -545,10 +555,10 @@ __global__ void __launch_bounds__(256, MODE == CHAIN_CHUNK ? 2 : 1) k_fb_chain(F
       uint8_t* img = a.Pimg + (cb + c) * Cfg::IMG_BYTES;
 #pragma unroll
       for (int jj = 0; jj < HC; ++jj) {
-        const uint32_t off = sw128_off(j0 + jj, i, NOUT * 128);
         const float h = tf32_hi(v[jj]);
-        *reinterpret_cast<float*>(img + off) = h;
-        *reinterpret_cast<float*>(img + Cfg::B_BYTES + off) = tf32_hi(v[jj] - h);
+        *reinterpret_cast<float*>(img + sw128_off(j0 + jj, i, Cfg::BATOM)) = h;
+        *reinterpret_cast<float*>(img + sw128_off(NOUT + j0 + jj, i, Cfg::BATOM)) =
+            tf32_hi(v[jj] - h);
       }
     }
     if (i == 0 && half == 0) {
@@ -746,6 +756,8 @@ __global__ void __launch_bounds__(32) k_fb_scan(FBArgs a) {
   const int N = a.N, C = a.C;
   const bool fwd = blockIdx.y == 0;
   const int lane = threadIdx.x;
+  griddep_wait();   // the matrices (and boundary vectors) of the previous pass
+  if (MODE == MODE_GROUP_REPLAY) griddep_launch_dependents();
   float* ring = sm;                      // RING x NP x LD
   float* v = ring + RING * NN;           // 64
   int s, chain = 0, c0, c1;
@@ -862,6 +874,7 @@ __global__ void __launch_bounds__(32) k_fb_scan(FBArgs a) {
     u0 = h0 ? ((y0[0] + y0[1]) + (y0[2] + y0[3])) * inv : 0.f;
     u1 = h1 ? ((y1[0] + y1[1]) + (y1[2] + y1[3])) * inv : 0.f;
   }
+  if (MODE == MODE_CHAINS) griddep_launch_dependents();
   if (nsteps > 0) {
     float lam = warp_sum(u0 + u1);
     if (!(lam > 0.f) || !isfinite(lam)) {
@@ -1097,6 +1110,7 @@ __global__ void __launch_bounds__(R_CHUNKS_MAX * 64) k_fb_replay(FBArgs a) {
     }
   }
   __syncthreads();
+  griddep_wait();   // the boundary vectors of the scan (the setup above needs none)
   const size_t base = (size_t)s * a.C;
   if (live) {
     float* vec = is_fwd ? av : bv;
@@ -1202,7 +1216,10 @@ template <int NP>
 static size_t smem_chain(int mode, int L) {
   using Cfg = ChainCfg<NP>;
   const size_t bb = mode == CHAIN_CHUNK ? Cfg::IMG_BYTES : Cfg::RING * Cfg::IMG_BYTES;
-  const size_t ee = mode == CHAIN_CHUNK ? (size_t)Cfg::RCH * L * NP * sizeof(float) : 0;
+  const size_t ee = mode == CHAIN_CHUNK
+                        ? ((size_t)Cfg::RCH * L * NP + ((Cfg::RCH * L + 1) & ~1) + NP * NP) *
+                              sizeof(float)
+                        : 0;
   return 1024 + 2 * (size_t)Cfg::ROWS_BYTES + bb + ee + sizeof(ChainMisc);
 }
 template <int NP>
@@ -1223,6 +1240,27 @@ static int replay_chunks(int NP, int L) {
   int rc = R_CHUNKS_MAX;
   while (rc > 1 && rc * smem_replay_chunk(NP, L) > SMEM_OPTIN) --rc;
   return rc;
+}
+
+// Launch a pass that consumes the previous pass's results as a programmatic
+// dependent of it: its blocks may be scheduled once every block of the
+// previous pass has signalled (griddepcontrol.launch_dependents), run their
+// independent setup, and wait (griddepcontrol.wait) before reading the
+// previous results.  On the legacy default stream it is an ordinary launch.
+static cudaError_t launch_dependent(void (*kernel)(FBArgs), dim3 grid, int block, size_t smem,
+                                   cudaStream_t st, const FBArgs& a) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  const bool legacy = st == nullptr || st == cudaStreamLegacy;
+  cfg.attrs = legacy ? nullptr : attr;
+  cfg.numAttrs = legacy ? 0 : 1;
+  return cudaLaunchKernelEx(&cfg, kernel, a);
 }
 
 template <int NP>
@@ -1260,6 +1298,7 @@ static cudaError_t launch_np(const FBArgs& a, cudaStream_t st) {
   using Cfg = ChainCfg<NP>;
   const int rc = replay_chunks(NP, a.L);
   const bool tc = a.products == FB_PRODUCTS_TC;
+  cudaError_t e = cudaSuccess;
   const dim3 pgrid((a.C + Cfg::RCH - 1) / Cfg::RCH, a.S);
   if (tc) {
     FBArgs p = a;   // the chunk pass writes the group pass's operand images
@@ -1272,7 +1311,8 @@ static cudaError_t launch_np(const FBArgs& a, cudaStream_t st) {
     // group products, the scan across groups (the chain scan over the group
     // arrays), then each group's chunk boundaries
     if (tc)
-      k_fb_chain<NP, CHAIN_GROUP><<<dim3(a.NG, a.S), 256, smem_chain<NP>(CHAIN_GROUP, 0), st>>>(a);
+      e = launch_dependent(k_fb_chain<NP, CHAIN_GROUP>, dim3(a.NG, a.S), 256,
+                           smem_chain<NP>(CHAIN_GROUP, 0), st, a);
     else
       k_fb_group_products<NP><<<dim3(a.NG, a.S), NP * 16, smem_group<NP>(), st>>>(a);
     FBArgs b = a;
@@ -1284,14 +1324,21 @@ static cudaError_t launch_np(const FBArgs& a, cudaStream_t st) {
     b.fwd = a.gfwd;
     b.bwd = a.gbwd;
     b.lam = a.glam;
-    k_fb_scan<NP, MODE_CHAINS><<<dim3(a.S * a.nchains, 2), 32, smem_scan<NP>(), st>>>(b);
-    k_fb_scan<NP, MODE_GROUP_REPLAY><<<dim3(a.S * a.NG, 2), 32, smem_scan<NP>(), st>>>(a);
+    if (e == cudaSuccess)
+      e = launch_dependent(k_fb_scan<NP, MODE_CHAINS>, dim3(a.S * a.nchains, 2), 32,
+                           smem_scan<NP>(), st, b);
+    if (e == cudaSuccess)
+      e = launch_dependent(k_fb_scan<NP, MODE_GROUP_REPLAY>, dim3(a.S * a.NG, 2), 32,
+                           smem_scan<NP>(), st, a);
   } else {
-    k_fb_scan<NP, MODE_CHAINS><<<dim3(a.S * a.nchains, 2), 32, smem_scan<NP>(), st>>>(a);
+    e = launch_dependent(k_fb_scan<NP, MODE_CHAINS>, dim3(a.S * a.nchains, 2), 32,
+                         smem_scan<NP>(), st, a);
   }
-  k_fb_replay<NP><<<dim3((a.C + rc - 1) / rc, a.S), rc * 64, rc * smem_replay_chunk(NP, a.L),
-                    st>>>(a);
-  return cudaGetLastError();
+  if (e == cudaSuccess)
+    e = launch_dependent(k_fb_replay<NP>, dim3((a.C + rc - 1) / rc, a.S), rc * 64,
+                         rc * smem_replay_chunk(NP, a.L), st, a);
+  const cudaError_t l = cudaGetLastError();
+  return e != cudaSuccess ? e : l;
 }
 
 int fb_chunk_count(const int* chain_len, int nchains, int L) {

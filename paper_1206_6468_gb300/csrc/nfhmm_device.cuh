@@ -123,6 +123,13 @@ __device__ __forceinline__ double bound_g_elem(float a) {
   return (double)h - (double)a;
 }
 
+// Programmatic dependent launch: wait for the grids this one depends on
+// (no-op without such a dependency); let dependent grids be scheduled.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
