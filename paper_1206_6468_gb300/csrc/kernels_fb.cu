@@ -75,7 +75,6 @@ struct ScaleAcc {
     m = frexpf(m * s, &ex);
     e += ex;
   }
-  __device__ __forceinline__ double log() const { return (double)e * 0.6931471805599453 + ::log((double)m); }
 };
 
 // 4-byte asynchronous copy (cp.async.ca): many in flight per thread, so a
@@ -752,7 +751,6 @@ __global__ void __launch_bounds__(32) k_fb_scan(FBArgs a) {
   constexpr int RING = ScanRing<NP>::R;
   constexpr int LD = NP + 4;
   constexpr int NN = NP * LD;
-  constexpr int CPL = (NP * NP / 4 + 31) / 32;   // 16-byte copies per lane per matrix
   const int N = a.N, C = a.C;
   const bool fwd = blockIdx.y == 0;
   const int lane = threadIdx.x;
@@ -782,6 +780,7 @@ __global__ void __launch_bounds__(32) k_fb_scan(FBArgs a) {
   const int nsteps = fwd ? c1 - c0 : c1 - c0 - 1;
   auto chunk_of = [&](int q) { return fwd ? c0 + q : c1 - 1 - q; };
   // this lane's 16-byte pieces of a matrix: source and padded destination offsets
+  constexpr int CPL = (NP * NP / 4 + 31) / 32;   // 16-byte copies per lane per matrix
   int soff[CPL], doff[CPL];
 #pragma unroll
   for (int m = 0; m < CPL; ++m) {
@@ -839,8 +838,8 @@ __global__ void __launch_bounds__(32) k_fb_scan(FBArgs a) {
     }
   };
   for (int q = 0; q < nsteps; ++q) {
+    __syncwarp();   // every lane is past step q - 1's reads of the slot refilled here
     prefetch(q + RING - 1);
-    __syncwarp();
     v[lane] = u0;
     v[lane + 32] = u1;
     cp_async_wait<RING - 1>();
@@ -1188,26 +1187,54 @@ __global__ void __launch_bounds__(R_CHUNKS_MAX * 64) k_fb_replay(FBArgs a) {
     }
   }
   __syncthreads();
-  if (live) {
+  // d-hat_t = a_t b_t / sum_n a_tn b_tn: the chunk's two warps take 16
+  // frames at a time, four threads per frame (a quarter of the states each);
+  // the stored vectors are only roughly normalised, so each is rescaled by
+  // its sum first (the scales cancel in d-hat but keep the products in range)
+  if (len > 0) {
+    constexpr int QS = NP / 4;
+    const int u = ((warp & 1) << 5) | lane;
+    const int n0 = (u & 3) * QS;
     float* dh = a.dhat + ((size_t)s * a.T + t0) * N;
     unsigned bad = 0;
-    for (int f = is_fwd ? 0 : 1; f < len; f += 2) {
-      // the stored vectors are only roughly normalised: rescale each first
-      const float a0 = h0 ? av[f * NP + lane] : 0.f, a1 = h1 ? av[f * NP + lane + 32] : 0.f;
-      const float b0 = h0 ? bv[f * NP + lane] : 0.f, b1 = h1 ? bv[f * NP + lane + 32] : 0.f;
-      const float fa = renorm_factor(warp_sum(a0 + a1)), fb = renorm_factor(warp_sum(b0 + b1));
-      const float d0 = (a0 * fa) * (b0 * fb);
-      const float d1 = (a1 * fa) * (b1 * fb);
-      float z = warp_sum(d0 + d1);
-      if (!(z > 0.f) || !isfinite(z)) {
-        bad = 1;
-        z = 1.f;
+    for (int f0 = 0; f0 < len; f0 += 16) {   // uniform in both warps of the chunk
+      const int f = f0 + (u >> 2);
+      const bool ok = f < len;
+      float av4[QS], bv4[QS];
+      float sa = 0.f, sb = 0.f;
+#pragma unroll
+      for (int k = 0; k < QS; ++k) {
+        const bool in = ok && n0 + k < N;
+        av4[k] = in ? av[f * NP + n0 + k] : 0.f;
+        bv4[k] = in ? bv[f * NP + n0 + k] : 0.f;
+        sa += av4[k];
+        sb += bv4[k];
       }
-      const float iz = 1.f / z;
-      if (h0) dh[(size_t)f * N + lane] = d0 * iz;
-      if (h1) dh[(size_t)f * N + lane + 32] = d1 * iz;
+      sa += __shfl_xor_sync(0xffffffffu, sa, 1);
+      sb += __shfl_xor_sync(0xffffffffu, sb, 1);
+      sa += __shfl_xor_sync(0xffffffffu, sa, 2);
+      sb += __shfl_xor_sync(0xffffffffu, sb, 2);
+      const float fa = renorm_factor(sa), fb = renorm_factor(sb);
+      float z = 0.f;
+#pragma unroll
+      for (int k = 0; k < QS; ++k) {
+        av4[k] = (av4[k] * fa) * (bv4[k] * fb);
+        z += av4[k];
+      }
+      z += __shfl_xor_sync(0xffffffffu, z, 1);
+      z += __shfl_xor_sync(0xffffffffu, z, 2);
+      if (ok) {
+        if (!(z > 0.f) || !isfinite(z)) {
+          bad = 1;
+          z = 1.f;
+        }
+        const float iz = 1.f / z;
+#pragma unroll
+        for (int k = 0; k < QS; ++k)
+          if (n0 + k < N) dh[(size_t)f * N + n0 + k] = av4[k] * iz;
+      }
     }
-    if (bad && lane == 0) atomicOr(a.err, ERR_FB_ZERO);
+    if (bad) atomicOr(a.err, ERR_FB_ZERO);
   }
 }
 
