@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(256) k_weights(WeightsArgs a) {
     } else {
       digamma_exp(alpha, psi, w);
     }
-    if (!isfinite(psi) || !isfinite(w)) bad |= ERR_NONFINITE;
+    if (!isfinite(psi + w)) bad |= ERR_NONFINITE;   // NaN or Inf in either
     a.alpha[row + k] = alpha;
     a.w32[row + k] = w;
     if (FMT == WF_TF32X2) {

@@ -3,13 +3,15 @@
 //   back-projection  R[t][k]    = sum_l Q[t][l] beta[k][l]   -> counts = w * R
 // Both are C[t][n] = sum_k A[t][k] B[n][k] with K contiguous in both operands.
 //
-// One CTA computes one 128 x BN output tile; the accumulator lives in TMEM.
-// Warp 0 streams K-blocks of A and B into a ring of shared-memory stages with
-// TMA (128-byte swizzle), warp 1 issues tcgen05.mma from one thread and frees
-// each stage with tcgen05.commit, warps 2-5 read the accumulator back with
-// tcgen05.ld and apply the epilogue.  Every mbarrier wait is bounded: a wait
-// that gives up sets ERR_TIMEOUT in the error word and the CTA winds down
-// (outstanding copies are awaited, TMEM is freed) instead of hanging.
+// A persistent CTA per SM computes a sequence of 128 x BN output tiles; the
+// accumulator lives in TMEM.  Warp 0 streams K-blocks of A and B into a ring
+// of shared-memory stages with TMA (128-byte swizzle), warp 1 issues
+// tcgen05.mma from one thread and frees each stage with tcgen05.commit, warps
+// 2-9 copy a finished tile's accumulator out of TMEM with tcgen05.ld, release
+// TMEM to the next tile's MMAs and apply the epilogue from registers.  Every
+// mbarrier wait is bounded: a wait that gives up sets ERR_TIMEOUT in the error
+// word and the CTA winds down (outstanding copies and MMAs are awaited, TMEM
+// is freed) instead of hanging.
 //
 // FP32 mode ("split TF32"): each operand x is stored as hi = tf32(x) and
 // lo = tf32(x - hi); each K-step issues hi*hi, hi*lo and lo*hi (~22
@@ -101,6 +103,11 @@ struct TcArgs {
 };
 
 // ------------------------------------------------------------------ kernel
+// Persistent: CTA b takes output tiles b, b + gridDim.x, ... (row-major over
+// (row tile, column tile), so the CTAs in flight share A row tiles in L2).
+// The stage ring runs on across tiles.  The epilogue warps copy a tile's
+// summed accumulator out of TMEM into registers and release TMEM at once, so
+// the MMA warp starts the next tile while they divide, take logs and store.
 template <int KIND, int BN, int EPI>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     k_tc_gemm(const __grid_constant__ Maps maps, const TcArgs p) {
@@ -112,15 +119,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * Cfg::STAGE_BYTES);
   uint64_t* empty = full + STAGES;
-  uint64_t* accum = empty + STAGES;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+  uint64_t* accum = empty + STAGES;        // MMA -> epilogue: a tile's accumulator is complete
+  uint64_t* tmem_free = accum + 1;         // epilogue -> MMA: it has been read out
+  uint64_t* drain = tmem_free + 1;         // the MMA thread's last commit (before TMEM is freed)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int col0 = blockIdx.x * BN, row0 = blockIdx.y * BM;
-  const int bitem = p.brows ? row0 / p.brows : 0;   // batch item of this row tile
-  const int bcol0 = col0 + bitem * p.bstride;         // its first B row
   const int nkb = (p.kdim + K::BK - 1) / K::BK;
+  const int ncol = (p.cols + BN - 1) / BN;
+  const int ntiles = ncol * ((p.rows + BM - 1) / BM);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -128,6 +136,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       mbar_init(&empty[s], 1);
     }
     mbar_init(accum, 1);
+    mbar_init(tmem_free, EPI_WARPS);
+    mbar_init(drain, 1);
     *abort_flag = 0;
     fence_barrier_init();
   }
@@ -146,188 +156,228 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     if (which == 1) return base + Cfg::A_BYTES;
     return base + K::NOPS * Cfg::A_BYTES + (which - 2) * Cfg::B_BYTES;
   };
+  auto give_up = [&]() {
+    *abort_flag = 1;
+    atomicOr(p.err, ERR_TIMEOUT);
+  };
 
   if (warp == 0) {
     // ---------------- TMA producer
     if (lane == 0) {
-      int issued = 0;
-      for (int kb = 0; kb < nkb && !*abort_flag; ++kb) {
-        const int s = kb % STAGES;
-        if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) - 1) & 1)) {
-          *abort_flag = 1;
-          atomicOr(p.err, ERR_TIMEOUT);
-          break;
+      long long it = 0;   // K-blocks issued over all of this CTA's tiles
+      for (int tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x) {
+        const int row0 = (tile / ncol) * BM, col0 = (tile % ncol) * BN;
+        const int bitem = p.brows ? row0 / p.brows : 0;   // batch item of this row tile
+        const int bcol0 = col0 + bitem * p.bstride;         // its first B row
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = (int)(it % STAGES);
+          if (it >= STAGES && !mbar_wait(&empty[s], (uint32_t)((it / STAGES) - 1) & 1)) {
+            give_up();
+            break;
+          }
+          mbar_expect_tx(&full[s], Cfg::STAGE_BYTES);
+          const int kx = kb * K::BK;
+          tma_load_2d(stage_ptr(s, 0), &maps.a_hi, &full[s], kx, row0);
+          tma_load_2d(stage_ptr(s, 2), &maps.b_hi, &full[s], kx, bcol0);
+          if (K::NOPS == 2) {
+            tma_load_2d(stage_ptr(s, 1), &maps.a_lo, &full[s], kx, row0);
+            tma_load_2d(stage_ptr(s, 3), &maps.b_lo, &full[s], kx, bcol0);
+          }
         }
-        mbar_expect_tx(&full[s], Cfg::STAGE_BYTES);
-        const int kx = kb * K::BK;
-        tma_load_2d(stage_ptr(s, 0), &maps.a_hi, &full[s], kx, row0);
-        tma_load_2d(stage_ptr(s, 2), &maps.b_hi, &full[s], kx, bcol0);
-        if (K::NOPS == 2) {
-          tma_load_2d(stage_ptr(s, 1), &maps.a_lo, &full[s], kx, row0);
-          tma_load_2d(stage_ptr(s, 3), &maps.b_lo, &full[s], kx, bcol0);
-        }
-        issued = kb + 1;
+        if (*abort_flag) break;
       }
-      // every copy issued must have landed before the CTA may exit
-      for (int kb = issued - STAGES > 0 ? issued - STAGES : 0; kb < issued; ++kb) {
-        if (!mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1)) atomicOr(p.err, ERR_TIMEOUT);
+      // every copy issued must have landed before the CTA may exit (the slot
+      // of each of the last STAGES K-blocks has no later use)
+      for (long long j = it - STAGES > 0 ? it - STAGES : 0; j < it; ++j) {
+        if (!mbar_wait(&full[j % STAGES], (uint32_t)(j / STAGES) & 1)) atomicOr(p.err, ERR_TIMEOUT);
       }
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer
     if (lane == 0) {
       constexpr uint32_t ID = idesc<KIND>(BM, BN);
-      for (int kb = 0; kb < nkb; ++kb) {
-        const int s = kb % STAGES;
-        if (*abort_flag || !mbar_wait(&full[s], (kb / STAGES) & 1)) {
-          *abort_flag = 1;
-          atomicOr(p.err, ERR_TIMEOUT);
+      long long it = 0;
+      int j = 0;   // this CTA's tile count
+      for (int tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x, ++j) {
+        // the previous tile's accumulator has been read out of TMEM
+        if (j > 0 && !mbar_wait(tmem_free, (uint32_t)(j - 1) & 1)) {
+          give_up();
           break;
         }
         tc_fence_after();
-        const uint32_t a0 = smem_u32(stage_ptr(s, 0)), a1 = smem_u32(stage_ptr(s, 1));
-        const uint32_t b0 = smem_u32(stage_ptr(s, 2)), b1 = smem_u32(stage_ptr(s, 3));
-        const uint32_t d_main = tmem + (uint32_t)((kb % Cfg::NMAIN) * BN);
-        const uint32_t d_cross = tmem + (uint32_t)(Cfg::NMAIN * BN);
-#pragma unroll
-        for (int kk = 0; kk < K::BK / K::KSTEP; ++kk) {
-          const uint32_t off = kk * K::KSTEP * K::ES;  // bytes along K inside the swizzle atom
-          mma<KIND>(d_main, sdesc(a0 + off), sdesc(b0 + off), ID,
-                    (kb >= Cfg::NMAIN || kk > 0) ? 1u : 0u);
-          if (K::NOPS == 2) {
-            mma<KIND>(d_cross, sdesc(a0 + off), sdesc(b1 + off), ID, (kb > 0 || kk > 0) ? 1u : 0u);
-            mma<KIND>(d_cross, sdesc(a1 + off), sdesc(b0 + off), ID, 1u);
+        bool ok = true;
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = (int)(it % STAGES);
+          if (*abort_flag || !mbar_wait(&full[s], (uint32_t)(it / STAGES) & 1)) {
+            give_up();
+            ok = false;
+            break;
           }
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(stage_ptr(s, 0)), a1 = smem_u32(stage_ptr(s, 1));
+          const uint32_t b0 = smem_u32(stage_ptr(s, 2)), b1 = smem_u32(stage_ptr(s, 3));
+          const uint32_t d_main = tmem + (uint32_t)((kb % Cfg::NMAIN) * BN);
+          const uint32_t d_cross = tmem + (uint32_t)(Cfg::NMAIN * BN);
+#pragma unroll
+          for (int kk = 0; kk < K::BK / K::KSTEP; ++kk) {
+            const uint32_t off = kk * K::KSTEP * K::ES;  // bytes along K inside the swizzle atom
+            mma<KIND>(d_main, sdesc(a0 + off), sdesc(b0 + off), ID,
+                      (kb >= Cfg::NMAIN || kk > 0) ? 1u : 0u);
+            if (K::NOPS == 2) {
+              mma<KIND>(d_cross, sdesc(a0 + off), sdesc(b1 + off), ID, (kb > 0 || kk > 0) ? 1u : 0u);
+              mma<KIND>(d_cross, sdesc(a1 + off), sdesc(b0 + off), ID, 1u);
+            }
+          }
+          mma_commit(&empty[s]);
         }
-        mma_commit(&empty[s]);
+        if (!ok) break;
+        mma_commit(accum);  // fires once every MMA issued above has completed
       }
-      mma_commit(accum);  // fires once every MMA issued above has completed
+      // whatever happened above, no MMA of this thread may be in flight when TMEM is freed
+      mma_commit(drain);
+      if (!mbar_wait(drain, 0)) atomicOr(p.err, ERR_TIMEOUT);
     }
   } else {
     // ---------------- epilogue: warps 2..9.  Warp w reads TMEM lanes
-    // 32*(w % 4) .. +31 (one output row per thread) and half (w - 2) / 4 of
-    // the tile's columns.  Its V (or w) values are loaded before the
-    // accumulator is ready, so their latency hides behind the main loop.
+    // 32*(w % 4) .. +31 (one output row per thread) and half (w - 2) / 4 of the
+    // tile's columns.
     constexpr int HALF = BN / 2;        // a multiple of 16
     constexpr int NCH = HALF / 16;
     const int quarter = warp & 3;
     const int half = (warp - 2) >> 2;
-    const int r = quarter * 32 + lane;
-    const int t = row0 + r;
-    const int tl = t - bitem * p.brows;               // row within its batch item
-    const bool rv = p.brows ? tl < p.bvalid : t < p.rows;
-    const int cbase = col0 + half * HALF;
-    float pre[HALF];
-    {
-      const float* src = EPI == TEPI_RATIO ? p.V + (size_t)tl * p.ldv : p.w + (size_t)t * p.ldw;
-#pragma unroll
-      for (int ch = 0; ch < NCH; ++ch) {
-        const int c = cbase + 16 * ch;
-        if (rv && c < p.cols) {
-          const float4* sp = reinterpret_cast<const float4*>(src + c);
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const float4 v4 = sp[i];
-            pre[16 * ch + 4 * i] = v4.x;
-            pre[16 * ch + 4 * i + 1] = v4.y;
-            pre[16 * ch + 4 * i + 2] = v4.z;
-            pre[16 * ch + 4 * i + 3] = v4.w;
-          }
-        } else {
-#pragma unroll
-          for (int i = 0; i < 16; ++i) pre[16 * ch + i] = 0.f;
-        }
-      }
-    }
-    const bool ok = mbar_wait(accum, 0);
-    if (!ok) atomicOr(p.err, ERR_TIMEOUT);
-    tc_fence_after();
-    double part = 0.0;
-    unsigned bad = 0;
     const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * HALF);
     const int nmain = nkb < Cfg::NMAIN ? nkb : Cfg::NMAIN;   // accumulators written
+    int j = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++j) {
+      const int row0 = (tile / ncol) * BM, col0 = (tile % ncol) * BN;
+      const int bitem = p.brows ? row0 / p.brows : 0;
+      const int r = quarter * 32 + lane;
+      const int t = row0 + r;
+      const int tl = t - bitem * p.brows;               // row within its batch item
+      const bool rv = p.brows ? tl < p.bvalid : t < p.rows;
+      const int cbase = col0 + half * HALF;
+      if (!mbar_wait(accum, (uint32_t)j & 1)) {
+        give_up();
+        break;
+      }
+      tc_fence_after();
+      // the tile's accumulators, summed, into registers; then TMEM is free
+      float acc[HALF];
 #pragma unroll
-    for (int ch = 0; ch < NCH; ++ch) {
-      // every accumulator's 16 columns in flight at once, then one wait
-      uint32_t raw[Cfg::NACC][16];
+      for (int i = 0; i < HALF; ++i) acc[i] = 0.f;
+      // two accumulators' 16 columns in flight at a time (bounded registers)
 #pragma unroll
-      for (int j = 0; j < Cfg::NACC; ++j)
-        if (j == 0 || j < nmain || (K::NOPS == 2 && j == Cfg::NMAIN))
-          tmem_ld16_nw(taddr + (uint32_t)(j * BN + 16 * ch), raw[j]);
-      tmem_wait_ld();
-      float acc[16];
+      for (int ch = 0; ch < NCH; ++ch) {
 #pragma unroll
-      for (int i = 0; i < 16; ++i) acc[i] = __uint_as_float(raw[0][i]);
+        for (int a0 = 0; a0 < Cfg::NACC; a0 += 2) {
+          uint32_t raw[2][16];
+          bool use[2];
 #pragma unroll
-      for (int j = 1; j < Cfg::NACC; ++j)
-        if (j < nmain || (K::NOPS == 2 && j == Cfg::NMAIN)) {
-#pragma unroll
-          for (int i = 0; i < 16; ++i) acc[i] += __uint_as_float(raw[j][i]);
-        }
-      const int c = cbase + 16 * ch;
-      if (!ok || !rv || c >= p.cols) continue;   // cols is a multiple of 16
-      const float* vv = pre + 16 * ch;
-      if (EPI == TEPI_RATIO) {
-        float q[16], vl[16];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const float v = vv[i], x = acc[i];
-          float qq = 0.f, l = 0.f;
-          if (v > 0.f) {
-            if (x > 0.f && isfinite(x)) {
-              qq = v / x;
-              l = v * logf(x);
-            } else {
-              bad |= ERR_VHAT_ZERO;
-            }
+          for (int u = 0; u < 2; ++u) {
+            const int a = a0 + u;
+            use[u] = a < Cfg::NACC && (a == 0 || a < nmain || (K::NOPS == 2 && a == Cfg::NMAIN));
+            if (use[u]) tmem_ld16_nw(taddr + (uint32_t)(a * BN + 16 * ch), raw[u]);
           }
-          q[i] = qq;
-          vl[i] = l;
-        }
-        // pairwise sum of the 16 terms in float, then into the double partial
+          tmem_wait_ld();
 #pragma unroll
-        for (int w = 8; w > 0; w >>= 1)
+          for (int u = 0; u < 2; ++u)
+            if (use[u]) {
 #pragma unroll
-          for (int i = 0; i < w; ++i) vl[i] += vl[i + w];
-        part += (double)vl[0];
-        if (KIND == KIND_TF32X3) {
-          float4* hp = reinterpret_cast<float4*>(p.out_f32 + (size_t)t * p.ldo + c);
-          float4* lp = reinterpret_cast<float4*>(p.out_lo + (size_t)t * p.ldo + c);
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            float h[4], l[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              h[j] = tf32_hi(q[4 * i + j]);
-              l[j] = tf32_hi(q[4 * i + j] - h[j]);
+              for (int i = 0; i < 16; ++i) acc[16 * ch + i] += __uint_as_float(raw[u][i]);
             }
-            hp[i] = make_float4(h[0], h[1], h[2], h[3]);
-            lp[i] = make_float4(l[0], l[1], l[2], l[3]);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tmem_free);
+      // the epilogue proper, from registers, beside the next tile's MMAs
+      double part = 0.0;
+      unsigned bad = 0;
+#pragma unroll 1
+      for (int ch = 0; ch < NCH; ++ch) {   // rolled: bounded register use
+        const int c = cbase + 16 * ch;
+        if (!rv || c >= p.cols) continue;   // cols is a multiple of 16
+        float x16[16];                      // columns 16 ch .. of acc, by selects
+#pragma unroll
+        for (int cc = 0; cc < NCH; ++cc)
+          if (cc == ch) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) x16[i] = acc[16 * cc + i];
+          }
+        const float* src = EPI == TEPI_RATIO ? p.V + (size_t)tl * p.ldv + c
+                                             : p.w + (size_t)t * p.ldw + c;
+        float vv[16];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float4 v4 = reinterpret_cast<const float4*>(src)[i];
+          vv[4 * i] = v4.x;
+          vv[4 * i + 1] = v4.y;
+          vv[4 * i + 2] = v4.z;
+          vv[4 * i + 3] = v4.w;
+        }
+        if (EPI == TEPI_RATIO) {
+          float* q = vv;     // Q = V / Vhat over V's registers, the bound terms over x16's
+          float* vl = x16;
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const float v = vv[i], x = x16[i];
+            float qq = 0.f, l = 0.f;
+            if (v > 0.f) {
+              if (x > 0.f && isfinite(x)) {
+                qq = v / x;
+                l = v * logf(x);
+              } else {
+                bad |= ERR_VHAT_ZERO;
+              }
+            }
+            q[i] = qq;
+            vl[i] = l;
+          }
+          // pairwise sum of the 16 terms in float, then into the double partial
+#pragma unroll
+          for (int w = 8; w > 0; w >>= 1)
+#pragma unroll
+            for (int i = 0; i < w; ++i) vl[i] += vl[i + w];
+          part += (double)vl[0];
+          if (KIND == KIND_TF32X3) {
+            float4* hp = reinterpret_cast<float4*>(p.out_f32 + (size_t)t * p.ldo + c);
+            float4* lp = reinterpret_cast<float4*>(p.out_lo + (size_t)t * p.ldo + c);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              float h[4], l[4];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                h[u] = tf32_hi(q[4 * i + u]);
+                l[u] = tf32_hi(q[4 * i + u] - h[u]);
+              }
+              hp[i] = make_float4(h[0], h[1], h[2], h[3]);
+              lp[i] = make_float4(l[0], l[1], l[2], l[3]);
+            }
+          } else {
+            uint4* bp = reinterpret_cast<uint4*>(p.out_bf16 + (size_t)t * p.ldo + c);
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+              uint32_t u[4];
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                const __nv_bfloat162 b2 = __floats2bfloat162_rn(q[8 * i + 2 * k], q[8 * i + 2 * k + 1]);
+                u[k] = *reinterpret_cast<const uint32_t*>(&b2);
+              }
+              bp[i] = make_uint4(u[0], u[1], u[2], u[3]);
+            }
           }
         } else {
-          uint4* bp = reinterpret_cast<uint4*>(p.out_bf16 + (size_t)t * p.ldo + c);
+          float4* op = reinterpret_cast<float4*>(p.out_f32 + (size_t)t * p.ldo + c);
 #pragma unroll
-          for (int i = 0; i < 2; ++i) {
-            uint32_t u[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              const __nv_bfloat162 b2 = __floats2bfloat162_rn(q[8 * i + 2 * j], q[8 * i + 2 * j + 1]);
-              u[j] = *reinterpret_cast<const uint32_t*>(&b2);
-            }
-            bp[i] = make_uint4(u[0], u[1], u[2], u[3]);
-          }
+          for (int i = 0; i < 4; ++i)
+            op[i] = make_float4(vv[4 * i] * x16[4 * i], vv[4 * i + 1] * x16[4 * i + 1],
+                                vv[4 * i + 2] * x16[4 * i + 2], vv[4 * i + 3] * x16[4 * i + 3]);
         }
-      } else {
-        float4* op = reinterpret_cast<float4*>(p.out_f32 + (size_t)t * p.ldo + c);
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-          op[i] = make_float4(vv[4 * i] * acc[4 * i], vv[4 * i + 1] * acc[4 * i + 1],
-                              vv[4 * i + 2] * acc[4 * i + 2], vv[4 * i + 3] * acc[4 * i + 3]);
       }
+      if (EPI == TEPI_RATIO && p.bpart && rv)
+        p.bpart[(size_t)t * p.nbpart + 2 * (tile % ncol) + half] = part;
+      if (bad) atomicOr(p.err, bad);
     }
-    if (EPI == TEPI_RATIO && p.bpart && ok && rv)
-      p.bpart[(size_t)t * p.nbpart + 2 * blockIdx.x + half] = part;
-    if (bad) atomicOr(p.err, bad);
   }
   tc_fence_before();
   __syncthreads();
@@ -391,7 +441,16 @@ cudaError_t launch_gemm(const Maps& maps, const TcArgs& a, cudaStream_t st) {
     attr = cudaFuncSetAttribute(k_tc_gemm<KIND, BN, EPI>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
   if (attr != cudaSuccess) return attr;
-  dim3 grid((a.cols + BN - 1) / BN, (a.rows + BM - 1) / BM);
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+      sms = 1;
+  }
+  const long long tiles = (long long)((a.cols + BN - 1) / BN) * ((a.rows + BM - 1) / BM);
+  if (tiles == 0) return cudaSuccess;
+  const int grid = (int)(tiles < sms ? tiles : sms);   // persistent: one CTA per SM
   k_tc_gemm<KIND, BN, EPI><<<grid, NUM_THREADS, Cfg::SMEM, st>>>(maps, a);
   return cudaGetLastError();
 }
