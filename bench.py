@@ -349,6 +349,10 @@ def run_batched(args, rank, world, local):
         print("bound after 3 sweeps:", ctx.sweep(3, bound=True), flush=True)
         ctx.close()
         return
+    # forward-backward geometry picked by the library's autotuner on these
+    # jobs (one sweep first: it times the forward-backward on its emissions)
+    ctx.sweep(1)
+    tuned = ctx.autotune(reps=3)
 
     def step_device():
         ctx.reinit(d_in["V"], d_in["W"], d_in["A"], d_in["pi"])
@@ -409,6 +413,8 @@ def run_batched(args, rank, world, local):
                    "jobs": len(lengths), "frames": T, "sweeps_per_step": sweeps,
                    "precision": args.precision, "contractions": "tcgen05" if tc else "fp32 SIMT",
                    "l2": "inputs larger than L2; flushed between steps (256 MB write)",
+                   "fb_geometry": {"chunk": tuned["fb_chunk"], "group": tuned["fb_group"],
+                                   "picked_by": "nfhmm_autotune", "fb_us": round(tuned["us"], 1)},
                    "parallelism": f"replicas x{world}"},
         "roofline": dict(roofline_of(prof, args.steps, T, 2, 40, 10, 513, args.precision, tc,
                                      peaks, args.steps * sweeps), fb_chunk=ctx.query("fb_chunk")),

@@ -1094,6 +1094,133 @@ int nfhmm_job_posteriors(nfhmm_ctx* c, long long job_id, float* dhat, int on_dev
   return leave(c);
 }
 
+int nfhmm_autotune(nfhmm_ctx* c, int reps, int* chunk_out, int* group_out, double* us_out) {
+  using namespace nfhmm;
+  if (!c) return fail(NFHMM_EINVAL, "NULL context");
+  if (c->jobs.empty() || !c->have_alpha)
+    return fail(NFHMM_ESTATE, "autotune times sweeps from the current state: run a sweep over "
+                              "the current jobs first");
+  if (reps <= 0) reps = 3;
+  int longest = 0;
+  for (const Job& j : c->jobs) longest = j.T > longest ? j.T : longest;
+  const int oldL = c->fb.L, oldG = c->fb.G;
+  const bool old_auto = c->group_auto;
+  const bool old_prof = c->profiling;
+  int rc = enter(c);
+  if (rc) return rc;
+  // the bound of the current state is formed now (the trials overwrite the
+  // weights it would be formed from later)
+  if (!c->bound_ok) {
+    if (!c->bpart_ok) {
+      rc = contract(c, true, false, 0, c->T_active);
+      if (rc) return rc;
+      c->bpart_ok = true;
+    }
+    rc = compute_bound(c);
+    if (rc) return rc;
+  }
+  CK(cudaStreamSynchronize(c->s_main));
+  const nfhmm_dims& d = c->d;
+  // a sweep reads only the counts and the posteriors (and the inputs); the
+  // bound and the separation also read alpha-hat and the log normalisers.
+  // Copies of those four are taken first: every trial starts from them and
+  // they are put back at the end.
+  void* live[4] = {c->c, c->dhat, c->alpha, c->logZ};
+  const size_t bytes[4] = {(size_t)c->T_active * c->Mp * sizeof(float),
+                           (size_t)d.S * d.T * d.N * sizeof(float),
+                           (size_t)c->T_active * c->Mp * sizeof(float),
+                           (size_t)d.S * c->max_jobs * sizeof(double)};
+  void* saved[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto cleanup = [&]() {
+    for (void* b : saved)
+      if (b) cudaFree(b);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  const bool f_alpha = c->have_alpha, f_bpart = c->bpart_ok, f_fterm = c->fterm_ok,
+             f_bound = c->bound_ok;
+  bool got = cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+  for (int i = 0; i < 4 && got; ++i) got = cudaMalloc(&saved[i], bytes[i]) == cudaSuccess;
+  if (!got) {
+    cleanup();
+    cudaGetLastError();
+    return fail(NFHMM_ENOMEM, "autotune: no room for a copy of the state");
+  }
+  auto copy_state = [&](bool save) -> cudaError_t {
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+      e = cudaMemcpyAsync(save ? saved[i] : live[i], save ? live[i] : saved[i], bytes[i],
+                          cudaMemcpyDeviceToDevice, c->s_main);
+    return e;
+  };
+  auto finish = [&](int code) {
+    copy_state(false);
+    cudaStreamSynchronize(c->s_main);
+    cleanup();
+    c->have_alpha = f_alpha;
+    c->bpart_ok = f_bpart;
+    c->fterm_ok = f_fterm;
+    c->bound_ok = f_bound;
+    c->profiling = old_prof;
+    return code;
+  };
+  if (copy_state(true) != cudaSuccess) return finish(fail(NFHMM_ECUDA, "autotune: state copy"));
+  c->profiling = false;
+  const int cand_L[] = {8, 12, 16, 20, 24, 32, 48, 64};
+  int bestL = oldL, bestG = oldG;
+  double best_us = 1e300;
+  for (int L : cand_L) {
+    if (L > longest && L != cand_L[0]) continue;
+    for (int pass = 0; pass < 2; ++pass) {
+      const int G = pass == 0 ? fb_default_group((longest + L - 1) / L) : 0;
+      if (pass == 1 && G == 0) continue;   // the automatic size was already "none"
+      c->fb.L = L;
+      c->fb.G = G;
+      rc = ensure_fb_capacity(c);
+      if (!rc) rc = commit_jobs(c);
+      if (rc) return finish(rc);
+      // two sweeps capture the graph, then `reps` sweeps are timed
+      cudaError_t e = copy_state(false);
+      if (e == cudaSuccess) rc = run_sweeps(c, 2, false);
+      if (e == cudaSuccess && !rc) e = cudaEventRecord(e0, c->s_main);
+      if (e == cudaSuccess && !rc) rc = run_sweeps(c, reps, false);
+      if (e == cudaSuccess && !rc) e = cudaEventRecord(e1, c->s_main);
+      if (e == cudaSuccess && !rc) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess && !rc) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (rc) return finish(rc);
+      if (e != cudaSuccess)
+        return finish(fail(NFHMM_ECUDA, std::string("autotune: ") + cudaGetErrorString(e)));
+      const double us = 1e3 * ms / reps;
+      if (us < best_us) {
+        best_us = us;
+        bestL = L;
+        bestG = G;
+      }
+    }
+  }
+  c->fb.L = bestL;
+  c->fb.G = bestG;
+  c->group_auto = false;
+  rc = ensure_fb_capacity(c);
+  if (!rc) rc = commit_jobs(c);
+  if (rc) {
+    c->fb.L = oldL;
+    c->fb.G = oldG;
+    c->group_auto = old_auto;
+    return finish(rc);
+  }
+  rc = finish(NFHMM_OK);
+  if (rc) return rc;
+  rc = sync_check(c);   // a trial's error word (none expected from a valid state)
+  if (rc) return rc;
+  if (chunk_out) *chunk_out = bestL;
+  if (group_out) *group_out = bestG;
+  if (us_out) *us_out = best_us;
+  return leave(c);
+}
+
 int nfhmm_set_option(nfhmm_ctx* c, int key, long long value) {
   if (!c) return fail(NFHMM_EINVAL, "NULL context");
   switch (key) {

@@ -93,6 +93,8 @@ _sigs = {
     "nfhmm_job_bounds": (_i, [_vp, _vp]),
     "nfhmm_job_posteriors": (_i, [_vp, ctypes.c_longlong, _vp, _i]),
     "nfhmm_set_option": (_i, [_vp, _i, ctypes.c_longlong]),
+    "nfhmm_autotune": (_i, [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i),
+                            ctypes.POINTER(ctypes.c_double)]),
     "nfhmm_serve": (_i, [ctypes.POINTER(_vp), _i, ctypes.POINTER(Request), _i,
                          ctypes.POINTER(ServeOpts), ctypes.POINTER(Result)]),
     "nfhmm_exact_create": (_i, [ctypes.POINTER(_vp), ctypes.POINTER(Dims), _vp, _vp, _vp, _vp, _i,
@@ -238,6 +240,14 @@ class VIContext:
         p, dev = _ptr(out)
         _check(_lib.nfhmm_job_posteriors(self._h, job_id, p, dev), "nfhmm_job_posteriors")
         return out
+
+    def autotune(self, reps: int = 3) -> dict:
+        """Time the forward-backward geometries on the current jobs (after a
+        sweep) and keep the fastest: {"fb_chunk", "fb_group", "us"}."""
+        L, G, us = _i(), _i(), ctypes.c_double()
+        _check(_lib.nfhmm_autotune(self._h, int(reps), ctypes.byref(L), ctypes.byref(G),
+                                   ctypes.byref(us)), "nfhmm_autotune")
+        return {"fb_chunk": L.value, "fb_group": G.value, "us": us.value}
 
     def set_option(self, key: str, value):
         """fb_chunk: frames per chunk (1..128); fb_products: "simt" or "tc";

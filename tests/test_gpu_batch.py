@@ -312,3 +312,35 @@ def test_profile_stride_times_every_kth_sweep(nf, stride):
         assert res[1][0][st][1] == 3 * len(range(0, 7, stride))
         assert res[0][0][st][2] == res[1][0][st][2]
     assert np.array_equal(res[0][1], res[1][1])
+
+
+def test_autotune_picks_a_geometry_and_keeps_the_state(nf):
+    """The autotuner times whole sweeps from a saved copy of the state: it
+    needs a sweep, leaves posteriors and bound untouched, applies one of its
+    candidates, and later sweeps equal those of a context set to that
+    geometry by hand at the same point (bit for bit: the same kernels run on
+    the same state)."""
+    p = synth.make_problem(seed=12, **synth.SMALL)
+    f = p.as_f32()
+    with nf.VIContext(f["V"], f["W"], f["A"], f["pi"], p.S, p.N, p.K) as ctx:
+        with pytest.raises(nf.NfhmmError) as e:
+            ctx.autotune()
+        assert e.value.code == nf.ESTATE
+        ctx.sweep(3)                       # no bound yet: the autotuner forms it first
+        d0 = ctx.posteriors()
+        r = ctx.autotune(reps=2)
+        assert r["fb_chunk"] in (8, 12, 16, 20, 24, 32, 48, 64) and r["us"] > 0
+        assert ctx.query("fb_chunk") == r["fb_chunk"]
+        assert ctx.query("fb_group") == r["fb_group"]
+        assert np.array_equal(ctx.posteriors(), d0)
+        L0 = ctx.bound()
+        L1, d1 = ctx.sweep(2, bound=True), ctx.posteriors()
+    with nf.VIContext(f["V"], f["W"], f["A"], f["pi"], p.S, p.N, p.K) as ref:
+        ref.sweep(3)
+        L0r = ref.bound()
+        ref.set_option("fb_chunk", r["fb_chunk"])
+        ref.set_option("fb_group", r["fb_group"])
+        L1r, d1r = ref.sweep(2, bound=True), ref.posteriors()
+    assert L0 == L0r
+    assert L1 == L1r
+    assert np.array_equal(d1, d1r)
