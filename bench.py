@@ -292,6 +292,35 @@ def measured_traffic(stage, workload):
     return val
 
 
+def stage_rooflines(prof, T, S, N, K, F, precision, tc, peaks):
+    """Achieved against peak for every sweep stage, from the same live
+    events (the contractions run beside the forward-backward, so their times
+    include sharing the SMs with it)."""
+    class _P:
+        pass
+    q = _P()
+    q.S, q.N, q.K, q.F, q.T = S, N, K, F, T
+    out = {}
+    for st in ("weights", "gemm1", "gemm2", "fb"):
+        ms, inv, _ = prof.get(st, (0.0, 0, 0))
+        if inv <= 0 or ms <= 0:
+            continue
+        bound_kind, amount, unit = stage_cost(st, q, precision, tc)
+        avg_s = ms / 1e3 / inv
+        if unit == "TFLOP/s":
+            achieved = amount / avg_s / 1e12
+            if bound_kind == "tensor":
+                peak = peaks["bf16_tflops_sustained"] * (1.0 if precision == "bf16" else TF32_OVER_BF16)
+            else:
+                peak = FP32_SIMT_PEAK_TFLOPS
+        else:
+            achieved = amount / avg_s / 1e9
+            peak = peaks["hbm_gbs"]
+        out[st] = {"bound": bound_kind, "achieved": round(achieved, 2), "peak": round(peak, 1),
+                   "unit": unit, "frac": round(achieved / peak, 4), "ms": round(1e3 * avg_s, 4)}
+    return out
+
+
 def roofline_of(prof, steps, T, S, N, K, F, precision, tc, peaks, sweeps_run):
     """Roofline object of the stage with the largest summed event time."""
     class _P:
@@ -418,6 +447,7 @@ def run_batched(args, rank, world, local):
                    "parallelism": f"replicas x{world}"},
         "roofline": dict(roofline_of(prof, args.steps, T, 2, 40, 10, 513, args.precision, tc,
                                      peaks, args.steps * sweeps), fb_chunk=ctx.query("fb_chunk")),
+        "roofline_by_stage": stage_rooflines(prof, T, 2, 40, 10, 513, args.precision, tc, peaks),
         "e2e": {"value": aggregate(fit, args.steps, world, tot_e2e), "unit": UNIT,
                 "h2d_bytes_per_step": int(sum(v.numel() * 4 for v in h_in.values())),
                 "d2h_bytes_per_step": int(h_dhat.numel() * 4 + 8)},
@@ -701,6 +731,8 @@ def main():
                      "launches_per_invocation": dom_launches / max(args.steps * sweeps, 1),
                      "stage_ms_per_invocation": stage_ms, "timed_sweeps": TIMED_NOTE,
                      "fb_chunk": ctx.query("fb_chunk")},
+        "roofline_by_stage": stage_rooflines(prof, p.T, p.S, p.N, p.K, p.F, args.precision, tc,
+                                             peaks),
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": int(sum(v.numel() * 4 for v in h_in.values())),
                 "d2h_bytes_per_step": int(h_dhat.numel() * 4 + 8)},
