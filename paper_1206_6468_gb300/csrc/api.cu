@@ -274,8 +274,9 @@ int sync_check(nfhmm_ctx* c) {
 // Reconstruction + ratio (GEMM1) and back-projection + counts (GEMM2) from
 // the weights in w32 (and the operand copies of the tensor-core path), for
 // frames [t0, t0 + rows).  The tensor-core form runs from frame 0 only.
-int contract(nfhmm_ctx* c, bool want_bpart, bool init, int t0, int rows) {
-  cudaStream_t st = c->s_main;
+int contract(nfhmm_ctx* c, bool want_bpart, bool init, int t0, int rows,
+             cudaStream_t on = nullptr) {
+  cudaStream_t st = on ? on : c->s_main;
   if (rows <= 0) return NFHMM_OK;
   if (c->use_tc && !init) {
     stage_begin(c, NFHMM_STAGE_GEMM1, st);
@@ -357,15 +358,17 @@ int one_sweep(nfhmm_ctx* c, bool want_bpart) {
   stage_begin(c, NFHMM_STAGE_WEIGHTS, c->s_main);
   launch_weights(wa, fmt, c->s_main);
   stage_end(c, NFHMM_STAGE_WEIGHTS, c->s_main, 1);
-  // forward-backward on the aux stream, concurrent with the contractions
+  // the contractions on the aux stream, concurrent with the forward-backward,
+  // which follows the weights on the main stream: its first pass is then a
+  // programmatic dependent of the weights kernel and sets up while it ends
   CK(cudaEventRecord(c->ev_fork, c->s_main));
   CK(cudaStreamWaitEvent(c->s_aux, c->ev_fork, 0));
-  stage_begin(c, NFHMM_STAGE_FB, c->s_aux);
-  int nfb = 0;
-  CK(launch_fb(c->fb, c->s_aux, &nfb));
-  stage_end(c, NFHMM_STAGE_FB, c->s_aux, nfb);
-  int rc = contract(c, want_bpart, false, 0, c->T_active);
+  int rc = contract(c, want_bpart, false, 0, c->T_active, c->s_aux);
   if (rc) return rc;
+  stage_begin(c, NFHMM_STAGE_FB, c->s_main);
+  int nfb = 0;
+  CK(launch_fb(c->fb, c->s_main, &nfb));
+  stage_end(c, NFHMM_STAGE_FB, c->s_main, nfb);
   CK(cudaEventRecord(c->ev_join, c->s_aux));
   CK(cudaStreamWaitEvent(c->s_main, c->ev_join, 0));
   return NFHMM_OK;
@@ -802,6 +805,7 @@ int create_ctx(nfhmm_ctx** out, const nfhmm_dims* dp, int max_jobs, const float*
   // total work sets it (chunks of 32 frames, one-level scan)
   c->fb.L = max_jobs == 1 ? fb_default_chunk(d.N, d.T) : (d.T < 32 ? d.T : 32);
   c->fb.products = FB_PRODUCTS_TC;
+  c->fb.inputs_stable = 1;   // the context's own copies of A and pi
   c->fb.G = max_jobs == 1 ? fb_default_group((d.T + c->fb.L - 1) / c->fb.L) : 0;
   c->group_auto = max_jobs == 1;
   c->fb.phi = c->phi;

@@ -32,6 +32,9 @@ constexpr int WB = 16;
 template <int FMT, bool BOUND>
 __global__ void __launch_bounds__(256) k_weights(WeightsArgs a) {
   extern __shared__ float wsm[];
+  // the forward-backward pass that follows may start launching (it waits for
+  // this kernel before it reads the emissions)
+  griddep_launch_dependents();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int NB = a.S * a.N;                 // blocks per frame
   const int NH = (NB + WB - 1) / WB;        // units per frame

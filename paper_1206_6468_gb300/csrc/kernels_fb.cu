@@ -276,19 +276,10 @@ __global__ void __launch_bounds__(256, MODE == CHAIN_CHUNK ? 2 : 1) k_fb_chain(F
   }
   const float* Ag = a.A + (size_t)s * N * N;
   if (MODE == CHAIN_CHUNK) {
-    // emissions of the tile's chunks and A, by asynchronous gathers
+    // A by asynchronous gathers: before the wait for the emissions' writer
+    // when A is the caller's stable copy, else after it
+    if (!a.inputs_stable) griddep_wait();
     for (int u = tid; u < N * N; u += 256) cp_async4(As + u, Ag + u);
-    for (int qq = 0; qq < Cfg::RCH; ++qq) {
-      const int cc = cbase + qq;
-      if (cc >= a.C) break;
-      const ChunkInfo ci = chunk_info(a, cc);
-      const float* src = a.phi + ((size_t)s * a.T + ci.t0) * N;
-      float* eq = e + qq * a.L * NP;
-      for (int u = tid; u < ci.len * N; u += 256) {
-        const int f = u / N, n = u - f * N;
-        cp_async4(eq + f * NP + n, src + u);
-      }
-    }
     cp_async_commit();
     if (tid < Cfg::RCH) ms->clen[tid] = cbase + tid < a.C ? chunk_info(a, cbase + tid).len : 0;
     cp_async_wait<0>();
@@ -303,6 +294,23 @@ __global__ void __launch_bounds__(256, MODE == CHAIN_CHUNK ? 2 : 1) k_fb_chain(F
       *reinterpret_cast<float*>(bbuf + sw128_off(j, k, Cfg::BATOM)) = h;
       *reinterpret_cast<float*>(bbuf + sw128_off(j + NOUT, k, Cfg::BATOM)) = tf32_hi(v - h);
     }
+    // the emissions, once the pass that wrote them (launched before this one
+    // on the stream, as a programmatic dependency) has finished
+    griddep_wait();
+    for (int qq = 0; qq < Cfg::RCH; ++qq) {
+      const int cc = cbase + qq;
+      if (cc >= a.C) break;
+      const ChunkInfo ci = chunk_info(a, cc);
+      const float* src = a.phi + ((size_t)s * a.T + ci.t0) * N;
+      float* eq = e + qq * a.L * NP;
+      for (int u = tid; u < ci.len * N; u += 256) {
+        const int f = u / N, n = u - f * N;
+        cp_async4(eq + f * NP + n, src + u);
+      }
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
     // e_t = exp(phi_t - max phi_t) for every frame of the tile: four
     // threads per frame (a quarter of the states each), the maxima kept per
     // frame and summed per chunk in double by one warp (fixed order)
@@ -1330,14 +1338,16 @@ static cudaError_t launch_np(const FBArgs& a, cudaStream_t st) {
   if (tc) {
     FBArgs p = a;   // the chunk pass writes the group pass's operand images
     if (a.G < 2) p.Pimg = nullptr;
-    k_fb_chain<NP, CHAIN_CHUNK><<<pgrid, 256, smem_chain<NP>(CHAIN_CHUNK, a.L), st>>>(p);
+    // a programmatic dependent of whatever wrote the emissions before it
+    e = launch_dependent(k_fb_chain<NP, CHAIN_CHUNK>, pgrid, 256,
+                         smem_chain<NP>(CHAIN_CHUNK, a.L), st, p);
   } else {
     k_fb_products_simt<NP><<<pgrid, 128, smem_products_simt<NP>(a.L), st>>>(a);
   }
   if (a.G >= 2) {
     // group products, the scan across groups (the chain scan over the group
     // arrays), then each group's chunk boundaries
-    if (tc)
+    if (tc && e == cudaSuccess)
       e = launch_dependent(k_fb_chain<NP, CHAIN_GROUP>, dim3(a.NG, a.S), 256,
                            smem_chain<NP>(CHAIN_GROUP, 0), st, a);
     else

@@ -88,6 +88,10 @@ enum { FB_PRODUCTS_SIMT = 0, FB_PRODUCTS_TC = 1 };
 struct FBArgs {
   int S, N, T, L, C;   // C = total chunks per source over all chains
   int products;        // FB_PRODUCTS_SIMT or FB_PRODUCTS_TC
+  // 1: A and pi are the caller's own stable copies, so the first pass may read
+  // them before its wait for the kernel that wrote the emissions (a sweep);
+  // 0: every input may have been written by that kernel (stateless calls)
+  int inputs_stable;
   int nchains;
   const int* chain_c0;     // nchains + 1: first chunk of each chain (chain_c0[nchains] = C)
   const int* chain_t0;     // nchains: first frame of each chain
