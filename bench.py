@@ -639,6 +639,10 @@ def main():
         print("bound after 3 sweeps:", ctx.sweep(3, bound=True), flush=True)
         ctx.close()
         return
+    # forward-backward geometry picked by the library's autotuner (whole sweeps
+    # from a saved state, before the warm-up; the step re-initialises anyway)
+    ctx.sweep(1)
+    tuned = ctx.autotune(reps=5)
 
     def step_device():
         ctx.reinit(d_in["V"], d_in["W"], d_in["A"], d_in["pi"])
@@ -723,6 +727,9 @@ def main():
                    "S": p.S, "N": p.N, "K": p.K, "F": p.F, "T": p.T, "sweeps_per_step": sweeps,
                    "precision": args.precision, "contractions": "tcgen05" if tc else "fp32 SIMT",
                    "l2": "flushed between steps (256 MB write)",
+                   "fb_geometry": {"chunk": tuned["fb_chunk"], "group": tuned["fb_group"],
+                                   "picked_by": "nfhmm_autotune",
+                                   "sweep_us": round(tuned["us"], 1)},
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": bound_kind, "kernel": dom, "achieved": achieved, "peak": peak,
                      "unit": unit, "frac": achieved / peak,
