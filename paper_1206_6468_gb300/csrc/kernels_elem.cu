@@ -32,8 +32,11 @@ constexpr int WB = 16;
 template <int FMT, bool BOUND>
 __global__ void __launch_bounds__(256) k_weights(WeightsArgs a) {
   extern __shared__ float wsm[];
-  // the forward-backward pass that follows may start launching (it waits for
-  // this kernel before it reads the emissions)
+  // launched as a programmatic dependent of the kernel before it on the
+  // stream (the replay that wrote d-hat): wait for it before reading
+  // anything; the forward-backward pass that follows may start launching at
+  // once (it waits for this kernel before it reads the emissions)
+  griddep_wait();
   griddep_launch_dependents();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int NB = a.S * a.N;                 // blocks per frame
@@ -117,23 +120,28 @@ void launch_element_table(int M, int Mp, int K, int N, int T, int2* ktab, cudaSt
 void launch_weights(const WeightsArgs& a, int fmt, cudaStream_t st) {
   const int warps = 8;
   const long long units = (long long)a.T * weights_units(a.S, a.N);
-  dim3 grid((unsigned)((units + warps - 1) / warps));
   const size_t smem = (size_t)warps * WB * a.K * sizeof(float);
   const bool b = a.fterm != nullptr;
+  void (*k)(WeightsArgs) = nullptr;
   switch (fmt) {
-    case WF_TF32X2:
-      if (b) k_weights<WF_TF32X2, true><<<grid, warps * 32, smem, st>>>(a);
-      else k_weights<WF_TF32X2, false><<<grid, warps * 32, smem, st>>>(a);
-      break;
-    case WF_BF16:
-      if (b) k_weights<WF_BF16, true><<<grid, warps * 32, smem, st>>>(a);
-      else k_weights<WF_BF16, false><<<grid, warps * 32, smem, st>>>(a);
-      break;
-    default:
-      if (b) k_weights<WF_F32, true><<<grid, warps * 32, smem, st>>>(a);
-      else k_weights<WF_F32, false><<<grid, warps * 32, smem, st>>>(a);
-      break;
+    case WF_TF32X2: k = b ? k_weights<WF_TF32X2, true> : k_weights<WF_TF32X2, false>; break;
+    case WF_BF16: k = b ? k_weights<WF_BF16, true> : k_weights<WF_BF16, false>; break;
+    default: k = b ? k_weights<WF_F32, true> : k_weights<WF_F32, false>; break;
   }
+  // a programmatic dependent of the previous kernel on the stream (ordinary
+  // launch on the legacy default stream)
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)((units + warps - 1) / warps));
+  cfg.blockDim = dim3(warps * 32);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  const bool legacy = st == nullptr || st == cudaStreamLegacy;
+  cfg.attrs = legacy ? nullptr : attr;
+  cfg.numAttrs = legacy ? 0 : 1;
+  cudaLaunchKernelEx(&cfg, k, a);
 }
 
 // ------------------------------------------------------------------- fills

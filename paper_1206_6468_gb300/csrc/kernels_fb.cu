@@ -1195,6 +1195,9 @@ __global__ void __launch_bounds__(R_CHUNKS_MAX * 64) k_fb_replay(FBArgs a) {
     }
   }
   __syncthreads();
+  // the sweep's next kernel (the weights, which waits for this one before it
+  // reads d-hat) may start launching
+  griddep_launch_dependents();
   // d-hat_t = a_t b_t / sum_n a_tn b_tn: the chunk's two warps take 16
   // frames at a time, four threads per frame (a quarter of the states each);
   // the stored vectors are only roughly normalised, so each is rescaled by
