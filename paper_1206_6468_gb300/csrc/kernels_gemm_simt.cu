@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(256) k_gemm_simt(GemmArgs g) {
           if (v > 0.f) {
             if (x > 0.f && isfinite(x)) {
               q = v / x;
-              part += (double)v * (double)logf(x);
+              if (g.bpart) part += (double)v * (double)logf(x);   // only when the bound is formed
             } else {
               bad |= ERR_VHAT_ZERO;
             }

@@ -318,6 +318,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         if (EPI == TEPI_RATIO) {
           float* q = vv;     // Q = V / Vhat over V's registers, the bound terms over x16's
           float* vl = x16;
+          // the bound's terms V log Vhat only on a sweep that forms them
+          const bool want_l = p.bpart != nullptr;
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
             const float v = vv[i], x = x16[i];
@@ -325,7 +327,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             if (v > 0.f) {
               if (x > 0.f && isfinite(x)) {
                 qq = v / x;
-                l = v * logf(x);
+                if (want_l) l = v * logf(x);
               } else {
                 bad |= ERR_VHAT_ZERO;
               }
@@ -333,12 +335,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             q[i] = qq;
             vl[i] = l;
           }
-          // pairwise sum of the 16 terms in float, then into the double partial
+          if (want_l) {
+            // pairwise sum of the 16 terms in float, then into the double partial
 #pragma unroll
-          for (int w = 8; w > 0; w >>= 1)
+            for (int w = 8; w > 0; w >>= 1)
 #pragma unroll
-            for (int i = 0; i < w; ++i) vl[i] += vl[i + w];
-          part += (double)vl[0];
+              for (int i = 0; i < w; ++i) vl[i] += vl[i + w];
+            part += (double)vl[0];
+          }
           if (KIND == KIND_TF32X3) {
             float4* hp = reinterpret_cast<float4*>(p.out_f32 + (size_t)t * p.ldo + c);
             float4* lp = reinterpret_cast<float4*>(p.out_lo + (size_t)t * p.ldo + c);
