@@ -48,7 +48,7 @@ FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA
 TF32_OVER_BF16 = 1.1 / 2.25                              # nominal dense ratio
 # stage events bracket every PROFILE_STRIDE-th sweep of the timed region
 # (the rest replay the same one-sweep graph without events)
-PROFILE_STRIDE = 5
+PROFILE_STRIDE = 10
 TIMED_NOTE = f"stages of every {PROFILE_STRIDE}th sweep bracketed by CUDA events"
 
 
