@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(256) k_weights(WeightsArgs a) {
       sg = z;
       big += (double)gb;
     } else {
-      digamma_exp(alpha, psi, w);
+      digamma_exp_fast(alpha, psi, w);
     }
     if (!isfinite(psi + w)) bad |= ERR_NONFINITE;   // NaN or Inf in either
     a.alpha[row + k] = alpha;

@@ -19,7 +19,7 @@ namespace nfhmm {
 // needed for large x.  Returns NaN for x <= 0 or NaN.  (A float32 emulation
 // over the accuracy test's arguments: 2.4e-7 in psi / (1 + |psi|) against
 // 5.3e-7 with the shift to 6, as fewer recurrence steps are rounded.)
-template <bool G>
+template <bool G, bool FAST = false>
 __device__ __forceinline__ void digamma_impl(float x, float& psi, float& w, float& gsmall,
                                              float& gbig) {
   if (!(x > 0.f)) {
@@ -52,16 +52,21 @@ __device__ __forceinline__ void digamma_impl(float x, float& psi, float& w, floa
                         r2 * (1.f / 240.f -
                               r2 * (1.f / 132.f - r2 * (691.f / 32760.f - r2 * (1.f / 12.f)))))));
   const float d = -0.5f * r - series;
-  const float lx = logf(x);
+  // FAST: psi and w from the hardware log2/exp2 approximations (x >= 3 here,
+  // d - acc in (-3, 0): within a few 1e-7 relative) -- the weights kernel of
+  // every sweep, so that forming the bound does not change the state; the
+  // bound's own terms and every other caller take the correctly rounded ones
+  const float lx = FAST ? __logf(x) : logf(x);
   psi = lx + d - acc;
-  w = x * expf(d - acc);
+  w = x * (FAST ? __expf(d - acc) : expf(d - acc));
   if (G) {
+    const float lxg = FAST ? logf(x) : lx;
     const float st =
         r * (1.f / 12.f -
              r2 * (1.f / 360.f -
                    r2 * (1.f / 1260.f -
                          r2 * (1.f / 1680.f - r2 * (1.f / 1188.f - r2 * (691.f / 360360.f))))));
-    gsmall = ((float)n + 0.5f) * lx + 0.91893853320467274f + st - logf(prod) -
+    gsmall = ((float)n + 0.5f) * lxg + 0.91893853320467274f + st - logf(prod) -
              (a - 1.f) * (d - acc);
     gbig = -((float)n + a);
   }
@@ -70,6 +75,11 @@ __device__ __forceinline__ void digamma_impl(float x, float& psi, float& w, floa
 __device__ __forceinline__ void digamma_exp(float x, float& psi, float& w) {
   float unused0, unused1;
   digamma_impl<false>(x, psi, w, unused0, unused1);
+}
+// the same with the hardware log2/exp2 approximations (the weights kernel)
+__device__ __forceinline__ void digamma_exp_fast(float x, float& psi, float& w) {
+  float unused0, unused1;
+  digamma_impl<false, true>(x, psi, w, unused0, unused1);
 }
 
 // digamma_exp plus the bound's per-element term g(x) = lnGamma(x) - (x-1) psi(x)
@@ -82,7 +92,7 @@ __device__ __forceinline__ void digamma_exp(float x, float& psi, float& w) {
 // returned separately (gbig, exact in double) so that no float sum holds it.
 __device__ __forceinline__ void digamma_exp_g(float x, float& psi, float& w, float& gsmall,
                                               float& gbig) {
-  digamma_impl<true>(x, psi, w, gsmall, gbig);
+  digamma_impl<true, true>(x, psi, w, gsmall, gbig);   // psi, w as digamma_exp_fast
 }
 
 __device__ __forceinline__ float digamma_f(float x) {
