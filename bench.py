@@ -443,7 +443,10 @@ def run_batched(args, rank, world, local):
                    "precision": args.precision, "contractions": "tcgen05" if tc else "fp32 SIMT",
                    "l2": "inputs larger than L2; flushed between steps (256 MB write)",
                    "fb_geometry": {"chunk": tuned["fb_chunk"], "group": tuned["fb_group"],
-                                   "picked_by": "nfhmm_autotune", "fb_us": round(tuned["us"], 1)},
+                                   "mode": "sequential x%d" % tuned["fb_mode"]
+                                   if tuned["fb_mode"] else "scan",
+                                   "picked_by": "nfhmm_autotune",
+                                   "sweep_us": round(tuned["us"], 1)},
                    "parallelism": f"replicas x{world}"},
         "roofline": dict(roofline_of(prof, args.steps, T, 2, 40, 10, 513, args.precision, tc,
                                      peaks, args.steps * sweeps), fb_chunk=ctx.query("fb_chunk")),
@@ -728,6 +731,8 @@ def main():
                    "precision": args.precision, "contractions": "tcgen05" if tc else "fp32 SIMT",
                    "l2": "flushed between steps (256 MB write)",
                    "fb_geometry": {"chunk": tuned["fb_chunk"], "group": tuned["fb_group"],
+                                   "mode": "sequential x%d" % tuned["fb_mode"]
+                                   if tuned["fb_mode"] else "scan",
                                    "picked_by": "nfhmm_autotune",
                                    "sweep_us": round(tuned["us"], 1)},
                    "parallelism": f"replicas x{world}"},

@@ -252,12 +252,23 @@ NFHMM_API int nfhmm_job_posteriors(nfhmm_ctx *c, long long job_id, float *dhat, 
  *                          k+1-th, ...) are bracketed by events, the others
  *                          run without them; stage launches are counted
  *                          for every sweep
+ *   NFHMM_OPT_FB_MODE      0 (default): the forward-backward as a scan over
+ *                          chunks (above); k >= 1: the sequential form, one
+ *                          warp per (source, job, direction) running the
+ *                          recursion frame by frame, k jobs' sources per
+ *                          block (clamped to what a block holds for N: 8 for
+ *                          N <= 40), on ceil(S * jobs / k) SMs that the
+ *                          contractions leave free (at most half of them).
+ *                          Its latency is the longest job's frames; it suits
+ *                          batches of many jobs.  The first use allocates an
+ *                          S x T x N float array (NFHMM_ENOMEM if no room)
  */
 #define NFHMM_OPT_FB_CHUNK    0
 #define NFHMM_OPT_FB_PRODUCTS 1
 #define NFHMM_OPT_GRAPHS      2
 #define NFHMM_OPT_FB_GROUP    3
 #define NFHMM_OPT_PROFILE_STRIDE 4
+#define NFHMM_OPT_FB_MODE     5
 
 /*
  * nfhmm_autotune -- choose the forward-backward geometry (frames per chunk
@@ -440,6 +451,7 @@ NFHMM_API long long nfhmm_kernel_launches(nfhmm_ctx *c);
 #define NFHMM_Q_FRAME_CAPACITY 4   /* frames the context's frame store holds */
 #define NFHMM_Q_MAX_JOBS       5   /* jobs the context can hold            */
 #define NFHMM_Q_FB_GROUP       6   /* chunks per group of the scan (0: none) */
+#define NFHMM_Q_FB_MODE        7   /* 0: scan; k >= 1: sequential, k per block */
 NFHMM_API int nfhmm_query(nfhmm_ctx *c, int key, long long *value);
 
 #ifdef __cplusplus

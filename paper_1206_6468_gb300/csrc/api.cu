@@ -208,7 +208,7 @@ void free_ctx(nfhmm_ctx* c) {
   void* bufs[] = {c->V, c->WM, c->WF, c->A, c->pi, c->alpha, c->w32, c->c, c->Q, c->phi,
                   c->dhat, c->wts, c->sep_tmp, c->v, c->bpart, c->frame_terms, c->logZ,
                   c->bound_dev, c->err, c->ktab, c->fb_scratch, c->d_tab, c->fterm,
-                  c->fb_seg};
+                  c->fb_seg, c->fb.beta};
   for (void* p : bufs)
     if (p) cudaFree(p);
   tc_free(c->tc);
@@ -363,6 +363,9 @@ int one_sweep(nfhmm_ctx* c, bool want_bpart) {
   // programmatic dependent of the weights kernel and sets up while it ends
   CK(cudaEventRecord(c->ev_fork, c->s_main));
   CK(cudaStreamWaitEvent(c->s_aux, c->ev_fork, 0));
+  // the sequential forward-backward holds a few SMs for the whole sweep: the
+  // persistent contractions size their grids to the others
+  c->tc.sm_reserve = c->fb.seq > 0 ? fb_seq_blocks(d.S * c->fb.nchains, c->fb.seq, d.N) : 0;
   int rc = contract(c, want_bpart, false, 0, c->T_active, c->s_aux);
   if (rc) return rc;
   stage_begin(c, NFHMM_STAGE_FB, c->s_main);
@@ -500,6 +503,18 @@ int groups_for(const nfhmm_ctx* c, int chunks) {
 // (Re)allocate the forward-backward scratch and the job tables for chunk
 // length fb.L and group size fb.G: room for every job set the frame store
 // and job slots allow.
+// The forward-backward form: 0 the scan over chunks, k >= 1 the sequential
+// form with k chains per block (at most fb_seq_max_cpc); its backward-vector
+// array (S x T x N) is allocated on first use and kept.
+int set_fb_mode(nfhmm_ctx* c, int cpc) {
+  if (cpc > 0 && !c->fb.beta) {
+    CK(dmalloc(c, (void**)&c->fb.beta, (size_t)c->d.S * c->d.T * c->d.N * sizeof(float)));
+  }
+  const int m = fb_seq_max_cpc(c->d.N);
+  c->fb.seq = cpc <= 0 ? 0 : cpc < m ? cpc : m;
+  return NFHMM_OK;
+}
+
 int ensure_fb_capacity(nfhmm_ctx* c) {
   const int need = (c->d.T + c->fb.L - 1) / c->fb.L + c->max_jobs;
   const int gneed = c->fb.G >= 2 ? need / c->fb.G + 1 + c->max_jobs : 0;
@@ -569,6 +584,9 @@ int commit_jobs(nfhmm_ctx* c) {
   c->fb.C = C;
   c->fb.NG = ng;
   c->fb.nchains = nj;
+  int longest = 0;
+  for (int j = 0; j < nj; ++j) longest = c->jobs[j].T > longest ? c->jobs[j].T : longest;
+  c->fb.maxlen = longest;
   c->have_alpha = false;
   c->bpart_ok = false;
   c->fterm_ok = false;
@@ -851,6 +869,7 @@ long long graph_key_of(const nfhmm_ctx* c, bool want_bpart, bool timed, int slot
   k = k * 4099 + c->fb.G;
   k = k * 1000033 + c->fb.NG;
   k = k * 3 + c->fb.products;
+  k = k * 67 + c->fb.seq;
   k = k * 2 + (want_bpart ? 1 : 0);
   k = k * 3 + (timed ? 1 + slot : 0);
   return k;
@@ -1107,7 +1126,7 @@ int nfhmm_autotune(nfhmm_ctx* c, int reps, int* chunk_out, int* group_out, doubl
   if (reps <= 0) reps = 3;
   int longest = 0;
   for (const Job& j : c->jobs) longest = j.T > longest ? j.T : longest;
-  const int oldL = c->fb.L, oldG = c->fb.G;
+  const int oldL = c->fb.L, oldG = c->fb.G, old_seq = c->fb.seq;
   const bool old_auto = c->group_auto;
   const bool old_prof = c->profiling;
   int rc = enter(c);
@@ -1171,19 +1190,44 @@ int nfhmm_autotune(nfhmm_ctx* c, int reps, int* chunk_out, int* group_out, doubl
   };
   if (copy_state(true) != cudaSuccess) return finish(fail(NFHMM_ECUDA, "autotune: state copy"));
   c->profiling = false;
+  // candidates: (chunk length, group size, 0) for the scan, then
+  // (-, -, k) for the sequential form with k chains per block
+  struct Cand {
+    int L, G, seq;
+  };
+  std::vector<Cand> cands;
   const int cand_L[] = {8, 12, 16, 20, 24, 32, 48, 64};
-  int bestL = oldL, bestG = oldG;
-  double best_us = 1e300;
   for (int L : cand_L) {
     if (L > longest && L != cand_L[0]) continue;
-    for (int pass = 0; pass < 2; ++pass) {
-      const int G = pass == 0 ? fb_default_group((longest + L - 1) / L) : 0;
-      if (pass == 1 && G == 0) continue;   // the automatic size was already "none"
-      c->fb.L = L;
-      c->fb.G = G;
-      rc = ensure_fb_capacity(c);
-      if (!rc) rc = commit_jobs(c);
-      if (rc) return finish(rc);
+    const int G = fb_default_group((longest + L - 1) / L);
+    cands.push_back({L, G, 0});
+    if (G != 0) cands.push_back({L, 0, 0});   // and without groups
+  }
+  const int chains = c->d.S * (int)c->jobs.size(), mcpc = fb_seq_max_cpc(c->d.N);
+  for (int k = 1; k <= mcpc; k *= 2) {
+    if (k / 2 >= chains) break;   // one block already holds every chain
+    cands.push_back({0, 0, k});
+  }
+  c->fb.seq = 0;
+  int bestL = oldL, bestG = oldG, best_seq = old_seq;
+  double best_us = 1e300;
+  for (const Cand& cd : cands) {
+    {
+      const int L = cd.seq ? c->fb.L : cd.L, G = cd.seq ? c->fb.G : cd.G;
+      if (cd.seq) {
+        // the sequential form (its scratch on first use; none: not a candidate)
+        if (set_fb_mode(c, cd.seq) != NFHMM_OK) {
+          cudaGetLastError();
+          set_last_error("");
+          continue;
+        }
+      } else {
+        c->fb.L = L;
+        c->fb.G = G;
+        rc = ensure_fb_capacity(c);
+        if (!rc) rc = commit_jobs(c);
+        if (rc) return finish(rc);
+      }
       // two sweeps capture the graph, then `reps` sweeps are timed
       cudaError_t e = copy_state(false);
       if (e == cudaSuccess) rc = run_sweeps(c, 2, false);
@@ -1201,7 +1245,9 @@ int nfhmm_autotune(nfhmm_ctx* c, int reps, int* chunk_out, int* group_out, doubl
         best_us = us;
         bestL = L;
         bestG = G;
+        best_seq = cd.seq;
       }
+      set_fb_mode(c, 0);
     }
   }
   c->fb.L = bestL;
@@ -1209,10 +1255,12 @@ int nfhmm_autotune(nfhmm_ctx* c, int reps, int* chunk_out, int* group_out, doubl
   c->group_auto = false;
   rc = ensure_fb_capacity(c);
   if (!rc) rc = commit_jobs(c);
+  if (!rc) rc = set_fb_mode(c, best_seq);
   if (rc) {
     c->fb.L = oldL;
     c->fb.G = oldG;
     c->group_auto = old_auto;
+    set_fb_mode(c, old_seq);
     return finish(rc);
   }
   rc = finish(NFHMM_OK);
@@ -1264,6 +1312,11 @@ int nfhmm_set_option(nfhmm_ctx* c, int key, long long value) {
     case NFHMM_OPT_GRAPHS: {
       c->use_graphs = value != 0;
       return NFHMM_OK;
+    }
+    case NFHMM_OPT_FB_MODE: {
+      if (value < 0 || value > 64)
+        return fail(NFHMM_EINVAL, "forward-backward mode must be 0 (scan) or 1..64 (sequential)");
+      return set_fb_mode(c, (int)value);
     }
     case NFHMM_OPT_PROFILE_STRIDE: {
       if (value < 1 || value > 1000000) return fail(NFHMM_EINVAL, "profile stride must be >= 1");
@@ -1548,6 +1601,7 @@ int nfhmm_query(nfhmm_ctx* c, int key, long long* value) {
     case NFHMM_Q_TENSOR_CORES: *value = c->use_tc ? 1 : 0; return NFHMM_OK;
     case NFHMM_Q_FB_CHUNK: *value = c->fb.L; return NFHMM_OK;
     case NFHMM_Q_FB_GROUP: *value = c->fb.G; return NFHMM_OK;
+    case NFHMM_Q_FB_MODE: *value = c->fb.seq; return NFHMM_OK;
     case NFHMM_Q_SWEEPS_DONE: *value = c->sweeps_done; return NFHMM_OK;
     case NFHMM_Q_DEVICE_BYTES: *value = (long long)c->device_bytes; return NFHMM_OK;
     case NFHMM_Q_FRAME_CAPACITY: *value = c->d.T; return NFHMM_OK;

@@ -1249,6 +1249,256 @@ __global__ void __launch_bounds__(R_CHUNKS_MAX * 64) k_fb_replay(FBArgs a) {
   }
 }
 
+// ------------------------------------------- 4. sequential form (many chains)
+// One warp per (source, chain, direction) runs the recursion frame by frame:
+// the forward warp a_t = (a_{t-1} A) diag(e_t) from a_0 = pi diag(e_0), the
+// backward warp b_t = A diag(e_{t+1}) b_{t+1} from b_{T-1} = 1.  Lane n owns
+// states n and n + 32; the chain's transition matrix sits in its registers as
+// f32x2 pairs along the summed index ((A_in, A_i+1,n) for the forward warp,
+// (A_ni, A_n,i+1) for the backward one), so that a 16-byte load of the
+// previous vector from shared memory feeds two packed FMAs per state; all of
+// a step's loads are issued before its FMAs.  Scaling: the vector stored at a
+// step is the matrix product of the previous stored vector times 2^-k, k the
+// exponent of that vector's largest entry (the maximum of non-negative floats
+// is that of their bit patterns: one redux.sync, whose latency the next
+// step's loads and FMAs hide), so stored vectors stay within one step's
+// growth or shrinkage of [1, 2); the forward warp sums the applied exponents
+// for log Z.  (A step that shrinks the vector below 2^-126 -- only possible
+// when A has near-zero entries between the states holding the mass and the
+// likely ones -- loses precision in that vector; the scan does not.)
+// Emissions come in blocks of 32 frames: lane r copies the log-emission row
+// of the block's r-th frame with cp.async one block ahead and, at the block
+// boundary, rewrites it in place as e = exp(phi - max) (the hardware
+// approximation), states n and n + 32 side by side for one 8-byte load per
+// lane.  (Measured on the GB300: spreading that preparation over the steps,
+// or odd row strides with 4-byte copies, made a step slower, not faster.)
+// The forward vectors are written to d-hat, the backward ones to a scratch
+// array, and a second kernel forms d-hat_t = a_t b_t / sum_n a_tn b_tn.
+// Per frame this is 2 N^2 FMAs against the scan's N^3 for chunk products, but
+// the latency is the chain's length in frame steps: the form for batches of
+// many chains, run on a few SMs beside the contractions (blocks of `cpc`
+// chains, two warps each).
+template <int NP>
+struct SeqCfg {
+  static constexpr bool TWO = NP > 32;   // two states per lane
+  // emission row stride (floats): 16-byte rows, RS/4 odd (conflict-free rows);
+  // with two states per lane the row holds positions 2 (n % 32) + n / 32
+  static constexpr int RS = TWO ? 68 : (((NP + 3) & ~3) | 4);
+  static constexpr int BLK = 32;         // frames per emission block (one per lane)
+  static constexpr int VEC = 64;         // floats per vector buffer
+  static constexpr int WARP_FLOATS = 2 * BLK * RS + 2 * VEC;
+  static constexpr int MAX_THREADS = 256;   // registers: A and a step's loads
+};
+
+template <int NP>
+static int seq_max_cpc() {
+  using Cfg = SeqCfg<NP>;
+  const int by_smem = (int)(SMEM_OPTIN / (2 * Cfg::WARP_FLOATS * sizeof(float)));
+  const int by_threads = Cfg::MAX_THREADS / 64;
+  return by_smem < by_threads ? by_smem : by_threads;
+}
+
+// One direction of one chain (the warp's whole job).
+template <int NP, bool FWD>
+__device__ __forceinline__ void seq_chain(const FBArgs& a, int s, int ch, float* eb, float* vb,
+                                          int lane) {
+  using Cfg = SeqCfg<NP>;
+  constexpr int RS = Cfg::RS, BLK = Cfg::BLK, VEC = Cfg::VEC;
+  constexpr bool TWO = Cfg::TWO;
+  const int N = a.N;
+  const int j0 = lane, j1 = lane + 32;
+  const bool h0 = j0 < N, h1 = TWO && j1 < N;
+  const float* Ag = a.A + (size_t)s * N * N;
+  auto A_of = [&](int i, int j) {   // the factor multiplying v_i in state j's sum
+    return (i < N && j < N) ? (FWD ? Ag[i * N + j] : Ag[j * N + i]) : 0.f;
+  };
+  float2 P0[NP / 2], P1[TWO ? NP / 2 : 1];
+#pragma unroll
+  for (int i = 0; i < NP; i += 2) {
+    P0[i / 2] = make_float2(A_of(i, j0), A_of(i + 1, j0));
+    if (TWO) P1[i / 2] = make_float2(A_of(i, j1), A_of(i + 1, j1));
+  }
+  const float2 start = FWD ? make_float2(h0 ? a.pi[(size_t)s * N + j0] : 0.f,
+                                         h1 ? a.pi[(size_t)s * N + j1] : 0.f)
+                           : make_float2(h0 ? 1.f : 0.f, h1 ? 1.f : 0.f);
+  const int t0 = a.chain_t0 ? a.chain_t0[ch] : 0;
+  const int T = a.chain_len ? a.chain_len[ch] : a.T;
+  float* op = (FWD ? a.dhat : a.beta) + ((size_t)s * a.T + t0) * N;   // row of the step's frame
+  if (!FWD && T > 0) op += (size_t)(T - 1) * N;
+  const float* ph = a.phi + ((size_t)s * a.T + t0) * N;
+  const bool v16 = (N & 3) == 0 && (reinterpret_cast<uintptr_t>(a.phi) & 15) == 0;
+  const int nblk = (T + BLK - 1) / BLK;
+  // frame of row r of block b: forward b*BLK + r, backward T-1 - b*BLK - r
+  auto issue = [&](int b) {
+    const int t = FWD ? b * BLK + lane : T - 1 - b * BLK - lane;
+    if (b < nblk && t >= 0 && t < T) {
+      float* dst = eb + (b & 1) * BLK * RS + lane * RS;
+      const float* src = ph + (size_t)t * N;
+      if (v16) {
+        for (int n = 0; n < N; n += 4) cp_async16(dst + n, src + n);
+      } else {
+        for (int n = 0; n < N; ++n) cp_async4(dst + n, src + n);
+      }
+    }
+    cp_async_commit();
+  };
+  griddep_wait();   // the emissions
+  double msum = 0.0;   // forward: the frame maxima of the rows this lane prepared
+  int kexp = 0;        // forward: exponents removed by the scaling
+  unsigned bad = 0;
+  float2 z = make_float2(0.f, 0.f);
+  unsigned mbprev = 0;   // bit pattern of the previous stored vector's largest entry
+  issue(0);
+  for (int b = 0; b < nblk; ++b) {
+    issue(b + 1);
+    cp_async_wait<1>();   // block b has landed
+    __syncwarp();
+    {
+      float* row = eb + (b & 1) * BLK * RS + lane * RS;
+      const int t = FWD ? b * BLK + lane : T - 1 - b * BLK - lane;
+      if (t >= 0 && t < T) {
+        float x[NP];
+        float m = -INFINITY;
+#pragma unroll
+        for (int n = 0; n < NP; ++n) {
+          x[n] = n < N ? row[n] : -INFINITY;
+          m = fmaxf(m, x[n]);
+        }
+#pragma unroll
+        for (int n = 0; n < (TWO ? 64 : NP); ++n) {
+          // hardware exp2 approximation: within a few 1e-7 relative, far
+          // inside the posteriors' tolerance, and a fraction of the cost
+          const float v = (n < NP && n < N) ? __expf(x[n < NP ? n : 0] - m) : 0.f;
+          row[TWO ? 2 * (n & 31) + (n >> 5) : n] = v;
+        }
+        if (FWD) msum += (double)m;
+      }
+    }
+    __syncwarp();
+    const int nf = min(BLK, T - b * BLK);
+    const float* erow = eb + (b & 1) * BLK * RS;
+    for (int r = 0; r < nf; ++r, erow += RS) {
+      const int q = b * BLK + r;   // step of this warp
+      const float2 e2 = TWO ? *reinterpret_cast<const float2*>(erow + 2 * lane)
+                            : make_float2(lane < NP ? erow[lane] : 0.f, 0.f);
+      if (q == 0) {
+        z = FWD ? __fmul2_rn(start, e2) : start;
+      } else {
+        // forward: (a_{t-1} A)_j;  backward: (A u_{t+1})_i with u = e (.) b
+        const float* v = vb + ((q - 1) & 1) * VEC;
+        float4 x[NP / 4];
+#pragma unroll
+        for (int i = 0; i < NP / 4; ++i) x[i] = *reinterpret_cast<const float4*>(v + 4 * i);
+        float2 c0[4], c1[4];
+#pragma unroll
+        for (int k = 0; k < NP / 4; ++k) {
+          const float2 lo = make_float2(x[k].x, x[k].y), hi = make_float2(x[k].z, x[k].w);
+          const int u = (2 * k) & 3, w = (2 * k + 1) & 3;
+          c0[u] = k < 2 ? __fmul2_rn(P0[2 * k], lo) : __ffma2_rn(P0[2 * k], lo, c0[u]);
+          c0[w] = k < 2 ? __fmul2_rn(P0[2 * k + 1], hi) : __ffma2_rn(P0[2 * k + 1], hi, c0[w]);
+          if (TWO) {
+            c1[u] = k < 2 ? __fmul2_rn(P1[2 * k], lo) : __ffma2_rn(P1[2 * k], lo, c1[u]);
+            c1[w] = k < 2 ? __fmul2_rn(P1[2 * k + 1], hi) : __ffma2_rn(P1[2 * k + 1], hi, c1[w]);
+          }
+        }
+        const float2 s0 = __fadd2_rn(__fadd2_rn(c0[0], c0[1]), __fadd2_rn(c0[2], c0[3]));
+        float2 y = make_float2(s0.x + s0.y, 0.f);
+        if (TWO) {
+          const float2 s1 = __fadd2_rn(__fadd2_rn(c1[0], c1[1]), __fadd2_rn(c1[2], c1[3]));
+          y.y = s1.x + s1.y;
+        }
+        // the previous vector's scale 2^-k, decoded only now: the reduction
+        // that produced its bit pattern ran during this step's loads and FMAs
+        int k = mbprev < 0x00800000u ? -126 : (int)(mbprev >> 23) - 127;  // subnormal: one factor
+        const bool okm = mbprev != 0u && mbprev < 0x7f000000u;   // else vanished or not finite
+        bad |= okm ? 0u : 1u;
+        k = okm ? k : 0;
+        kexp += k;
+        const float sc = pow2f(-k);
+        y = __fmul2_rn(y, make_float2(sc, sc));
+        z = FWD ? __fmul2_rn(y, e2) : y;
+      }
+      if (h0) op[j0] = z.x;
+      if (h1) op[j1] = z.y;
+      op += FWD ? N : -N;
+      const float2 u = FWD ? z : __fmul2_rn(z, e2);
+      float* vn = vb + (q & 1) * VEC;
+      vn[j0] = u.x;
+      if (TWO) vn[j1] = u.y;
+      // the next step's scale comes from this vector's largest entry
+      mbprev = __reduce_max_sync(0xffffffffu, __float_as_uint(fmaxf(z.x, z.y)));
+      __syncwarp();
+    }
+  }
+  cp_async_wait<0>();
+  if (FWD) {
+    // log Z = sum_t max_n phi_tn + ln 2 (exponents removed) + ln sum_n a_{T-1,n}
+    const double mt = warp_sum_d(msum);
+    const float sl = warp_sum(z.x + z.y);
+    if (lane == 0)
+      a.logZ[(size_t)s * a.nchains + ch] = T > 0 ? mt + LN2 * (double)kexp + log((double)sl) : 0.0;
+  }
+  if (bad && lane == 0) atomicOr(a.err, ERR_FB_ZERO);
+}
+
+template <int NP>
+__global__ void __launch_bounds__(SeqCfg<NP>::MAX_THREADS) k_fb_seq(FBArgs a) {
+  using Cfg = SeqCfg<NP>;
+  extern __shared__ __align__(16) float sm[];
+  if (!a.inputs_stable) griddep_wait();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = blockIdx.x * (blockDim.x >> 6) + (warp >> 1);
+  if (g >= a.S * a.nchains) return;
+  const int s = g / a.nchains, ch = g - s * a.nchains;
+  float* eb = sm + warp * Cfg::WARP_FLOATS;   // two emission blocks
+  float* vb = eb + 2 * Cfg::BLK * Cfg::RS;    // two vectors
+  if ((warp & 1) == 0)
+    seq_chain<NP, true>(a, s, ch, eb, vb, lane);
+  else
+    seq_chain<NP, false>(a, s, ch, eb, vb, lane);
+}
+
+
+// d-hat_t = a_t b_t / sum_n a_tn b_tn for the sequential form: four threads
+// per frame (a quarter of the states each), 64 frames of one chain per block;
+// a_t is read from d-hat and overwritten.  The stored vectors have their
+// largest entry in [1, 2), so the products stay in range.
+template <int NP>
+__global__ void __launch_bounds__(256) k_fb_seq_combine(FBArgs a) {
+  constexpr int QS = NP / 4;
+  const int N = a.N;
+  const int g = blockIdx.y;
+  const int s = g / a.nchains, ch = g - s * a.nchains;
+  const int t0 = a.chain_t0 ? a.chain_t0[ch] : 0;
+  const int T = a.chain_len ? a.chain_len[ch] : a.T;
+  griddep_wait();
+  if ((int)blockIdx.x * 64 >= T) return;   // the whole block
+  const int f = blockIdx.x * 64 + (threadIdx.x >> 2);
+  const int n0 = (threadIdx.x & 3) * QS;
+  const bool ok = f < T;
+  const size_t row = ((size_t)s * a.T + t0 + (ok ? f : 0)) * N;
+  float p[QS];
+  float z = 0.f;
+#pragma unroll
+  for (int k = 0; k < QS; ++k) {
+    const bool in = ok && n0 + k < N;
+    p[k] = in ? a.dhat[row + n0 + k] * a.beta[row + n0 + k] : 0.f;
+    z += p[k];
+  }
+  z += __shfl_xor_sync(0xffffffffu, z, 1);
+  z += __shfl_xor_sync(0xffffffffu, z, 2);
+  if (ok) {
+    if (!(z > 0.f) || !isfinite(z)) {
+      atomicOr(a.err, ERR_FB_ZERO);
+      z = 1.f;
+    }
+    const float iz = 1.f / z;
+#pragma unroll
+    for (int k = 0; k < QS; ++k)
+      if (n0 + k < N) a.dhat[row + n0 + k] = p[k] * iz;
+  }
+}
+
 // ------------------------------------------------------------------ launch
 template <int NP>
 static size_t smem_chain(int mode, int L) {
@@ -1331,8 +1581,25 @@ static cudaError_t launch_np(const FBArgs& a, cudaStream_t st) {
       attr = cudaFuncSetAttribute(k_fb_products_simt<NP>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem_products_simt<NP>(FB_MAX_L));
+    if (attr == cudaSuccess)
+      attr = cudaFuncSetAttribute(k_fb_seq<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)SMEM_OPTIN);
   }
   if (attr != cudaSuccess) return attr;
+  if (a.seq > 0) {
+    // the sequential form: recursions (a programmatic dependent of whatever
+    // wrote the emissions), then d-hat
+    const int cpc = a.seq < seq_max_cpc<NP>() ? a.seq : seq_max_cpc<NP>();
+    const int chains = a.S * a.nchains;
+    cudaError_t e = launch_dependent(
+        k_fb_seq<NP>, dim3((chains + cpc - 1) / cpc), 64 * cpc,
+        (size_t)cpc * 2 * SeqCfg<NP>::WARP_FLOATS * sizeof(float), st, a);
+    if (e == cudaSuccess && a.maxlen > 0)
+      e = launch_dependent(k_fb_seq_combine<NP>, dim3((a.maxlen + 63) / 64, chains), 256, 0, st,
+                           a);
+    const cudaError_t l = cudaGetLastError();
+    return e != cudaSuccess ? e : l;
+  }
   using Cfg = ChainCfg<NP>;
   const int rc = replay_chunks(NP, a.L);
   const bool tc = a.products == FB_PRODUCTS_TC;
@@ -1442,8 +1709,29 @@ int fb_default_group(int C) {
   return G < 2 ? 2 : G;
 }
 
+int fb_seq_max_cpc(int N) {
+  switch (pad8(N)) {
+    case 8: return seq_max_cpc<8>();
+    case 16: return seq_max_cpc<16>();
+    case 24: return seq_max_cpc<24>();
+    case 32: return seq_max_cpc<32>();
+    case 40: return seq_max_cpc<40>();
+    case 48: return seq_max_cpc<48>();
+    case 56: return seq_max_cpc<56>();
+    case 64: return seq_max_cpc<64>();
+    default: return 1;
+  }
+}
+
+int fb_seq_blocks(int chains, int cpc, int N) {
+  const int m = fb_seq_max_cpc(N);
+  if (cpc > m) cpc = m;
+  if (cpc < 1) cpc = 1;
+  return (chains + cpc - 1) / cpc;
+}
+
 cudaError_t launch_fb(const FBArgs& a, cudaStream_t st, int* launches) {
-  if (launches) *launches += a.G >= 2 ? 5 : 3;
+  if (launches) *launches += a.seq > 0 ? (a.maxlen > 0 ? 2 : 1) : a.G >= 2 ? 5 : 3;
   switch (pad8(a.N)) {
     case 8: return launch_np<8>(a, st);
     case 16: return launch_np<16>(a, st);

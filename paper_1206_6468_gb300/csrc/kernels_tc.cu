@@ -438,7 +438,7 @@ bool make_map(CUtensorMap* m, const void* base, int elem_bytes, int inner, int o
 }
 
 template <int KIND, int BN, int EPI>
-cudaError_t launch_gemm(const Maps& maps, const TcArgs& a, cudaStream_t st) {
+cudaError_t launch_gemm(const Maps& maps, const TcArgs& a, cudaStream_t st, int reserve = 0) {
   using Cfg = TileCfg<KIND, BN>;
   static cudaError_t attr = cudaErrorNotReady;
   if (attr == cudaErrorNotReady)
@@ -454,7 +454,9 @@ cudaError_t launch_gemm(const Maps& maps, const TcArgs& a, cudaStream_t st) {
   }
   const long long tiles = (long long)((a.cols + BN - 1) / BN) * ((a.rows + BM - 1) / BM);
   if (tiles == 0) return cudaSuccess;
-  const int grid = (int)(tiles < sms ? tiles : sms);   // persistent: one CTA per SM
+  // persistent: one CTA per SM, less the SMs reserved (at most half of them)
+  const int avail = sms - (reserve < sms / 2 ? reserve : sms / 2);
+  const int grid = (int)(tiles < avail ? tiles : avail);
   k_tc_gemm<KIND, BN, EPI><<<grid, NUM_THREADS, Cfg::SMEM, st>>>(maps, a);
   return cudaGetLastError();
 }
@@ -564,11 +566,11 @@ int tc_gemm1(TcPlan& p, int rows, double* bpart, cudaStream_t st) {
   cudaError_t e;
   if (p.precision == 1) {
     a.out_bf16 = reinterpret_cast<__nv_bfloat16*>(p.q_hi);
-    e = launch_gemm<KIND_BF16, BN1, TEPI_RATIO>(*maps_of(p, 0), a, st);
+    e = launch_gemm<KIND_BF16, BN1, TEPI_RATIO>(*maps_of(p, 0), a, st, p.sm_reserve);
   } else {
     a.out_f32 = reinterpret_cast<float*>(p.q_hi);
     a.out_lo = reinterpret_cast<float*>(p.q_lo);
-    e = launch_gemm<KIND_TF32X3, BN1, TEPI_RATIO>(*maps_of(p, 0), a, st);
+    e = launch_gemm<KIND_TF32X3, BN1, TEPI_RATIO>(*maps_of(p, 0), a, st, p.sm_reserve);
   }
   if (e != cudaSuccess) {
     g_tc_err = cudaGetErrorString(e);
@@ -589,9 +591,9 @@ int tc_gemm2(TcPlan& p, int rows, cudaStream_t st) {
   a.err = p.err;
   cudaError_t e;
   if (p.precision == 1)
-    e = launch_gemm<KIND_BF16, BN2, TEPI_SCALE>(*maps_of(p, 1), a, st);
+    e = launch_gemm<KIND_BF16, BN2, TEPI_SCALE>(*maps_of(p, 1), a, st, p.sm_reserve);
   else
-    e = launch_gemm<KIND_TF32X3, BN2, TEPI_SCALE>(*maps_of(p, 1), a, st);
+    e = launch_gemm<KIND_TF32X3, BN2, TEPI_SCALE>(*maps_of(p, 1), a, st, p.sm_reserve);
   if (e != cudaSuccess) {
     g_tc_err = cudaGetErrorString(e);
     return -1;

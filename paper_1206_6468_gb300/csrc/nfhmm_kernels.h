@@ -93,6 +93,11 @@ struct FBArgs {
   // 0: every input may have been written by that kernel (stateless calls)
   int inputs_stable;
   int nchains;
+  // seq > 0: the sequential form instead of the scan (one warp per chain and
+  // direction, blocks of `seq` chains; the chunk geometry is then unused);
+  // maxlen = frames of the longest chain; beta: S x T x N backward vectors
+  int seq, maxlen;
+  float* beta;
   const int* chain_c0;     // nchains + 1: first chunk of each chain (chain_c0[nchains] = C)
   const int* chain_t0;     // nchains: first frame of each chain
   const int* chain_len;    // nchains: frames of each chain
@@ -134,6 +139,10 @@ int fb_default_chunk(int N, int T);
 // group size for chains of about C chunks (0: no groups)
 int fb_default_group(int C);
 int fb_max_states();
+// sequential form: the most chains a block can hold for N states, and the
+// blocks a launch over `chains` (source, chain) pairs takes
+int fb_seq_max_cpc(int N);
+int fb_seq_blocks(int chains, int cpc, int N);
 cudaError_t launch_fb(const FBArgs& a, cudaStream_t st, int* launches);
 
 // Bound.

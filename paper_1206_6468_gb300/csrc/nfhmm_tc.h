@@ -24,6 +24,7 @@ struct TcPlan {
   const float* bF_src = nullptr;  // beta by frequency (Fp x Mp), float
   const float* bM_src = nullptr;  // beta by element (Mp x Fp), float
   int nbpart = 0;                 // columns of the bound-partial array
+  int sm_reserve = 0;             // SMs left free for a kernel running beside the contractions
   const float* V = nullptr;
   const float* w32 = nullptr;
   float* Q = nullptr;

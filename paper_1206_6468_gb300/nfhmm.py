@@ -29,8 +29,9 @@ INIT_UNIFORM, INIT_PRIOR = 0, 1
 SEP_MEAN, SEP_EXPECTATION = 0, 1
 STAGES = {"weights": 0, "gemm1": 1, "gemm2": 2, "fb": 3, "bound": 4, "init": 5}
 QUERIES = {"tensor_cores": 0, "fb_chunk": 1, "sweeps_done": 2, "device_bytes": 3,
-           "frame_capacity": 4, "max_jobs": 5, "fb_group": 6}
-OPTIONS = {"fb_chunk": 0, "fb_products": 1, "graphs": 2, "fb_group": 3, "profile_stride": 4}
+           "frame_capacity": 4, "max_jobs": 5, "fb_group": 6, "fb_mode": 7}
+OPTIONS = {"fb_chunk": 0, "fb_products": 1, "graphs": 2, "fb_group": 3, "profile_stride": 4,
+           "fb_mode": 5}
 FB_PRODUCTS = {"simt": 0, "tc": 1}
 PRECISIONS = {"fp32": FP32, "bf16": BF16, "fp32_simt": FP32_SIMT}
 
@@ -242,17 +243,22 @@ class VIContext:
         return out
 
     def autotune(self, reps: int = 3) -> dict:
-        """Time the forward-backward geometries on the current jobs (after a
-        sweep) and keep the fastest: {"fb_chunk", "fb_group", "us"}."""
+        """Time the forward-backward forms on the current jobs (after a sweep)
+        and keep the fastest: {"fb_chunk", "fb_group", "fb_mode", "us"}
+        (fb_mode 0: the scan over chunks; k >= 1: the sequential form, k
+        chains per block)."""
         L, G, us = _i(), _i(), ctypes.c_double()
         _check(_lib.nfhmm_autotune(self._h, int(reps), ctypes.byref(L), ctypes.byref(G),
                                    ctypes.byref(us)), "nfhmm_autotune")
-        return {"fb_chunk": L.value, "fb_group": G.value, "us": us.value}
+        return {"fb_chunk": L.value, "fb_group": G.value, "fb_mode": self.query("fb_mode"),
+                "us": us.value}
 
     def set_option(self, key: str, value):
         """fb_chunk: frames per chunk (1..128); fb_products: "simt" or "tc";
         fb_group: chunks per group (-1 automatic, 0 none); graphs: 0/1;
-        profile_stride: time the stages of every k-th sweep of a run."""
+        profile_stride: time the stages of every k-th sweep of a run;
+        fb_mode: 0 the scan over chunks, k >= 1 the sequential form with k
+        chains per block."""
         if key == "fb_products":
             value = FB_PRODUCTS[value]
         _check(_lib.nfhmm_set_option(self._h, OPTIONS[key], int(value)), "nfhmm_set_option")

@@ -38,7 +38,7 @@ def _f32(x):
     return np.ascontiguousarray(x, dtype=np.float32)
 
 
-def _alone(nf, jobs, j, chunk, precision="fp32", init_mode=0, V=None):
+def _alone(nf, jobs, j, chunk, precision="fp32", init_mode=0, V=None, fb_mode=0):
     """Job j in a context of its own, with the batch's forward-backward
     geometry (chunk, group): the same kernels' arithmetic for its frames."""
     V = _f32(jobs.V[j]) if V is None else V
@@ -46,6 +46,7 @@ def _alone(nf, jobs, j, chunk, precision="fp32", init_mode=0, V=None):
                        gamma=jobs.gamma, precision=precision, init_mode=init_mode)
     ctx.set_option("fb_chunk", chunk[0])
     ctx.set_option("fb_group", chunk[1])
+    ctx.set_option("fb_mode", fb_mode)
     return ctx
 
 
@@ -76,8 +77,10 @@ def test_batch_equals_each_job_alone(nf, precision, init_mode):
         assert L == bounds[j], f"job {j}: {L} vs {bounds[j]}"
 
 
-def test_batch_against_oracle(nf):
-    """A three-job batch against the oracle run job by job: the bound of
+@pytest.mark.parametrize("fb_mode", [0, 4])
+def test_batch_against_oracle(nf, fb_mode):
+    """A three-job batch against the oracle run job by job (the scan, and the
+    sequential forward-backward with four chains per block): the bound of
     every job after each of five sweeps (relative 1e-6), d-hat after the
     first sweep (1e-5, both sides starting from the same initial state) and
     after the fifth (1e-4: end to end, FP32 rounding at near-tie frames
@@ -93,6 +96,8 @@ def test_batch_against_oracle(nf):
         first.append(vi.run(V, W, A, pi, p.S, p.N, p.K, p.gamma, 1)["dhat"])
     with nf.VIContext(jobs.stacked_V(), _f32(jobs.W), _f32(jobs.A), _f32(jobs.pi), jobs.S,
                       jobs.N, jobs.K, job_frames=lengths) as b:
+        b.set_option("fb_mode", fb_mode)
+        assert b.query("fb_mode") == fb_mode
         Ls = []
         for i in range(5):
             b.sweep(1)
@@ -110,15 +115,18 @@ def test_batch_against_oracle(nf):
     assert abs(L_total - want) <= BOUND_RTOL * abs(want)
 
 
-def test_jobs_come_and_go(nf):
+@pytest.mark.parametrize("fb_mode", [0, 2])
+def test_jobs_come_and_go(nf, fb_mode):
     """Add, sweep, remove from the middle, add again: every job's state is
-    the one it has alone after the same number of sweeps."""
+    the one it has alone after the same number of sweeps (the scan, and the
+    sequential forward-backward, whose blocks follow the job count)."""
     lengths = [90, 250, 33, 400]
     jobs = _jobs(lengths, seed=8, sigma=1.5)
     f = {k: _f32(getattr(jobs, k)) for k in ("W", "A", "pi")}
     with nf.Batch(f["W"], f["A"], f["pi"], jobs.S, jobs.N, jobs.K, capacity=500,
                   max_jobs=3) as b:
         chunk = _geometry(b)
+        b.set_option("fb_mode", fb_mode)
         ids = [b.add(_f32(jobs.V[j])) for j in range(3)]
         b.sweep(3)
         b.remove(ids[1])                       # the frames of the third job move down
@@ -134,7 +142,7 @@ def test_jobs_come_and_go(nf):
         bounds = dict(zip([j[0] for j in b.jobs()], b.job_bounds()))
     for j, sweeps, idx in ((0, 7, 0), (2, 7, 2), (3, 2, 3)):
         V = np.ascontiguousarray(_f32(jobs.V[j])[:300]) if j == 3 else _f32(jobs.V[j])
-        with _alone(nf, jobs, j, chunk, V=V) as a:
+        with _alone(nf, jobs, j, chunk, V=V, fb_mode=fb_mode) as a:
             L = a.sweep(sweeps, bound=True)
             d = a.posteriors()
         assert np.array_equal(got[ids[idx]], d), j
@@ -330,6 +338,7 @@ def test_autotune_picks_a_geometry_and_keeps_the_state(nf):
         d0 = ctx.posteriors()
         r = ctx.autotune(reps=2)
         assert r["fb_chunk"] in (8, 12, 16, 20, 24, 32, 48, 64) and r["us"] > 0
+        assert r["fb_mode"] in (0, 1, 2) and ctx.query("fb_mode") == r["fb_mode"]
         assert ctx.query("fb_chunk") == r["fb_chunk"]
         assert ctx.query("fb_group") == r["fb_group"]
         assert np.array_equal(ctx.posteriors(), d0)
@@ -340,7 +349,78 @@ def test_autotune_picks_a_geometry_and_keeps_the_state(nf):
         L0r = ref.bound()
         ref.set_option("fb_chunk", r["fb_chunk"])
         ref.set_option("fb_group", r["fb_group"])
+        ref.set_option("fb_mode", r["fb_mode"])
         L1r, d1r = ref.sweep(2, bound=True), ref.posteriors()
     assert L0 == L0r
     assert L1 == L1r
     assert np.array_equal(d1, d1r)
+
+
+@pytest.mark.parametrize("N, K", [(4, 5), (37, 3), (40, 2)])
+def test_sequential_form_against_oracle(nf, N, K):
+    """The sequential forward-backward against the oracle's forward-backward
+    (Section 3.2) on the emissions of the first sweep: chains of 1 to 777
+    frames (across the 32-frame emission blocks, ragged), one state per lane
+    (N = 4) and two (N = 37, 40; 37 also takes the 4-byte copies of rows that
+    are not 16-byte multiples).  After one sweep d-hat of every job is within
+    1e-5 of the oracle's and the bound within 1e-6 relative; a batch with the
+    scan form agrees to the same tolerances."""
+    lengths = [1, 31, 32, 33, 64, 65, 130, 777]
+    jobs = synth.make_jobs(2, N, K, 65, lengths, self_prob=0.9, energy_sigma=1.0, seed=21)
+    refs = []
+    for j in range(len(lengths)):
+        p = jobs.problem(j)
+        V, W, A, pi = (x.astype(np.float32).astype(np.float64) for x in (p.V, p.W, p.A, p.pi))
+        refs.append(vi.run(V, W, A, pi, p.S, p.N, p.K, p.gamma, 1))
+    out = {}
+    for mode in (0, 8):
+        with nf.VIContext(jobs.stacked_V(), _f32(jobs.W), _f32(jobs.A), _f32(jobs.pi), jobs.S,
+                          jobs.N, jobs.K, job_frames=lengths) as b:
+            b.set_option("fb_mode", mode)
+            b.sweep(1)
+            out[mode] = ([b.job_posteriors(k) for k in b.job_ids], b.job_bounds())
+    for mode, (post, bounds) in out.items():
+        for j, ref in enumerate(refs):
+            assert np.max(np.abs(post[j] - ref["dhat"])) <= D_TOL, (mode, j)
+            assert abs(bounds[j] - ref["bounds"][-1]) <= BOUND_RTOL * abs(ref["bounds"][-1]), (mode, j)
+            assert np.allclose(post[j].sum(axis=-1), 1.0, atol=1e-5), (mode, j)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_sequential_batch_equals_each_job_alone(nf, precision):
+    """With the sequential form each chain's recursion, the d-hat pass and
+    every contraction tile do the same arithmetic whatever else the batch
+    holds or how many SMs the contractions keep: a batch and each job alone
+    agree bit for bit."""
+    lengths = [5, 130, 777, 64, 300]
+    jobs = _jobs(lengths, seed=13)
+    with nf.VIContext(jobs.stacked_V(), _f32(jobs.W), _f32(jobs.A), _f32(jobs.pi), jobs.S,
+                      jobs.N, jobs.K, precision=precision, job_frames=lengths) as b:
+        b.set_option("fb_mode", 2)
+        b.sweep(3, bound=True)
+        bounds = b.job_bounds()
+        post = [b.job_posteriors(i) for i in b.job_ids]
+    for j in range(len(lengths)):
+        with _alone(nf, jobs, j, (16, 0), precision) as a:
+            a.set_option("fb_mode", 2)
+            L = a.sweep(3, bound=True)
+            d = a.posteriors()
+        assert np.array_equal(post[j], d), f"job {j}"
+        assert L == bounds[j], f"job {j}: {L} vs {bounds[j]}"
+
+
+def test_fb_mode_option_bounds(nf):
+    p = synth.make_problem(seed=4, **synth.SMALL)
+    f = p.as_f32()
+    with nf.VIContext(f["V"], f["W"], f["A"], f["pi"], p.S, p.N, p.K) as ctx:
+        assert ctx.query("fb_mode") == 0
+        for bad in (-1, 65):
+            with pytest.raises(nf.NfhmmError) as e:
+                ctx.set_option("fb_mode", bad)
+            assert e.value.code == nf.EINVAL
+        ctx.set_option("fb_mode", 64)        # clamped to what a block holds
+        assert 1 <= ctx.query("fb_mode") < 64
+        L = ctx.sweep(2, bound=True)
+        ctx.set_option("fb_mode", 0)
+        assert ctx.query("fb_mode") == 0
+    assert np.isfinite(L)
