@@ -260,8 +260,8 @@ NFHMM_API int nfhmm_job_posteriors(nfhmm_ctx *c, long long job_id, float *dhat, 
  *                          N <= 40), on ceil(S * jobs / k) SMs that the
  *                          contractions leave free (at most half of them).
  *                          Its latency is the longest job's frames; it suits
- *                          batches of many jobs.  The first use allocates an
- *                          S x T x N float array (NFHMM_ENOMEM if no room)
+ *                          batches of many jobs.  The first use allocates
+ *                          S x T x (N + 68) floats (NFHMM_ENOMEM if no room)
  */
 #define NFHMM_OPT_FB_CHUNK    0
 #define NFHMM_OPT_FB_PRODUCTS 1

@@ -208,7 +208,7 @@ void free_ctx(nfhmm_ctx* c) {
   void* bufs[] = {c->V, c->WM, c->WF, c->A, c->pi, c->alpha, c->w32, c->c, c->Q, c->phi,
                   c->dhat, c->wts, c->sep_tmp, c->v, c->bpart, c->frame_terms, c->logZ,
                   c->bound_dev, c->err, c->ktab, c->fb_scratch, c->d_tab, c->fterm,
-                  c->fb_seg, c->fb.beta};
+                  c->fb_seg, c->fb.beta, c->fb.emis};
   for (void* p : bufs)
     if (p) cudaFree(p);
   tc_free(c->tc);
@@ -505,10 +505,14 @@ int groups_for(const nfhmm_ctx* c, int chunks) {
 // and job slots allow.
 // The forward-backward form: 0 the scan over chunks, k >= 1 the sequential
 // form with k chains per block (at most fb_seq_max_cpc); its backward-vector
-// array (S x T x N) is allocated on first use and kept.
+// array (S x T x N floats) and emission rows (S x T x 68) are allocated on
+// first use and kept.
 int set_fb_mode(nfhmm_ctx* c, int cpc) {
   if (cpc > 0 && !c->fb.beta) {
     CK(dmalloc(c, (void**)&c->fb.beta, (size_t)c->d.S * c->d.T * c->d.N * sizeof(float)));
+  }
+  if (cpc > 0 && !c->fb.emis) {
+    CK(dmalloc(c, (void**)&c->fb.emis, (size_t)c->d.S * c->d.T * 68 * sizeof(float)));
   }
   const int m = fb_seq_max_cpc(c->d.N);
   c->fb.seq = cpc <= 0 ? 0 : cpc < m ? cpc : m;

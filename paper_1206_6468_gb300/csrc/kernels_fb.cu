@@ -1266,24 +1266,24 @@ __global__ void __launch_bounds__(R_CHUNKS_MAX * 64) k_fb_replay(FBArgs a) {
 // for log Z.  (A step that shrinks the vector below 2^-126 -- only possible
 // when A has near-zero entries between the states holding the mass and the
 // likely ones -- loses precision in that vector; the scan does not.)
-// Emissions come in blocks of 32 frames: lane r copies the log-emission row
-// of the block's r-th frame with cp.async one block ahead and, at the block
-// boundary, rewrites it in place as e = exp(phi - max) (the hardware
-// approximation), states n and n + 32 side by side for one 8-byte load per
-// lane.  (Measured on the GB300: spreading that preparation over the steps,
-// or odd row strides with 4-byte copies, made a step slower, not faster.)
+// Emissions: a first pass (k_fb_seq_emit, one warp per frame, HBM-bound)
+// writes every frame's e = exp(phi - max) (the hardware approximation) as a
+// row of 68 floats, states n and n + 32 side by side at 2 (n % 32) + n / 32
+// and the frame maximum at 64; the recursion warps copy those rows 32 frames
+// at a time with cp.async one block ahead (lane r the block's r-th frame) and
+// read one 8-byte pair per lane and step.  (Measured on the GB300: preparing
+// the rows inside the recursion warps cost ~80 of a step's ~520 cycles.)
 // The forward vectors are written to d-hat, the backward ones to a scratch
 // array, and a second kernel forms d-hat_t = a_t b_t / sum_n a_tn b_tn.
 // Per frame this is 2 N^2 FMAs against the scan's N^3 for chunk products, but
 // the latency is the chain's length in frame steps: the form for batches of
 // many chains, run on a few SMs beside the contractions (blocks of `cpc`
 // chains, two warps each).
+constexpr int SEQ_ROW = 68;   // prepared emission row: 64 state positions, the maximum, padding
 template <int NP>
 struct SeqCfg {
   static constexpr bool TWO = NP > 32;   // two states per lane
-  // emission row stride (floats): 16-byte rows, RS/4 odd (conflict-free rows);
-  // with two states per lane the row holds positions 2 (n % 32) + n / 32
-  static constexpr int RS = TWO ? 68 : (((NP + 3) & ~3) | 4);
+  static constexpr int RS = SEQ_ROW;     // emission row stride (floats; 16-byte rows)
   static constexpr int BLK = 32;         // frames per emission block (one per lane)
   static constexpr int VEC = 64;         // floats per vector buffer
   static constexpr int WARP_FLOATS = 2 * BLK * RS + 2 * VEC;
@@ -1325,25 +1325,21 @@ __device__ __forceinline__ void seq_chain(const FBArgs& a, int s, int ch, float*
   const int T = a.chain_len ? a.chain_len[ch] : a.T;
   float* op = (FWD ? a.dhat : a.beta) + ((size_t)s * a.T + t0) * N;   // row of the step's frame
   if (!FWD && T > 0) op += (size_t)(T - 1) * N;
-  const float* ph = a.phi + ((size_t)s * a.T + t0) * N;
-  const bool v16 = (N & 3) == 0 && (reinterpret_cast<uintptr_t>(a.phi) & 15) == 0;
+  const float* em = a.emis + ((size_t)s * a.T + t0) * SEQ_ROW;
   const int nblk = (T + BLK - 1) / BLK;
   // frame of row r of block b: forward b*BLK + r, backward T-1 - b*BLK - r
   auto issue = [&](int b) {
     const int t = FWD ? b * BLK + lane : T - 1 - b * BLK - lane;
     if (b < nblk && t >= 0 && t < T) {
       float* dst = eb + (b & 1) * BLK * RS + lane * RS;
-      const float* src = ph + (size_t)t * N;
-      if (v16) {
-        for (int n = 0; n < N; n += 4) cp_async16(dst + n, src + n);
-      } else {
-        for (int n = 0; n < N; ++n) cp_async4(dst + n, src + n);
-      }
+      const float* src = em + (size_t)t * SEQ_ROW;
+#pragma unroll
+      for (int n = 0; n < SEQ_ROW; n += 4) cp_async16(dst + n, src + n);
     }
     cp_async_commit();
   };
-  griddep_wait();   // the emissions
-  double msum = 0.0;   // forward: the frame maxima of the rows this lane prepared
+  griddep_wait();   // the prepared emissions
+  double msum = 0.0;   // forward: the frame maxima of the rows this lane copied
   int kexp = 0;        // forward: exponents removed by the scaling
   unsigned bad = 0;
   float2 z = make_float2(0.f, 0.f);
@@ -1353,34 +1349,15 @@ __device__ __forceinline__ void seq_chain(const FBArgs& a, int s, int ch, float*
     issue(b + 1);
     cp_async_wait<1>();   // block b has landed
     __syncwarp();
-    {
-      float* row = eb + (b & 1) * BLK * RS + lane * RS;
-      const int t = FWD ? b * BLK + lane : T - 1 - b * BLK - lane;
-      if (t >= 0 && t < T) {
-        float x[NP];
-        float m = -INFINITY;
-#pragma unroll
-        for (int n = 0; n < NP; ++n) {
-          x[n] = n < N ? row[n] : -INFINITY;
-          m = fmaxf(m, x[n]);
-        }
-#pragma unroll
-        for (int n = 0; n < (TWO ? 64 : NP); ++n) {
-          // hardware exp2 approximation: within a few 1e-7 relative, far
-          // inside the posteriors' tolerance, and a fraction of the cost
-          const float v = (n < NP && n < N) ? __expf(x[n < NP ? n : 0] - m) : 0.f;
-          row[TWO ? 2 * (n & 31) + (n >> 5) : n] = v;
-        }
-        if (FWD) msum += (double)m;
-      }
+    if (FWD) {
+      const int t = b * BLK + lane;
+      if (t < T) msum += (double)eb[(b & 1) * BLK * RS + lane * RS + 64];
     }
-    __syncwarp();
     const int nf = min(BLK, T - b * BLK);
     const float* erow = eb + (b & 1) * BLK * RS;
     for (int r = 0; r < nf; ++r, erow += RS) {
       const int q = b * BLK + r;   // step of this warp
-      const float2 e2 = TWO ? *reinterpret_cast<const float2*>(erow + 2 * lane)
-                            : make_float2(lane < NP ? erow[lane] : 0.f, 0.f);
+      const float2 e2 = *reinterpret_cast<const float2*>(erow + 2 * lane);
       if (q == 0) {
         z = FWD ? __fmul2_rn(start, e2) : start;
       } else {
@@ -1458,6 +1435,40 @@ __global__ void __launch_bounds__(SeqCfg<NP>::MAX_THREADS) k_fb_seq(FBArgs a) {
     seq_chain<NP, false>(a, s, ch, eb, vb, lane);
 }
 
+
+// The sequential form's emission rows: e = exp(phi - max_n phi) of every
+// frame, states n and n + 32 at 2 (n % 32) + n / 32 (zeros past N), the
+// maximum at 64.  One warp per frame, eight frames per warp, 64 frames of one
+// chain per block; the row maximum by one redux.sync over order-preserving
+// integer keys.
+template <int NP>
+__global__ void __launch_bounds__(256) k_fb_seq_emit(FBArgs a) {
+  const int N = a.N;
+  const int g = blockIdx.y;
+  const int s = g / a.nchains, ch = g - s * a.nchains;
+  const int t0 = a.chain_t0 ? a.chain_t0[ch] : 0;
+  const int T = a.chain_len ? a.chain_len[ch] : a.T;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  griddep_wait();   // the log-emissions
+  // the recursions may be scheduled now; they wait for this pass to finish
+  griddep_launch_dependents();
+  if ((int)blockIdx.x * 64 >= T) return;   // the whole block
+  const bool h0 = lane < N, h1 = lane + 32 < N;
+  for (int i = 0; i < 8; ++i) {   // uniform in the warp
+    const int f = blockIdx.x * 64 + warp * 8 + i;
+    if (f >= T) break;
+    const size_t fr = (size_t)s * a.T + t0 + f;
+    const float* x = a.phi + fr * N;
+    const float x0 = h0 ? x[lane] : -INFINITY, x1 = h1 ? x[lane + 32] : -INFINITY;
+    const unsigned u = __float_as_uint(fmaxf(x0, x1));
+    const unsigned key = __reduce_max_sync(0xffffffffu, (u & 0x80000000u) ? ~u : (u | 0x80000000u));
+    const float m = __uint_as_float((key & 0x80000000u) ? (key & 0x7fffffffu) : ~key);
+    float* row = a.emis + fr * SEQ_ROW;
+    *reinterpret_cast<float2*>(row + 2 * lane) =
+        make_float2(h0 ? __expf(x0 - m) : 0.f, h1 ? __expf(x1 - m) : 0.f);
+    if (lane == 0) row[64] = m;
+  }
+}
 
 // d-hat_t = a_t b_t / sum_n a_tn b_tn for the sequential form: four threads
 // per frame (a quarter of the states each), 64 frames of one chain per block;
@@ -1591,9 +1602,17 @@ static cudaError_t launch_np(const FBArgs& a, cudaStream_t st) {
     // wrote the emissions), then d-hat
     const int cpc = a.seq < seq_max_cpc<NP>() ? a.seq : seq_max_cpc<NP>();
     const int chains = a.S * a.nchains;
-    cudaError_t e = launch_dependent(
-        k_fb_seq<NP>, dim3((chains + cpc - 1) / cpc), 64 * cpc,
-        (size_t)cpc * 2 * SeqCfg<NP>::WARP_FLOATS * sizeof(float), st, a);
+    cudaError_t e = cudaSuccess;
+    if (a.maxlen > 0)
+      e = launch_dependent(k_fb_seq_emit<NP>, dim3((a.maxlen + 63) / 64, chains), 256, 0, st, a);
+    // at least 120 KB of shared memory per block, so that no two blocks share
+    // an SM: each warp keeps its sub-partition to itself (with up to four
+    // chains per block, two), and the SMs the contractions leave free are
+    // exactly the blocks' count
+    size_t smem = (size_t)cpc * 2 * SeqCfg<NP>::WARP_FLOATS * sizeof(float);
+    if (smem < 120 * 1024) smem = 120 * 1024;
+    if (e == cudaSuccess)
+      e = launch_dependent(k_fb_seq<NP>, dim3((chains + cpc - 1) / cpc), 64 * cpc, smem, st, a);
     if (e == cudaSuccess && a.maxlen > 0)
       e = launch_dependent(k_fb_seq_combine<NP>, dim3((a.maxlen + 63) / 64, chains), 256, 0, st,
                            a);
@@ -1731,7 +1750,7 @@ int fb_seq_blocks(int chains, int cpc, int N) {
 }
 
 cudaError_t launch_fb(const FBArgs& a, cudaStream_t st, int* launches) {
-  if (launches) *launches += a.seq > 0 ? (a.maxlen > 0 ? 2 : 1) : a.G >= 2 ? 5 : 3;
+  if (launches) *launches += a.seq > 0 ? (a.maxlen > 0 ? 3 : 1) : a.G >= 2 ? 5 : 3;
   switch (pad8(a.N)) {
     case 8: return launch_np<8>(a, st);
     case 16: return launch_np<16>(a, st);

@@ -95,9 +95,11 @@ struct FBArgs {
   int nchains;
   // seq > 0: the sequential form instead of the scan (one warp per chain and
   // direction, blocks of `seq` chains; the chunk geometry is then unused);
-  // maxlen = frames of the longest chain; beta: S x T x N backward vectors
+  // maxlen = frames of the longest chain; beta: S x T x N backward vectors;
+  // emis: S x T x 68 prepared emission rows
   int seq, maxlen;
   float* beta;
+  float* emis;
   const int* chain_c0;     // nchains + 1: first chunk of each chain (chain_c0[nchains] = C)
   const int* chain_t0;     // nchains: first frame of each chain
   const int* chain_len;    // nchains: frames of each chain
