@@ -375,6 +375,9 @@ def run_batched(args, rank, world, local):
                           precision=args.precision, job_frames=lengths.tolist())
     sweeps = args.sweeps
     if args.ncu_case:
+        # the form the bench runs: one sweep, the autotuner, three sweeps
+        ctx.sweep(1)
+        print("autotuned:", ctx.autotune(reps=1), flush=True)
         print("bound after 3 sweeps:", ctx.sweep(3, bound=True), flush=True)
         ctx.close()
         return
