@@ -63,6 +63,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-case", action="store_true",
                     help="run one context for 3 sweeps and exit (a small case for ncu)")
+    ap.add_argument("--fb-mode", type=int, default=None,
+                    help="with --ncu-case --workload batched: the forward-backward form "
+                         "(0 scan, k >= 1 sequential with k chains per block) instead of the "
+                         "autotuner's choice")
     ap.add_argument("--workload", default="single",
                     choices=["single", "batched", "serving", "exact"],
                     help="single: one S2 N40 K10 F513 T3000 job per step (the headline); "
@@ -375,9 +379,13 @@ def run_batched(args, rank, world, local):
                           precision=args.precision, job_frames=lengths.tolist())
     sweeps = args.sweeps
     if args.ncu_case:
-        # the form the bench runs: one sweep, the autotuner, three sweeps
-        ctx.sweep(1)
-        print("autotuned:", ctx.autotune(reps=1), flush=True)
+        # the form the bench runs (one sweep, the autotuner), or the one asked
+        # for, then three sweeps
+        if args.fb_mode is None:
+            ctx.sweep(1)
+            print("autotuned:", ctx.autotune(reps=1), flush=True)
+        else:
+            ctx.set_option("fb_mode", args.fb_mode)
         print("bound after 3 sweeps:", ctx.sweep(3, bound=True), flush=True)
         ctx.close()
         return
