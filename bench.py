@@ -296,10 +296,23 @@ def measured_traffic(stage, workload):
     return val
 
 
-def stage_rooflines(prof, T, S, N, K, F, precision, tc, peaks):
+def fb_serial_steps(longest, mode, L, G):
+    """Frame steps on the forward-backward's critical path: the longest
+    chain's frames for the sequential form; for the scan, a chunk's frames
+    twice (products, replay) plus the scan across the longest chain's chunks
+    (over groups and within one when grouped)."""
+    if mode > 0:
+        return longest, "sequential"
+    C = -(-longest // L)
+    return 2 * L + (G + -(-C // G) if G >= 2 else C), "scan"
+
+
+def stage_rooflines(prof, T, S, N, K, F, precision, tc, peaks, fb_path=None):
     """Achieved against peak for every sweep stage, from the same live
     events (the contractions run beside the forward-backward, so their times
-    include sharing the SMs with it)."""
+    include sharing the SMs with it).  fb_path = (serial steps, form): the
+    forward-backward also gets its critical-path model, the live time per
+    serial frame step."""
     class _P:
         pass
     q = _P()
@@ -322,6 +335,9 @@ def stage_rooflines(prof, T, S, N, K, F, precision, tc, peaks):
             peak = peaks["hbm_gbs"]
         out[st] = {"bound": bound_kind, "achieved": round(achieved, 2), "peak": round(peak, 1),
                    "unit": unit, "frac": round(achieved / peak, 4), "ms": round(1e3 * avg_s, 4)}
+        if st == "fb" and fb_path:
+            out[st]["critical_path"] = {"form": fb_path[1], "serial_steps": int(fb_path[0]),
+                                        "ns_per_step": round(1e9 * avg_s / fb_path[0], 1)}
     return out
 
 
@@ -461,7 +477,10 @@ def run_batched(args, rank, world, local):
                    "parallelism": f"replicas x{world}"},
         "roofline": dict(roofline_of(prof, args.steps, T, 2, 40, 10, 513, args.precision, tc,
                                      peaks, args.steps * sweeps), fb_chunk=ctx.query("fb_chunk")),
-        "roofline_by_stage": stage_rooflines(prof, T, 2, 40, 10, 513, args.precision, tc, peaks),
+        "roofline_by_stage": stage_rooflines(
+            prof, T, 2, 40, 10, 513, args.precision, tc, peaks,
+            fb_serial_steps(int(lengths.max()), ctx.query("fb_mode"), ctx.query("fb_chunk"),
+                            ctx.query("fb_group"))),
         "e2e": {"value": aggregate(fit, args.steps, world, tot_e2e), "unit": UNIT,
                 "h2d_bytes_per_step": int(sum(v.numel() * 4 for v in h_in.values())),
                 "d2h_bytes_per_step": int(h_dhat.numel() * 4 + 8)},
@@ -754,8 +773,10 @@ def main():
                      "launches_per_invocation": dom_launches / max(args.steps * sweeps, 1),
                      "stage_ms_per_invocation": stage_ms, "timed_sweeps": TIMED_NOTE,
                      "fb_chunk": ctx.query("fb_chunk")},
-        "roofline_by_stage": stage_rooflines(prof, p.T, p.S, p.N, p.K, p.F, args.precision, tc,
-                                             peaks),
+        "roofline_by_stage": stage_rooflines(
+            prof, p.T, p.S, p.N, p.K, p.F, args.precision, tc, peaks,
+            fb_serial_steps(p.T, ctx.query("fb_mode"), ctx.query("fb_chunk"),
+                            ctx.query("fb_group"))),
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": int(sum(v.numel() * 4 for v in h_in.values())),
                 "d2h_bytes_per_step": int(h_dhat.numel() * 4 + 8)},
