@@ -1272,7 +1272,9 @@ __global__ void __launch_bounds__(R_CHUNKS_MAX * 64) k_fb_replay(FBArgs a) {
 // and the frame maximum at 64; the recursion warps copy those rows 32 frames
 // at a time with cp.async one block ahead (lane r the block's r-th frame) and
 // read one 8-byte pair per lane and step.  (Measured on the GB300: preparing
-// the rows inside the recursion warps cost ~80 of a step's ~520 cycles.)
+// the rows inside the recursion warps cost ~80 of a step's ~520 cycles.)  A
+// block's stored vectors collect in shared memory and leave in one coalesced
+// pass at the block's end, instead of two scattered stores per step.
 // The forward vectors are written to d-hat, the backward ones to a scratch
 // array, and a second kernel forms d-hat_t = a_t b_t / sum_n a_tn b_tn.
 // Per frame this is 2 N^2 FMAs against the scan's N^3 for chunk products, but
@@ -1286,7 +1288,8 @@ struct SeqCfg {
   static constexpr int RS = SEQ_ROW;     // emission row stride (floats; 16-byte rows)
   static constexpr int BLK = 32;         // frames per emission block (one per lane)
   static constexpr int VEC = 64;         // floats per vector buffer
-  static constexpr int WARP_FLOATS = 2 * BLK * RS + 2 * VEC;
+  static constexpr int OUT = BLK * NP;   // a block's stored vectors (rows of N floats)
+  static constexpr int WARP_FLOATS = 2 * BLK * RS + 2 * VEC + OUT;
   static constexpr int MAX_THREADS = 256;   // registers: A and a step's loads
 };
 
@@ -1301,7 +1304,7 @@ static int seq_max_cpc() {
 // One direction of one chain (the warp's whole job).
 template <int NP, bool FWD>
 __device__ __forceinline__ void seq_chain(const FBArgs& a, int s, int ch, float* eb, float* vb,
-                                          int lane) {
+                                          float* ob, int lane) {
   using Cfg = SeqCfg<NP>;
   constexpr int RS = Cfg::RS, BLK = Cfg::BLK, VEC = Cfg::VEC;
   constexpr bool TWO = Cfg::TWO;
@@ -1323,8 +1326,7 @@ __device__ __forceinline__ void seq_chain(const FBArgs& a, int s, int ch, float*
                            : make_float2(h0 ? 1.f : 0.f, h1 ? 1.f : 0.f);
   const int t0 = a.chain_t0 ? a.chain_t0[ch] : 0;
   const int T = a.chain_len ? a.chain_len[ch] : a.T;
-  float* op = (FWD ? a.dhat : a.beta) + ((size_t)s * a.T + t0) * N;   // row of the step's frame
-  if (!FWD && T > 0) op += (size_t)(T - 1) * N;
+  float* out = (FWD ? a.dhat : a.beta) + ((size_t)s * a.T + t0) * N;   // the chain's first row
   const float* em = a.emis + ((size_t)s * a.T + t0) * SEQ_ROW;
   const int nblk = (T + BLK - 1) / BLK;
   // frame of row r of block b: forward b*BLK + r, backward T-1 - b*BLK - r
@@ -1395,9 +1397,10 @@ __device__ __forceinline__ void seq_chain(const FBArgs& a, int s, int ch, float*
         y = __fmul2_rn(y, make_float2(sc, sc));
         z = FWD ? __fmul2_rn(y, e2) : y;
       }
-      if (h0) op[j0] = z.x;
-      if (h1) op[j1] = z.y;
-      op += FWD ? N : -N;
+      // the block's vectors in frame order, written out together below
+      const int orow = FWD ? r : nf - 1 - r;
+      if (h0) ob[orow * N + j0] = z.x;
+      if (h1) ob[orow * N + j1] = z.y;
       const float2 u = FWD ? z : __fmul2_rn(z, e2);
       float* vn = vb + (q & 1) * VEC;
       vn[j0] = u.x;
@@ -1405,6 +1408,17 @@ __device__ __forceinline__ void seq_chain(const FBArgs& a, int s, int ch, float*
       // the next step's scale comes from this vector's largest entry
       mbprev = __reduce_max_sync(0xffffffffu, __float_as_uint(fmaxf(z.x, z.y)));
       __syncwarp();
+    }
+    // the block's nf rows, contiguous in memory (frames ascending), by
+    // coalesced stores; the buffer is rewritten only after the next block's
+    // opening __syncwarp
+    float* dst = out + (size_t)(FWD ? b * BLK : T - b * BLK - nf) * N;
+    const int cnt = nf * N;
+    if ((N & 3) == 0 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+      for (int i = lane; i < cnt / 4; i += 32)
+        reinterpret_cast<float4*>(dst)[i] = reinterpret_cast<const float4*>(ob)[i];
+    } else {
+      for (int i = lane; i < cnt; i += 32) dst[i] = ob[i];
     }
   }
   cp_async_wait<0>();
@@ -1429,10 +1443,11 @@ __global__ void __launch_bounds__(SeqCfg<NP>::MAX_THREADS) k_fb_seq(FBArgs a) {
   const int s = g / a.nchains, ch = g - s * a.nchains;
   float* eb = sm + warp * Cfg::WARP_FLOATS;   // two emission blocks
   float* vb = eb + 2 * Cfg::BLK * Cfg::RS;    // two vectors
+  float* ob = vb + 2 * Cfg::VEC;              // a block's stored vectors
   if ((warp & 1) == 0)
-    seq_chain<NP, true>(a, s, ch, eb, vb, lane);
+    seq_chain<NP, true>(a, s, ch, eb, vb, ob, lane);
   else
-    seq_chain<NP, false>(a, s, ch, eb, vb, lane);
+    seq_chain<NP, false>(a, s, ch, eb, vb, ob, lane);
 }
 
 
