@@ -255,7 +255,11 @@ def stage_cost(stage, p, precision, tc):
             return "tensor", flops, "TFLOP/s"
         return "alu", flops, "TFLOP/s"
     if stage == "weights":
-        return "hbm", 4.0 * (3 * T * M + 2 * S * T * N), "GB/s"
+        # counts in, w (float) and the contraction operand out (bf16: 2 bytes,
+        # split tf32: 8), d-hat in and phi-hat out; alpha-hat is stored by the
+        # last sweep of a run only
+        op = (2 if precision == "bf16" else 8) if tc else 0
+        return "hbm", 4.0 * (2 * T * M + 2 * S * T * N) + op * T * M, "GB/s"
     if stage == "fb":
         return "hbm", 4.0 * (2 * S * T * N + S * N * N), "GB/s"
     if stage == "bound":

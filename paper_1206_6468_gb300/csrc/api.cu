@@ -329,8 +329,10 @@ int contract(nfhmm_ctx* c, bool want_bpart, bool init, int t0, int rows,
   return NFHMM_OK;
 }
 
-int one_sweep(nfhmm_ctx* c, bool want_bpart) {
-  // with the bound wanted, the weights kernel also forms its per-frame sums
+int one_sweep(nfhmm_ctx* c, bool want_bpart, bool keep_alpha) {
+  // with the bound wanted, the weights kernel also forms its per-frame sums;
+  // alpha-hat is stored only by the last sweep of a run (keep_alpha), the one
+  // whose state the bound, the weights, the separation and checkpoints read
   const nfhmm_dims& d = c->d;
   if (c->T_active == 0) return NFHMM_OK;
   WeightsArgs wa{};
@@ -344,7 +346,7 @@ int one_sweep(nfhmm_ctx* c, bool want_bpart) {
   wa.ktab = c->ktab;
   wa.counts = c->c;
   wa.dhat = c->dhat;
-  wa.alpha = c->alpha;
+  wa.alpha = keep_alpha ? c->alpha : nullptr;
   wa.w32 = c->w32;
   wa.phi = c->phi;
   wa.fterm = want_bpart ? c->fterm : nullptr;
@@ -865,7 +867,8 @@ int create_ctx(nfhmm_ctx** out, const nfhmm_dims* dp, int max_jobs, const float*
 // The launch configuration a captured sweep depends on; timed: its stages
 // are bracketed by events (then slot alternates between two instances, so
 // that one may still be in flight while the other is launched).
-long long graph_key_of(const nfhmm_ctx* c, bool want_bpart, bool timed, int slot) {
+long long graph_key_of(const nfhmm_ctx* c, bool want_bpart, bool timed, int slot,
+                       bool keep_alpha) {
   long long k = c->T_active;
   k = k * 1000003 + c->fb.C;
   k = k * 1048583 + c->fb.nchains;
@@ -875,16 +878,18 @@ long long graph_key_of(const nfhmm_ctx* c, bool want_bpart, bool timed, int slot
   k = k * 3 + c->fb.products;
   k = k * 67 + c->fb.seq;
   k = k * 2 + (want_bpart ? 1 : 0);
+  k = k * 2 + (keep_alpha ? 1 : 0);
   k = k * 3 + (timed ? 1 + slot : 0);
   return k;
 }
 
 // n sweeps launched one by one; with profiling, the stages of sweep i are
 // timed when (first + i) is a multiple of the profiling stride.
-int sweeps_direct(nfhmm_ctx* c, int n, bool want_bpart, long long first = 0) {
+int sweeps_direct(nfhmm_ctx* c, int n, bool want_bpart, long long first = 0,
+                  bool keep_alpha = true) {
   for (int i = 0; i < n; ++i) {
     c->prof_gate = (first + i) % c->prof_stride == 0;
-    const int rc = one_sweep(c, want_bpart && i == n - 1);
+    const int rc = one_sweep(c, want_bpart && i == n - 1, keep_alpha && i == n - 1);
     c->prof_gate = true;
     if (rc) return rc;
   }
@@ -896,22 +901,22 @@ int sweeps_direct(nfhmm_ctx* c, int n, bool want_bpart, long long first = 0) {
 // run uncaptured once, else launched one by one.  With profiling, every
 // prof_stride-th sweep replays a graph with stage events (two instances in
 // turn; an instance's previous events are read before it is launched again).
-int run_graph(nfhmm_ctx* c, bool want_bpart, long long index);
+int run_graph(nfhmm_ctx* c, bool want_bpart, long long index, bool keep_alpha);
 int run_sweeps(nfhmm_ctx* c, int n, bool want_bpart) {
   if (!c->use_graphs || c->T_active == 0 || n < 1) return sweeps_direct(c, n, want_bpart);
   for (int i = 0; i < n; ++i) {
-    const int rc = run_graph(c, want_bpart && i == n - 1, i);
+    const int rc = run_graph(c, want_bpart && i == n - 1, i, i == n - 1);
     if (rc) return rc;
   }
   return NFHMM_OK;
 }
 
-int run_graph(nfhmm_ctx* c, bool want_bpart, long long index) {
+int run_graph(nfhmm_ctx* c, bool want_bpart, long long index, bool keep_alpha) {
   const bool timed = c->profiling && index % c->prof_stride == 0;
   const int slot = (int)((index / c->prof_stride) & 1);
   // the index the sweep is captured with: one that gives it the same gate
   const long long cap_index = timed || c->prof_stride == 1 ? 0 : 1;
-  const long long key = graph_key_of(c, want_bpart, timed, slot);
+  const long long key = graph_key_of(c, want_bpart, timed, slot, keep_alpha);
   SweepGraph* g = nullptr;
   for (auto& x : c->graphs)
     if (x.key == key) g = &x;
@@ -924,7 +929,7 @@ int run_graph(nfhmm_ctx* c, bool want_bpart, long long index) {
   }
   g->last_use = ++c->graph_clock;
   if (!g->exec) {
-    if (g->seen++ == 0) return sweeps_direct(c, 1, want_bpart, index);   // first uncaptured
+    if (g->seen++ == 0) return sweeps_direct(c, 1, want_bpart, index, keep_alpha);   // first uncaptured
     const long long l0 = c->launches;
     long long s0[NFHMM_NUM_STAGES];
     for (int i = 0; i < NFHMM_NUM_STAGES; ++i) s0[i] = c->stages[i].launches;
@@ -932,10 +937,10 @@ int run_graph(nfhmm_ctx* c, bool want_bpart, long long index) {
     if (cudaStreamBeginCapture(c->s_main, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
       cudaGetLastError();
       c->use_graphs = false;
-      return sweeps_direct(c, 1, want_bpart, index);
+      return sweeps_direct(c, 1, want_bpart, index, keep_alpha);
     }
     c->capturing = g;
-    const int rc = sweeps_direct(c, 1, want_bpart, cap_index);
+    const int rc = sweeps_direct(c, 1, want_bpart, cap_index, keep_alpha);
     c->capturing = nullptr;
     const cudaError_t e = cudaStreamEndCapture(c->s_main, &graph);
     const bool good = !rc && e == cudaSuccess && graph &&
@@ -952,7 +957,7 @@ int run_graph(nfhmm_ctx* c, bool want_bpart, long long index) {
       drop_graph(c, *g);
       c->use_graphs = false;
       if (rc) return rc;
-      return sweeps_direct(c, 1, want_bpart, index);   // capture unavailable: launch directly
+      return sweeps_direct(c, 1, want_bpart, index, keep_alpha);   // capture unavailable: launch directly
     }
   }
   harvest(c, *g);   // its events are about to be recorded again

@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(256) k_weights(WeightsArgs a) {
       digamma_exp_fast(alpha, psi, w);
     }
     if (!isfinite(psi + w)) bad |= ERR_NONFINITE;   // NaN or Inf in either
-    a.alpha[row + k] = alpha;
+    if (a.alpha) a.alpha[row + k] = alpha;
     a.w32[row + k] = w;
     if (FMT == WF_TF32X2) {
       const float hi = tf32_hi(w);

@@ -30,7 +30,7 @@ struct WeightsArgs {
   const int2* ktab;     // Mp entries: (block g, s*T*N + n), g < 0 for padding
   const float* counts;  // T x Mp
   const float* dhat;    // S x T x N
-  float* alpha;         // T x Mp
+  float* alpha;         // T x Mp, or null: alpha-hat not stored (not the last sweep of a run)
   float* w32;           // T x Mp, w in float (always written)
   void* wop_hi;         // format-specific operand copies (may be null)
   void* wop_lo;
