@@ -56,3 +56,35 @@ def test_bad_dims_rejected(lib, dims, msg):
     rc = lib.call_raw("nfhmm_vi_init")(ctypes.byref(h), ctypes.byref(d), p, p, p, p, 0, None)
     assert rc == lib.EINVAL
     assert msg in lib._lib.nfhmm_last_error().decode()
+
+
+def _header_defines(prefix):
+    import re
+    from paper_1206_6468_gb300 import nfhmm
+    text = open(nfhmm.HEADER_PATH).read()
+    return {m.group(1): int(m.group(2))
+            for m in re.finditer(r"#define\s+(" + prefix + r"\w+)\s+(-?\d+)", text)}
+
+
+def test_binding_option_and_query_codes_match_the_header(lib):
+    """The ctypes binding's names for nfhmm_set_option / nfhmm_query keys are
+    the header's values (a key added on one side only would silently set or
+    read the wrong property)."""
+    opts = _header_defines("NFHMM_OPT_")
+    qs = _header_defines("NFHMM_Q_")
+    assert {k.lower().replace("nfhmm_opt_", ""): v for k, v in opts.items()} == lib.OPTIONS
+    assert {k.lower().replace("nfhmm_q_", ""): v for k, v in qs.items()} == lib.QUERIES
+
+
+def test_bench_forward_backward_critical_path_model():
+    """Serial frame steps on the forward-backward's critical path, as the
+    bench reports them: the longest chain for the sequential form; a chunk
+    twice plus the scan across chunks (or groups) for the scan."""
+    import importlib.util, os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(root, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    assert bench.fb_serial_steps(7993, 2, 64, 0) == (7993, "sequential")
+    assert bench.fb_serial_steps(3000, 0, 12, 12) == (2 * 12 + 12 + 21, "scan")   # 250 chunks
+    assert bench.fb_serial_steps(3000, 0, 32, 0) == (2 * 32 + 94, "scan")          # 94 chunks
