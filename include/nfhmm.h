@@ -271,21 +271,23 @@ NFHMM_API int nfhmm_job_posteriors(nfhmm_ctx *c, long long job_id, float *dhat, 
 #define NFHMM_OPT_FB_MODE     5
 
 /*
- * nfhmm_autotune -- choose the forward-backward geometry (frames per chunk
- * and chunks per group of the scan) for the context's current jobs by timing
- * whole sweeps on them: every candidate chunk length in
- * {8, 12, 16, 20, 24, 32, 48, 64} (at most the longest job's frames) with
- * groups of the automatic size and without groups; each candidate runs two
+ * nfhmm_autotune -- choose the forward-backward form and geometry for the
+ * context's current jobs by timing whole sweeps on them: the scan with every
+ * candidate chunk length in {8, 12, 16, 20, 24, 32, 48, 64} (at most the
+ * longest job's frames), with groups of the automatic size and without
+ * groups, then the sequential form (NFHMM_OPT_FB_MODE) with 1, 2 and 4 jobs'
+ * sources per block (as far as a block holds them); each candidate runs two
  * sweeps (which capture its graph) and then `reps` sweeps (reps <= 0: 3)
  * between CUDA events, every trial starting from the same state: the counts,
  * posteriors, alpha-hat and log normalisers are copied aside first and put
  * back at the end, so the
  * context's posteriors, bound and flags are unchanged (the bound of the current
  * state is formed before the trials if it was not yet); it needs room for that
- * copy (NFHMM_ENOMEM otherwise).  The fastest geometry is then set as by
- * NFHMM_OPT_FB_CHUNK and NFHMM_OPT_FB_GROUP.  Needs a sweep over the current
+ * copy (NFHMM_ENOMEM otherwise).  The fastest candidate is then set as by
+ * NFHMM_OPT_FB_CHUNK, NFHMM_OPT_FB_GROUP and NFHMM_OPT_FB_MODE.  Needs a sweep over the current
  * jobs (NFHMM_ESTATE otherwise).  Writes the chosen chunk length, group size
- * and its mean sweep time in microseconds to the non-NULL outputs.
+ * and its mean sweep time in microseconds to the non-NULL outputs; the chosen
+ * form is read back with NFHMM_Q_FB_MODE.
  * Synchronises.
  */
 NFHMM_API int nfhmm_autotune(nfhmm_ctx *c, int reps, int *chunk_out, int *group_out,

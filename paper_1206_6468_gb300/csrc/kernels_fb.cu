@@ -1,4 +1,7 @@
-// Forward-backward for the q(D^(s)) step of Section 3.2, parallel in time.
+// Forward-backward for the q(D^(s)) step of Section 3.2, in two forms: the
+// scan, parallel in time (below), for a few long chains; and the sequential
+// form (section 4 further down: one warp per chain and direction, frame by
+// frame) for batches of many chains.
 //
 // With emissions e_t = exp(phi_t - max_n phi_t) and G_t = A diag(e_t), the
 // forward row vector obeys a_t = a_{t-1} G_t (a_0 = pi diag(e_0)) and the
@@ -6,7 +9,7 @@
 // into C chunks of L; chunk c covers frames t0..t1-1 and has the transfer
 // matrix P_c = G_t0 ... G_{t1-1} (for c = 0 the first factor is diag(e_0)),
 // so that a_{t1-1} = a_{t0-1} P_c (a_{L-1} = pi P_0) and b_{t0-1} = P_c b_{t1-1}.
-// Three launches:
+// The scan, in three launches (five with groups of chunks, section 2'):
 //   1. products: P_c of every chunk on the tensor cores.  Row i of P_c is
 //      the forward recursion started from state i, so each row evolves on
 //      its own: a 128-row tile holds the rows of floor(128/NP) chunks, one
