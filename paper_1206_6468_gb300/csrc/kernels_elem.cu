@@ -50,6 +50,7 @@ __global__ void __launch_bounds__(256) k_weights(WeightsArgs a) {
   const size_t row = (size_t)t * a.Mp;
   const size_t toff = (size_t)t * a.N;
   unsigned bad = 0;
+  float chk = 0.f;
   float sa = 0.f, ca = 0.f, sg = 0.f, cg = 0.f;   // Kahan sums of alpha and g (small part)
   double big = 0.0;                                // sum of the exact large parts of g
   for (int k = k0 + lane; k < k1; k += 32) {
@@ -58,7 +59,7 @@ __global__ void __launch_bounds__(256) k_weights(WeightsArgs a) {
     float psi, w;
     if (BOUND) {
       float gs, gb;
-      digamma_exp_g(alpha, psi, w, gs, gb);
+      digamma_exp_g_ge1(alpha, psi, w, gs, gb);
       float y = alpha - ca, z = sa + y;
       ca = (z - sa) - y;
       sa = z;
@@ -68,9 +69,9 @@ __global__ void __launch_bounds__(256) k_weights(WeightsArgs a) {
       sg = z;
       big += (double)gb;
     } else {
-      digamma_exp_fast(alpha, psi, w);
+      digamma_exp_fast_ge1(alpha, psi, w);
     }
-    if (!isfinite(psi + w)) bad |= ERR_NONFINITE;   // NaN or Inf in either
+    chk = fmaf(0.f, psi + w, chk);   // stays 0 unless psi or w is NaN or infinite
     if (a.alpha) a.alpha[row + k] = alpha;
     a.w32[row + k] = w;
     if (FMT == WF_TF32X2) {
@@ -90,6 +91,7 @@ __global__ void __launch_bounds__(256) k_weights(WeightsArgs a) {
     for (int j = 0; j < a.K; ++j) x += pb[j];
     a.phi[a.ktab[b * a.K].y + toff] = a.gamma * x;
   }
+  if (!(chk == 0.f)) bad |= ERR_NONFINITE;
   bad = __reduce_or_sync(FULL, bad);
   if (bad && lane == 0) atomicOr(a.err, bad);
   if (BOUND) {

@@ -19,7 +19,12 @@ namespace nfhmm {
 // needed for large x.  Returns NaN for x <= 0 or NaN.  (A float32 emulation
 // over the accuracy test's arguments: 2.4e-7 in psi / (1 + |psi|) against
 // 5.3e-7 with the shift to 6, as fewer recurrence steps are rounded.)
-template <bool G, bool FAST = false>
+// GE1: the caller's x is >= 1 as a rule (alpha-hat of Eq. 6 is counts +
+// gamma d-hat + 1 with all three terms >= 0): the first two recurrence steps,
+// all that x >= 1 needs, run as straight-line selects; the loop finishes any
+// smaller x.  The same operations in the same order as the loop: the result
+// is bit for bit that of GE1 = false.
+template <bool G, bool FAST = false, bool GE1 = false>
 __device__ __forceinline__ void digamma_impl(float x, float& psi, float& w, float& gsmall,
                                              float& gbig) {
   if (!(x > 0.f)) {
@@ -36,6 +41,16 @@ __device__ __forceinline__ void digamma_impl(float x, float& psi, float& w, floa
   // (x)(x+1)...(x+n-1) of the lnGamma shift.
   float num = 0.f, prod = 1.f;
   int n = 0;
+  if (GE1) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const bool step = x < 3.f;
+      num = step ? fmaf(num, x, prod) : num;
+      prod = step ? prod * x : prod;
+      x = step ? x + 1.f : x;
+      n += step ? 1 : 0;
+    }
+  }
 #pragma unroll 1
   for (; n < 7 && x < 3.f; ++n) {
     num = fmaf(num, x, prod);
@@ -93,6 +108,15 @@ __device__ __forceinline__ void digamma_exp_fast(float x, float& psi, float& w) 
 __device__ __forceinline__ void digamma_exp_g(float x, float& psi, float& w, float& gsmall,
                                               float& gbig) {
   digamma_impl<true, true>(x, psi, w, gsmall, gbig);   // psi, w as digamma_exp_fast
+}
+// the two above for arguments >= 1 as a rule (the weights kernel's alpha-hat)
+__device__ __forceinline__ void digamma_exp_fast_ge1(float x, float& psi, float& w) {
+  float unused0, unused1;
+  digamma_impl<false, true, true>(x, psi, w, unused0, unused1);
+}
+__device__ __forceinline__ void digamma_exp_g_ge1(float x, float& psi, float& w, float& gsmall,
+                                                  float& gbig) {
+  digamma_impl<true, true, true>(x, psi, w, gsmall, gbig);
 }
 
 __device__ __forceinline__ float digamma_f(float x) {
