@@ -64,9 +64,10 @@ def parse():
     ap.add_argument("--ncu-case", action="store_true",
                     help="run one context for 3 sweeps and exit (a small case for ncu)")
     ap.add_argument("--fb-mode", type=int, default=None,
-                    help="with --ncu-case --workload batched: the forward-backward form "
-                         "(0 scan, k >= 1 sequential with k chains per block) instead of the "
-                         "autotuner's choice")
+                    help="the forward-backward form (0 scan, k >= 1 sequential with k chains "
+                         "per block): with --ncu-case --workload batched instead of the "
+                         "autotuner's choice; with --workload serving for the serving batches "
+                         "(default: the scan)")
     ap.add_argument("--workload", default="single",
                     choices=["single", "batched", "serving", "exact"],
                     help="single: one S2 N40 K10 F513 T3000 job per step (the headline); "
@@ -523,11 +524,15 @@ def run_serving(args, rank, world, local):
     capacity, max_jobs = 1 << 17, 512
 
     def batches():
-        return [nfhmm.Batch(np.ascontiguousarray(m.W, dtype=np.float32),
-                            np.ascontiguousarray(m.A, dtype=np.float32),
-                            np.ascontiguousarray(m.pi, dtype=np.float32), m.S, m.N, m.K,
-                            capacity=capacity, max_jobs=max_jobs, precision=args.precision)
-                for m in models]
+        out = [nfhmm.Batch(np.ascontiguousarray(m.W, dtype=np.float32),
+                           np.ascontiguousarray(m.A, dtype=np.float32),
+                           np.ascontiguousarray(m.pi, dtype=np.float32), m.S, m.N, m.K,
+                           capacity=capacity, max_jobs=max_jobs, precision=args.precision)
+               for m in models]
+        if args.fb_mode is not None:
+            for b in out:
+                b.set_option("fb_mode", args.fb_mode)
+        return out
 
     warm = batches()
     nfhmm.serve(warm, reqs[:8], max_sweeps=5, realtime=False, want_posteriors=False)
@@ -561,7 +566,8 @@ def run_serving(args, rank, world, local):
                                "until |dL| < 1e-5 |L| or 100 sweeps",
                    "requests": n_req, "completed": len(ok), "frames": int(Ts.sum()),
                    "batch_capacity_frames": capacity, "max_jobs": max_jobs,
-                   "precision": args.precision, "parallelism": f"replicas x{world}"},
+                   "precision": args.precision, "parallelism": f"replicas x{world}",
+                   "fb_mode": "sequential x%d" % args.fb_mode if args.fb_mode else "scan"},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "max": float(lat.max())},
         "sweeps": {"mean": float(np.mean([r["sweeps"] for r in ok])),
