@@ -256,8 +256,8 @@ NFHMM_API int nfhmm_job_posteriors(nfhmm_ctx *c, long long job_id, float *dhat, 
  *                          chunks (above); k >= 1: the sequential form, one
  *                          warp per (source, job, direction) running the
  *                          recursion frame by frame, k jobs' sources per
- *                          block (clamped to what a block holds for N: 8 for
- *                          N <= 40), on ceil(S * jobs / k) SMs that the
+ *                          block (clamped to 4, what a block holds), on
+ *                          ceil(S * jobs / k) SMs that the
  *                          contractions leave free (at most half of them).
  *                          Its latency is the longest job's frames; it suits
  *                          batches of many jobs.  The first use allocates
