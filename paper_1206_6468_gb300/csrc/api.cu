@@ -278,15 +278,34 @@ int contract(nfhmm_ctx* c, bool want_bpart, bool init, int t0, int rows,
              cudaStream_t on = nullptr) {
   cudaStream_t st = on ? on : c->s_main;
   if (rows <= 0) return NFHMM_OK;
-  if (c->use_tc && !init) {
-    stage_begin(c, NFHMM_STAGE_GEMM1, st);
-    const int n1 = tc_gemm1(c->tc, rows, want_bpart ? c->bpart : nullptr, st);
-    if (n1 < 0) return fail(NFHMM_ECUDA, "tensor-core contraction: " + tc_last_error());
-    stage_end(c, NFHMM_STAGE_GEMM1, st, n1);
-    stage_begin(c, NFHMM_STAGE_GEMM2, st);
-    const int n2 = tc_gemm2(c->tc, rows, st);
-    if (n2 < 0) return fail(NFHMM_ECUDA, "tensor-core contraction: " + tc_last_error());
-    stage_end(c, NFHMM_STAGE_GEMM2, st, n2);
+  // the sweep's contractions run on the tensor cores; so does the initial
+  // state's (w = 1 on frames [t0, t0 + rows)) in split-TF32 mode, whose
+  // accuracy is FP32's (BF16 contexts keep the FP32 CUDA-core initial state)
+  if (c->use_tc && (!init || c->tc.w_format == WF_TF32X2)) {
+    const int reserve = c->tc.sm_reserve;
+    if (init) {
+      // the operand copies of the initial w, on the frames being initialised;
+      // nothing runs beside these contractions
+      const size_t o = (size_t)t0 * c->Mp;
+      stage_begin(c, NFHMM_STAGE_INIT, st);
+      launch_split_tf32(c->w32 + o, reinterpret_cast<float*>(c->tc.w_hi) + o,
+                        reinterpret_cast<float*>(c->tc.w_lo) + o, (size_t)rows * c->Mp, st);
+      stage_end(c, NFHMM_STAGE_INIT, st, 1);
+      c->tc.sm_reserve = 0;
+    }
+    const int stage1 = init ? NFHMM_STAGE_INIT : NFHMM_STAGE_GEMM1;
+    const int stage2 = init ? NFHMM_STAGE_INIT : NFHMM_STAGE_GEMM2;
+    stage_begin(c, stage1, st);
+    const int n1 = tc_gemm1(c->tc, t0, rows, want_bpart ? c->bpart : nullptr, st);
+    if (n1 >= 0) stage_end(c, stage1, st, n1);
+    int n2 = -1;
+    if (n1 >= 0) {
+      stage_begin(c, stage2, st);
+      n2 = tc_gemm2(c->tc, t0, rows, st);
+      if (n2 >= 0) stage_end(c, stage2, st, n2);
+    }
+    c->tc.sm_reserve = reserve;
+    if (n1 < 0 || n2 < 0) return fail(NFHMM_ECUDA, "tensor-core contraction: " + tc_last_error());
     return NFHMM_OK;
   }
   const int stage1 = init ? NFHMM_STAGE_INIT : NFHMM_STAGE_GEMM1;
@@ -442,8 +461,9 @@ int load_model(nfhmm_ctx* c, const float* W, const float* A, const float* pi, in
 
 // Copy the spectrograms of n jobs (frames[j] rows from Vs[j]) into frames
 // [t0, t0 + T) of the frame store, back to back, validate them and set those
-// frames' initial state: z-hat from equal weights (w = 1 through the FP32
-// contractions) and d-hat from init_mode (the prior marginals restart at
+// frames' initial state: z-hat from equal weights (w = 1 through the
+// contractions: the tensor cores' in split-TF32 mode, the CUDA cores' FP32 ones
+// otherwise) and d-hat from init_mode (the prior marginals restart at
 // every job).  Queued on s_main.
 int load_frames(nfhmm_ctx* c, int t0, int T, const float* const* Vs, int on_device,
                 const int* frames, int n) {

@@ -85,6 +85,7 @@ struct Maps {
 
 struct TcArgs {
   int rows, cols, kdim;           // T, output columns, K
+  int row_off;                    // first row (one item: rows [row_off, row_off + rows))
   int nbpart;
   const float* V;                 // RATIO: T x ldv
   int ldv;
@@ -166,7 +167,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     if (lane == 0) {
       long long it = 0;   // K-blocks issued over all of this CTA's tiles
       for (int tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x) {
-        const int row0 = (tile / ncol) * BM, col0 = (tile % ncol) * BN;
+        const int row0 = p.row_off + (tile / ncol) * BM, col0 = (tile % ncol) * BN;
         const int bitem = p.brows ? row0 / p.brows : 0;   // batch item of this row tile
         const int bcol0 = col0 + bitem * p.bstride;         // its first B row
         for (int kb = 0; kb < nkb; ++kb, ++it) {
@@ -249,12 +250,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     const int nmain = nkb < Cfg::NMAIN ? nkb : Cfg::NMAIN;   // accumulators written
     int j = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++j) {
-      const int row0 = (tile / ncol) * BM, col0 = (tile % ncol) * BN;
+      const int row0 = p.row_off + (tile / ncol) * BM, col0 = (tile % ncol) * BN;
       const int bitem = p.brows ? row0 / p.brows : 0;
       const int r = quarter * 32 + lane;
       const int t = row0 + r;
       const int tl = t - bitem * p.brows;               // row within its batch item
-      const bool rv = p.brows ? tl < p.bvalid : t < p.rows;
+      const bool rv = p.brows ? tl < p.bvalid : t < p.row_off + p.rows;
       const int cbase = col0 + half * HALF;
       if (!mbar_wait(accum, (uint32_t)j & 1)) {
         give_up();
@@ -552,9 +553,10 @@ int tc_refresh_beta(TcPlan& p, cudaStream_t st) {
   return 2;
 }
 
-int tc_gemm1(TcPlan& p, int rows, double* bpart, cudaStream_t st) {
+int tc_gemm1(TcPlan& p, int row_off, int rows, double* bpart, cudaStream_t st) {
   TcArgs a{};
   a.rows = rows;
+  a.row_off = row_off;
   a.cols = p.Fp;
   a.kdim = p.Mp;
   a.nbpart = p.nbpart;
@@ -579,9 +581,10 @@ int tc_gemm1(TcPlan& p, int rows, double* bpart, cudaStream_t st) {
   return 1;
 }
 
-int tc_gemm2(TcPlan& p, int rows, cudaStream_t st) {
+int tc_gemm2(TcPlan& p, int row_off, int rows, cudaStream_t st) {
   TcArgs a{};
   a.rows = rows;
+  a.row_off = row_off;
   a.cols = p.Mp;
   a.kdim = p.Fp;
   a.w = p.w32;

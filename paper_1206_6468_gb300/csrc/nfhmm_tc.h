@@ -70,9 +70,9 @@ int tc_plan(TcPlan& p, int precision, int T, int M, int Mp, int F, int Fp, const
             unsigned* err, cudaStream_t st);
 // Refresh the operand copies of beta from WM/WF (returns launches).
 int tc_refresh_beta(TcPlan& p, cudaStream_t st);
-// rows: frames [0, rows) of the plan's T (returns launches, or -1)
-int tc_gemm1(TcPlan& p, int rows, double* bpart, cudaStream_t st);
-int tc_gemm2(TcPlan& p, int rows, cudaStream_t st);
+// frames [row_off, row_off + rows) of the plan's T (returns launches, or -1)
+int tc_gemm1(TcPlan& p, int row_off, int rows, double* bpart, cudaStream_t st);
+int tc_gemm2(TcPlan& p, int row_off, int rows, cudaStream_t st);
 void tc_free(TcPlan& p);
 
 }  // namespace nfhmm
