@@ -20,6 +20,12 @@ frame-iterations per step = T * 50.
 * ``cpu_baseline``: the FP64 oracle on a bounded sample of the same
   workload, timed on this host's cores (rank 0, one GPU only).
 
+The default run (one GPU) adds three sub-lines to the same JSON line, each
+timed the same way with its own clock record: ``batched_fp32`` and
+``batched_bf16`` (64 jobs, T ~ U[500, 8000], one batch; the BF16 form is
+the precision form of the contractions) and ``serving`` (Poisson arrivals
+at 200 jobs/s for 5 s through continuous batching, with p50/p99 latency).
+
 ``--impl reference`` times the FP64 oracle alone (the reference arm).
 Multi-GPU (torchrun): each rank runs its own independent jobs (replicas, no
 collective on the data path); ``value`` is all ranks' frame-iterations over
@@ -79,6 +85,10 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-saturate", action="store_true",
                     help="serving: every request queued at the start (peak throughput)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="single workload only: skip the batched and serving sub-lines")
+    ap.add_argument("--extra-steps", type=int, default=4,
+                    help="timed steps of each batched sub-line (after 3 warm-up steps)")
     return ap.parse_args()
 
 
@@ -123,16 +133,23 @@ def max_over_ranks(x: float, world: int) -> float:
     return float(t.item())
 
 
-def load_peaks():
+def load_peaks(probe=None):
+    """Roofline denominators: MEASURED_PEAKS.json (else the fallback), and
+    the tensor-core rates measured in this run by nfhmm_mma_rate (probe)."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
         with open(path) as f:
             d = json.load(f)
-        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"],
-                "bf16_tflops_sustained": d.get("bf16_tflops_sustained", d["bf16_tflops"]),
-                "source": "measured"}
-    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
-            "source": "fallback"}
+        out = {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"],
+               "bf16_tflops_sustained": d.get("bf16_tflops_sustained", d["bf16_tflops"]),
+               "source": "measured"}
+    else:
+        out = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+               "source": "fallback"}
+    if probe:
+        out["tf32_probe"] = probe.get("tf32")
+        out["probe_record"] = probe
+    return out
 
 
 class ClockSampler:
@@ -187,6 +204,54 @@ class ClockSampler:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_sample_single_thread(seconds_hint: float = 8.0):
+    """The oracle timed with its BLAS held to one thread: a child process
+    started with OPENBLAS_NUM_THREADS=1 (the BLAS reads it at load time)."""
+    env = dict(os.environ)
+    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.oracle_sample(seconds_hint=%r)))" % (ROOT, seconds_hint))
+    try:
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                           timeout=120)
+        v, _, sample = json.loads(r.stdout.strip().splitlines()[-1])
+        return v, sample
+    except (OSError, subprocess.SubprocessError, ValueError, IndexError):
+        return None, None
+
+
+def cpu_baseline_record():
+    """The FP64 oracle on the host: all cores, and one BLAS thread."""
+    v, cores, sample = oracle_sample(seconds_hint=12.0)
+    v1, sample1 = oracle_sample_single_thread(seconds_hint=8.0)
+    rec = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+           "cpu_model": cpu_model(), "os_cpu_count": os.cpu_count()}
+    if v1 is not None:
+        rec["single_thread"] = {"value": v1, "unit": UNIT, "cores": 1,
+                                "blas_threads": "OPENBLAS_NUM_THREADS=1", "sample": sample1}
+    return rec
 
 
 def oracle_sample(seconds_hint: float = 20.0, sweeps: int = None):
@@ -312,6 +377,20 @@ def fb_serial_steps(longest, mode, L, G):
     return 2 * L + (G + -(-C // G) if G >= 2 else C), "scan"
 
 
+def tensor_peak(precision, peaks):
+    """(peak TFLOP/s, note) of a tensor-core contraction of this precision.
+    The split-TF32 (FP32) form runs tf32 MMAs: their rate measured in this run
+    by nfhmm_mma_rate, else the measured bf16 sustained rate x the nominal
+    1.1/2.25 tf32/bf16 ratio; it issues three tf32 MMAs per product, so its
+    own ceiling is a third of the peak (reported beside it)."""
+    if precision == "bf16":
+        return peaks["bf16_tflops_sustained"], f"{peaks['source']} bf16 sustained (MEASURED_PEAKS.json)"
+    if peaks.get("tf32_probe"):
+        return peaks["tf32_probe"], "tf32 MMA rate measured in this run (nfhmm_mma_rate, burst)"
+    return (peaks["bf16_tflops_sustained"] * TF32_OVER_BF16,
+            f"{peaks['source']} bf16 sustained x 1.1/2.25 (tf32)")
+
+
 def stage_rooflines(prof, T, S, N, K, F, precision, tc, peaks, fb_path=None):
     """Achieved against peak for every sweep stage, from the same live
     events (the contractions run beside the forward-backward, so their times
@@ -329,10 +408,14 @@ def stage_rooflines(prof, T, S, N, K, F, precision, tc, peaks, fb_path=None):
             continue
         bound_kind, amount, unit = stage_cost(st, q, precision, tc)
         avg_s = ms / 1e3 / inv
+        extra = {}
         if unit == "TFLOP/s":
             achieved = amount / avg_s / 1e12
             if bound_kind == "tensor":
-                peak = peaks["bf16_tflops_sustained"] * (1.0 if precision == "bf16" else TF32_OVER_BF16)
+                peak, _ = tensor_peak(precision, peaks)
+                if precision == "fp32":
+                    extra = {"mmas_per_product": 3, "split_tf32_ceiling": round(peak / 3, 1),
+                             "frac_of_split_ceiling": round(3 * achieved / peak, 4)}
             else:
                 peak = FP32_SIMT_PEAK_TFLOPS
         else:
@@ -340,13 +423,15 @@ def stage_rooflines(prof, T, S, N, K, F, precision, tc, peaks, fb_path=None):
             peak = peaks["hbm_gbs"]
         out[st] = {"bound": bound_kind, "achieved": round(achieved, 2), "peak": round(peak, 1),
                    "unit": unit, "frac": round(achieved / peak, 4), "ms": round(1e3 * avg_s, 4)}
+        out[st].update(extra)
         if st == "fb" and fb_path:
             out[st]["critical_path"] = {"form": fb_path[1], "serial_steps": int(fb_path[0]),
                                         "ns_per_step": round(1e9 * avg_s / fb_path[0], 1)}
     return out
 
 
-def roofline_of(prof, steps, T, S, N, K, F, precision, tc, peaks, sweeps_run):
+def roofline_of(prof, T, S, N, K, F, precision, tc, peaks, sweeps_run, traffic_workload=None,
+                fb_path=None):
     """Roofline object of the stage with the largest summed event time."""
     class _P:
         pass
@@ -359,8 +444,7 @@ def roofline_of(prof, steps, T, S, N, K, F, precision, tc, peaks, sweeps_run):
     if unit == "TFLOP/s":
         achieved = amount / avg_s / 1e12
         if bound_kind == "tensor":
-            peak = peaks["bf16_tflops_sustained"] * (1.0 if precision == "bf16" else TF32_OVER_BF16)
-            note = f"{peaks['source']} bf16 sustained" + ("" if precision == "bf16" else " x 1.1/2.25 (tf32)")
+            peak, note = tensor_peak(precision, peaks)
         else:
             peak = FP32_SIMT_PEAK_TFLOPS
             note = "derived FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 x 2.07 GHz"
@@ -368,25 +452,62 @@ def roofline_of(prof, steps, T, S, N, K, F, precision, tc, peaks, sweeps_run):
         achieved = amount / avg_s / 1e9
         peak = peaks["hbm_gbs"]
         note = f"{peaks['source']} HBM copy bandwidth"
-    return {"bound": bound_kind, "kernel": dom, "achieved": achieved, "peak": peak, "unit": unit,
-            "frac": achieved / peak, "traffic": None, "peak_source": note,
-            "launch_ms": 1e3 * avg_s, "launches_per_invocation": dom_launches / max(sweeps_run, 1),
-            "stage_ms_per_invocation": {s: round(prof[s][0] / max(prof[s][1], 1), 4)
-                                        for s in prof},
-            "timed_sweeps": TIMED_NOTE}
+    out = {"bound": bound_kind, "kernel": dom, "achieved": achieved, "peak": peak, "unit": unit,
+           "frac": achieved / peak,
+           "traffic": measured_traffic(dom, traffic_workload) if traffic_workload else None,
+           "peak_source": note, "launch_ms": 1e3 * avg_s,
+           "launches_per_invocation": dom_launches / max(sweeps_run, 1),
+           "stage_ms_per_invocation": {s: round(prof[s][0] / max(prof[s][1], 1), 4)
+                                       for s in prof},
+           "timed_sweeps": TIMED_NOTE}
+    if dom == "fb" and fb_path:
+        # a serial chain: its latency, not HBM, is what limits it
+        out["limit"] = {"kind": "serial chain (critical path)", "form": fb_path[1],
+                        "serial_frame_steps": int(fb_path[0]),
+                        "ns_per_step": round(1e9 * avg_s / fb_path[0], 1)}
+    return out
 
 
-def run_batched(args, rank, world, local):
-    """64 jobs of T ~ U[500, 8000] frames sharing one S2 N40 K10 F513 model,
-    run as one batch: one step = initial state + 50 sweeps + bound of all."""
+def timed_steps(fn, n, world, flush, stream):
+    """n steps of fn, each timed by CUDA events on the launching stream,
+    with L2 flushed (a 256 MB write) before each; barrier and synchronise on
+    both sides."""
     import torch
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(n)]
+    barrier(world)
+    torch.cuda.synchronize()
+    for e0, e1 in evs:
+        flush.zero_()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    return [e0.elapsed_time(e1) for e0, e1 in evs]
 
-    from paper_1206_6468_gb300 import nfhmm, synth
-    dev = torch.device("cuda", local)
-    torch.cuda.set_device(dev)
-    lengths = synth.batched_lengths(16 if args.ncu_case else 64, 500, 8000, seed=job_seed(rank))
+
+def batched_jobs(rank, n_jobs=64):
+    from paper_1206_6468_gb300 import synth
+    lengths = synth.batched_lengths(n_jobs, 500, 8000, seed=job_seed(rank))
     jobs = synth.make_jobs(2, 40, 10, 513, lengths, self_prob=0.95, energy_sigma=1.5,
                            seed=job_seed(rank))
+    return lengths, jobs
+
+
+def run_batched(args, rank, world, local, precision=None, data=None, steps=None, warmup=None):
+    """64 jobs of T ~ U[500, 8000] frames sharing one S2 N40 K10 F513 model,
+    run as one batch: one step = initial state + 50 sweeps + bound of all.
+    Returns the line (None for --ncu-case)."""
+    import torch
+
+    from paper_1206_6468_gb300 import nfhmm
+    precision = precision or args.precision
+    steps = steps or args.steps
+    warmup = max(3, warmup or args.warmup)
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    lengths, jobs = data or batched_jobs(rank, 16 if args.ncu_case else 64)
     f32 = {"V": jobs.stacked_V()}
     for k in ("W", "A", "pi"):
         f32[k] = np.ascontiguousarray(getattr(jobs, k), dtype=np.float32)
@@ -397,7 +518,7 @@ def run_batched(args, rank, world, local):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     ctx = nfhmm.VIContext(d_in["V"], d_in["W"], d_in["A"], d_in["pi"], jobs.S, jobs.N, jobs.K,
-                          precision=args.precision, job_frames=lengths.tolist())
+                          precision=precision, job_frames=lengths.tolist())
     sweeps = args.sweeps
     if args.ncu_case:
         # the form the bench runs (one sweep, the autotuner), or the one asked
@@ -409,9 +530,9 @@ def run_batched(args, rank, world, local):
             ctx.set_option("fb_mode", args.fb_mode)
         print("bound after 3 sweeps:", ctx.sweep(3, bound=True), flush=True)
         ctx.close()
-        return
+        return None
     # forward-backward geometry picked by the library's autotuner on these
-    # jobs (one sweep first: it times the forward-backward on its emissions)
+    # jobs (one sweep first: it times whole sweeps from the current state)
     ctx.sweep(1)
     tuned = ctx.autotune(reps=3)
 
@@ -427,52 +548,39 @@ def run_batched(args, rank, world, local):
 
     ctx.set_option("profile_stride", PROFILE_STRIDE)
     ctx.profile_enable(True)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step_device()
     torch.cuda.synchronize()
-
-    def timed(fn, n):
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(n)]
-        barrier(world)
-        torch.cuda.synchronize()
-        for e0, e1 in evs:
-            flush.zero_()
-            e0.record(stream)
-            fn()
-            e1.record(stream)
-        torch.cuda.synchronize()
-        barrier(world)
-        return [e0.elapsed_time(e1) for e0, e1 in evs]
-
     sampler = ClockSampler(local)
     sampler.start()
     for st in nfhmm.STAGES:
         ctx.profile_read(st, reset=True)
     l0 = ctx.kernel_launches()
-    ms = timed(step_device, args.steps)
+    ms = timed_steps(step_device, steps, world, flush, stream)
     launches = ctx.kernel_launches() - l0
     prof = {st: ctx.profile_read(st, reset=True) for st in nfhmm.STAGES}
     for _ in range(2):
         step_e2e()
-    ms_e2e = timed(step_e2e, args.steps)
+    ms_e2e = timed_steps(step_e2e, steps, world, flush, stream)
     ctx.profile_enable(False)
     clocks = sampler.stop()
     tot_ms = max_over_ranks(sum(ms), world)
     tot_e2e = max_over_ranks(sum(ms_e2e), world)
     fit = T * sweeps
-    peaks = load_peaks()
+    peaks = load_peaks(getattr(args, "_tensor_probe", None))
     tc = bool(ctx.query("tensor_cores"))
+    fb_path = fb_serial_steps(int(lengths.max()), ctx.query("fb_mode"), ctx.query("fb_chunk"),
+                              ctx.query("fb_group"))
     line = {
-        "metric": METRIC, "value": aggregate(fit, args.steps, world, tot_ms), "unit": UNIT,
-        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "bf16",
+        "metric": METRIC, "value": aggregate(fit, steps, world, tot_ms), "unit": UNIT,
+        "n_gpus": world, "steps": steps, "warmup": warmup,
+        "ms_per_step": tot_ms / steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if precision == "fp32" else "bf16",
         "data": "synthetic",
-        "config": {"workload": f"batched: 64 jobs, T ~ U[500, 8000] (sum {T}), S2 N40 K10 F513, "
-                               f"{sweeps} sweeps + bound per step",
+        "config": {"workload": f"batched: {len(lengths)} jobs, T ~ U[500, 8000] (sum {T}), "
+                               f"S2 N40 K10 F513, {sweeps} sweeps + bound per step",
                    "jobs": len(lengths), "frames": T, "sweeps_per_step": sweeps,
-                   "precision": args.precision, "contractions": "tcgen05" if tc else "fp32 SIMT",
+                   "precision": precision, "contractions": "tcgen05" if tc else "fp32 SIMT",
                    "l2": "inputs larger than L2; flushed between steps (256 MB write)",
                    "fb_geometry": {"chunk": tuned["fb_chunk"], "group": tuned["fb_group"],
                                    "mode": "sequential x%d" % tuned["fb_mode"]
@@ -480,28 +588,28 @@ def run_batched(args, rank, world, local):
                                    "picked_by": "nfhmm_autotune",
                                    "sweep_us": round(tuned["us"], 1)},
                    "parallelism": f"replicas x{world}"},
-        "roofline": dict(roofline_of(prof, args.steps, T, 2, 40, 10, 513, args.precision, tc,
-                                     peaks, args.steps * sweeps), fb_chunk=ctx.query("fb_chunk")),
-        "roofline_by_stage": stage_rooflines(
-            prof, T, 2, 40, 10, 513, args.precision, tc, peaks,
-            fb_serial_steps(int(lengths.max()), ctx.query("fb_mode"), ctx.query("fb_chunk"),
-                            ctx.query("fb_group"))),
-        "e2e": {"value": aggregate(fit, args.steps, world, tot_e2e), "unit": UNIT,
+        "roofline": roofline_of(prof, T, 2, 40, 10, 513, precision, tc, peaks, steps * sweeps,
+                                fb_path=fb_path),
+        "roofline_by_stage": stage_rooflines(prof, T, 2, 40, 10, 513, precision, tc, peaks,
+                                             fb_path),
+        "e2e": {"value": aggregate(fit, steps, world, tot_e2e), "unit": UNIT,
                 "h2d_bytes_per_step": int(sum(v.numel() * 4 for v in h_in.values())),
                 "d2h_bytes_per_step": int(h_dhat.numel() * 4 + 8)},
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
     ctx.close()
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    del d_in, h_in, h_dhat, flush
+    torch.cuda.empty_cache()
+    return line
 
 
 def run_serving(args, rank, world, local):
     """Continuous batching: requests arrive as a Poisson process (rate
     --serve-rate per second for --serve-seconds), T log-uniform in
     [200, 10000], half on an S=2 and half on an S=3 model (N40 K10 F513);
-    each runs until its bound moves by less than 1e-5 relative or 100 sweeps."""
+    each runs until its bound moves by less than 1e-5 relative or 100 sweeps.
+    Returns the line."""
     import torch
 
     from paper_1206_6468_gb300 import nfhmm, synth
@@ -567,7 +675,9 @@ def run_serving(args, rank, world, local):
                    "requests": n_req, "completed": len(ok), "frames": int(Ts.sum()),
                    "batch_capacity_frames": capacity, "max_jobs": max_jobs,
                    "precision": args.precision, "parallelism": f"replicas x{world}",
-                   "fb_mode": "sequential x%d" % args.fb_mode if args.fb_mode else "scan"},
+                   "fb_mode": "sequential x%d" % args.fb_mode if args.fb_mode else "scan",
+                   "timing": "host wall clock from the first arrival to the last result "
+                             "(latency = result time - arrival time)"},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "max": float(lat.max())},
         "sweeps": {"mean": float(np.mean([r["sweeps"] for r in ok])),
@@ -580,8 +690,7 @@ def run_serving(args, rank, world, local):
     }
     for b in bs:
         b.close()
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
 
 
 def run_exact(args, rank, world, local):
@@ -646,21 +755,9 @@ def run_exact(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
-def main():
-    args = parse()
-    rank, world, local = dist_setup()
-    if args.impl == "reference":
-        run_reference(args, rank, world)
-        return
-    if args.workload == "batched":
-        run_batched(args, rank, world, local)
-        return
-    if args.workload == "serving":
-        run_serving(args, rank, world, local)
-        return
-    if args.workload == "exact":
-        run_exact(args, rank, world, local)
-        return
+def run_single(args, rank, world, local):
+    """One paper-size job per step: initial state, 50 sweeps, bound.  Returns
+    the line (None for --ncu-case)."""
     import torch
 
     from paper_1206_6468_gb300 import nfhmm, synth
@@ -681,7 +778,7 @@ def main():
     if args.ncu_case:
         print("bound after 3 sweeps:", ctx.sweep(3, bound=True), flush=True)
         ctx.close()
-        return
+        return None
     # forward-backward geometry picked by the library's autotuner (whole sweeps
     # from a saved state, before the warm-up; the step re-initialises anyway)
     ctx.sweep(1)
@@ -705,33 +802,19 @@ def main():
         step_device()
     torch.cuda.synchronize()
 
-    def timed(step_fn, nsteps):
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(nsteps)]
-        barrier(world)
-        torch.cuda.synchronize()
-        for e0, e1 in evs:
-            flush.zero_()
-            e0.record(stream)
-            step_fn()
-            e1.record(stream)
-        torch.cuda.synchronize()
-        barrier(world)
-        return [e0.elapsed_time(e1) for e0, e1 in evs]
-
     sampler = ClockSampler(local if "CUDA_VISIBLE_DEVICES" not in os.environ else
                            int(os.environ["CUDA_VISIBLE_DEVICES"].split(",")[local]))
     sampler.start()
     for st in nfhmm.STAGES:
         ctx.profile_read(st, reset=True)
     l0 = ctx.kernel_launches()
-    ms = timed(step_device, args.steps)
+    ms = timed_steps(step_device, args.steps, world, flush, stream)
     launches = ctx.kernel_launches() - l0
     prof = {st: ctx.profile_read(st, reset=True) for st in nfhmm.STAGES}
     # end-to-end through host buffers (profiling on, as above)
     for _ in range(2):
         step_e2e()
-    ms_e2e = timed(step_e2e, args.steps)
+    ms_e2e = timed_steps(step_e2e, args.steps, world, flush, stream)
     ctx.profile_enable(False)
     clocks = sampler.stop()
 
@@ -741,26 +824,10 @@ def main():
     value = aggregate(frames_its, args.steps, world, tot_ms)
     e2e_value = aggregate(frames_its, args.steps, world, tot_e2e)
 
-    peaks = load_peaks()
+    peaks = load_peaks(getattr(args, "_tensor_probe", None))
     tc = bool(ctx.query("tensor_cores"))
-    dom = max((s for s in prof if s != "init"), key=lambda s: prof[s][0])
-    dom_ms, dom_inv, dom_launches = prof[dom]
-    bound_kind, amount, unit = stage_cost(dom, p, args.precision, tc)
-    avg_s = dom_ms / 1e3 / max(dom_inv, 1)
-    if unit == "TFLOP/s":
-        achieved = amount / avg_s / 1e12
-        if bound_kind == "tensor":
-            peak = peaks["bf16_tflops_sustained"] * (1.0 if args.precision == "bf16" else TF32_OVER_BF16)
-            peak_note = f"{peaks['source']} bf16 sustained" + ("" if args.precision == "bf16" else " x 1.1/2.25 (tf32)")
-        else:
-            peak = FP32_SIMT_PEAK_TFLOPS
-            peak_note = "derived FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 x 2.07 GHz"
-    else:
-        achieved = amount / avg_s / 1e9
-        peak = peaks["hbm_gbs"]
-        peak_note = f"{peaks['source']} HBM copy bandwidth"
-    stage_ms = {s: round(prof[s][0] / max(prof[s][1], 1), 4) for s in prof}
-
+    fb_path = fb_serial_steps(p.T, ctx.query("fb_mode"), ctx.query("fb_chunk"),
+                              ctx.query("fb_group"))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
@@ -776,29 +843,79 @@ def main():
                                    "picked_by": "nfhmm_autotune",
                                    "sweep_us": round(tuned["us"], 1)},
                    "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": bound_kind, "kernel": dom, "achieved": achieved, "peak": peak,
-                     "unit": unit, "frac": achieved / peak,
-                     "traffic": measured_traffic(dom, f"paper_size_{args.precision}"),
-                     "peak_source": peak_note, "launch_ms": 1e3 * avg_s,
-                     "launches_per_invocation": dom_launches / max(args.steps * sweeps, 1),
-                     "stage_ms_per_invocation": stage_ms, "timed_sweeps": TIMED_NOTE,
-                     "fb_chunk": ctx.query("fb_chunk")},
-        "roofline_by_stage": stage_rooflines(
-            prof, p.T, p.S, p.N, p.K, p.F, args.precision, tc, peaks,
-            fb_serial_steps(p.T, ctx.query("fb_mode"), ctx.query("fb_chunk"),
-                            ctx.query("fb_group"))),
+        "roofline": dict(roofline_of(prof, p.T, p.S, p.N, p.K, p.F, args.precision, tc, peaks,
+                                     args.steps * sweeps, f"paper_size_{args.precision}",
+                                     fb_path), fb_chunk=ctx.query("fb_chunk")),
+        "roofline_by_stage": stage_rooflines(prof, p.T, p.S, p.N, p.K, p.F, args.precision, tc,
+                                             peaks, fb_path),
+        "tensor_peaks_measured": peaks.get("probe_record"),
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": int(sum(v.numel() * 4 for v in h_in.values())),
                 "d2h_bytes_per_step": int(h_dhat.numel() * 4 + 8)},
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, cores, sample = oracle_sample(seconds_hint=15.0)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": sample}
     ctx.close()
-    if rank == 0:
+    del d_in, h_in, h_dhat, flush
+    torch.cuda.empty_cache()
+    return line
+
+
+SUB_KEYS = ("value", "unit", "ms_per_step", "steps", "warmup", "dtype", "config", "e2e",
+            "roofline", "roofline_by_stage", "gpu_launches", "clocks", "latency_ms", "sweeps")
+
+
+def sub_line(line):
+    return {k: line[k] for k in SUB_KEYS if k in line}
+
+
+def measure_tensor_peaks():
+    """The tensor cores' dense rates measured by the library (tf32, bf16)."""
+    from paper_1206_6468_gb300 import nfhmm
+    rec = {}
+    for prec in ("fp32", "bf16"):
+        try:
+            rec["tf32" if prec == "fp32" else "bf16"] = round(nfhmm.mma_rate(prec), 1)
+        except nfhmm.NfhmmError:
+            pass
+    rec["how"] = ("nfhmm_mma_rate: every SM issues back-to-back 128x256 MMAs (K 8 tf32 / 16 "
+                  "bf16) from shared memory into TMEM; CUDA events over 5 launches")
+    return rec
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if args.workload == "exact":
+        run_exact(args, rank, world, local)
+        return
+    if not args.ncu_case:
+        import torch
+        torch.cuda.set_device(torch.device("cuda", local))
+        args._tensor_probe = measure_tensor_peaks()
+    if args.workload == "batched":
+        line = run_batched(args, rank, world, local)
+    elif args.workload == "serving":
+        line = run_serving(args, rank, world, local)
+    else:
+        line = run_single(args, rank, world, local)
+        if line is not None and world == 1 and not args.no_extras:
+            # the batched (FP32 and BF16) and serving forms, each timed as its own line
+            data = batched_jobs(rank)
+            b32 = run_batched(args, rank, world, local, "fp32", data, args.extra_steps, 3)
+            b16 = run_batched(args, rank, world, local, "bf16", data, args.extra_steps, 3)
+            del data
+            sv = run_serving(args, rank, world, local)
+            line["batched_fp32"] = sub_line(b32)
+            line["batched_bf16"] = sub_line(b16)
+            line["serving"] = sub_line(sv)
+            line["bf16_batched_over_fp32_single"] = b16["value"] / line["value"]
+        if line is not None and rank == 0 and world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline_record()
+    if line is not None and rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

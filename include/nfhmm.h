@@ -262,6 +262,20 @@ NFHMM_API int nfhmm_job_posteriors(nfhmm_ctx *c, long long job_id, float *dhat, 
  *                          Its latency is the longest job's frames; it suits
  *                          batches of many jobs.  The first use allocates
  *                          S x T x (N + 68) floats (NFHMM_ENOMEM if no room)
+ *   NFHMM_OPT_TEST_WAIT_TIMEOUT  test hook of the failure path (tensor-core
+ *                          contexts only): v in [1, 10^9] makes the next
+ *                          sweep's reconstruction contraction first wait v
+ *                          nanoseconds on a barrier that nothing completes.
+ *                          The wait gives up as every bounded device wait
+ *                          does: its block sets the error word, waits for
+ *                          its own copies and tensor-core operations in
+ *                          flight, frees its tensor memory and returns, and
+ *                          the next call that synchronises (a bound, a host
+ *                          output) returns NFHMM_ETIMEOUT.  That sweep is
+ *                          launched directly, not from a captured graph, and
+ *                          its state is not usable (restore one with
+ *                          nfhmm_set_state); the context stays usable.
+ *                          0 clears a pending hook
  */
 #define NFHMM_OPT_FB_CHUNK    0
 #define NFHMM_OPT_FB_PRODUCTS 1
@@ -269,6 +283,7 @@ NFHMM_API int nfhmm_job_posteriors(nfhmm_ctx *c, long long job_id, float *dhat, 
 #define NFHMM_OPT_FB_GROUP    3
 #define NFHMM_OPT_PROFILE_STRIDE 4
 #define NFHMM_OPT_FB_MODE     5
+#define NFHMM_OPT_TEST_WAIT_TIMEOUT 6
 
 /*
  * nfhmm_autotune -- choose the forward-backward form and geometry for the
@@ -375,8 +390,14 @@ NFHMM_API const char *nfhmm_last_error(void);
  * chains (the q(D^(s)) step of Section 3.2), all pointers on device:
  * phi S x T x N (emissions exp(phi)), A S x N x N row-stochastic, pi S x N;
  * writes dhat S x T x N and logZ[S] (FP64 log normalisers).  chunk_len: frames
- * per time chunk of the parallel-in-time form (0 = library default, >= T =
- * one serial chunk).  Allocates its scratch on the stream.  Asynchronous.
+ * per time chunk of the parallel-in-time form (0 = library default; values
+ * above 128 are clamped to 128 and values above T to T, so T > 128 always
+ * gives ceil(T / L) chunks).  Allocates its scratch on the stream.
+ * Asynchronous.  A failure on the device has no context to report it
+ * through: if a bounded device wait gave up, or a chain's normaliser
+ * vanished (data of probability zero under the chain: a transition or an
+ * emission that excludes every state), every logZ[s] is set to NaN and d-hat
+ * is undefined; check logZ once the stream has been synchronised.
  */
 NFHMM_API int nfhmm_forward_backward(int S, int N, int T, const float *phi, const float *A,
                            const float *pi, float *dhat, double *logZ, int chunk_len,
@@ -405,11 +426,26 @@ NFHMM_API int nfhmm_forward_backward(int S, int N, int T, const float *phi, cons
  * share the array and it keeps the last call's contents: calls whose work
  * overlaps on the GPU (different streams, or different host threads without
  * ordering) race on it.  Asynchronous; inputs and outputs on the device.
+ * Device-side failures are reported as by nfhmm_forward_backward: every
+ * logZ[s] NaN.
  */
 #define NFHMM_NOALLOC_SCRATCH_BYTES (32u << 20)
 NFHMM_API int nfhmm_forward_backward_noalloc(int S, int N, int T, const float *phi,
                                              const float *A, const float *pi, float *dhat,
                                              double *logZ, int chunk_len, void *cuda_stream);
+
+/*
+ * nfhmm_mma_rate -- the measured dense rate (TFLOP/s, FP32 accumulate) of
+ * this GPU's tcgen05 tensor cores for the operand kind of a precision:
+ * NFHMM_FP32 times kind::tf32 MMAs (one pass; the split-TF32 contractions
+ * issue three per product, so their ceiling is a third of it), NFHMM_BF16
+ * kind::f16 MMAs on bf16 operands.  Every SM issues back-to-back 128 x 256
+ * MMAs (K = 8 tf32 or 16 bf16 per instruction) from shared memory into one
+ * TMEM accumulator; the launches are timed with CUDA events on cuda_stream.
+ * The paper has no counterpart: this is the denominator of the contractions'
+ * roofline.  Allocates 4 bytes of device memory; synchronises.
+ */
+NFHMM_API int nfhmm_mma_rate(int precision, double *tflops_out, void *cuda_stream);
 
 /*
  * nfhmm_digamma -- the library's device psi and exp(psi) on n values x >= 1

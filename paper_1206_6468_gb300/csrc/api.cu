@@ -119,6 +119,7 @@ struct nfhmm_ctx {
   FBArgs fb{};
   TcPlan tc{};
   bool use_tc = false;
+  unsigned long long inject_wait_ns = 0;   // test hook for the next sweep (NFHMM_OPT_TEST_WAIT_TIMEOUT)
   double konst = 0.0;
   // host staging (pinned)
   double* h_bound = nullptr;  // max_jobs + 1
@@ -273,16 +274,16 @@ int sync_check(nfhmm_ctx* c) {
 
 // Reconstruction + ratio (GEMM1) and back-projection + counts (GEMM2) from
 // the weights in w32 (and the operand copies of the tensor-core path), for
-// frames [t0, t0 + rows).  The tensor-core form runs from frame 0 only.
+// frames [t0, t0 + rows); both forms take the row offset.  reserve: SMs the
+// persistent tensor-core grids leave to a kernel running beside them.
 int contract(nfhmm_ctx* c, bool want_bpart, bool init, int t0, int rows,
-             cudaStream_t on = nullptr) {
+             cudaStream_t on = nullptr, int reserve = 0) {
   cudaStream_t st = on ? on : c->s_main;
   if (rows <= 0) return NFHMM_OK;
   // the sweep's contractions run on the tensor cores; so does the initial
   // state's (w = 1 on frames [t0, t0 + rows)) in split-TF32 mode, whose
   // accuracy is FP32's (BF16 contexts keep the FP32 CUDA-core initial state)
   if (c->use_tc && (!init || c->tc.w_format == WF_TF32X2)) {
-    const int reserve = c->tc.sm_reserve;
     if (init) {
       // the operand copies of the initial w, on the frames being initialised;
       // nothing runs beside these contractions
@@ -291,20 +292,19 @@ int contract(nfhmm_ctx* c, bool want_bpart, bool init, int t0, int rows,
       launch_split_tf32(c->w32 + o, reinterpret_cast<float*>(c->tc.w_hi) + o,
                         reinterpret_cast<float*>(c->tc.w_lo) + o, (size_t)rows * c->Mp, st);
       stage_end(c, NFHMM_STAGE_INIT, st, 1);
-      c->tc.sm_reserve = 0;
+      reserve = 0;
     }
     const int stage1 = init ? NFHMM_STAGE_INIT : NFHMM_STAGE_GEMM1;
     const int stage2 = init ? NFHMM_STAGE_INIT : NFHMM_STAGE_GEMM2;
     stage_begin(c, stage1, st);
-    const int n1 = tc_gemm1(c->tc, t0, rows, want_bpart ? c->bpart : nullptr, st);
+    const int n1 = tc_gemm1(c->tc, t0, rows, want_bpart ? c->bpart : nullptr, reserve, st);
     if (n1 >= 0) stage_end(c, stage1, st, n1);
     int n2 = -1;
     if (n1 >= 0) {
       stage_begin(c, stage2, st);
-      n2 = tc_gemm2(c->tc, t0, rows, st);
+      n2 = tc_gemm2(c->tc, t0, rows, reserve, st);
       if (n2 >= 0) stage_end(c, stage2, st, n2);
     }
-    c->tc.sm_reserve = reserve;
     if (n1 < 0 || n2 < 0) return fail(NFHMM_ECUDA, "tensor-core contraction: " + tc_last_error());
     return NFHMM_OK;
   }
@@ -386,8 +386,10 @@ int one_sweep(nfhmm_ctx* c, bool want_bpart, bool keep_alpha) {
   CK(cudaStreamWaitEvent(c->s_aux, c->ev_fork, 0));
   // the sequential forward-backward holds a few SMs for the whole sweep: the
   // persistent contractions size their grids to the others
-  c->tc.sm_reserve = c->fb.seq > 0 ? fb_seq_blocks(d.S * c->fb.nchains, c->fb.seq, d.N) : 0;
-  int rc = contract(c, want_bpart, false, 0, c->T_active, c->s_aux);
+  const int reserve = c->fb.seq > 0 ? fb_seq_blocks(d.S * c->fb.nchains, c->fb.seq, d.N) : 0;
+  c->tc.inject_wait_ns = c->inject_wait_ns;   // the test hook, once
+  c->inject_wait_ns = 0;
+  int rc = contract(c, want_bpart, false, 0, c->T_active, c->s_aux, reserve);
   if (rc) return rc;
   stage_begin(c, NFHMM_STAGE_FB, c->s_main);
   int nfb = 0;
@@ -923,7 +925,9 @@ int sweeps_direct(nfhmm_ctx* c, int n, bool want_bpart, long long first = 0,
 // turn; an instance's previous events are read before it is launched again).
 int run_graph(nfhmm_ctx* c, bool want_bpart, long long index, bool keep_alpha);
 int run_sweeps(nfhmm_ctx* c, int n, bool want_bpart) {
-  if (!c->use_graphs || c->T_active == 0 || n < 1) return sweeps_direct(c, n, want_bpart);
+  // a sweep carrying the wait hook is launched directly (a graph would keep it)
+  if (!c->use_graphs || c->T_active == 0 || n < 1 || c->inject_wait_ns)
+    return sweeps_direct(c, n, want_bpart);
   for (int i = 0; i < n; ++i) {
     const int rc = run_graph(c, want_bpart && i == n - 1, i, i == n - 1);
     if (rc) return rc;
@@ -1347,6 +1351,13 @@ int nfhmm_set_option(nfhmm_ctx* c, int key, long long value) {
         return fail(NFHMM_EINVAL, "forward-backward mode must be 0 (scan) or 1..64 (sequential)");
       return set_fb_mode(c, (int)value);
     }
+    case NFHMM_OPT_TEST_WAIT_TIMEOUT: {
+      if (!c->use_tc) return fail(NFHMM_EINVAL, "the wait hook needs a tensor-core context");
+      if (value < 0 || value > 1000000000)
+        return fail(NFHMM_EINVAL, "wait hook must be 0 or 1..10^9 nanoseconds");
+      c->inject_wait_ns = (unsigned long long)value;
+      return NFHMM_OK;
+    }
     case NFHMM_OPT_PROFILE_STRIDE: {
       if (value < 1 || value > 1000000) return fail(NFHMM_EINVAL, "profile stride must be >= 1");
       c->prof_stride = (int)value;
@@ -1573,7 +1584,11 @@ int nfhmm_forward_backward(int S, int N, int T, const float* phi, const float* A
   fb_carve_scratch(a, scratch);
   a.err = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(scratch) + bytes - 256);
   CK(cudaMemsetAsync(a.err, 0, 4, st));
-  const cudaError_t le = launch_fb(a, st, nullptr);
+  cudaError_t le = launch_fb(a, st, nullptr);
+  if (le == cudaSuccess) {
+    launch_flag_errors(a.err, logZ, S, st);   // a device-side failure: logZ NaN
+    le = cudaGetLastError();
+  }
   CK(cudaFreeAsync(scratch, st));
   CK(le);
   return NFHMM_OK;

@@ -98,6 +98,10 @@ int nfhmm_forward_backward_noalloc(int S, int N, int T, const float* phi, const 
   if (e != cudaSuccess) return fail(NFHMM_ECUDA, cudaGetErrorString(e));
   e = launch_fb(a, st, nullptr);
   if (e != cudaSuccess) return fail(NFHMM_ECUDA, cudaGetErrorString(e));
+  // the error word stays in the shared array: a set word turns logZ into NaN
+  launch_flag_errors(a.err, logZ, S, st);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(NFHMM_ECUDA, cudaGetErrorString(e));
   return NFHMM_OK;
 }
 

@@ -405,6 +405,18 @@ void launch_sep_mask(const float* V, int Fp, float* out, int S, int T, int F, cu
 }
 
 // ----------------------------------------------------------------- digamma
+// A stateless forward-backward has no context to carry its error word back
+// to the caller: a set word turns its log normalisers into NaN.
+__global__ void k_flag_errors(const unsigned* err, double* logZ, int n) {
+  if (*err == 0u) return;
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    logZ[i] = __longlong_as_double(0x7ff8000000000000ll);
+}
+
+void launch_flag_errors(const unsigned* err, double* logZ, int n, cudaStream_t st) {
+  k_flag_errors<<<1, 32, 0, st>>>(err, logZ, n);
+}
+
 __global__ void k_digamma(const float* x, float* psi, float* w, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x) {

@@ -101,6 +101,10 @@ struct TcArgs {
   // of which the first bvalid are real; item b reads B rows from b * bstride
   // on, and V (RATIO) is shared by the items.  brows = 0: one item.
   int brows, bvalid, bstride;
+  // test hook, 0 in normal use: the MMA thread first waits this many
+  // nanoseconds on a barrier nothing arrives on, so that the wait gives up
+  // and the CTA takes its wind-down path (error word ERR_TIMEOUT)
+  unsigned long long inject_wait_ns;
 };
 
 // ------------------------------------------------------------------ kernel
@@ -123,7 +127,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   uint64_t* accum = empty + STAGES;        // MMA -> epilogue: a tile's accumulator is complete
   uint64_t* tmem_free = accum + 1;         // epilogue -> MMA: it has been read out
   uint64_t* drain = tmem_free + 1;         // the MMA thread's last commit (before TMEM is freed)
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  uint64_t* never = drain + 1;             // test hook: a barrier nothing arrives on
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(never + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -139,6 +144,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     mbar_init(accum, 1);
     mbar_init(tmem_free, EPI_WARPS);
     mbar_init(drain, 1);
+    mbar_init(never, 1);
     *abort_flag = 0;
     fence_barrier_init();
   }
@@ -172,7 +178,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         const int bcol0 = col0 + bitem * p.bstride;         // its first B row
         for (int kb = 0; kb < nkb; ++kb, ++it) {
           const int s = (int)(it % STAGES);
-          if (it >= STAGES && !mbar_wait(&empty[s], (uint32_t)((it / STAGES) - 1) & 1)) {
+          if (it >= STAGES &&
+              !mbar_wait(&empty[s], (uint32_t)((it / STAGES) - 1) & 1, abort_flag)) {
             give_up();
             break;
           }
@@ -199,9 +206,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       constexpr uint32_t ID = idesc<KIND>(BM, BN);
       long long it = 0;
       int j = 0;   // this CTA's tile count
+      if (p.inject_wait_ns && !mbar_wait(never, 0, abort_flag, p.inject_wait_ns)) give_up();
       for (int tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x, ++j) {
         // the previous tile's accumulator has been read out of TMEM
-        if (j > 0 && !mbar_wait(tmem_free, (uint32_t)(j - 1) & 1)) {
+        if (j > 0 && !mbar_wait(tmem_free, (uint32_t)(j - 1) & 1, abort_flag)) {
           give_up();
           break;
         }
@@ -209,7 +217,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         bool ok = true;
         for (int kb = 0; kb < nkb; ++kb, ++it) {
           const int s = (int)(it % STAGES);
-          if (*abort_flag || !mbar_wait(&full[s], (uint32_t)(it / STAGES) & 1)) {
+          if (*abort_flag || !mbar_wait(&full[s], (uint32_t)(it / STAGES) & 1, abort_flag)) {
             give_up();
             ok = false;
             break;
@@ -257,7 +265,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       const int tl = t - bitem * p.brows;               // row within its batch item
       const bool rv = p.brows ? tl < p.bvalid : t < p.row_off + p.rows;
       const int cbase = col0 + half * HALF;
-      if (!mbar_wait(accum, (uint32_t)j & 1)) {
+      if (!mbar_wait(accum, (uint32_t)j & 1, abort_flag)) {
         give_up();
         break;
       }
@@ -438,21 +446,38 @@ bool make_map(CUtensorMap* m, const void* base, int elem_bytes, int inner, int o
   return true;
 }
 
+constexpr int kMaxDevices = 64;
+
+// Per device: the SM count, and whether a kernel's shared-memory opt-in has
+// been made there (function attributes are per device).
+int sm_count(int dev) {
+  static int sms[kMaxDevices] = {};
+  if (dev < 0 || dev >= kMaxDevices) return 1;
+  if (sms[dev] == 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+      n = 1;
+    sms[dev] = n;
+  }
+  return sms[dev];
+}
+
 template <int KIND, int BN, int EPI>
 cudaError_t launch_gemm(const Maps& maps, const TcArgs& a, cudaStream_t st, int reserve = 0) {
   using Cfg = TileCfg<KIND, BN>;
-  static cudaError_t attr = cudaErrorNotReady;
-  if (attr == cudaErrorNotReady)
-    attr = cudaFuncSetAttribute(k_tc_gemm<KIND, BN, EPI>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
-  if (attr != cudaSuccess) return attr;
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
-      sms = 1;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  static cudaError_t attr[kMaxDevices];
+  static bool attr_set[kMaxDevices] = {};
+  if (!attr_set[dev]) {
+    attr[dev] = cudaFuncSetAttribute(k_tc_gemm<KIND, BN, EPI>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+    attr_set[dev] = true;
   }
+  if (attr[dev] != cudaSuccess) return attr[dev];
+  const int sms = sm_count(dev);
   const long long tiles = (long long)((a.cols + BN - 1) / BN) * ((a.rows + BM - 1) / BM);
   if (tiles == 0) return cudaSuccess;
   // persistent: one CTA per SM, less the SMs reserved (at most half of them)
@@ -553,8 +578,10 @@ int tc_refresh_beta(TcPlan& p, cudaStream_t st) {
   return 2;
 }
 
-int tc_gemm1(TcPlan& p, int row_off, int rows, double* bpart, cudaStream_t st) {
+int tc_gemm1(TcPlan& p, int row_off, int rows, double* bpart, int reserve, cudaStream_t st) {
   TcArgs a{};
+  a.inject_wait_ns = p.inject_wait_ns;   // one-shot test hook
+  p.inject_wait_ns = 0;
   a.rows = rows;
   a.row_off = row_off;
   a.cols = p.Fp;
@@ -568,11 +595,11 @@ int tc_gemm1(TcPlan& p, int row_off, int rows, double* bpart, cudaStream_t st) {
   cudaError_t e;
   if (p.precision == 1) {
     a.out_bf16 = reinterpret_cast<__nv_bfloat16*>(p.q_hi);
-    e = launch_gemm<KIND_BF16, BN1, TEPI_RATIO>(*maps_of(p, 0), a, st, p.sm_reserve);
+    e = launch_gemm<KIND_BF16, BN1, TEPI_RATIO>(*maps_of(p, 0), a, st, reserve);
   } else {
     a.out_f32 = reinterpret_cast<float*>(p.q_hi);
     a.out_lo = reinterpret_cast<float*>(p.q_lo);
-    e = launch_gemm<KIND_TF32X3, BN1, TEPI_RATIO>(*maps_of(p, 0), a, st, p.sm_reserve);
+    e = launch_gemm<KIND_TF32X3, BN1, TEPI_RATIO>(*maps_of(p, 0), a, st, reserve);
   }
   if (e != cudaSuccess) {
     g_tc_err = cudaGetErrorString(e);
@@ -581,7 +608,7 @@ int tc_gemm1(TcPlan& p, int row_off, int rows, double* bpart, cudaStream_t st) {
   return 1;
 }
 
-int tc_gemm2(TcPlan& p, int row_off, int rows, cudaStream_t st) {
+int tc_gemm2(TcPlan& p, int row_off, int rows, int reserve, cudaStream_t st) {
   TcArgs a{};
   a.rows = rows;
   a.row_off = row_off;
@@ -594,9 +621,9 @@ int tc_gemm2(TcPlan& p, int row_off, int rows, cudaStream_t st) {
   a.err = p.err;
   cudaError_t e;
   if (p.precision == 1)
-    e = launch_gemm<KIND_BF16, BN2, TEPI_SCALE>(*maps_of(p, 1), a, st, p.sm_reserve);
+    e = launch_gemm<KIND_BF16, BN2, TEPI_SCALE>(*maps_of(p, 1), a, st, reserve);
   else
-    e = launch_gemm<KIND_TF32X3, BN2, TEPI_SCALE>(*maps_of(p, 1), a, st, p.sm_reserve);
+    e = launch_gemm<KIND_TF32X3, BN2, TEPI_SCALE>(*maps_of(p, 1), a, st, reserve);
   if (e != cudaSuccess) {
     g_tc_err = cudaGetErrorString(e);
     return -1;

@@ -170,6 +170,9 @@ void launch_sep_weights(const float* alpha, const double* v, int T, int M, int M
                         float* wts, cudaStream_t st);
 void launch_sep_mask(const float* V, int Fp, float* out, int S, int T, int F, cudaStream_t st);
 
+// Stateless calls: every logZ[i], i < n, becomes NaN if the error word is set.
+void launch_flag_errors(const unsigned* err, double* logZ, int n, cudaStream_t st);
+
 // Digamma test entry.
 void launch_digamma(const float* x, float* psi, float* w, size_t n, cudaStream_t st);
 

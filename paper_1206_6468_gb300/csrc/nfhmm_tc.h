@@ -24,7 +24,9 @@ struct TcPlan {
   const float* bF_src = nullptr;  // beta by frequency (Fp x Mp), float
   const float* bM_src = nullptr;  // beta by element (Mp x Fp), float
   int nbpart = 0;                 // columns of the bound-partial array
-  int sm_reserve = 0;             // SMs left free for a kernel running beside the contractions
+  // test hook: the next tc_gemm1 launch makes its MMA thread wait this long on
+  // a barrier nothing arrives on (see k_tc_gemm); cleared by that launch
+  unsigned long long inject_wait_ns = 0;
   const float* V = nullptr;
   const float* w32 = nullptr;
   float* Q = nullptr;
@@ -70,9 +72,11 @@ int tc_plan(TcPlan& p, int precision, int T, int M, int Mp, int F, int Fp, const
             unsigned* err, cudaStream_t st);
 // Refresh the operand copies of beta from WM/WF (returns launches).
 int tc_refresh_beta(TcPlan& p, cudaStream_t st);
-// frames [row_off, row_off + rows) of the plan's T (returns launches, or -1)
-int tc_gemm1(TcPlan& p, int row_off, int rows, double* bpart, cudaStream_t st);
-int tc_gemm2(TcPlan& p, int row_off, int rows, cudaStream_t st);
+// frames [row_off, row_off + rows) of the plan's T (returns launches, or -1);
+// reserve: SMs the persistent grid leaves free for a kernel running beside it
+// (at most half of them)
+int tc_gemm1(TcPlan& p, int row_off, int rows, double* bpart, int reserve, cudaStream_t st);
+int tc_gemm2(TcPlan& p, int row_off, int rows, int reserve, cudaStream_t st);
 void tc_free(TcPlan& p);
 
 }  // namespace nfhmm

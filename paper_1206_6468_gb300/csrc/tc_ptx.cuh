@@ -37,8 +37,12 @@ __device__ __forceinline__ unsigned long long globaltimer() {
   return t;
 }
 // Bounded wait for the phase with the given parity; false if it gave up
-// (after WAIT_NS nanoseconds or SPIN_LIMIT polls, whichever comes first).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// (after limit_ns nanoseconds or SPIN_LIMIT polls, whichever comes first, or
+// as soon as *abort is set, when abort is given: another warp of the block
+// gave up and the pipeline is winding down).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          const volatile int* abort = nullptr,
+                                          unsigned long long limit_ns = WAIT_NS) {
   const uint32_t addr = smem_u32(bar);
   const unsigned long long t0 = globaltimer();
   for (uint32_t i = 0; i < SPIN_LIMIT; ++i) {
@@ -50,7 +54,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
         : "r"(addr), "r"(parity)
         : "memory");
     if (done) return true;
-    if ((i & 255) == 255 && globaltimer() - t0 > WAIT_NS) return false;
+    if ((i & 255) == 255) {
+      if (abort && *abort) return false;
+      if (globaltimer() - t0 > limit_ns) return false;
+    }
   }
   return false;
 }

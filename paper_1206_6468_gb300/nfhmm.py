@@ -31,7 +31,7 @@ STAGES = {"weights": 0, "gemm1": 1, "gemm2": 2, "fb": 3, "bound": 4, "init": 5}
 QUERIES = {"tensor_cores": 0, "fb_chunk": 1, "sweeps_done": 2, "device_bytes": 3,
            "frame_capacity": 4, "max_jobs": 5, "fb_group": 6, "fb_mode": 7}
 OPTIONS = {"fb_chunk": 0, "fb_products": 1, "graphs": 2, "fb_group": 3, "profile_stride": 4,
-           "fb_mode": 5}
+           "fb_mode": 5, "test_wait_timeout": 6}
 FB_PRODUCTS = {"simt": 0, "tc": 1}
 PRECISIONS = {"fp32": FP32, "bf16": BF16, "fp32_simt": FP32_SIMT}
 
@@ -75,6 +75,7 @@ _sigs = {
     "nfhmm_forward_backward": (_i, [_i, _i, _i, _vp, _vp, _vp, _vp, _vp, _i, _vp]),
     "nfhmm_forward_backward_noalloc": (_i, [_i, _i, _i, _vp, _vp, _vp, _vp, _vp, _i, _vp]),
     "nfhmm_digamma": (_i, [_vp, _vp, _vp, ctypes.c_size_t, _vp]),
+    "nfhmm_mma_rate": (_i, [_i, ctypes.POINTER(ctypes.c_double), _vp]),
     "nfhmm_profile_enable": (_i, [_vp, _i]),
     "nfhmm_profile_read": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(ctypes.c_longlong),
@@ -258,7 +259,8 @@ class VIContext:
         fb_group: chunks per group (-1 automatic, 0 none); graphs: 0/1;
         profile_stride: time the stages of every k-th sweep of a run;
         fb_mode: 0 the scan over chunks, k >= 1 the sequential form with k
-        chains per block."""
+        chains per block; test_wait_timeout: ns, the failure-path test hook
+        (NFHMM_OPT_TEST_WAIT_TIMEOUT)."""
         if key == "fb_products":
             value = FB_PRODUCTS[value]
         _check(_lib.nfhmm_set_option(self._h, OPTIONS[key], int(value)), "nfhmm_set_option")
@@ -532,6 +534,15 @@ def digamma(x, stream=None):
     _check(_lib.nfhmm_digamma(_ptr(x)[0], _ptr(psi)[0], _ptr(w)[0], x.numel(), _stream(stream)),
            "nfhmm_digamma")
     return psi, w
+
+
+def mma_rate(precision: str = "fp32", stream=None) -> float:
+    """Measured dense tensor-core rate in TFLOP/s for the operand kind of a
+    precision (fp32: one tf32 pass; bf16) -- see nfhmm_mma_rate."""
+    out = ctypes.c_double()
+    _check(_lib.nfhmm_mma_rate(PRECISIONS[precision], ctypes.byref(out), _stream(stream)),
+           "nfhmm_mma_rate")
+    return out.value
 
 
 def call_raw(name: str):

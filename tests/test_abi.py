@@ -88,3 +88,34 @@ def test_bench_forward_backward_critical_path_model():
     assert bench.fb_serial_steps(7993, 2, 64, 0) == (7993, "sequential")
     assert bench.fb_serial_steps(3000, 0, 12, 12) == (2 * 12 + 12 + 21, "scan")   # 250 chunks
     assert bench.fb_serial_steps(3000, 0, 32, 0) == (2 * 32 + 94, "scan")          # 94 chunks
+
+
+def test_bench_tensor_peaks_and_split_tf32_ceiling():
+    """The contractions' roofline denominators: the tf32 rate measured in the
+    run when there is one (else bf16 sustained x the nominal tf32/bf16
+    ratio), bf16 from the measured peaks; the split-TF32 form issues three
+    tf32 MMAs per product, so its ceiling is a third of the tf32 peak."""
+    import importlib.util
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    spec = importlib.util.spec_from_file_location("bench_mod2", os.path.join(root, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    peaks = bench.load_peaks({"tf32": 1300.0, "bf16": 2500.0})
+    pk, note = bench.tensor_peak("fp32", peaks)
+    assert pk == 1300.0 and "measured in this run" in note
+    assert bench.tensor_peak("bf16", peaks)[0] == peaks["bf16_tflops_sustained"]
+    no_probe = bench.load_peaks(None)
+    assert bench.tensor_peak("fp32", no_probe)[0] == no_probe["bf16_tflops_sustained"] * 1.1 / 2.25
+    # one launch of 0.1 ms per stage; 2 T F M flops per contraction launch
+    prof = {"weights": (1.0, 10, 10), "gemm1": (1.0, 10, 10), "gemm2": (1.0, 10, 10),
+            "fb": (1.0, 10, 50)}
+    r = bench.stage_rooflines(prof, 3000, 2, 40, 10, 513, "fp32", True, peaks, (57, "scan"))
+    achieved = 2.0 * 3000 * 513 * 800 / 1e-4 / 1e12
+    assert abs(r["gemm1"]["achieved"] - round(achieved, 2)) < 1e-9
+    assert r["gemm1"]["split_tf32_ceiling"] == round(1300.0 / 3, 1)
+    assert abs(r["gemm1"]["frac_of_split_ceiling"] - round(3 * achieved / 1300.0, 4)) < 1e-9
+    assert r["fb"]["critical_path"]["ns_per_step"] == round(1e5 / 57, 1)
+    dom = bench.roofline_of(prof, 3000, 2, 40, 10, 513, "fp32", True, peaks, 10,
+                            fb_path=(57, "scan"))
+    assert dom["kernel"] in prof and dom["peak"] > 0

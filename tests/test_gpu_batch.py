@@ -424,3 +424,76 @@ def test_fb_mode_option_bounds(nf):
         ctx.set_option("fb_mode", 0)
         assert ctx.query("fb_mode") == 0
     assert np.isfinite(L)
+
+
+# ------------------------------------------- many tiles per persistent CTA
+
+MANY_TILE_LENGTHS = [5000, 3001, 7000, 129, 4500, 900, 8000, 1, 2300]   # 30,831 frames
+
+
+@pytest.fixture(scope="module")
+def many_tile_case():
+    """Nine jobs of uneven length on one S2 N40 K10 F513 model (the paper's
+    sizes), and per job the oracle's state after one sweep (rounded to
+    float32, as a context holds it) with the oracle's next sweep from it."""
+    jobs = synth.make_jobs(2, 40, 10, 513, MANY_TILE_LENGTHS, self_prob=0.95, energy_sigma=1.5,
+                           seed=21)
+    jobs.W, jobs.A, jobs.pi = (x.astype(np.float32).astype(np.float64)
+                               for x in (jobs.W, jobs.A, jobs.pi))
+    B = vi.element_mask(jobs.S, jobs.N, jobs.K)
+    states, refs = [], []
+    for j in range(len(MANY_TILE_LENGTHS)):
+        p = jobs.problem(j)
+        V = p.V.astype(np.float32).astype(np.float64)
+        c0, d0 = vi.init_state(V, p.W, p.S, p.N, p.K)
+        st = vi.sweep(V, p.W, p.A, p.pi, p.S, p.N, p.K, p.gamma, c0, d0, B)
+        c32, d32 = st["counts"].astype(np.float32), st["dhat"].astype(np.float32)
+        ref = vi.sweep(V, p.W, p.A, p.pi, p.S, p.N, p.K, p.gamma, c32.astype(np.float64),
+                       d32.astype(np.float64), B)
+        ref["bound"] = vi.bound(V, p.W, ref["alpha"], ref["logZ"], p.gamma, p.S, p.K,
+                                Vhat=ref["Vhat"])
+        states.append((c32, d32))
+        refs.append(ref)
+    return jobs, states, refs
+
+
+@pytest.mark.parametrize("fb_mode", [0, 4])
+def test_many_tiles_per_cta_one_sweep_from_oracle_state(nf, many_tile_case, fb_mode):
+    """A batch at the paper's sizes whose contractions walk several output
+    tiles per persistent CTA: 30,831 frames give 241 row tiles, so 1,205
+    reconstruction tiles (5 of 128 columns per row tile) and 1,446
+    back-projection tiles (6 of 160) on at most 152 CTAs -- about 8-10 tiles
+    each, through the TMEM hand-over between tiles and the stage ring that
+    runs on across them; the sequential forward-backward (fb_mode 4) also
+    takes SMs from their grid.  One sweep from the oracle's state after one
+    sweep, every output of every job against the oracle's same sweep:
+    alpha-hat, phi-hat (up to its per-frame constant) and counts element by
+    element (2e-5 relative), d-hat (1e-5) and each job's bound (1e-6)."""
+    from scipy.special import digamma as sp_digamma
+    jobs, states, refs = many_tile_case
+    counts = np.concatenate([c for c, _ in states], axis=0)
+    dhat = np.concatenate([d for _, d in states], axis=1)
+    with nf.VIContext(jobs.stacked_V(), _f32(jobs.W), _f32(jobs.A), _f32(jobs.pi), jobs.S,
+                      jobs.N, jobs.K, job_frames=MANY_TILE_LENGTHS) as b:
+        b.set_option("fb_mode", fb_mode)
+        b.set_state(counts, dhat, 1)
+        b.sweep(1)
+        bounds = b.job_bounds()
+        alpha = b.weights().astype(np.float64)
+        phi = b.surrogate().astype(np.float64)
+        counts_g, dhat_g, _ = b.get_state()
+    t0 = 0
+    for j, (T, ref) in enumerate(zip(MANY_TILE_LENGTHS, refs)):
+        sl = slice(t0, t0 + T)
+        t0 += T
+        a = alpha[sl]
+        assert np.max(np.abs(a - ref["alpha"]) / ref["alpha"]) <= 2e-5, j
+        a0 = ref["alpha"].sum(axis=1)
+        phi_ref = ref["phi"] + jobs.gamma * jobs.K * sp_digamma(a0)[None, :, None]
+        assert np.max(np.abs(phi[:, sl] - phi_ref) / (1.0 + np.abs(phi_ref))) <= 2e-5, j
+        c = counts_g[sl].astype(np.float64)
+        big = ref["counts"] > 1e-2 * ref["counts"].max()
+        assert np.max(np.abs(c[big] - ref["counts"][big]) / ref["counts"][big]) <= 2e-5, j
+        assert np.max(np.abs(c - ref["counts"])) <= 2e-5 * ref["counts"].max(), j
+        assert np.max(np.abs(dhat_g[:, sl] - ref["dhat"])) <= D_TOL, j
+        assert abs(bounds[j] - ref["bound"]) <= BOUND_RTOL * abs(ref["bound"]), j

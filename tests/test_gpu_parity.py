@@ -204,28 +204,31 @@ def test_trajectory_paper_size(nf):
 
     Strict parity (d-hat max-abs <= 1e-5, bound relative <= 1e-6) for every
     sweep of the trajectory, each started from the oracle's state at that
-    sweep (re-anchored), and the end-to-end bound at every sweep.  End to
-    end, d-hat differences at near-tie frames grow about 3-4x per sweep on
-    this workload -- the FP64 oracle itself diverges the same way when its
-    state is rounded to float32 between sweeps -- so the end-to-end d-hat is
-    held to 1e-5 for the first sweep and reported after that."""
+    sweep (re-anchored).  End to end: every sweep of the GPU's own
+    trajectory against the oracle's sweep from the same state (every frame,
+    every output); the bound at every sweep against the FP64 trajectory; and
+    d-hat to 1e-5 on every frame outside the sweep's ill-conditioned set --
+    the frames where the FP64 oracle itself, its state perturbed between
+    sweeps as a float32 implementation's is, moves by more than the
+    tolerance (oracle_trajectories).  That set is large while the posteriors
+    are diffuse (a few hundred frames after sweeps 2-4) and small by the
+    last sweep."""
+    from oracle_trajectories import check_sweep_from_own_state, ill_conditioned, trajectories
     p = _f32_problem(synth.make_problem(seed=0, **synth.PAPER_SIZE))
     n = 6
     B = vi.element_mask(p.S, p.N, p.K)
+    exact, perturbed = trajectories(p, n)
     counts, dhat = vi.init_state(p.V, p.W, p.S, p.N, p.K)
-    ref_states, ref_bounds, ref_dhat = [], [], []
-    for _ in range(n):
+    ref_states = []
+    for k in range(n):
         c32, d32 = counts.astype(np.float32), dhat.astype(np.float32)
         st = vi.sweep(p.V, p.W, p.A, p.pi, p.S, p.N, p.K, p.gamma, c32.astype(np.float64),
                       d32.astype(np.float64), B)
         ref_states.append((c32, d32, st["dhat"],
                            vi.bound(p.V, p.W, st["alpha"], st["logZ"], p.gamma, p.S, p.K,
                                     Vhat=st["Vhat"])))
-        full = vi.sweep(p.V, p.W, p.A, p.pi, p.S, p.N, p.K, p.gamma, counts, dhat, B)
-        counts, dhat = full["counts"], full["dhat"]
-        ref_dhat.append(dhat)
-        ref_bounds.append(vi.bound(p.V, p.W, full["alpha"], full["logZ"], p.gamma, p.S, p.K,
-                                   Vhat=full["Vhat"]))
+        counts, dhat = exact[k]["counts"], exact[k]["dhat"]
+    sizes, errs = [], []
     with _ctx(nf, p, device=True) as ctx:
         for k, (c32, d32, d_ref, L_ref) in enumerate(ref_states):
             ctx.set_state(c32, d32, k)
@@ -234,13 +237,23 @@ def test_trajectory_paper_size(nf):
             assert abs(L - L_ref) <= BOUND_RTOL * abs(L_ref), k
         f = p.as_f32()
         ctx.reinit(f["V"], f["W"], f["A"], f["pi"])
-        errs = []
         for k in range(n):
+            c_in, d_in, _ = ctx.get_state()
             L = ctx.sweep(1, bound=True)
-            assert abs(L - ref_bounds[k]) <= BOUND_RTOL * abs(ref_bounds[k]), k
-            errs.append(maxabs(ctx.posteriors(), ref_dhat[k]))
+            counts_g, d_g, _ = ctx.get_state()
+            # this sweep of the GPU's own trajectory, from its own state
+            check_sweep_from_own_state(p, c_in, d_in, ctx.weights(), counts_g, d_g, L, D_TOL,
+                                       REL_TOL, BOUND_RTOL)
+            assert abs(L - exact[k]["bound"]) <= BOUND_RTOL * abs(exact[k]["bound"]), k
+            err = np.abs(d_g - exact[k]["dhat"]).max(axis=(0, 2))
+            ill = ill_conditioned(exact[k]["dhat"], perturbed[k], D_TOL)
+            sizes.append(int(ill.sum()))
+            errs.append(float(err.max()))
+            assert err[~ill].max() <= D_TOL, (k, float(err[~ill].max()))
     print("end-to-end d-hat max-abs per sweep:", ["%.1e" % e for e in errs])
+    print("ill-conditioned frames per sweep:", sizes, "of", p.T)
     assert errs[0] <= D_TOL
+    assert sizes[-1] <= 0.05 * p.T
 
 
 @pytest.mark.parametrize("shape", [

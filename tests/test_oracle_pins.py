@@ -374,6 +374,16 @@ def test_separation_invariants():
     Vs = vi.separate(p.V, p.W, alpha, p.S, p.N, p.K, masked=False)
     full = (p.V.sum(axis=1)[:, None] * alpha / alpha.sum(axis=1, keepdims=True)) @ p.W
     assert np.allclose(Vs.sum(axis=0), full, rtol=1e-13, atol=1e-15)
+    # every dictionary element sums to 1 over frequency (a distribution, Section
+    # 2.1), so the mean-weight reconstruction of frame t holds v_t quanta in
+    # total, and source s holds its posterior-mean share of them: a wrong
+    # scaling of the weights or a wrong element slice per source fails here
+    v = p.V.sum(axis=1)
+    assert np.allclose(Vs.sum(axis=(0, 2)), v, rtol=1e-12, atol=1e-12)
+    NK = p.N * p.K
+    for s in range(p.S):
+        share = alpha[:, s * NK:(s + 1) * NK].sum(axis=1) / alpha.sum(axis=1)
+        assert np.allclose(Vs[s].sum(axis=1), v * share, rtol=1e-12, atol=1e-12)
     Vm = vi.separate(p.V, p.W, alpha, p.S, p.N, p.K, masked=True)
     assert np.allclose(Vm.sum(axis=0), p.V, rtol=1e-13, atol=1e-15)
     assert Vm.min() >= 0.0

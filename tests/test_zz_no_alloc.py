@@ -85,3 +85,24 @@ def test_noalloc_rejects_oversized_problem(lib):
             ctypes.c_void_p(logZ.data_ptr()), 0, ctypes.c_void_p(0))
     assert rc == lib.EINVAL
     assert "bytes of scratch" in lib._lib.nfhmm_last_error().decode()
+
+
+def test_noalloc_reports_zero_probability_then_recovers(lib):
+    """A device-side failure (here data of probability zero under one chain:
+    an emission excludes the only state its transitions allow) turns every
+    log normaliser into NaN; the array keeps that call's error word, and the
+    next call clears it and gives the allocating entry point's results."""
+    import torch
+    from test_gpu_failure import zero_probability_inputs
+    stream = torch.cuda.current_stream().cuda_stream
+    phi, A, pi = zero_probability_inputs()
+    _, z_bad = _call(lib, "nfhmm_forward_backward_noalloc", phi, A, pi, 0, stream)
+    torch.cuda.synchronize()
+    assert torch.isnan(z_bad).all()
+    phi, A, pi = (x[:1].contiguous() for x in (phi, A, pi))
+    d_ref, z_ref = _call(lib, "nfhmm_forward_backward", phi, A, pi, 0, stream)
+    d_na, z_na = _call(lib, "nfhmm_forward_backward_noalloc", phi, A, pi, 0, stream)
+    torch.cuda.synchronize()
+    assert torch.isfinite(z_na).all()
+    assert float((d_na - d_ref).abs().max()) <= D_TOL
+    assert float((z_na - z_ref).abs().max()) <= 1e-6 * max(1.0, float(z_ref.abs().max()))
