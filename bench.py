@@ -74,6 +74,10 @@ def parse():
                          "per block): with --ncu-case --workload batched instead of the "
                          "autotuner's choice; with --workload serving for the serving batches "
                          "(default: the scan)")
+    ap.add_argument("--fb-chunk", type=int, default=None,
+                    help="with --ncu-case (single workload): frames per forward-backward chunk")
+    ap.add_argument("--fb-group", type=int, default=None,
+                    help="with --ncu-case (single workload): chunks per group (0: none)")
     ap.add_argument("--workload", default="single",
                     choices=["single", "batched", "serving", "exact"],
                     help="single: one S2 N40 K10 F513 T3000 job per step (the headline); "
@@ -776,6 +780,10 @@ def run_single(args, rank, world, local):
                           gamma=p.gamma, precision=args.precision)
     sweeps = args.sweeps
     if args.ncu_case:
+        if args.fb_chunk is not None:
+            ctx.set_option("fb_chunk", args.fb_chunk)
+        if args.fb_group is not None:
+            ctx.set_option("fb_group", args.fb_group)
         print("bound after 3 sweeps:", ctx.sweep(3, bound=True), flush=True)
         ctx.close()
         return None

@@ -9,9 +9,12 @@ implementation: it is found here by running the FP64 oracle itself with its
 state perturbed between sweeps as a float32 implementation's state is --
 rounded to float32, and rounded with counts multiplied by (1 + 1e-6 xi),
 xi ~ N(0, 1) (three seeds; 1e-6 is the scale of a float32 contraction's
-relative error over ~1000 terms).  A frame whose posteriors move by more than the
-tolerance under any of these perturbations is ill-conditioned at that
-sweep; the GPU's posteriors are held to the tolerance on every other frame.
+relative error over ~1000 terms).  A frame whose posteriors move by more than a
+threshold under any of these perturbations is ill-conditioned at that sweep
+(the tests take a tenth of the tolerance: a few random perturbations only
+estimate a frame's sensitivity, and the GPU's own rounding is one more,
+differently aimed); the GPU's posteriors are held to the tolerance on every
+other frame.
 """
 import numpy as np
 

@@ -18,6 +18,10 @@ pytestmark = pytest.mark.gpu
 D_TOL = 1e-5
 BOUND_RTOL = 1e-6
 REL_TOL = 2e-5
+# a frame is ill-conditioned at a sweep when FP32-sized perturbations of the
+# oracle's state move its posteriors by more than a tenth of the tolerance:
+# a margin of 10 on a sensitivity estimated from a few random perturbations
+SENSITIVE = D_TOL / 10
 
 
 @pytest.fixture(scope="module")
@@ -228,7 +232,7 @@ def test_trajectory_paper_size(nf):
                            vi.bound(p.V, p.W, st["alpha"], st["logZ"], p.gamma, p.S, p.K,
                                     Vhat=st["Vhat"])))
         counts, dhat = exact[k]["counts"], exact[k]["dhat"]
-    sizes, errs = [], []
+    sizes, errs, outside = [], [], []
     with _ctx(nf, p, device=True) as ctx:
         for k, (c32, d32, d_ref, L_ref) in enumerate(ref_states):
             ctx.set_state(c32, d32, k)
@@ -246,13 +250,15 @@ def test_trajectory_paper_size(nf):
                                        REL_TOL, BOUND_RTOL)
             assert abs(L - exact[k]["bound"]) <= BOUND_RTOL * abs(exact[k]["bound"]), k
             err = np.abs(d_g - exact[k]["dhat"]).max(axis=(0, 2))
-            ill = ill_conditioned(exact[k]["dhat"], perturbed[k], D_TOL)
+            ill = ill_conditioned(exact[k]["dhat"], perturbed[k], SENSITIVE)
             sizes.append(int(ill.sum()))
             errs.append(float(err.max()))
-            assert err[~ill].max() <= D_TOL, (k, float(err[~ill].max()))
+            outside.append(float(err[~ill].max()) if (~ill).any() else 0.0)
     print("end-to-end d-hat max-abs per sweep:", ["%.1e" % e for e in errs])
+    print("  outside the ill-conditioned set:", ["%.1e" % e for e in outside])
     print("ill-conditioned frames per sweep:", sizes, "of", p.T)
     assert errs[0] <= D_TOL
+    assert max(outside) <= D_TOL
     assert sizes[-1] <= 0.05 * p.T
 
 

@@ -35,6 +35,10 @@ SWEEPS = (1, 2, 10)
 D_TOL = 1e-5
 BOUND_RTOL = 1e-6
 REL_TOL = 2e-5
+# a frame is ill-conditioned at a sweep when FP32-sized perturbations of the
+# oracle's state move its posteriors by more than a tenth of the tolerance:
+# a margin of 10 on a sensitivity estimated from a few random perturbations
+SENSITIVE = D_TOL / 10
 
 
 def rel(a, b):
@@ -189,7 +193,7 @@ def test_fp32_end_to_end_validity(nf, problem, traj):
     p = problem
     f = p.as_f32()
     exact, perturbed = traj
-    sizes = []
+    sizes, errs, outside = [], [], []
     with nf.VIContext(f["V"], f["W"], f["A"], f["pi"], p.S, p.N, p.K, gamma=p.gamma) as ctx:
         for k in range(len(exact)):
             c_in, d_in, _ = ctx.get_state()
@@ -198,9 +202,13 @@ def test_fp32_end_to_end_validity(nf, problem, traj):
             check_sweep_from_own_state(p, c_in, d_in, ctx.weights(), counts, d, L, D_TOL,
                                        REL_TOL, BOUND_RTOL)
             assert abs(L - exact[k]["bound"]) <= BOUND_RTOL * abs(exact[k]["bound"]), k
-            ill = ill_conditioned(exact[k]["dhat"], perturbed[k], D_TOL)
+            ill = ill_conditioned(exact[k]["dhat"], perturbed[k], SENSITIVE)
             sizes.append(int(ill.sum()))
             err = np.abs(d - exact[k]["dhat"]).max(axis=(0, 2))
-            assert err[~ill].max() <= D_TOL, (k, float(err[~ill].max()))
+            errs.append(float(err.max()))
+            outside.append(float(err[~ill].max()) if (~ill).any() else 0.0)
+    print("end-to-end d-hat max-abs per sweep:", ["%.1e" % e for e in errs])
+    print("  outside the ill-conditioned set:", ["%.1e" % e for e in outside])
     print("ill-conditioned frames per sweep:", sizes, "of", p.T)
+    assert max(outside) <= D_TOL
     assert sizes[-1] <= 0.05 * p.T
