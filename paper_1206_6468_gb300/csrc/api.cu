@@ -361,6 +361,7 @@ int one_sweep(nfhmm_ctx* c, bool want_bpart, bool keep_alpha) {
   wa.S = d.S;
   wa.N = d.N;
   wa.K = d.K;
+  wa.Tstride = d.T;
   wa.gamma = (float)d.gamma;
   wa.ktab = c->ktab;
   wa.counts = c->c;
@@ -423,7 +424,7 @@ int compute_bound(nfhmm_ctx* c) {
   b.bpart = c->bpart;
   b.nbpart = c->nbpart;
   b.fterm = c->fterm_ok ? c->fterm : nullptr;
-  b.funits = weights_units(c->d.S, c->d.N);
+  b.funits = weights_units(c->d.S, c->d.N, c->Mp);
   b.logZ = c->logZ;
   b.frame_terms = c->frame_terms;
   b.out = c->bound_dev;
@@ -454,7 +455,7 @@ int load_model(nfhmm_ctx* c, const float* W, const float* A, const float* pi, in
   stage_begin(c, NFHMM_STAGE_INIT, st);
   launch_validate(c->V, 0, d.F, c->Fp, c->WM, c->M, c->A, c->pi, d.S, d.N, c->err, st);
   launch_transpose(c->WM, c->Mp, c->Fp, c->Fp, c->WF, c->Mp, c->Mp, c->Fp, st);
-  launch_element_table(c->M, c->Mp, d.K, d.N, d.T, c->ktab, st);
+  launch_element_table(c->M, c->Mp, d.K, d.N, c->ktab, st);
   int n = 3;
   if (c->use_tc) n += tc_refresh_beta(c->tc, st);
   stage_end(c, NFHMM_STAGE_INIT, st, n);
@@ -829,7 +830,7 @@ int create_ctx(nfhmm_ctx** out, const nfhmm_dims* dp, int max_jobs, const float*
   DMALLOC(c->v, T * 8);
   DMALLOC(c->bpart, T * c->nbpart * 8);
   DMALLOC(c->frame_terms, T * 8);
-  DMALLOC(c->fterm, T * 16 * weights_units(d.S, d.N));
+  DMALLOC(c->fterm, T * 16 * weights_units(d.S, d.N, c->Mp));
   DMALLOC(c->fb_seg, (size_t)3 * max_jobs * sizeof(int));
   DMALLOC(c->logZ, S * max_jobs * 8);
   DMALLOC(c->bound_dev, (max_jobs + 1) * 8);

@@ -17,25 +17,154 @@ namespace nfhmm {
 constexpr unsigned FULL = 0xffffffffu;
 
 // ------------------------------------------------------------ weights (Eq. 6, 8)
-// One warp per unit of WB consecutive blocks g = (s, n) of one frame t (WB*K
-// consecutive elements): each lane takes every 32nd element of the unit
-// (coalesced loads and stores), forms alpha-hat (Eq. 6), psi and
-// w = exp(psi), and parks psi in shared memory; then lane b sums the K values
-// of the unit's block b in element order, which is Eq. 8's sum over the
-// block (deterministic, no shuffles or atomics).  Padding elements k >= M are
-// never touched (zero since the frame was loaded).  The element table
-// ktab[k] = (g, s*T*N + n) replaces integer division on the hot path.
-// With BOUND, the warp also sums alpha-hat and the bound's element terms
-// g(alpha) over its unit (Kahan-compensated in float per lane, then double)
-// into fterm[t][h] for unit h of the frame.
+// Per element: alpha-hat (Eq. 6), psi and w = exp(psi) (the weights of
+// Eq. 7), written as float and as the contraction's operand format; per
+// dictionary block (s, n): Eq. 8's sum of psi over its K consecutive
+// elements, in element order (deterministic, no shuffles or atomics).
+// The element table ktab[k] = (s, n) of element k replaces integer division
+// on the hot path; d-hat and phi-hat are S x Tstride x N.
+// With BOUND, the kernel also sums alpha-hat and the bound's element terms
+// g(alpha) (Kahan-compensated in float per lane, then double) into
+// fterm[t][h] for unit h of the frame.
+//
+// Two forms.  The frame form (Mp <= 1536): one warp per frame, warps
+// striding over frames; lane q takes the four consecutive elements 4q..4q+3,
+// 4(q+32).., so every load and store is a 16-byte vector; the frame's psi
+// is parked in shared memory and lane b then sums block b.  One unit per
+// frame.  The unit form (any size): one warp per unit of WB consecutive
+// blocks of a frame, one element per lane and step.
 constexpr int WB = 16;
+constexpr int WFRAME_MAX = 1536;   // 8 warps x Mp floats within the default 48 KB
+constexpr int WFRAME_WARPS = 8;
+
 template <int FMT, bool BOUND>
-__global__ void __launch_bounds__(256) k_weights(WeightsArgs a) {
+__device__ __forceinline__ void weights_elem(float alpha, float& psi, float& w, float& sa,
+                                             float& ca, float& sg, float& cg, double& big) {
+  if (BOUND) {
+    float gs, gb;
+    digamma_exp_g_ge1(alpha, psi, w, gs, gb);
+    float y = alpha - ca, z = sa + y;
+    ca = (z - sa) - y;
+    sa = z;
+    y = gs - cg;
+    z = sg + y;
+    cg = (z - sg) - y;
+    sg = z;
+    big += (double)gb;
+  } else {
+    digamma_exp_fast_ge1(alpha, psi, w);
+  }
+}
+
+template <int FMT, bool BOUND>
+__global__ void __launch_bounds__(WFRAME_WARPS * 32) k_weights_frame(WeightsArgs a) {
   extern __shared__ float wsm[];
   // launched as a programmatic dependent of the kernel before it on the
   // stream (the replay that wrote d-hat): wait for it before reading
   // anything; the forward-backward pass that follows may start launching at
   // once (it waits for this kernel before it reads the emissions)
+  griddep_wait();
+  griddep_launch_dependents();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int NB = a.S * a.N;
+  const int M4 = (a.M + 3) >> 2;
+  const size_t SN = (size_t)a.Tstride * a.N;   // source stride of d-hat and phi-hat
+  float* ps = wsm + warp * a.Mp;
+  const int nwarps = gridDim.x * WFRAME_WARPS;
+  unsigned bad = 0;
+  float chk = 0.f;
+  for (int t = blockIdx.x * WFRAME_WARPS + warp; t < a.T; t += nwarps) {
+    const size_t row = (size_t)t * a.Mp;
+    const size_t toff = (size_t)t * a.N;
+    float sa = 0.f, ca = 0.f, sg = 0.f, cg = 0.f;
+    double big = 0.0;
+    for (int q = lane; q < M4; q += 32) {
+      const int k = 4 * q;
+      const float4 c4 = *reinterpret_cast<const float4*>(a.counts + row + k);
+      const int4 e01 = *reinterpret_cast<const int4*>(a.ktab + k);
+      const int4 e23 = *reinterpret_cast<const int4*>(a.ktab + k + 2);
+      const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
+      const int es[4] = {e01.x, e01.z, e23.x, e23.z};
+      const int en[4] = {e01.y, e01.w, e23.y, e23.w};
+      const bool full = k + 4 <= a.M;
+      float al[4], psi[4], w[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float d = a.dhat[(size_t)es[u] * SN + toff + en[u]];
+        al[u] = cv[u] + a.gamma * d + 1.f;
+        if (full || k + u < a.M) {
+          weights_elem<FMT, BOUND>(al[u], psi[u], w[u], sa, ca, sg, cg, big);
+        } else {
+          psi[u] = 0.f;
+          w[u] = 0.f;
+        }
+        chk = fmaf(0.f, psi[u] + w[u], chk);   // stays 0 unless psi or w is NaN or infinite
+      }
+      *reinterpret_cast<float4*>(ps + k) = make_float4(psi[0], psi[1], psi[2], psi[3]);
+      if (full) {
+        if (a.alpha)
+          *reinterpret_cast<float4*>(a.alpha + row + k) = make_float4(al[0], al[1], al[2], al[3]);
+        *reinterpret_cast<float4*>(a.w32 + row + k) = make_float4(w[0], w[1], w[2], w[3]);
+        if (FMT == WF_TF32X2) {
+          float h[4], l[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            h[u] = tf32_hi(w[u]);
+            l[u] = tf32_hi(w[u] - h[u]);
+          }
+          *reinterpret_cast<float4*>(reinterpret_cast<float*>(a.wop_hi) + row + k) =
+              make_float4(h[0], h[1], h[2], h[3]);
+          *reinterpret_cast<float4*>(reinterpret_cast<float*>(a.wop_lo) + row + k) =
+              make_float4(l[0], l[1], l[2], l[3]);
+        } else if (FMT == WF_BF16) {
+          const __nv_bfloat162 b01 = __floats2bfloat162_rn(w[0], w[1]);
+          const __nv_bfloat162 b23 = __floats2bfloat162_rn(w[2], w[3]);
+          uint2 pk;
+          pk.x = *reinterpret_cast<const uint32_t*>(&b01);
+          pk.y = *reinterpret_cast<const uint32_t*>(&b23);
+          *reinterpret_cast<uint2*>(reinterpret_cast<__nv_bfloat16*>(a.wop_hi) + row + k) = pk;
+        }
+      } else {
+        // the frame's last elements: padding (k >= M) is never touched
+        for (int u = 0; u < 4 && k + u < a.M; ++u) {
+          if (a.alpha) a.alpha[row + k + u] = al[u];
+          a.w32[row + k + u] = w[u];
+          if (FMT == WF_TF32X2) {
+            const float h = tf32_hi(w[u]);
+            reinterpret_cast<float*>(a.wop_hi)[row + k + u] = h;
+            reinterpret_cast<float*>(a.wop_lo)[row + k + u] = tf32_hi(w[u] - h);
+          } else if (FMT == WF_BF16) {
+            reinterpret_cast<__nv_bfloat16*>(a.wop_hi)[row + k + u] = __float2bfloat16_rn(w[u]);
+          }
+        }
+      }
+    }
+    __syncwarp();
+    for (int b = lane; b < NB; b += 32) {
+      const float* pb = ps + b * a.K;
+      float x = 0.f;
+      for (int j = 0; j < a.K; ++j) x += pb[j];
+      const int2 e = a.ktab[b * a.K];
+      a.phi[(size_t)e.x * SN + toff + e.y] = a.gamma * x;
+    }
+    if (BOUND) {
+      const double s0 = warp_sum_d((double)sa - (double)ca);
+      const double sgt = warp_sum_d(((double)sg - (double)cg) + big);
+      if (lane == 0) {
+        a.fterm[2 * (size_t)t] = s0;
+        a.fterm[2 * (size_t)t + 1] = sgt;
+      }
+    }
+    __syncwarp();   // every lane is done with ps before the next frame
+  }
+  if (!(chk == 0.f)) bad |= ERR_NONFINITE;
+  bad = __reduce_or_sync(FULL, bad);
+  if (bad && lane == 0) atomicOr(a.err, bad);
+}
+
+template <int FMT, bool BOUND>
+__global__ void __launch_bounds__(256) k_weights(WeightsArgs a) {
+  extern __shared__ float wsm[];
   griddep_wait();
   griddep_launch_dependents();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -46,6 +175,7 @@ __global__ void __launch_bounds__(256) k_weights(WeightsArgs a) {
   const int t = (int)(u / NH), h = (int)(u - (long long)t * NH);
   const int UE = WB * a.K;
   const int k0 = h * UE, k1 = min(k0 + UE, a.M);
+  const size_t SN = (size_t)a.Tstride * a.N;
   float* ps = wsm + warp * UE;
   const size_t row = (size_t)t * a.Mp;
   const size_t toff = (size_t)t * a.N;
@@ -54,23 +184,10 @@ __global__ void __launch_bounds__(256) k_weights(WeightsArgs a) {
   float sa = 0.f, ca = 0.f, sg = 0.f, cg = 0.f;   // Kahan sums of alpha and g (small part)
   double big = 0.0;                                // sum of the exact large parts of g
   for (int k = k0 + lane; k < k1; k += 32) {
-    const int dy = a.ktab[k].y;
-    const float alpha = a.counts[row + k] + a.gamma * a.dhat[dy + toff] + 1.f;
+    const int2 e = a.ktab[k];
+    const float alpha = a.counts[row + k] + a.gamma * a.dhat[(size_t)e.x * SN + toff + e.y] + 1.f;
     float psi, w;
-    if (BOUND) {
-      float gs, gb;
-      digamma_exp_g_ge1(alpha, psi, w, gs, gb);
-      float y = alpha - ca, z = sa + y;
-      ca = (z - sa) - y;
-      sa = z;
-      y = gs - cg;
-      z = sg + y;
-      cg = (z - sg) - y;
-      sg = z;
-      big += (double)gb;
-    } else {
-      digamma_exp_fast_ge1(alpha, psi, w);
-    }
+    weights_elem<FMT, BOUND>(alpha, psi, w, sa, ca, sg, cg, big);
     chk = fmaf(0.f, psi + w, chk);   // stays 0 unless psi or w is NaN or infinite
     if (a.alpha) a.alpha[row + k] = alpha;
     a.w32[row + k] = w;
@@ -89,7 +206,8 @@ __global__ void __launch_bounds__(256) k_weights(WeightsArgs a) {
     const float* pb = ps + lane * a.K;
     float x = 0.f;
     for (int j = 0; j < a.K; ++j) x += pb[j];
-    a.phi[a.ktab[b * a.K].y + toff] = a.gamma * x;
+    const int2 e = a.ktab[b * a.K];
+    a.phi[(size_t)e.x * SN + toff + e.y] = a.gamma * x;
   }
   if (!(chk == 0.f)) bad |= ERR_NONFINITE;
   bad = __reduce_or_sync(FULL, bad);
@@ -103,39 +221,62 @@ __global__ void __launch_bounds__(256) k_weights(WeightsArgs a) {
     }
   }
 }
-int weights_units(int S, int N) { return (S * N + WB - 1) / WB; }
 
-__global__ void k_element_table(int M, int Mp, int K, int N, int T, int2* ktab) {
+static bool weights_frame_form(int Mp) { return Mp <= WFRAME_MAX; }
+
+int weights_units(int S, int N, int Mp) {
+  return weights_frame_form(Mp) ? 1 : (S * N + WB - 1) / WB;
+}
+
+__global__ void k_element_table(int M, int Mp, int K, int N, int2* ktab) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= Mp) return;
   if (k < M) {
     const int g = k / K, s = g / N, n = g - s * N;
-    ktab[k] = make_int2(g, (int)((size_t)s * T * N + n));
+    ktab[k] = make_int2(s, n);
   } else {
-    ktab[k] = make_int2(-1 - k, 0);
+    ktab[k] = make_int2(0, 0);   // padding: a valid index, never used for a result
   }
 }
-void launch_element_table(int M, int Mp, int K, int N, int T, int2* ktab, cudaStream_t st) {
-  k_element_table<<<(Mp + 255) / 256, 256, 0, st>>>(M, Mp, K, N, T, ktab);
+void launch_element_table(int M, int Mp, int K, int N, int2* ktab, cudaStream_t st) {
+  k_element_table<<<(Mp + 255) / 256, 256, 0, st>>>(M, Mp, K, N, ktab);
 }
 
 void launch_weights(const WeightsArgs& a, int fmt, cudaStream_t st) {
-  const int warps = 8;
-  const long long units = (long long)a.T * weights_units(a.S, a.N);
-  const size_t smem = (size_t)warps * WB * a.K * sizeof(float);
   const bool b = a.fterm != nullptr;
   void (*k)(WeightsArgs) = nullptr;
-  switch (fmt) {
-    case WF_TF32X2: k = b ? k_weights<WF_TF32X2, true> : k_weights<WF_TF32X2, false>; break;
-    case WF_BF16: k = b ? k_weights<WF_BF16, true> : k_weights<WF_BF16, false>; break;
-    default: k = b ? k_weights<WF_F32, true> : k_weights<WF_F32, false>; break;
+  cudaLaunchConfig_t cfg = {};
+  if (weights_frame_form(a.Mp)) {
+    switch (fmt) {
+      case WF_TF32X2: k = b ? k_weights_frame<WF_TF32X2, true> : k_weights_frame<WF_TF32X2, false>; break;
+      case WF_BF16: k = b ? k_weights_frame<WF_BF16, true> : k_weights_frame<WF_BF16, false>; break;
+      default: k = b ? k_weights_frame<WF_F32, true> : k_weights_frame<WF_F32, false>; break;
+    }
+    // warps stride over frames: enough blocks to fill every SM a few times
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+      sms = 1;
+    const long long need = ((long long)a.T + WFRAME_WARPS - 1) / WFRAME_WARPS;
+    const long long cap = (long long)sms * 8;
+    cfg.gridDim = dim3((unsigned)(need < cap ? need : cap));
+    cfg.blockDim = dim3(WFRAME_WARPS * 32);
+    cfg.dynamicSmemBytes = (size_t)WFRAME_WARPS * a.Mp * sizeof(float);
+  } else {
+    switch (fmt) {
+      case WF_TF32X2: k = b ? k_weights<WF_TF32X2, true> : k_weights<WF_TF32X2, false>; break;
+      case WF_BF16: k = b ? k_weights<WF_BF16, true> : k_weights<WF_BF16, false>; break;
+      default: k = b ? k_weights<WF_F32, true> : k_weights<WF_F32, false>; break;
+    }
+    const int warps = 8;
+    const long long units = (long long)a.T * ((a.S * a.N + WB - 1) / WB);
+    cfg.gridDim = dim3((unsigned)((units + warps - 1) / warps));
+    cfg.blockDim = dim3(warps * 32);
+    cfg.dynamicSmemBytes = (size_t)warps * WB * a.K * sizeof(float);
   }
+  if (a.T == 0) return;
   // a programmatic dependent of the previous kernel on the stream (ordinary
   // launch on the legacy default stream)
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)((units + warps - 1) / warps));
-  cfg.blockDim = dim3(warps * 32);
-  cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;

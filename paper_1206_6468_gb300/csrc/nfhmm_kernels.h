@@ -26,8 +26,9 @@ enum WFormat { WF_F32 = 0, WF_TF32X2 = 1, WF_BF16 = 2 };
 
 struct WeightsArgs {
   int T, M, Mp, S, N, K;
+  int Tstride;          // frame stride of d-hat and phi-hat (S x Tstride x N)
   float gamma;
-  const int2* ktab;     // Mp entries: (block g, s*T*N + n), g < 0 for padding
+  const int2* ktab;     // Mp entries: (s, n) of element k ((0, 0) for padding)
   const float* counts;  // T x Mp
   const float* dhat;    // S x T x N
   float* alpha;         // T x Mp, or null: alpha-hat not stored (not the last sweep of a run)
@@ -35,13 +36,13 @@ struct WeightsArgs {
   void* wop_hi;         // format-specific operand copies (may be null)
   void* wop_lo;
   float* phi;           // S x T x N (without the -gamma K psi(alpha_t0) constant)
-  double* fterm;        // null, or T x weights_units(S, N) x 2: per unit of the frame,
+  double* fterm;        // null, or T x weights_units(S, N, Mp) x 2: per unit of the frame,
                         // (sum_k alpha_tk, sum_k g(alpha_tk)) for the bound
   unsigned* err;
 };
 void launch_weights(const WeightsArgs& a, int fmt, cudaStream_t st);
-int weights_units(int S, int N);   // units (of 16 blocks) per frame of the weights kernel
-void launch_element_table(int M, int Mp, int K, int N, int T, int2* ktab, cudaStream_t st);
+int weights_units(int S, int N, int Mp);   // units per frame of the weights kernel's bound sums
+void launch_element_table(int M, int Mp, int K, int N, int2* ktab, cudaStream_t st);
 
 // Fill buf[t*ld + k] = (k < M) ? value : 0 for t < T, k < ld.
 void launch_fill_rows(float* buf, int T, int M, int ld, float value, cudaStream_t st);

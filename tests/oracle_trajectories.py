@@ -8,7 +8,7 @@ Which frames those are is a property of the iteration, not of the
 implementation: it is found here by running the FP64 oracle itself with its
 state perturbed between sweeps as a float32 implementation's state is --
 rounded to float32, and rounded with counts multiplied by (1 + 1e-6 xi),
-xi ~ N(0, 1) (three seeds; 1e-6 is the scale of a float32 contraction's
+xi ~ N(0, 1) (five seeds; 1e-6 is the scale of a float32 contraction's
 relative error over ~1000 terms).  A frame whose posteriors move by more than a
 threshold under any of these perturbations is ill-conditioned at that sweep
 (the tests take a tenth of the tolerance: a few random perturbations only
@@ -21,7 +21,7 @@ import numpy as np
 from oracle import vi
 
 
-def trajectories(p, n_sweeps, noise=1e-6, seeds=(0, 1, 2)):
+def trajectories(p, n_sweeps, noise=1e-6, seeds=(0, 1, 2, 3, 4)):
     """Sweeps 1..n_sweeps of the FP64 oracle from the initial state, and of
     its perturbed runs.  Returns (exact, perturbed): exact[k] = dict(dhat,
     bound, alpha, counts) after sweep k + 1; perturbed[k] = list of d-hat
