@@ -276,6 +276,24 @@ NFHMM_API int nfhmm_job_posteriors(nfhmm_ctx *c, long long job_id, float *dhat, 
  *                          its state is not usable (restore one with
  *                          nfhmm_set_state); the context stays usable.
  *                          0 clears a pending hook
+ *   NFHMM_OPT_TILE_GEMM1   column tile of the reconstruction contraction
+ *                          (Vhat = beta w, output columns = frequencies) on
+ *                          the tensor cores: 64, 96 or 128 (FP32; default
+ *                          128), or 64, 96, 128 or 192 (BF16)
+ *   NFHMM_OPT_TILE_GEMM2   column tile of the back-projection (counts,
+ *                          output columns = elements): 64, 96, 128 or 160
+ *                          (FP32; default 160), or also 192 (BF16)
+ *   NFHMM_OPT_TILE_STAGES1, NFHMM_OPT_TILE_STAGES2  depth of each
+ *                          contraction's shared-memory ring of operand
+ *                          stages: 0 (default) the deepest that fits the
+ *                          tile, else 2 .. that depth (NFHMM_Q_TILE_STAGES*
+ *                          reads it back).  A depth the new tile cannot hold
+ *                          falls back to 0
+ *                          Every row tile is 128 frames; results differ
+ *                          between tile shapes only by rounding (the order
+ *                          of the accumulation and of the bound's partial
+ *                          sums).  Tensor-core contexts only (NFHMM_EINVAL
+ *                          otherwise); synchronises.
  */
 #define NFHMM_OPT_FB_CHUNK    0
 #define NFHMM_OPT_FB_PRODUCTS 1
@@ -284,14 +302,24 @@ NFHMM_API int nfhmm_job_posteriors(nfhmm_ctx *c, long long job_id, float *dhat, 
 #define NFHMM_OPT_PROFILE_STRIDE 4
 #define NFHMM_OPT_FB_MODE     5
 #define NFHMM_OPT_TEST_WAIT_TIMEOUT 6
+#define NFHMM_OPT_TILE_GEMM1  7
+#define NFHMM_OPT_TILE_GEMM2  8
+#define NFHMM_OPT_TILE_STAGES1 9
+#define NFHMM_OPT_TILE_STAGES2 10
 
 /*
- * nfhmm_autotune -- choose the forward-backward form and geometry for the
- * context's current jobs by timing whole sweeps on them: the scan with every
+ * nfhmm_autotune -- choose the forward-backward form and geometry, then the
+ * contractions' tile shapes, for the context's current jobs by timing whole
+ * sweeps on them.  Forward-backward first: the scan with every
  * candidate chunk length in {8, 12, 16, 20, 24, 32, 48, 64} (at most the
  * longest job's frames), with groups of the automatic size and without
  * groups, then the sequential form (NFHMM_OPT_FB_MODE) with 1, 2 and 4 jobs'
- * sources per block (as far as a block holds them); each candidate runs two
+ * sources per block (as far as a block holds them).  Then, with the form
+ * chosen and on tensor-core contexts, the tile shapes one coordinate at a
+ * time: the reconstruction's column tile over NFHMM_OPT_TILE_GEMM1's
+ * choices, the back-projection's over NFHMM_OPT_TILE_GEMM2's, then each
+ * ring depth from 2 to the deepest (read back with NFHMM_Q_TILE_*).  Each
+ * candidate runs two
  * sweeps (which capture its graph) and then `reps` sweeps (reps <= 0: 3)
  * between CUDA events, every trial starting from the same state: the counts,
  * posteriors, alpha-hat and log normalisers are copied aside first and put
@@ -490,6 +518,10 @@ NFHMM_API long long nfhmm_kernel_launches(nfhmm_ctx *c);
 #define NFHMM_Q_MAX_JOBS       5   /* jobs the context can hold            */
 #define NFHMM_Q_FB_GROUP       6   /* chunks per group of the scan (0: none) */
 #define NFHMM_Q_FB_MODE        7   /* 0: scan; k >= 1: sequential, k per block */
+#define NFHMM_Q_TILE_GEMM1     8   /* column tile of the reconstruction (0: not tensor cores) */
+#define NFHMM_Q_TILE_GEMM2     9   /* column tile of the back-projection   */
+#define NFHMM_Q_TILE_STAGES1  10   /* ring depth of the reconstruction     */
+#define NFHMM_Q_TILE_STAGES2  11   /* ring depth of the back-projection    */
 NFHMM_API int nfhmm_query(nfhmm_ctx *c, int key, long long *value);
 
 #ifdef __cplusplus

@@ -423,8 +423,9 @@ int compute_bound(nfhmm_ctx* c) {
   b.v = c->v;
   b.bpart = c->bpart;
   b.nbpart = c->nbpart;
+  b.nbpart_used = c->use_tc ? tc_bpart_used(c->tc) : gemm_simt_col_tiles(c->Fp);
   b.fterm = c->fterm_ok ? c->fterm : nullptr;
-  b.funits = weights_units(c->d.S, c->d.N, c->Mp);
+  b.funits = weights_units(c->d.S, c->d.N, c->d.K, c->d.T);
   b.logZ = c->logZ;
   b.frame_terms = c->frame_terms;
   b.out = c->bound_dev;
@@ -814,8 +815,9 @@ int create_ctx(nfhmm_ctx** out, const nfhmm_dims* dp, int max_jobs, const float*
   CKI(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
   CKI(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
   const size_t T = d.T, Mp = c->Mp, Fp = c->Fp, S = d.S, N = d.N;
+  // bound partials per frame: room for the narrowest reconstruction tile
   c->nbpart = gemm_simt_col_tiles(c->Fp);
-  if (tc_col_tiles_gemm1(c->Fp) > c->nbpart) c->nbpart = tc_col_tiles_gemm1(c->Fp);
+  if (tc_bpart_columns_max(c->Fp) > c->nbpart) c->nbpart = tc_bpart_columns_max(c->Fp);
   DMALLOC(c->V, T * Fp * 4);
   DMALLOC(c->WM, Mp * Fp * 4);
   DMALLOC(c->WF, Fp * Mp * 4);
@@ -830,7 +832,7 @@ int create_ctx(nfhmm_ctx** out, const nfhmm_dims* dp, int max_jobs, const float*
   DMALLOC(c->v, T * 8);
   DMALLOC(c->bpart, T * c->nbpart * 8);
   DMALLOC(c->frame_terms, T * 8);
-  DMALLOC(c->fterm, T * 16 * weights_units(d.S, d.N, c->Mp));
+  DMALLOC(c->fterm, T * 16 * weights_units(d.S, d.N, d.K, d.T));
   DMALLOC(c->fb_seg, (size_t)3 * max_jobs * sizeof(int));
   DMALLOC(c->logZ, S * max_jobs * 8);
   DMALLOC(c->bound_dev, (max_jobs + 1) * 8);
@@ -900,6 +902,10 @@ long long graph_key_of(const nfhmm_ctx* c, bool want_bpart, bool timed, int slot
   k = k * 1000033 + c->fb.NG;
   k = k * 3 + c->fb.products;
   k = k * 67 + c->fb.seq;
+  k = k * 257 + c->tc.bn1;
+  k = k * 257 + c->tc.bn2;
+  k = k * 17 + c->tc.st1;
+  k = k * 17 + c->tc.st2;
   k = k * 2 + (want_bpart ? 1 : 0);
   k = k * 2 + (keep_alpha ? 1 : 0);
   k = k * 3 + (timed ? 1 + slot : 0);
@@ -1245,6 +1251,23 @@ int nfhmm_autotune(nfhmm_ctx* c, int reps, int* chunk_out, int* group_out, doubl
   c->fb.seq = 0;
   int bestL = oldL, bestG = oldG, best_seq = old_seq;
   double best_us = 1e300;
+  // two sweeps from the saved state capture the candidate's graph, then
+  // `reps` sweeps are timed; rc: an error code, us: mean sweep time
+  auto time_sweeps = [&](double* us) -> int {
+    cudaError_t e = copy_state(false);
+    int r = NFHMM_OK;
+    if (e == cudaSuccess) r = run_sweeps(c, 2, false);
+    if (e == cudaSuccess && !r) e = cudaEventRecord(e0, c->s_main);
+    if (e == cudaSuccess && !r) r = run_sweeps(c, reps, false);
+    if (e == cudaSuccess && !r) e = cudaEventRecord(e1, c->s_main);
+    if (e == cudaSuccess && !r) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess && !r) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (r) return r;
+    if (e != cudaSuccess) return fail(NFHMM_ECUDA, std::string("autotune: ") + cudaGetErrorString(e));
+    *us = 1e3 * ms / reps;
+    return NFHMM_OK;
+  };
   for (const Cand& cd : cands) {
     {
       const int L = cd.seq ? c->fb.L : cd.L, G = cd.seq ? c->fb.G : cd.G;
@@ -1262,19 +1285,9 @@ int nfhmm_autotune(nfhmm_ctx* c, int reps, int* chunk_out, int* group_out, doubl
         if (!rc) rc = commit_jobs(c);
         if (rc) return finish(rc);
       }
-      // two sweeps capture the graph, then `reps` sweeps are timed
-      cudaError_t e = copy_state(false);
-      if (e == cudaSuccess) rc = run_sweeps(c, 2, false);
-      if (e == cudaSuccess && !rc) e = cudaEventRecord(e0, c->s_main);
-      if (e == cudaSuccess && !rc) rc = run_sweeps(c, reps, false);
-      if (e == cudaSuccess && !rc) e = cudaEventRecord(e1, c->s_main);
-      if (e == cudaSuccess && !rc) e = cudaEventSynchronize(e1);
-      float ms = 0.f;
-      if (e == cudaSuccess && !rc) e = cudaEventElapsedTime(&ms, e0, e1);
+      double us = 0.0;
+      rc = time_sweeps(&us);
       if (rc) return finish(rc);
-      if (e != cudaSuccess)
-        return finish(fail(NFHMM_ECUDA, std::string("autotune: ") + cudaGetErrorString(e)));
-      const double us = 1e3 * ms / reps;
       if (us < best_us) {
         best_us = us;
         bestL = L;
@@ -1296,6 +1309,49 @@ int nfhmm_autotune(nfhmm_ctx* c, int reps, int* chunk_out, int* group_out, doubl
     c->group_auto = old_auto;
     set_fb_mode(c, old_seq);
     return finish(rc);
+  }
+  // the contractions' tile shapes beside the chosen form, one coordinate at
+  // a time (column tile of each contraction, then each ring depth), starting
+  // from the current shape, whose time under this form is measured first
+  if (c->use_tc) {
+    const int o1 = c->tc.bn1, o2 = c->tc.bn2, os1 = c->tc.st1, os2 = c->tc.st2;
+    int b[4] = {o1, o2, os1, os2};
+    double t_best = 0.0;
+    rc = time_sweeps(&t_best);
+    for (int coord = 0; coord < 4 && !rc; ++coord) {
+      std::vector<int> vals;
+      if (coord < 2) {
+        int cand[8];
+        const int n = tc_tile_candidates(c->tc.precision, coord, cand, 8);
+        vals.assign(cand, cand + n);
+      } else {
+        const int m = tc_max_stages(c->tc.precision, b[coord - 2]);
+        for (int st = 2; st < m; ++st) vals.push_back(st);   // m itself is depth 0
+        vals.push_back(0);
+      }
+      for (int v : vals) {
+        if (v == b[coord]) continue;
+        int t[4] = {b[0], b[1], b[2], b[3]};
+        t[coord] = v;
+        if (coord < 2) {   // a narrower or wider tile keeps the deepest ring
+          t[2 + coord] = 0;
+        }
+        if (tc_set_tiles(c->tc, t[0], t[1], t[2], t[3]) != 0) continue;
+        double us = 0.0;
+        rc = time_sweeps(&us);
+        if (rc) break;
+        if (us < t_best) {
+          t_best = us;
+          for (int i = 0; i < 4; ++i) b[i] = t[i];
+        }
+      }
+    }
+    if (rc || tc_set_tiles(c->tc, b[0], b[1], b[2], b[3]) != 0) {
+      tc_set_tiles(c->tc, o1, o2, os1, os2);
+      if (!rc) rc = fail(NFHMM_ECUDA, "autotune: tile shape: " + tc_last_error());
+      return finish(rc);
+    }
+    best_us = t_best;
   }
   rc = finish(NFHMM_OK);
   if (rc) return rc;
@@ -1351,6 +1407,30 @@ int nfhmm_set_option(nfhmm_ctx* c, int key, long long value) {
       if (value < 0 || value > 64)
         return fail(NFHMM_EINVAL, "forward-backward mode must be 0 (scan) or 1..64 (sequential)");
       return set_fb_mode(c, (int)value);
+    }
+    case NFHMM_OPT_TILE_GEMM1:
+    case NFHMM_OPT_TILE_GEMM2:
+    case NFHMM_OPT_TILE_STAGES1:
+    case NFHMM_OPT_TILE_STAGES2: {
+      if (!c->use_tc) return fail(NFHMM_EINVAL, "tile shapes apply to tensor-core contexts");
+      if (value < 0 || value > 1024) return fail(NFHMM_EINVAL, "tile option out of range");
+      int bn1 = c->tc.bn1, bn2 = c->tc.bn2, st1 = c->tc.st1, st2 = c->tc.st2;
+      if (key == NFHMM_OPT_TILE_GEMM1) bn1 = (int)value;
+      if (key == NFHMM_OPT_TILE_GEMM2) bn2 = (int)value;
+      if (key == NFHMM_OPT_TILE_STAGES1) st1 = (int)value;
+      if (key == NFHMM_OPT_TILE_STAGES2) st2 = (int)value;
+      // a narrower tile's deepest ring is deeper: keep a depth the new tile allows
+      if (st1 > tc_max_stages(c->tc.precision, bn1)) st1 = 0;
+      if (st2 > tc_max_stages(c->tc.precision, bn2)) st2 = 0;
+      int rc = enter(c);   // the plan's maps are read by launches already queued
+      if (rc) return rc;
+      CK(cudaStreamSynchronize(c->s_main));
+      CK(cudaStreamSynchronize(c->s_aux));
+      if (tc_set_tiles(c->tc, bn1, bn2, st1, st2) != 0)
+        return fail(NFHMM_EINVAL, "tile shape: " + tc_last_error());
+      c->bpart_ok = false;   // the bound's partials are counted per tile shape
+      c->bound_ok = false;
+      return leave(c);
     }
     case NFHMM_OPT_TEST_WAIT_TIMEOUT: {
       if (!c->use_tc) return fail(NFHMM_EINVAL, "the wait hook needs a tensor-core context");
@@ -1647,6 +1727,14 @@ int nfhmm_query(nfhmm_ctx* c, int key, long long* value) {
     case NFHMM_Q_FB_CHUNK: *value = c->fb.L; return NFHMM_OK;
     case NFHMM_Q_FB_GROUP: *value = c->fb.G; return NFHMM_OK;
     case NFHMM_Q_FB_MODE: *value = c->fb.seq; return NFHMM_OK;
+    case NFHMM_Q_TILE_GEMM1: *value = c->use_tc ? c->tc.bn1 : 0; return NFHMM_OK;
+    case NFHMM_Q_TILE_GEMM2: *value = c->use_tc ? c->tc.bn2 : 0; return NFHMM_OK;
+    case NFHMM_Q_TILE_STAGES1:
+      *value = !c->use_tc ? 0 : c->tc.st1 ? c->tc.st1 : tc_max_stages(c->tc.precision, c->tc.bn1);
+      return NFHMM_OK;
+    case NFHMM_Q_TILE_STAGES2:
+      *value = !c->use_tc ? 0 : c->tc.st2 ? c->tc.st2 : tc_max_stages(c->tc.precision, c->tc.bn2);
+      return NFHMM_OK;
     case NFHMM_Q_SWEEPS_DONE: *value = c->sweeps_done; return NFHMM_OK;
     case NFHMM_Q_DEVICE_BYTES: *value = (long long)c->device_bytes; return NFHMM_OK;
     case NFHMM_Q_FRAME_CAPACITY: *value = c->d.T; return NFHMM_OK;

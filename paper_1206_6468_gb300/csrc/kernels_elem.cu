@@ -27,15 +27,23 @@ constexpr unsigned FULL = 0xffffffffu;
 // g(alpha) (Kahan-compensated in float per lane, then double) into
 // fterm[t][h] for unit h of the frame.
 //
-// Two forms.  The frame form (Mp <= 1536): one warp per frame, warps
-// striding over frames; lane q takes the four consecutive elements 4q..4q+3,
-// 4(q+32).., so every load and store is a 16-byte vector; the frame's psi
-// is parked in shared memory and lane b then sums block b.  One unit per
-// frame.  The unit form (any size): one warp per unit of WB consecutive
-// blocks of a frame, one element per lane and step.
+// Two forms.  The segment form (a segment of SB whole blocks holds at most
+// 128 elements, a multiple of 4): one warp per (frame, segment), warps
+// striding over them; lane q takes the four consecutive elements 4q..4q+3
+// of the segment, so every load and store is a 16-byte vector and one pass
+// covers the segment; psi is parked in shared memory and lane b then sums
+// block b of the segment.  The unit form (any K): one warp per unit of WB
+// consecutive blocks of a frame, one element per lane and step.
 constexpr int WB = 16;
-constexpr int WFRAME_MAX = 1536;   // 8 warps x Mp floats within the default 48 KB
-constexpr int WFRAME_WARPS = 8;
+constexpr int WSEG_MAX = 128;   // elements per segment
+constexpr int WSEG_WARPS = 8;
+
+// blocks per segment of the segment form, or 0 when K admits none
+static int weights_seg_blocks(int K) {
+  for (int sb = WSEG_MAX / K; sb >= 1; --sb)
+    if ((sb * K) % 4 == 0) return sb;
+  return 0;
+}
 
 template <int FMT, bool BOUND>
 __device__ __forceinline__ void weights_elem(float alpha, float& psi, float& w, float& sa,
@@ -57,8 +65,8 @@ __device__ __forceinline__ void weights_elem(float alpha, float& psi, float& w, 
 }
 
 template <int FMT, bool BOUND>
-__global__ void __launch_bounds__(WFRAME_WARPS * 32) k_weights_frame(WeightsArgs a) {
-  extern __shared__ float wsm[];
+__global__ void __launch_bounds__(WSEG_WARPS * 32) k_weights_seg(WeightsArgs a, int SB, int NSEG) {
+  __shared__ __align__(16) float wsm[WSEG_WARPS][WSEG_MAX];
   // launched as a programmatic dependent of the kernel before it on the
   // stream (the replay that wrote d-hat): wait for it before reading
   // anything; the forward-backward pass that follows may start launching at
@@ -67,55 +75,58 @@ __global__ void __launch_bounds__(WFRAME_WARPS * 32) k_weights_frame(WeightsArgs
   griddep_launch_dependents();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int NB = a.S * a.N;
-  const int M4 = (a.M + 3) >> 2;
+  const int SE = SB * a.K;                      // elements per segment (a multiple of 4)
   const size_t SN = (size_t)a.Tstride * a.N;   // source stride of d-hat and phi-hat
-  float* ps = wsm + warp * a.Mp;
-  const int nwarps = gridDim.x * WFRAME_WARPS;
+  float* ps = wsm[warp];
+  const unsigned units = (unsigned)a.T * (unsigned)NSEG;
+  const unsigned nwarps = gridDim.x * WSEG_WARPS;
   unsigned bad = 0;
   float chk = 0.f;
-  for (int t = blockIdx.x * WFRAME_WARPS + warp; t < a.T; t += nwarps) {
+  for (unsigned u = blockIdx.x * WSEG_WARPS + warp; u < units; u += nwarps) {
+    const int t = (int)(u / (unsigned)NSEG), h = (int)(u - (unsigned)t * NSEG);
+    const int k0 = h * SE, k1 = min(k0 + SE, a.M);
     const size_t row = (size_t)t * a.Mp;
     const size_t toff = (size_t)t * a.N;
     float sa = 0.f, ca = 0.f, sg = 0.f, cg = 0.f;
     double big = 0.0;
-    for (int q = lane; q < M4; q += 32) {
-      const int k = 4 * q;
+    const int k = k0 + 4 * lane;
+    if (k < k1) {
       const float4 c4 = *reinterpret_cast<const float4*>(a.counts + row + k);
       const int4 e01 = *reinterpret_cast<const int4*>(a.ktab + k);
       const int4 e23 = *reinterpret_cast<const int4*>(a.ktab + k + 2);
       const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
       const int es[4] = {e01.x, e01.z, e23.x, e23.z};
       const int en[4] = {e01.y, e01.w, e23.y, e23.w};
-      const bool full = k + 4 <= a.M;
+      const bool full = k + 4 <= k1;
       float al[4], psi[4], w[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const float d = a.dhat[(size_t)es[u] * SN + toff + en[u]];
-        al[u] = cv[u] + a.gamma * d + 1.f;
-        if (full || k + u < a.M) {
-          weights_elem<FMT, BOUND>(al[u], psi[u], w[u], sa, ca, sg, cg, big);
+      for (int v = 0; v < 4; ++v) {
+        const float d = a.dhat[(size_t)es[v] * SN + toff + en[v]];
+        al[v] = cv[v] + a.gamma * d + 1.f;
+        if (full || k + v < k1) {
+          weights_elem<FMT, BOUND>(al[v], psi[v], w[v], sa, ca, sg, cg, big);
         } else {
-          psi[u] = 0.f;
-          w[u] = 0.f;
+          psi[v] = 0.f;
+          w[v] = 0.f;
         }
-        chk = fmaf(0.f, psi[u] + w[u], chk);   // stays 0 unless psi or w is NaN or infinite
+        chk = fmaf(0.f, psi[v] + w[v], chk);   // stays 0 unless psi or w is NaN or infinite
       }
-      *reinterpret_cast<float4*>(ps + k) = make_float4(psi[0], psi[1], psi[2], psi[3]);
+      *reinterpret_cast<float4*>(ps + 4 * lane) = make_float4(psi[0], psi[1], psi[2], psi[3]);
       if (full) {
         if (a.alpha)
           *reinterpret_cast<float4*>(a.alpha + row + k) = make_float4(al[0], al[1], al[2], al[3]);
         *reinterpret_cast<float4*>(a.w32 + row + k) = make_float4(w[0], w[1], w[2], w[3]);
         if (FMT == WF_TF32X2) {
-          float h[4], l[4];
+          float hh[4], ll[4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            h[u] = tf32_hi(w[u]);
-            l[u] = tf32_hi(w[u] - h[u]);
+          for (int v = 0; v < 4; ++v) {
+            hh[v] = tf32_hi(w[v]);
+            ll[v] = tf32_hi(w[v] - hh[v]);
           }
           *reinterpret_cast<float4*>(reinterpret_cast<float*>(a.wop_hi) + row + k) =
-              make_float4(h[0], h[1], h[2], h[3]);
+              make_float4(hh[0], hh[1], hh[2], hh[3]);
           *reinterpret_cast<float4*>(reinterpret_cast<float*>(a.wop_lo) + row + k) =
-              make_float4(l[0], l[1], l[2], l[3]);
+              make_float4(ll[0], ll[1], ll[2], ll[3]);
         } else if (FMT == WF_BF16) {
           const __nv_bfloat162 b01 = __floats2bfloat162_rn(w[0], w[1]);
           const __nv_bfloat162 b23 = __floats2bfloat162_rn(w[2], w[3]);
@@ -126,36 +137,36 @@ __global__ void __launch_bounds__(WFRAME_WARPS * 32) k_weights_frame(WeightsArgs
         }
       } else {
         // the frame's last elements: padding (k >= M) is never touched
-        for (int u = 0; u < 4 && k + u < a.M; ++u) {
-          if (a.alpha) a.alpha[row + k + u] = al[u];
-          a.w32[row + k + u] = w[u];
+        for (int v = 0; v < 4 && k + v < k1; ++v) {
+          if (a.alpha) a.alpha[row + k + v] = al[v];
+          a.w32[row + k + v] = w[v];
           if (FMT == WF_TF32X2) {
-            const float h = tf32_hi(w[u]);
-            reinterpret_cast<float*>(a.wop_hi)[row + k + u] = h;
-            reinterpret_cast<float*>(a.wop_lo)[row + k + u] = tf32_hi(w[u] - h);
+            const float hh = tf32_hi(w[v]);
+            reinterpret_cast<float*>(a.wop_hi)[row + k + v] = hh;
+            reinterpret_cast<float*>(a.wop_lo)[row + k + v] = tf32_hi(w[v] - hh);
           } else if (FMT == WF_BF16) {
-            reinterpret_cast<__nv_bfloat16*>(a.wop_hi)[row + k + u] = __float2bfloat16_rn(w[u]);
+            reinterpret_cast<__nv_bfloat16*>(a.wop_hi)[row + k + v] = __float2bfloat16_rn(w[v]);
           }
         }
       }
     }
     __syncwarp();
-    for (int b = lane; b < NB; b += 32) {
-      const float* pb = ps + b * a.K;
+    for (int bb = lane; bb < SB && h * SB + bb < NB; bb += 32) {   // block bb of the segment
+      const float* pb = ps + bb * a.K;
       float x = 0.f;
       for (int j = 0; j < a.K; ++j) x += pb[j];
-      const int2 e = a.ktab[b * a.K];
+      const int2 e = a.ktab[(h * SB + bb) * a.K];
       a.phi[(size_t)e.x * SN + toff + e.y] = a.gamma * x;
     }
     if (BOUND) {
       const double s0 = warp_sum_d((double)sa - (double)ca);
       const double sgt = warp_sum_d(((double)sg - (double)cg) + big);
       if (lane == 0) {
-        a.fterm[2 * (size_t)t] = s0;
-        a.fterm[2 * (size_t)t + 1] = sgt;
+        a.fterm[2 * (size_t)u] = s0;
+        a.fterm[2 * (size_t)u + 1] = sgt;
       }
     }
-    __syncwarp();   // every lane is done with ps before the next frame
+    __syncwarp();   // every lane is done with ps before the next segment
   }
   if (!(chk == 0.f)) bad |= ERR_NONFINITE;
   bad = __reduce_or_sync(FULL, bad);
@@ -222,10 +233,21 @@ __global__ void __launch_bounds__(256) k_weights(WeightsArgs a) {
   }
 }
 
-static bool weights_frame_form(int Mp) { return Mp <= WFRAME_MAX; }
+// The segment form when K admits one and the unit counts fit 32 bits.
+static int weights_seg_form(int S, int N, int K, int T, int* SB, int* NSEG) {
+  const int sb = weights_seg_blocks(K);
+  if (sb == 0) return 0;
+  const int nseg = (S * N + sb - 1) / sb;
+  if ((long long)T * nseg >= (1ll << 31)) return 0;
+  if (SB) *SB = sb;
+  if (NSEG) *NSEG = nseg;
+  return 1;
+}
 
-int weights_units(int S, int N, int Mp) {
-  return weights_frame_form(Mp) ? 1 : (S * N + WB - 1) / WB;
+int weights_units(int S, int N, int K, int T) {
+  int nseg = 0;
+  if (weights_seg_form(S, N, K, T, nullptr, &nseg)) return nseg;
+  return (S * N + WB - 1) / WB;
 }
 
 __global__ void k_element_table(int M, int Mp, int K, int N, int2* ktab) {
@@ -245,23 +267,26 @@ void launch_element_table(int M, int Mp, int K, int N, int2* ktab, cudaStream_t 
 void launch_weights(const WeightsArgs& a, int fmt, cudaStream_t st) {
   const bool b = a.fterm != nullptr;
   void (*k)(WeightsArgs) = nullptr;
+  void (*k2)(WeightsArgs, int, int) = nullptr;
   cudaLaunchConfig_t cfg = {};
-  if (weights_frame_form(a.Mp)) {
+  int SB = 0, NSEG = 0;
+  const bool seg = weights_seg_form(a.S, a.N, a.K, a.Tstride, &SB, &NSEG);
+  if (seg) {
     switch (fmt) {
-      case WF_TF32X2: k = b ? k_weights_frame<WF_TF32X2, true> : k_weights_frame<WF_TF32X2, false>; break;
-      case WF_BF16: k = b ? k_weights_frame<WF_BF16, true> : k_weights_frame<WF_BF16, false>; break;
-      default: k = b ? k_weights_frame<WF_F32, true> : k_weights_frame<WF_F32, false>; break;
+      case WF_TF32X2: k2 = b ? k_weights_seg<WF_TF32X2, true> : k_weights_seg<WF_TF32X2, false>; break;
+      case WF_BF16: k2 = b ? k_weights_seg<WF_BF16, true> : k_weights_seg<WF_BF16, false>; break;
+      default: k2 = b ? k_weights_seg<WF_F32, true> : k_weights_seg<WF_F32, false>; break;
     }
-    // warps stride over frames: enough blocks to fill every SM a few times
+    // warps stride over the (frame, segment) units
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
       sms = 1;
-    const long long need = ((long long)a.T + WFRAME_WARPS - 1) / WFRAME_WARPS;
-    const long long cap = (long long)sms * 8;
+    const long long need = ((long long)a.T * NSEG + WSEG_WARPS - 1) / WSEG_WARPS;
+    const long long cap = (long long)sms * 16;
     cfg.gridDim = dim3((unsigned)(need < cap ? need : cap));
-    cfg.blockDim = dim3(WFRAME_WARPS * 32);
-    cfg.dynamicSmemBytes = (size_t)WFRAME_WARPS * a.Mp * sizeof(float);
+    cfg.blockDim = dim3(WSEG_WARPS * 32);
+    cfg.dynamicSmemBytes = 0;
   } else {
     switch (fmt) {
       case WF_TF32X2: k = b ? k_weights<WF_TF32X2, true> : k_weights<WF_TF32X2, false>; break;
@@ -284,7 +309,10 @@ void launch_weights(const WeightsArgs& a, int fmt, cudaStream_t st) {
   const bool legacy = st == nullptr || st == cudaStreamLegacy;
   cfg.attrs = legacy ? nullptr : attr;
   cfg.numAttrs = legacy ? 0 : 1;
-  cudaLaunchKernelEx(&cfg, k, a);
+  if (seg)
+    cudaLaunchKernelEx(&cfg, k2, a, SB, NSEG);
+  else
+    cudaLaunchKernelEx(&cfg, k, a);
 }
 
 // ------------------------------------------------------------------- fills
@@ -436,7 +464,7 @@ __global__ void k_bound_frames(BoundArgs a) {
   sg = warp_sum_d(sg);
   if (lane == 0) {
     double vl = 0.0;
-    for (int j = 0; j < a.nbpart; ++j) vl += a.bpart[(size_t)t * a.nbpart + j];
+    for (int j = 0; j < a.nbpart_used; ++j) vl += a.bpart[(size_t)t * a.nbpart + j];
     const double psi0 = digamma_d(s0);
     const double term = vl - a.v[t] * psi0 + a.konst - lgamma(s0) + sg + psi0 * (s0 - (double)a.M) -
                         (double)a.S * (double)a.gamma * (double)a.K * psi0;
@@ -455,7 +483,7 @@ __global__ void k_bound_frames_fused(BoundArgs a) {
     sg += a.fterm[2 * ((size_t)t * a.funits + h) + 1];
   }
   double vl = 0.0;
-  for (int j = 0; j < a.nbpart; ++j) vl += a.bpart[(size_t)t * a.nbpart + j];
+  for (int j = 0; j < a.nbpart_used; ++j) vl += a.bpart[(size_t)t * a.nbpart + j];
   const double psi0 = digamma_d(s0);
   a.frame_terms[t] = vl - a.v[t] * psi0 + a.konst - lgamma(s0) + sg + psi0 * (s0 - (double)a.M) -
                      (double)a.S * (double)a.gamma * (double)a.K * psi0;

@@ -41,9 +41,10 @@ namespace {
 using namespace tc;
 
 constexpr int BM = 128;
-constexpr int BN1 = 128;           // reconstruction: columns = frequencies
-constexpr int BN2 = 160;           // back-projection: columns = elements
+constexpr int BN1 = 128;           // default reconstruction tile: columns = frequencies
+constexpr int BN2 = 160;           // default back-projection tile: columns = elements
 constexpr int BNX = 64;            // exact inference back-projection: the S*K elements of a joint state
+constexpr int SMEM_BUDGET = 227 * 1024;   // per-block opt-in limit
 constexpr int EPI_WARPS = 8;                    // two per TMEM lane quarter
 constexpr int NUM_THREADS = 64 + EPI_WARPS * 32;  // TMA warp, MMA warp, epilogue
 enum TcEpi { TEPI_RATIO = 0, TEPI_SCALE = 1 };
@@ -56,7 +57,6 @@ struct KindCfg<KIND_TF32X3> {
   static constexpr int BK = 32;           // 128 bytes of K per stage row
   static constexpr int KSTEP = 8;         // K per MMA instruction
   static constexpr int NOPS = 2;          // hi and lo copies
-  static constexpr int STAGES = 3;
 };
 template <>
 struct KindCfg<KIND_BF16> {
@@ -64,7 +64,6 @@ struct KindCfg<KIND_BF16> {
   static constexpr int BK = 64;
   static constexpr int KSTEP = 16;
   static constexpr int NOPS = 1;
-  static constexpr int STAGES = 6;
 };
 
 template <int KIND, int BN>
@@ -73,7 +72,11 @@ struct TileCfg {
   static constexpr int A_BYTES = BM * 128;          // one operand copy of A per stage
   static constexpr int B_BYTES = BN * 128;
   static constexpr int STAGE_BYTES = K::NOPS * (A_BYTES + B_BYTES);
-  static constexpr int SMEM = K::STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+  static constexpr int EXTRA = 1024 /*align*/ + 256 /*barriers*/;
+  // the deepest shared-memory ring that fits (at most 8 stages)
+  static constexpr int MAX_STAGES =
+      (SMEM_BUDGET - EXTRA) / STAGE_BYTES < 8 ? (SMEM_BUDGET - EXTRA) / STAGE_BYTES : 8;
+  static constexpr int smem(int stages) { return stages * STAGE_BYTES + EXTRA; }
   static constexpr int TMEM_COLS = 512;
   static constexpr int NACC = 512 / BN;                          // accumulators of BN columns
   static constexpr int NMAIN = K::NOPS == 2 ? NACC - 1 : NACC;   // for hi*hi (or BF16) products
@@ -101,6 +104,7 @@ struct TcArgs {
   // of which the first bvalid are real; item b reads B rows from b * bstride
   // on, and V (RATIO) is shared by the items.  brows = 0: one item.
   int brows, bvalid, bstride;
+  int stages;                     // depth of the shared-memory ring (2 .. MAX_STAGES)
   // test hook, 0 in normal use: the MMA thread first waits this many
   // nanoseconds on a barrier nothing arrives on, so that the wait gives up
   // and the CTA takes its wind-down path (error word ERR_TIMEOUT)
@@ -118,7 +122,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     k_tc_gemm(const __grid_constant__ Maps maps, const TcArgs p) {
   using K = KindCfg<KIND>;
   using Cfg = TileCfg<KIND, BN>;
-  constexpr int STAGES = K::STAGES;
+  static_assert(Cfg::MAX_STAGES >= 2, "tile too large for a two-stage ring");
+  static_assert(BN % 32 == 0 && BN <= 256, "the epilogue halves are multiples of 16 columns");
+  const int STAGES = p.stages;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -172,14 +178,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     // ---------------- TMA producer
     if (lane == 0) {
       long long it = 0;   // K-blocks issued over all of this CTA's tiles
+      int s = 0;          // its ring slot, it % STAGES
+      uint32_t ph = 0;    // and (it / STAGES) & 1
       for (int tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x) {
         const int row0 = p.row_off + (tile / ncol) * BM, col0 = (tile % ncol) * BN;
         const int bitem = p.brows ? row0 / p.brows : 0;   // batch item of this row tile
         const int bcol0 = col0 + bitem * p.bstride;         // its first B row
-        for (int kb = 0; kb < nkb; ++kb, ++it) {
-          const int s = (int)(it % STAGES);
-          if (it >= STAGES &&
-              !mbar_wait(&empty[s], (uint32_t)((it / STAGES) - 1) & 1, abort_flag)) {
+        for (int kb = 0; kb < nkb; ++kb) {
+          if (it >= STAGES && !mbar_wait(&empty[s], ph ^ 1u, abort_flag)) {
             give_up();
             break;
           }
@@ -190,6 +196,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           if (K::NOPS == 2) {
             tma_load_2d(stage_ptr(s, 1), &maps.a_lo, &full[s], kx, row0);
             tma_load_2d(stage_ptr(s, 3), &maps.b_lo, &full[s], kx, bcol0);
+          }
+          ++it;
+          if (++s == STAGES) {
+            s = 0;
+            ph ^= 1u;
           }
         }
         if (*abort_flag) break;
@@ -204,7 +215,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     // ---------------- MMA issuer
     if (lane == 0) {
       constexpr uint32_t ID = idesc<KIND>(BM, BN);
-      long long it = 0;
+      int s = 0;          // ring slot of the next K-block
+      uint32_t ph = 0;    // and the phase its full barrier completes
       int j = 0;   // this CTA's tile count
       if (p.inject_wait_ns && !mbar_wait(never, 0, abort_flag, p.inject_wait_ns)) give_up();
       for (int tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x, ++j) {
@@ -215,9 +227,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         }
         tc_fence_after();
         bool ok = true;
-        for (int kb = 0; kb < nkb; ++kb, ++it) {
-          const int s = (int)(it % STAGES);
-          if (*abort_flag || !mbar_wait(&full[s], (uint32_t)(it / STAGES) & 1, abort_flag)) {
+        for (int kb = 0; kb < nkb; ++kb) {
+          if (*abort_flag || !mbar_wait(&full[s], ph, abort_flag)) {
             give_up();
             ok = false;
             break;
@@ -238,6 +249,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             }
           }
           mma_commit(&empty[s]);
+          if (++s == STAGES) {
+            s = 0;
+            ph ^= 1u;
+          }
         }
         if (!ok) break;
         mma_commit(accum);  // fires once every MMA issued above has completed
@@ -463,17 +478,19 @@ int sm_count(int dev) {
 }
 
 template <int KIND, int BN, int EPI>
-cudaError_t launch_gemm(const Maps& maps, const TcArgs& a, cudaStream_t st, int reserve = 0) {
+cudaError_t launch_gemm(const Maps& maps, TcArgs a, cudaStream_t st, int reserve = 0) {
   using Cfg = TileCfg<KIND, BN>;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  if (a.stages < 2 || a.stages > Cfg::MAX_STAGES) a.stages = Cfg::MAX_STAGES;
   static cudaError_t attr[kMaxDevices];
   static bool attr_set[kMaxDevices] = {};
   if (!attr_set[dev]) {
     attr[dev] = cudaFuncSetAttribute(k_tc_gemm<KIND, BN, EPI>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     Cfg::smem(Cfg::MAX_STAGES));
     attr_set[dev] = true;
   }
   if (attr[dev] != cudaSuccess) return attr[dev];
@@ -483,8 +500,40 @@ cudaError_t launch_gemm(const Maps& maps, const TcArgs& a, cudaStream_t st, int 
   // persistent: one CTA per SM, less the SMs reserved (at most half of them)
   const int avail = sms - (reserve < sms / 2 ? reserve : sms / 2);
   const int grid = (int)(tiles < avail ? tiles : avail);
-  k_tc_gemm<KIND, BN, EPI><<<grid, NUM_THREADS, Cfg::SMEM, st>>>(maps, a);
+  k_tc_gemm<KIND, BN, EPI><<<grid, NUM_THREADS, Cfg::smem(a.stages), st>>>(maps, a);
   return cudaGetLastError();
+}
+
+// The column tiles the tile-shape tuner may choose, per contraction and kind.
+// FP32 (split TF32) keeps at least two accumulators for the hi*hi products
+// (BN <= 160); BF16 may take wider tiles.
+template <int EPI, int KIND>
+cudaError_t launch_tile(int bn, const Maps& maps, const TcArgs& a, cudaStream_t st, int reserve) {
+  switch (bn) {
+    case 64: return launch_gemm<KIND, 64, EPI>(maps, a, st, reserve);
+    case 96: return launch_gemm<KIND, 96, EPI>(maps, a, st, reserve);
+    case 128: return launch_gemm<KIND, 128, EPI>(maps, a, st, reserve);
+    case 160:
+      if (EPI == TEPI_SCALE) return launch_gemm<KIND, 160, EPI>(maps, a, st, reserve);
+      break;
+    case 192:
+      if (KIND == KIND_BF16) return launch_gemm<KIND, 192, EPI>(maps, a, st, reserve);
+      break;
+    default: break;
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int KIND>
+int max_stages(int bn) {
+  switch (bn) {
+    case 64: return TileCfg<KIND, 64>::MAX_STAGES;
+    case 96: return TileCfg<KIND, 96>::MAX_STAGES;
+    case 128: return TileCfg<KIND, 128>::MAX_STAGES;
+    case 160: return TileCfg<KIND, 160>::MAX_STAGES;
+    case 192: return TileCfg<KIND, 192>::MAX_STAGES;
+    default: return 0;
+  }
 }
 
 }  // namespace
@@ -504,6 +553,77 @@ int tc_col_tiles_gemm1(int Fp) { return 2 * ((Fp + BN1 - 1) / BN1); }
 
 static Maps* maps_of(TcPlan& p, int which) {
   return reinterpret_cast<Maps*>(&p.maps[which * 4][0]);
+}
+
+// The tile shapes the tuner chooses from: column tiles of each contraction
+// (its output columns per 128-row tile) for each kind.
+static const int kTilesF32[2][4] = {{64, 96, 128, 0}, {64, 96, 128, 160}};
+static const int kTilesBF16[2][5] = {{64, 96, 128, 192, 0}, {64, 96, 128, 160, 192}};
+
+int tc_tile_candidates(int precision, int which, int* out, int max_out) {
+  int n = 0;
+  const int* list = precision == 1 ? kTilesBF16[which] : kTilesF32[which];
+  const int len = precision == 1 ? 5 : 4;
+  for (int i = 0; i < len && n < max_out; ++i)
+    if (list[i]) out[n++] = list[i];
+  return n;
+}
+
+int tc_max_stages(int precision, int bn) {
+  return precision == 1 ? max_stages<KIND_BF16>(bn) : max_stages<KIND_TF32X3>(bn);
+}
+
+int tc_bpart_columns_max(int Fp) { return 2 * ((Fp + 63) / 64); }
+int tc_bpart_used(const TcPlan& p) { return 2 * ((p.Fp + p.bn1 - 1) / p.bn1); }
+
+// (Re)encode the B operands' tensor maps for the plan's column tiles.
+static bool encode_b_maps(TcPlan& p) {
+  const bool bf = p.precision == 1;
+  const int es = bf ? 2 : 4;
+  const int bk = bf ? KindCfg<KIND_BF16>::BK : KindCfg<KIND_TF32X3>::BK;
+  Maps* m1 = maps_of(p, 0);
+  Maps* m2 = maps_of(p, 1);
+  bool ok = make_map(&m1->b_hi, p.bF_hi, es, p.Mp, p.Fp, p.Mp, bk, p.bn1) &&
+            make_map(&m2->b_hi, p.bM_hi, es, p.Fp, p.Mp, p.Fp, bk, p.bn2);
+  if (ok && !bf)
+    ok = make_map(&m1->b_lo, p.bF_lo, es, p.Mp, p.Fp, p.Mp, bk, p.bn1) &&
+         make_map(&m2->b_lo, p.bM_lo, es, p.Fp, p.Mp, p.Fp, bk, p.bn2);
+  if (ok && bf) {  // unused lo maps: copies of hi (never read)
+    m1->b_lo = m1->b_hi;
+    m2->b_lo = m2->b_hi;
+  }
+  return ok;
+}
+
+int tc_set_tiles(TcPlan& p, int bn1, int bn2, int st1, int st2) {
+  int c1[8], c2[8];
+  const int n1 = tc_tile_candidates(p.precision, 0, c1, 8);
+  const int n2 = tc_tile_candidates(p.precision, 1, c2, 8);
+  bool ok1 = false, ok2 = false;
+  for (int i = 0; i < n1; ++i) ok1 |= c1[i] == bn1;
+  for (int i = 0; i < n2; ++i) ok2 |= c2[i] == bn2;
+  if (!ok1 || !ok2) {
+    g_tc_err = "column tile not among the tuner's shapes for this precision";
+    return -1;
+  }
+  if ((st1 != 0 && (st1 < 2 || st1 > tc_max_stages(p.precision, bn1))) ||
+      (st2 != 0 && (st2 < 2 || st2 > tc_max_stages(p.precision, bn2)))) {
+    g_tc_err = "ring depth must be 0 (deepest) or 2.." + std::to_string(tc_max_stages(p.precision, bn1)) +
+               " / " + std::to_string(tc_max_stages(p.precision, bn2));
+    return -1;
+  }
+  const int o1 = p.bn1, o2 = p.bn2;
+  p.bn1 = bn1;
+  p.bn2 = bn2;
+  if (!encode_b_maps(p)) {
+    p.bn1 = o1;
+    p.bn2 = o2;
+    encode_b_maps(p);
+    return -1;
+  }
+  p.st1 = st1;
+  p.st2 = st2;
+  return 0;
 }
 
 int tc_plan(TcPlan& p, int precision, int T, int M, int Mp, int F, int Fp, const float* V,
@@ -546,21 +666,19 @@ int tc_plan(TcPlan& p, int precision, int T, int M, int Mp, int F, int Fp, const
   Maps* m1 = maps_of(p, 0);
   Maps* m2 = maps_of(p, 1);
   bool ok = make_map(&m1->a_hi, p.w_hi, es, Mp, T, Mp, bk, BM) &&
-            make_map(&m1->b_hi, p.bF_hi, es, Mp, Fp, Mp, bk, BN1) &&
-            make_map(&m2->a_hi, p.q_hi, es, Fp, T, Fp, bk, BM) &&
-            make_map(&m2->b_hi, p.bM_hi, es, Fp, Mp, Fp, bk, BN2);
+            make_map(&m2->a_hi, p.q_hi, es, Fp, T, Fp, bk, BM);
   if (ok && !bf)
     ok = make_map(&m1->a_lo, p.w_lo, es, Mp, T, Mp, bk, BM) &&
-         make_map(&m1->b_lo, p.bF_lo, es, Mp, Fp, Mp, bk, BN1) &&
-         make_map(&m2->a_lo, p.q_lo, es, Fp, T, Fp, bk, BM) &&
-         make_map(&m2->b_lo, p.bM_lo, es, Fp, Mp, Fp, bk, BN2);
+         make_map(&m2->a_lo, p.q_lo, es, Fp, T, Fp, bk, BM);
   if (!ok) return -1;
   if (bf) {  // unused lo maps: copies of hi (never read)
     m1->a_lo = m1->a_hi;
-    m1->b_lo = m1->b_hi;
     m2->a_lo = m2->a_hi;
-    m2->b_lo = m2->b_hi;
   }
+  p.bn1 = BN1;
+  p.bn2 = BN2;
+  p.st1 = p.st2 = 0;
+  if (!encode_b_maps(p)) return -1;
   p.bF_src = WF;
   p.bM_src = WM;
   return 0;
@@ -593,13 +711,14 @@ int tc_gemm1(TcPlan& p, int row_off, int rows, double* bpart, int reserve, cudaS
   a.bpart = bpart;
   a.err = p.err;
   cudaError_t e;
+  a.stages = p.st1;
   if (p.precision == 1) {
     a.out_bf16 = reinterpret_cast<__nv_bfloat16*>(p.q_hi);
-    e = launch_gemm<KIND_BF16, BN1, TEPI_RATIO>(*maps_of(p, 0), a, st, reserve);
+    e = launch_tile<TEPI_RATIO, KIND_BF16>(p.bn1, *maps_of(p, 0), a, st, reserve);
   } else {
     a.out_f32 = reinterpret_cast<float*>(p.q_hi);
     a.out_lo = reinterpret_cast<float*>(p.q_lo);
-    e = launch_gemm<KIND_TF32X3, BN1, TEPI_RATIO>(*maps_of(p, 0), a, st, reserve);
+    e = launch_tile<TEPI_RATIO, KIND_TF32X3>(p.bn1, *maps_of(p, 0), a, st, reserve);
   }
   if (e != cudaSuccess) {
     g_tc_err = cudaGetErrorString(e);
@@ -620,10 +739,11 @@ int tc_gemm2(TcPlan& p, int row_off, int rows, int reserve, cudaStream_t st) {
   a.ldo = p.Mp;
   a.err = p.err;
   cudaError_t e;
+  a.stages = p.st2;
   if (p.precision == 1)
-    e = launch_gemm<KIND_BF16, BN2, TEPI_SCALE>(*maps_of(p, 1), a, st, reserve);
+    e = launch_tile<TEPI_SCALE, KIND_BF16>(p.bn2, *maps_of(p, 1), a, st, reserve);
   else
-    e = launch_gemm<KIND_TF32X3, BN2, TEPI_SCALE>(*maps_of(p, 1), a, st, reserve);
+    e = launch_tile<TEPI_SCALE, KIND_TF32X3>(p.bn2, *maps_of(p, 1), a, st, reserve);
   if (e != cudaSuccess) {
     g_tc_err = cudaGetErrorString(e);
     return -1;

@@ -36,12 +36,13 @@ struct WeightsArgs {
   void* wop_hi;         // format-specific operand copies (may be null)
   void* wop_lo;
   float* phi;           // S x T x N (without the -gamma K psi(alpha_t0) constant)
-  double* fterm;        // null, or T x weights_units(S, N, Mp) x 2: per unit of the frame,
+  double* fterm;        // null, or T x weights_units(S, N, K, Tstride) x 2: per unit of the frame,
                         // (sum_k alpha_tk, sum_k g(alpha_tk)) for the bound
   unsigned* err;
 };
 void launch_weights(const WeightsArgs& a, int fmt, cudaStream_t st);
-int weights_units(int S, int N, int Mp);   // units per frame of the weights kernel's bound sums
+// units per frame of the weights kernel's bound sums (T: frame capacity)
+int weights_units(int S, int N, int K, int T);
 void launch_element_table(int M, int Mp, int K, int N, int2* ktab, cudaStream_t st);
 
 // Fill buf[t*ld + k] = (k < M) ? value : 0 for t < T, k < ld.
@@ -157,7 +158,8 @@ struct BoundArgs {
   double konst;            // lnGamma(M + gamma S K) - S K lnGamma(1 + gamma)
   const float* alpha;      // T x Mp
   const double* v;         // T
-  const double* bpart; int nbpart;
+  const double* bpart; int nbpart;   // bpart: T x nbpart (row stride)
+  int nbpart_used;         // partials per frame the contraction that formed them wrote
   const double* fterm;     // null, or T x funits x 2 per-unit sums from the weights kernel
   int funits;
   const double* logZ;      // S x njobs

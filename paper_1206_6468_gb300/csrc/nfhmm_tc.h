@@ -24,6 +24,9 @@ struct TcPlan {
   const float* bF_src = nullptr;  // beta by frequency (Fp x Mp), float
   const float* bM_src = nullptr;  // beta by element (Mp x Fp), float
   int nbpart = 0;                 // columns of the bound-partial array
+  // tile shape: column tile of each contraction, and its shared-memory ring
+  // depth (0: the deepest that fits); see tc_set_tiles
+  int bn1 = 128, bn2 = 160, st1 = 0, st2 = 0;
   // test hook: the next tc_gemm1 launch makes its MMA thread wait this long on
   // a barrier nothing arrives on (see k_tc_gemm); cleared by that launch
   unsigned long long inject_wait_ns = 0;
@@ -65,6 +68,16 @@ int tc_exact_gemm2(ExactTc& p, cudaStream_t st);
 void tc_exact_free(ExactTc& p);
 
 bool tc_available();
+// Tile shapes: the column tiles the tuner may choose for contraction `which`
+// (0 reconstruction, 1 back-projection) at a precision; the deepest ring for
+// a column tile; set a plan's shape (re-encodes its tensor maps; 0 on
+// success, -1 with tc_last_error otherwise).
+int tc_tile_candidates(int precision, int which, int* out, int max_out);
+int tc_max_stages(int precision, int bn);
+int tc_set_tiles(TcPlan& p, int bn1, int bn2, int st1, int st2);
+// bound partials per frame: allocated for the narrowest tile, used by the plan's
+int tc_bpart_columns_max(int Fp);
+int tc_bpart_used(const TcPlan& p);
 std::string tc_last_error();
 int tc_col_tiles_gemm1(int Fp);
 int tc_plan(TcPlan& p, int precision, int T, int M, int Mp, int F, int Fp, const float* V,

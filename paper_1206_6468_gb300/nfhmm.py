@@ -29,9 +29,11 @@ INIT_UNIFORM, INIT_PRIOR = 0, 1
 SEP_MEAN, SEP_EXPECTATION = 0, 1
 STAGES = {"weights": 0, "gemm1": 1, "gemm2": 2, "fb": 3, "bound": 4, "init": 5}
 QUERIES = {"tensor_cores": 0, "fb_chunk": 1, "sweeps_done": 2, "device_bytes": 3,
-           "frame_capacity": 4, "max_jobs": 5, "fb_group": 6, "fb_mode": 7}
+           "frame_capacity": 4, "max_jobs": 5, "fb_group": 6, "fb_mode": 7, "tile_gemm1": 8,
+           "tile_gemm2": 9, "tile_stages1": 10, "tile_stages2": 11}
 OPTIONS = {"fb_chunk": 0, "fb_products": 1, "graphs": 2, "fb_group": 3, "profile_stride": 4,
-           "fb_mode": 5, "test_wait_timeout": 6}
+           "fb_mode": 5, "test_wait_timeout": 6, "tile_gemm1": 7, "tile_gemm2": 8,
+           "tile_stages1": 9, "tile_stages2": 10}
 FB_PRODUCTS = {"simt": 0, "tc": 1}
 PRECISIONS = {"fp32": FP32, "bf16": BF16, "fp32_simt": FP32_SIMT}
 
@@ -251,8 +253,22 @@ class VIContext:
         L, G, us = _i(), _i(), ctypes.c_double()
         _check(_lib.nfhmm_autotune(self._h, int(reps), ctypes.byref(L), ctypes.byref(G),
                                    ctypes.byref(us)), "nfhmm_autotune")
-        return {"fb_chunk": L.value, "fb_group": G.value, "fb_mode": self.query("fb_mode"),
-                "us": us.value}
+        out = {"fb_chunk": L.value, "fb_group": G.value, "fb_mode": self.query("fb_mode"),
+               "us": us.value}
+        if self.query("tensor_cores"):
+            out["tiles"] = self.tiles()
+        return out
+
+    def tiles(self) -> dict:
+        """The contractions' tile shapes: column tile and ring depth of each."""
+        return {k: self.query(k) for k in ("tile_gemm1", "tile_gemm2", "tile_stages1",
+                                           "tile_stages2")}
+
+    def set_tiles(self, gemm1=None, gemm2=None, stages1=None, stages2=None):
+        for k, v in (("tile_gemm1", gemm1), ("tile_gemm2", gemm2), ("tile_stages1", stages1),
+                     ("tile_stages2", stages2)):
+            if v is not None:
+                self.set_option(k, v)
 
     def set_option(self, key: str, value):
         """fb_chunk: frames per chunk (1..128); fb_products: "simt" or "tc";
@@ -260,7 +276,8 @@ class VIContext:
         profile_stride: time the stages of every k-th sweep of a run;
         fb_mode: 0 the scan over chunks, k >= 1 the sequential form with k
         chains per block; test_wait_timeout: ns, the failure-path test hook
-        (NFHMM_OPT_TEST_WAIT_TIMEOUT)."""
+        (NFHMM_OPT_TEST_WAIT_TIMEOUT); tile_gemm1, tile_gemm2: column tiles of
+        the contractions; tile_stages1, tile_stages2: their ring depths."""
         if key == "fb_products":
             value = FB_PRODUCTS[value]
         _check(_lib.nfhmm_set_option(self._h, OPTIONS[key], int(value)), "nfhmm_set_option")
