@@ -591,6 +591,7 @@ def run_batched(args, rank, world, local, precision=None, data=None, steps=None,
                                    if tuned["fb_mode"] else "scan",
                                    "picked_by": "nfhmm_autotune",
                                    "sweep_us": round(tuned["us"], 1)},
+                   "contraction_tiles": dict(tuned.get("tiles") or {}, picked_by="nfhmm_autotune"),
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline_of(prof, T, 2, 40, 10, 513, precision, tc, peaks, steps * sweeps,
                                 fb_path=fb_path),
@@ -850,6 +851,7 @@ def run_single(args, rank, world, local):
                                    if tuned["fb_mode"] else "scan",
                                    "picked_by": "nfhmm_autotune",
                                    "sweep_us": round(tuned["us"], 1)},
+                   "contraction_tiles": dict(tuned.get("tiles") or {}, picked_by="nfhmm_autotune"),
                    "parallelism": f"replicas x{world}"},
         "roofline": dict(roofline_of(prof, p.T, p.S, p.N, p.K, p.F, args.precision, tc, peaks,
                                      args.steps * sweeps, f"paper_size_{args.precision}",
