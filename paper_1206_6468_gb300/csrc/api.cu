@@ -1419,9 +1419,10 @@ int nfhmm_set_option(nfhmm_ctx* c, int key, long long value) {
       if (key == NFHMM_OPT_TILE_GEMM2) bn2 = (int)value;
       if (key == NFHMM_OPT_TILE_STAGES1) st1 = (int)value;
       if (key == NFHMM_OPT_TILE_STAGES2) st2 = (int)value;
-      // a narrower tile's deepest ring is deeper: keep a depth the new tile allows
-      if (st1 > tc_max_stages(c->tc.precision, bn1)) st1 = 0;
-      if (st2 > tc_max_stages(c->tc.precision, bn2)) st2 = 0;
+      // a new column tile keeps the depth only if it can hold it (else the
+      // deepest); a depth asked for explicitly is validated as given
+      if (key == NFHMM_OPT_TILE_GEMM1 && st1 > tc_max_stages(c->tc.precision, bn1)) st1 = 0;
+      if (key == NFHMM_OPT_TILE_GEMM2 && st2 > tc_max_stages(c->tc.precision, bn2)) st2 = 0;
       int rc = enter(c);   // the plan's maps are read by launches already queued
       if (rc) return rc;
       CK(cudaStreamSynchronize(c->s_main));

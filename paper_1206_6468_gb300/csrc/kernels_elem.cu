@@ -27,23 +27,14 @@ constexpr unsigned FULL = 0xffffffffu;
 // g(alpha) (Kahan-compensated in float per lane, then double) into
 // fterm[t][h] for unit h of the frame.
 //
-// Two forms.  The segment form (a segment of SB whole blocks holds at most
-// 128 elements, a multiple of 4): one warp per (frame, segment), warps
-// striding over them; lane q takes the four consecutive elements 4q..4q+3
-// of the segment, so every load and store is a 16-byte vector and one pass
-// covers the segment; psi is parked in shared memory and lane b then sums
-// block b of the segment.  The unit form (any K): one warp per unit of WB
-// consecutive blocks of a frame, one element per lane and step.
+// One warp per unit of WB consecutive blocks g = (s, n) of one frame t (WB*K
+// consecutive elements): each lane takes every 32nd element of the unit
+// (coalesced loads and stores), forms alpha-hat, psi and w, and parks psi in
+// shared memory; then lane b sums the K values of the unit's block b in
+// element order.  (Forms with four consecutive elements per lane and
+// 16-byte vectors -- a warp per frame, or per segment of whole blocks --
+// measured slower on GB300: fewer resident warps for the same work.)
 constexpr int WB = 16;
-constexpr int WSEG_MAX = 128;   // elements per segment
-constexpr int WSEG_WARPS = 8;
-
-// blocks per segment of the segment form, or 0 when K admits none
-static int weights_seg_blocks(int K) {
-  for (int sb = WSEG_MAX / K; sb >= 1; --sb)
-    if ((sb * K) % 4 == 0) return sb;
-  return 0;
-}
 
 template <int FMT, bool BOUND>
 __device__ __forceinline__ void weights_elem(float alpha, float& psi, float& w, float& sa,
@@ -62,115 +53,6 @@ __device__ __forceinline__ void weights_elem(float alpha, float& psi, float& w, 
   } else {
     digamma_exp_fast_ge1(alpha, psi, w);
   }
-}
-
-template <int FMT, bool BOUND>
-__global__ void __launch_bounds__(WSEG_WARPS * 32) k_weights_seg(WeightsArgs a, int SB, int NSEG) {
-  __shared__ __align__(16) float wsm[WSEG_WARPS][WSEG_MAX];
-  // launched as a programmatic dependent of the kernel before it on the
-  // stream (the replay that wrote d-hat): wait for it before reading
-  // anything; the forward-backward pass that follows may start launching at
-  // once (it waits for this kernel before it reads the emissions)
-  griddep_wait();
-  griddep_launch_dependents();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int NB = a.S * a.N;
-  const int SE = SB * a.K;                      // elements per segment (a multiple of 4)
-  const size_t SN = (size_t)a.Tstride * a.N;   // source stride of d-hat and phi-hat
-  float* ps = wsm[warp];
-  const unsigned units = (unsigned)a.T * (unsigned)NSEG;
-  const unsigned nwarps = gridDim.x * WSEG_WARPS;
-  unsigned bad = 0;
-  float chk = 0.f;
-  for (unsigned u = blockIdx.x * WSEG_WARPS + warp; u < units; u += nwarps) {
-    const int t = (int)(u / (unsigned)NSEG), h = (int)(u - (unsigned)t * NSEG);
-    const int k0 = h * SE, k1 = min(k0 + SE, a.M);
-    const size_t row = (size_t)t * a.Mp;
-    const size_t toff = (size_t)t * a.N;
-    float sa = 0.f, ca = 0.f, sg = 0.f, cg = 0.f;
-    double big = 0.0;
-    const int k = k0 + 4 * lane;
-    if (k < k1) {
-      const float4 c4 = *reinterpret_cast<const float4*>(a.counts + row + k);
-      const int4 e01 = *reinterpret_cast<const int4*>(a.ktab + k);
-      const int4 e23 = *reinterpret_cast<const int4*>(a.ktab + k + 2);
-      const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
-      const int es[4] = {e01.x, e01.z, e23.x, e23.z};
-      const int en[4] = {e01.y, e01.w, e23.y, e23.w};
-      const bool full = k + 4 <= k1;
-      float al[4], psi[4], w[4];
-#pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        const float d = a.dhat[(size_t)es[v] * SN + toff + en[v]];
-        al[v] = cv[v] + a.gamma * d + 1.f;
-        if (full || k + v < k1) {
-          weights_elem<FMT, BOUND>(al[v], psi[v], w[v], sa, ca, sg, cg, big);
-        } else {
-          psi[v] = 0.f;
-          w[v] = 0.f;
-        }
-        chk = fmaf(0.f, psi[v] + w[v], chk);   // stays 0 unless psi or w is NaN or infinite
-      }
-      *reinterpret_cast<float4*>(ps + 4 * lane) = make_float4(psi[0], psi[1], psi[2], psi[3]);
-      if (full) {
-        if (a.alpha)
-          *reinterpret_cast<float4*>(a.alpha + row + k) = make_float4(al[0], al[1], al[2], al[3]);
-        *reinterpret_cast<float4*>(a.w32 + row + k) = make_float4(w[0], w[1], w[2], w[3]);
-        if (FMT == WF_TF32X2) {
-          float hh[4], ll[4];
-#pragma unroll
-          for (int v = 0; v < 4; ++v) {
-            hh[v] = tf32_hi(w[v]);
-            ll[v] = tf32_hi(w[v] - hh[v]);
-          }
-          *reinterpret_cast<float4*>(reinterpret_cast<float*>(a.wop_hi) + row + k) =
-              make_float4(hh[0], hh[1], hh[2], hh[3]);
-          *reinterpret_cast<float4*>(reinterpret_cast<float*>(a.wop_lo) + row + k) =
-              make_float4(ll[0], ll[1], ll[2], ll[3]);
-        } else if (FMT == WF_BF16) {
-          const __nv_bfloat162 b01 = __floats2bfloat162_rn(w[0], w[1]);
-          const __nv_bfloat162 b23 = __floats2bfloat162_rn(w[2], w[3]);
-          uint2 pk;
-          pk.x = *reinterpret_cast<const uint32_t*>(&b01);
-          pk.y = *reinterpret_cast<const uint32_t*>(&b23);
-          *reinterpret_cast<uint2*>(reinterpret_cast<__nv_bfloat16*>(a.wop_hi) + row + k) = pk;
-        }
-      } else {
-        // the frame's last elements: padding (k >= M) is never touched
-        for (int v = 0; v < 4 && k + v < k1; ++v) {
-          if (a.alpha) a.alpha[row + k + v] = al[v];
-          a.w32[row + k + v] = w[v];
-          if (FMT == WF_TF32X2) {
-            const float hh = tf32_hi(w[v]);
-            reinterpret_cast<float*>(a.wop_hi)[row + k + v] = hh;
-            reinterpret_cast<float*>(a.wop_lo)[row + k + v] = tf32_hi(w[v] - hh);
-          } else if (FMT == WF_BF16) {
-            reinterpret_cast<__nv_bfloat16*>(a.wop_hi)[row + k + v] = __float2bfloat16_rn(w[v]);
-          }
-        }
-      }
-    }
-    __syncwarp();
-    for (int bb = lane; bb < SB && h * SB + bb < NB; bb += 32) {   // block bb of the segment
-      const float* pb = ps + bb * a.K;
-      float x = 0.f;
-      for (int j = 0; j < a.K; ++j) x += pb[j];
-      const int2 e = a.ktab[(h * SB + bb) * a.K];
-      a.phi[(size_t)e.x * SN + toff + e.y] = a.gamma * x;
-    }
-    if (BOUND) {
-      const double s0 = warp_sum_d((double)sa - (double)ca);
-      const double sgt = warp_sum_d(((double)sg - (double)cg) + big);
-      if (lane == 0) {
-        a.fterm[2 * (size_t)u] = s0;
-        a.fterm[2 * (size_t)u + 1] = sgt;
-      }
-    }
-    __syncwarp();   // every lane is done with ps before the next segment
-  }
-  if (!(chk == 0.f)) bad |= ERR_NONFINITE;
-  bad = __reduce_or_sync(FULL, bad);
-  if (bad && lane == 0) atomicOr(a.err, bad);
 }
 
 template <int FMT, bool BOUND>
@@ -233,20 +115,9 @@ __global__ void __launch_bounds__(256) k_weights(WeightsArgs a) {
   }
 }
 
-// The segment form when K admits one and the unit counts fit 32 bits.
-static int weights_seg_form(int S, int N, int K, int T, int* SB, int* NSEG) {
-  const int sb = weights_seg_blocks(K);
-  if (sb == 0) return 0;
-  const int nseg = (S * N + sb - 1) / sb;
-  if ((long long)T * nseg >= (1ll << 31)) return 0;
-  if (SB) *SB = sb;
-  if (NSEG) *NSEG = nseg;
-  return 1;
-}
-
 int weights_units(int S, int N, int K, int T) {
-  int nseg = 0;
-  if (weights_seg_form(S, N, K, T, nullptr, &nseg)) return nseg;
+  (void)K;
+  (void)T;
   return (S * N + WB - 1) / WB;
 }
 
@@ -267,27 +138,8 @@ void launch_element_table(int M, int Mp, int K, int N, int2* ktab, cudaStream_t 
 void launch_weights(const WeightsArgs& a, int fmt, cudaStream_t st) {
   const bool b = a.fterm != nullptr;
   void (*k)(WeightsArgs) = nullptr;
-  void (*k2)(WeightsArgs, int, int) = nullptr;
   cudaLaunchConfig_t cfg = {};
-  int SB = 0, NSEG = 0;
-  const bool seg = weights_seg_form(a.S, a.N, a.K, a.Tstride, &SB, &NSEG);
-  if (seg) {
-    switch (fmt) {
-      case WF_TF32X2: k2 = b ? k_weights_seg<WF_TF32X2, true> : k_weights_seg<WF_TF32X2, false>; break;
-      case WF_BF16: k2 = b ? k_weights_seg<WF_BF16, true> : k_weights_seg<WF_BF16, false>; break;
-      default: k2 = b ? k_weights_seg<WF_F32, true> : k_weights_seg<WF_F32, false>; break;
-    }
-    // warps stride over the (frame, segment) units
-    int dev = 0, sms = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
-      sms = 1;
-    const long long need = ((long long)a.T * NSEG + WSEG_WARPS - 1) / WSEG_WARPS;
-    const long long cap = (long long)sms * 16;
-    cfg.gridDim = dim3((unsigned)(need < cap ? need : cap));
-    cfg.blockDim = dim3(WSEG_WARPS * 32);
-    cfg.dynamicSmemBytes = 0;
-  } else {
+  {
     switch (fmt) {
       case WF_TF32X2: k = b ? k_weights<WF_TF32X2, true> : k_weights<WF_TF32X2, false>; break;
       case WF_BF16: k = b ? k_weights<WF_BF16, true> : k_weights<WF_BF16, false>; break;
@@ -309,10 +161,7 @@ void launch_weights(const WeightsArgs& a, int fmt, cudaStream_t st) {
   const bool legacy = st == nullptr || st == cudaStreamLegacy;
   cfg.attrs = legacy ? nullptr : attr;
   cfg.numAttrs = legacy ? 0 : 1;
-  if (seg)
-    cudaLaunchKernelEx(&cfg, k2, a, SB, NSEG);
-  else
-    cudaLaunchKernelEx(&cfg, k, a);
+  cudaLaunchKernelEx(&cfg, k, a);
 }
 
 // ------------------------------------------------------------------- fills
