@@ -287,8 +287,13 @@ NFHMM_API int nfhmm_job_posteriors(nfhmm_ctx *c, long long job_id, float *dhat, 
  *                          contraction's shared-memory ring of operand
  *                          stages: 0 (default) the deepest that fits the
  *                          tile, else 2 .. that depth (NFHMM_Q_TILE_STAGES*
- *                          reads it back).  A depth the new tile cannot hold
- *                          falls back to 0
+ *                          reads it back).  A new column tile that cannot
+ *                          hold the depth falls back to 0; a depth asked for
+ *                          beyond the tile's deepest is rejected
+ *   NFHMM_OPT_TILE_PREFETCH1, NFHMM_OPT_TILE_PREFETCH2  L2 prefetch distance
+ *                          of each contraction's operand copies: 0 (default)
+ *                          none, else 1..64 K-blocks beyond the ring are
+ *                          asked into L2 ahead of their copies
  *                          Every row tile is 128 frames; results differ
  *                          between tile shapes only by rounding (the order
  *                          of the accumulation and of the bound's partial
@@ -306,6 +311,8 @@ NFHMM_API int nfhmm_job_posteriors(nfhmm_ctx *c, long long job_id, float *dhat, 
 #define NFHMM_OPT_TILE_GEMM2  8
 #define NFHMM_OPT_TILE_STAGES1 9
 #define NFHMM_OPT_TILE_STAGES2 10
+#define NFHMM_OPT_TILE_PREFETCH1 11
+#define NFHMM_OPT_TILE_PREFETCH2 12
 
 /*
  * nfhmm_autotune -- choose the forward-backward form and geometry, then the
@@ -318,7 +325,8 @@ NFHMM_API int nfhmm_job_posteriors(nfhmm_ctx *c, long long job_id, float *dhat, 
  * chosen and on tensor-core contexts, the tile shapes one coordinate at a
  * time: the reconstruction's column tile over NFHMM_OPT_TILE_GEMM1's
  * choices, the back-projection's over NFHMM_OPT_TILE_GEMM2's, then each
- * ring depth from 2 to the deepest (read back with NFHMM_Q_TILE_*).  Each
+ * ring depth from 2 to the deepest, then each L2 prefetch distance over
+ * {0, 4, 8, 16} (read back with NFHMM_Q_TILE_*).  Each
  * candidate runs two
  * sweeps (which capture its graph) and then `reps` sweeps (reps <= 0: 3)
  * between CUDA events, every trial starting from the same state: the counts,
@@ -522,6 +530,8 @@ NFHMM_API long long nfhmm_kernel_launches(nfhmm_ctx *c);
 #define NFHMM_Q_TILE_GEMM2     9   /* column tile of the back-projection   */
 #define NFHMM_Q_TILE_STAGES1  10   /* ring depth of the reconstruction     */
 #define NFHMM_Q_TILE_STAGES2  11   /* ring depth of the back-projection    */
+#define NFHMM_Q_TILE_PREFETCH1 12  /* L2 prefetch distance, reconstruction */
+#define NFHMM_Q_TILE_PREFETCH2 13  /* L2 prefetch distance, back-projection */
 NFHMM_API int nfhmm_query(nfhmm_ctx *c, int key, long long *value);
 
 #ifdef __cplusplus

@@ -906,6 +906,8 @@ long long graph_key_of(const nfhmm_ctx* c, bool want_bpart, bool timed, int slot
   k = k * 257 + c->tc.bn2;
   k = k * 17 + c->tc.st1;
   k = k * 17 + c->tc.st2;
+  k = k * 67 + c->tc.pf1;
+  k = k * 67 + c->tc.pf2;
   k = k * 2 + (want_bpart ? 1 : 0);
   k = k * 2 + (keep_alpha ? 1 : 0);
   k = k * 3 + (timed ? 1 + slot : 0);
@@ -1346,6 +1348,32 @@ int nfhmm_autotune(nfhmm_ctx* c, int reps, int* chunk_out, int* group_out, doubl
         }
       }
     }
+    // then the L2 prefetch distance of each contraction
+    const int opf1 = c->tc.pf1, opf2 = c->tc.pf2;
+    if (!rc && tc_set_tiles(c->tc, b[0], b[1], b[2], b[3]) != 0)
+      rc = fail(NFHMM_ECUDA, "autotune: tile shape: " + tc_last_error());
+    for (int which = 0; which < 2 && !rc; ++which) {
+      int& pf = which == 0 ? c->tc.pf1 : c->tc.pf2;
+      const int keep = pf;
+      int best_pf = keep;
+      const int dists[] = {0, 4, 8, 16};
+      for (int d : dists) {
+        if (d == keep) continue;
+        pf = d;
+        double us = 0.0;
+        rc = time_sweeps(&us);
+        if (rc) break;
+        if (us < t_best) {
+          t_best = us;
+          best_pf = d;
+        }
+      }
+      pf = best_pf;
+    }
+    if (rc) {
+      c->tc.pf1 = opf1;
+      c->tc.pf2 = opf2;
+    }
     if (rc || tc_set_tiles(c->tc, b[0], b[1], b[2], b[3]) != 0) {
       tc_set_tiles(c->tc, o1, o2, os1, os2);
       if (!rc) rc = fail(NFHMM_ECUDA, "autotune: tile shape: " + tc_last_error());
@@ -1432,6 +1460,13 @@ int nfhmm_set_option(nfhmm_ctx* c, int key, long long value) {
       c->bpart_ok = false;   // the bound's partials are counted per tile shape
       c->bound_ok = false;
       return leave(c);
+    }
+    case NFHMM_OPT_TILE_PREFETCH1:
+    case NFHMM_OPT_TILE_PREFETCH2: {
+      if (!c->use_tc) return fail(NFHMM_EINVAL, "tile options apply to tensor-core contexts");
+      if (value < 0 || value > 64) return fail(NFHMM_EINVAL, "prefetch distance must be in [0, 64]");
+      (key == NFHMM_OPT_TILE_PREFETCH1 ? c->tc.pf1 : c->tc.pf2) = (int)value;
+      return NFHMM_OK;
     }
     case NFHMM_OPT_TEST_WAIT_TIMEOUT: {
       if (!c->use_tc) return fail(NFHMM_EINVAL, "the wait hook needs a tensor-core context");
@@ -1733,6 +1768,8 @@ int nfhmm_query(nfhmm_ctx* c, int key, long long* value) {
     case NFHMM_Q_TILE_STAGES1:
       *value = !c->use_tc ? 0 : c->tc.st1 ? c->tc.st1 : tc_max_stages(c->tc.precision, c->tc.bn1);
       return NFHMM_OK;
+    case NFHMM_Q_TILE_PREFETCH1: *value = c->use_tc ? c->tc.pf1 : 0; return NFHMM_OK;
+    case NFHMM_Q_TILE_PREFETCH2: *value = c->use_tc ? c->tc.pf2 : 0; return NFHMM_OK;
     case NFHMM_Q_TILE_STAGES2:
       *value = !c->use_tc ? 0 : c->tc.st2 ? c->tc.st2 : tc_max_stages(c->tc.precision, c->tc.bn2);
       return NFHMM_OK;

@@ -105,6 +105,7 @@ struct TcArgs {
   // on, and V (RATIO) is shared by the items.  brows = 0: one item.
   int brows, bvalid, bstride;
   int stages;                     // depth of the shared-memory ring (2 .. MAX_STAGES)
+  int prefetch;                   // K-blocks beyond the ring brought into L2 ahead (0: none)
   // test hook, 0 in normal use: the MMA thread first waits this many
   // nanoseconds on a barrier nothing arrives on, so that the wait gives up
   // and the CTA takes its wind-down path (error word ERR_TIMEOUT)
@@ -180,6 +181,25 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       long long it = 0;   // K-blocks issued over all of this CTA's tiles
       int s = 0;          // its ring slot, it % STAGES
       uint32_t ph = 0;    // and (it / STAGES) & 1
+      // the L2 prefetch runs `prefetch` K-blocks ahead of the loads, over the
+      // same sequence of (tile, K-block)
+      int ptile = blockIdx.x, pkb = 0;
+      auto prefetch_next = [&]() {
+        if (ptile >= ntiles) return;
+        const int prow0 = p.row_off + (ptile / ncol) * BM, pcol0 = (ptile % ncol) * BN;
+        const int pbcol0 = pcol0 + (p.brows ? prow0 / p.brows : 0) * p.bstride;
+        tma_prefetch_l2_2d(&maps.a_hi, pkb * K::BK, prow0);
+        tma_prefetch_l2_2d(&maps.b_hi, pkb * K::BK, pbcol0);
+        if (K::NOPS == 2) {
+          tma_prefetch_l2_2d(&maps.a_lo, pkb * K::BK, prow0);
+          tma_prefetch_l2_2d(&maps.b_lo, pkb * K::BK, pbcol0);
+        }
+        if (++pkb == nkb) {
+          pkb = 0;
+          ptile += gridDim.x;
+        }
+      };
+      for (int i = 0; i < p.prefetch; ++i) prefetch_next();
       for (int tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x) {
         const int row0 = p.row_off + (tile / ncol) * BM, col0 = (tile % ncol) * BN;
         const int bitem = p.brows ? row0 / p.brows : 0;   // batch item of this row tile
@@ -189,6 +209,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             give_up();
             break;
           }
+          if (p.prefetch) prefetch_next();
           mbar_expect_tx(&full[s], Cfg::STAGE_BYTES);
           const int kx = kb * K::BK;
           tma_load_2d(stage_ptr(s, 0), &maps.a_hi, &full[s], kx, row0);
@@ -712,6 +733,7 @@ int tc_gemm1(TcPlan& p, int row_off, int rows, double* bpart, int reserve, cudaS
   a.err = p.err;
   cudaError_t e;
   a.stages = p.st1;
+  a.prefetch = p.pf1;
   if (p.precision == 1) {
     a.out_bf16 = reinterpret_cast<__nv_bfloat16*>(p.q_hi);
     e = launch_tile<TEPI_RATIO, KIND_BF16>(p.bn1, *maps_of(p, 0), a, st, reserve);
@@ -740,6 +762,7 @@ int tc_gemm2(TcPlan& p, int row_off, int rows, int reserve, cudaStream_t st) {
   a.err = p.err;
   cudaError_t e;
   a.stages = p.st2;
+  a.prefetch = p.pf2;
   if (p.precision == 1)
     e = launch_tile<TEPI_SCALE, KIND_BF16>(p.bn2, *maps_of(p, 1), a, st, reserve);
   else

@@ -27,6 +27,8 @@ struct TcPlan {
   // tile shape: column tile of each contraction, and its shared-memory ring
   // depth (0: the deepest that fits); see tc_set_tiles
   int bn1 = 128, bn2 = 160, st1 = 0, st2 = 0;
+  // L2 prefetch distance of each contraction's operand loads, in K-blocks (0: none)
+  int pf1 = 0, pf2 = 0;
   // test hook: the next tc_gemm1 launch makes its MMA thread wait this long on
   // a barrier nothing arrives on (see k_tc_gemm); cleared by that launch
   unsigned long long inject_wait_ns = 0;

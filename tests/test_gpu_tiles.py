@@ -70,13 +70,14 @@ def _check(p, ref, L, alpha, phi, counts, dhat):
     assert abs(L - ref["bound"]) <= BOUND_RTOL * abs(ref["bound"])
 
 
-@pytest.mark.parametrize("gemm1,gemm2,stages", [
-    (64, 64, 0), (96, 96, 0), (128, 128, 0), (64, 160, 2), (96, 160, 3), (128, 96, 2)])
-def test_tile_shape_one_sweep_from_oracle_state(nf, paper_case, gemm1, gemm2, stages):
+@pytest.mark.parametrize("gemm1,gemm2,stages,prefetch", [
+    (64, 64, 0, 0), (96, 96, 0, 8), (128, 128, 0, 4), (64, 160, 2, 0), (96, 160, 3, 16),
+    (128, 96, 2, 0)])
+def test_tile_shape_one_sweep_from_oracle_state(nf, paper_case, gemm1, gemm2, stages, prefetch):
     p, c32, d32, ref = paper_case
     f = p.as_f32()
     with nf.VIContext(f["V"], f["W"], f["A"], f["pi"], p.S, p.N, p.K, gamma=p.gamma) as ctx:
-        ctx.set_tiles(gemm1, gemm2, stages, stages)
+        ctx.set_tiles(gemm1, gemm2, stages, stages, prefetch, prefetch)
         t = ctx.tiles()
         assert (t["tile_gemm1"], t["tile_gemm2"]) == (gemm1, gemm2)
         if stages:
@@ -164,7 +165,8 @@ def test_tuned_context_equals_hand_set(nf, job_frames):
         b.set_option("fb_group", tuned["fb_group"])
         b.set_option("fb_mode", tuned["fb_mode"])
         t = tuned["tiles"]
-        b.set_tiles(t["tile_gemm1"], t["tile_gemm2"], t["tile_stages1"], t["tile_stages2"])
+        b.set_tiles(t["tile_gemm1"], t["tile_gemm2"], t["tile_stages1"], t["tile_stages2"],
+                    t["tile_prefetch1"], t["tile_prefetch2"])
         assert b.tiles() == t
         Lb = b.sweep(3, bound=True)
         db = b.posteriors()
