@@ -290,6 +290,13 @@ NFHMM_API int nfhmm_job_posteriors(nfhmm_ctx *c, long long job_id, float *dhat, 
  *                          reads it back).  A new column tile that cannot
  *                          hold the depth falls back to 0; a depth asked for
  *                          beyond the tile's deepest is rejected
+ *   NFHMM_OPT_TILE_EPI_STAGE1, NFHMM_OPT_TILE_EPI_STAGE2  1: the epilogue's
+ *                          second operand (V for the reconstruction, w for the
+ *                          back-projection) is copied into shared memory for
+ *                          each tile while its MMAs run, instead of being
+ *                          read from global memory 16 columns at a time after
+ *                          them; it takes ring depth (some FP32 tiles cannot
+ *                          hold it: NFHMM_EINVAL).  0 (default): not staged
  *   NFHMM_OPT_TILE_PREFETCH1, NFHMM_OPT_TILE_PREFETCH2  L2 prefetch distance
  *                          of each contraction's operand copies: 0 (default)
  *                          none, else 1..64 K-blocks beyond the ring are
@@ -313,6 +320,8 @@ NFHMM_API int nfhmm_job_posteriors(nfhmm_ctx *c, long long job_id, float *dhat, 
 #define NFHMM_OPT_TILE_STAGES2 10
 #define NFHMM_OPT_TILE_PREFETCH1 11
 #define NFHMM_OPT_TILE_PREFETCH2 12
+#define NFHMM_OPT_TILE_EPI_STAGE1 13
+#define NFHMM_OPT_TILE_EPI_STAGE2 14
 
 /*
  * nfhmm_autotune -- choose the forward-backward form and geometry, then the
@@ -324,8 +333,9 @@ NFHMM_API int nfhmm_job_posteriors(nfhmm_ctx *c, long long job_id, float *dhat, 
  * sources per block (as far as a block holds them).  Then, with the form
  * chosen and on tensor-core contexts, the tile shapes one coordinate at a
  * time: the reconstruction's column tile over NFHMM_OPT_TILE_GEMM1's
- * choices, the back-projection's over NFHMM_OPT_TILE_GEMM2's, then each
- * ring depth from 2 to the deepest, then each L2 prefetch distance over
+ * choices, the back-projection's over NFHMM_OPT_TILE_GEMM2's, the staging
+ * of each epilogue operand, then each ring depth from 2 to the deepest, then
+ * each L2 prefetch distance over
  * {0, 4, 8, 16} (read back with NFHMM_Q_TILE_*).  Each
  * candidate runs two
  * sweeps (which capture its graph) and then `reps` sweeps (reps <= 0: 3)
@@ -532,6 +542,8 @@ NFHMM_API long long nfhmm_kernel_launches(nfhmm_ctx *c);
 #define NFHMM_Q_TILE_STAGES2  11   /* ring depth of the back-projection    */
 #define NFHMM_Q_TILE_PREFETCH1 12  /* L2 prefetch distance, reconstruction */
 #define NFHMM_Q_TILE_PREFETCH2 13  /* L2 prefetch distance, back-projection */
+#define NFHMM_Q_TILE_EPI_STAGE1 14 /* epilogue operand staged, reconstruction */
+#define NFHMM_Q_TILE_EPI_STAGE2 15 /* epilogue operand staged, back-projection */
 NFHMM_API int nfhmm_query(nfhmm_ctx *c, int key, long long *value);
 
 #ifdef __cplusplus

@@ -908,6 +908,7 @@ long long graph_key_of(const nfhmm_ctx* c, bool want_bpart, bool timed, int slot
   k = k * 17 + c->tc.st2;
   k = k * 67 + c->tc.pf1;
   k = k * 67 + c->tc.pf2;
+  k = k * 4 + c->tc.ep1 * 2 + c->tc.ep2;
   k = k * 2 + (want_bpart ? 1 : 0);
   k = k * 2 + (keep_alpha ? 1 : 0);
   k = k * 3 + (timed ? 1 + slot : 0);
@@ -1316,41 +1317,47 @@ int nfhmm_autotune(nfhmm_ctx* c, int reps, int* chunk_out, int* group_out, doubl
   // a time (column tile of each contraction, then each ring depth), starting
   // from the current shape, whose time under this form is measured first
   if (c->use_tc) {
-    const int o1 = c->tc.bn1, o2 = c->tc.bn2, os1 = c->tc.st1, os2 = c->tc.st2;
-    int b[4] = {o1, o2, os1, os2};
+    // shape: column tile, ring depth and staged epilogue operand of each
+    // contraction, as {bn1, bn2, st1, st2, ep1, ep2}
+    const int o[6] = {c->tc.bn1, c->tc.bn2, c->tc.st1, c->tc.st2, c->tc.ep1, c->tc.ep2};
+    int b[6] = {o[0], o[1], o[2], o[3], o[4], o[5]};
     double t_best = 0.0;
     rc = time_sweeps(&t_best);
-    for (int coord = 0; coord < 4 && !rc; ++coord) {
+    const int order[6] = {0, 1, 4, 5, 2, 3};
+    for (int oi = 0; oi < 6 && !rc; ++oi) {
+      const int coord = order[oi];
       std::vector<int> vals;
       if (coord < 2) {
         int cand[8];
         const int n = tc_tile_candidates(c->tc.precision, coord, cand, 8);
         vals.assign(cand, cand + n);
+      } else if (coord >= 4) {
+        vals = {0, 1};
       } else {
-        const int m = tc_max_stages(c->tc.precision, b[coord - 2]);
+        const int m = tc_max_stages(c->tc.precision, b[coord - 2], b[coord + 2] != 0);
         for (int st = 2; st < m; ++st) vals.push_back(st);   // m itself is depth 0
         vals.push_back(0);
       }
       for (int v : vals) {
         if (v == b[coord]) continue;
-        int t[4] = {b[0], b[1], b[2], b[3]};
+        int t[6] = {b[0], b[1], b[2], b[3], b[4], b[5]};
         t[coord] = v;
-        if (coord < 2) {   // a narrower or wider tile keeps the deepest ring
-          t[2 + coord] = 0;
-        }
-        if (tc_set_tiles(c->tc, t[0], t[1], t[2], t[3]) != 0) continue;
+        // a new column tile or epilogue staging starts from the deepest ring it allows
+        if (coord < 2) t[2 + coord] = 0;
+        if (coord >= 4) t[coord - 2] = 0;
+        if (tc_set_tiles(c->tc, t[0], t[1], t[2], t[3], t[4], t[5]) != 0) continue;
         double us = 0.0;
         rc = time_sweeps(&us);
         if (rc) break;
         if (us < t_best) {
           t_best = us;
-          for (int i = 0; i < 4; ++i) b[i] = t[i];
+          for (int i = 0; i < 6; ++i) b[i] = t[i];
         }
       }
     }
     // then the L2 prefetch distance of each contraction
     const int opf1 = c->tc.pf1, opf2 = c->tc.pf2;
-    if (!rc && tc_set_tiles(c->tc, b[0], b[1], b[2], b[3]) != 0)
+    if (!rc && tc_set_tiles(c->tc, b[0], b[1], b[2], b[3], b[4], b[5]) != 0)
       rc = fail(NFHMM_ECUDA, "autotune: tile shape: " + tc_last_error());
     for (int which = 0; which < 2 && !rc; ++which) {
       int& pf = which == 0 ? c->tc.pf1 : c->tc.pf2;
@@ -1374,8 +1381,8 @@ int nfhmm_autotune(nfhmm_ctx* c, int reps, int* chunk_out, int* group_out, doubl
       c->tc.pf1 = opf1;
       c->tc.pf2 = opf2;
     }
-    if (rc || tc_set_tiles(c->tc, b[0], b[1], b[2], b[3]) != 0) {
-      tc_set_tiles(c->tc, o1, o2, os1, os2);
+    if (rc || tc_set_tiles(c->tc, b[0], b[1], b[2], b[3], b[4], b[5]) != 0) {
+      tc_set_tiles(c->tc, o[0], o[1], o[2], o[3], o[4], o[5]);
       if (!rc) rc = fail(NFHMM_ECUDA, "autotune: tile shape: " + tc_last_error());
       return finish(rc);
     }
@@ -1439,23 +1446,34 @@ int nfhmm_set_option(nfhmm_ctx* c, int key, long long value) {
     case NFHMM_OPT_TILE_GEMM1:
     case NFHMM_OPT_TILE_GEMM2:
     case NFHMM_OPT_TILE_STAGES1:
-    case NFHMM_OPT_TILE_STAGES2: {
+    case NFHMM_OPT_TILE_STAGES2:
+    case NFHMM_OPT_TILE_EPI_STAGE1:
+    case NFHMM_OPT_TILE_EPI_STAGE2: {
       if (!c->use_tc) return fail(NFHMM_EINVAL, "tile shapes apply to tensor-core contexts");
       if (value < 0 || value > 1024) return fail(NFHMM_EINVAL, "tile option out of range");
       int bn1 = c->tc.bn1, bn2 = c->tc.bn2, st1 = c->tc.st1, st2 = c->tc.st2;
+      int ep1 = c->tc.ep1, ep2 = c->tc.ep2;
       if (key == NFHMM_OPT_TILE_GEMM1) bn1 = (int)value;
       if (key == NFHMM_OPT_TILE_GEMM2) bn2 = (int)value;
       if (key == NFHMM_OPT_TILE_STAGES1) st1 = (int)value;
       if (key == NFHMM_OPT_TILE_STAGES2) st2 = (int)value;
-      // a new column tile keeps the depth only if it can hold it (else the
-      // deepest); a depth asked for explicitly is validated as given
-      if (key == NFHMM_OPT_TILE_GEMM1 && st1 > tc_max_stages(c->tc.precision, bn1)) st1 = 0;
-      if (key == NFHMM_OPT_TILE_GEMM2 && st2 > tc_max_stages(c->tc.precision, bn2)) st2 = 0;
+      if (key == NFHMM_OPT_TILE_EPI_STAGE1 || key == NFHMM_OPT_TILE_EPI_STAGE2) {
+        if (value > 1) return fail(NFHMM_EINVAL, "epilogue staging is 0 or 1");
+        (key == NFHMM_OPT_TILE_EPI_STAGE1 ? ep1 : ep2) = (int)value;
+      }
+      // a new column tile or staging keeps the depth only if it can hold it
+      // (else the deepest); a depth asked for explicitly is validated as given
+      if ((key == NFHMM_OPT_TILE_GEMM1 || key == NFHMM_OPT_TILE_EPI_STAGE1) &&
+          st1 > tc_max_stages(c->tc.precision, bn1, ep1 != 0))
+        st1 = 0;
+      if ((key == NFHMM_OPT_TILE_GEMM2 || key == NFHMM_OPT_TILE_EPI_STAGE2) &&
+          st2 > tc_max_stages(c->tc.precision, bn2, ep2 != 0))
+        st2 = 0;
       int rc = enter(c);   // the plan's maps are read by launches already queued
       if (rc) return rc;
       CK(cudaStreamSynchronize(c->s_main));
       CK(cudaStreamSynchronize(c->s_aux));
-      if (tc_set_tiles(c->tc, bn1, bn2, st1, st2) != 0)
+      if (tc_set_tiles(c->tc, bn1, bn2, st1, st2, ep1, ep2) != 0)
         return fail(NFHMM_EINVAL, "tile shape: " + tc_last_error());
       c->bpart_ok = false;   // the bound's partials are counted per tile shape
       c->bound_ok = false;
@@ -1766,12 +1784,18 @@ int nfhmm_query(nfhmm_ctx* c, int key, long long* value) {
     case NFHMM_Q_TILE_GEMM1: *value = c->use_tc ? c->tc.bn1 : 0; return NFHMM_OK;
     case NFHMM_Q_TILE_GEMM2: *value = c->use_tc ? c->tc.bn2 : 0; return NFHMM_OK;
     case NFHMM_Q_TILE_STAGES1:
-      *value = !c->use_tc ? 0 : c->tc.st1 ? c->tc.st1 : tc_max_stages(c->tc.precision, c->tc.bn1);
+      *value = !c->use_tc ? 0
+               : c->tc.st1 ? c->tc.st1
+                           : tc_max_stages(c->tc.precision, c->tc.bn1, c->tc.ep1 != 0);
       return NFHMM_OK;
     case NFHMM_Q_TILE_PREFETCH1: *value = c->use_tc ? c->tc.pf1 : 0; return NFHMM_OK;
+    case NFHMM_Q_TILE_EPI_STAGE1: *value = c->use_tc ? c->tc.ep1 : 0; return NFHMM_OK;
+    case NFHMM_Q_TILE_EPI_STAGE2: *value = c->use_tc ? c->tc.ep2 : 0; return NFHMM_OK;
     case NFHMM_Q_TILE_PREFETCH2: *value = c->use_tc ? c->tc.pf2 : 0; return NFHMM_OK;
     case NFHMM_Q_TILE_STAGES2:
-      *value = !c->use_tc ? 0 : c->tc.st2 ? c->tc.st2 : tc_max_stages(c->tc.precision, c->tc.bn2);
+      *value = !c->use_tc ? 0
+               : c->tc.st2 ? c->tc.st2
+                           : tc_max_stages(c->tc.precision, c->tc.bn2, c->tc.ep2 != 0);
       return NFHMM_OK;
     case NFHMM_Q_SWEEPS_DONE: *value = c->sweeps_done; return NFHMM_OK;
     case NFHMM_Q_DEVICE_BYTES: *value = (long long)c->device_bytes; return NFHMM_OK;

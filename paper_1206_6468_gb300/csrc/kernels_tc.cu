@@ -73,10 +73,21 @@ struct TileCfg {
   static constexpr int B_BYTES = BN * 128;
   static constexpr int STAGE_BYTES = K::NOPS * (A_BYTES + B_BYTES);
   static constexpr int EXTRA = 1024 /*align*/ + 256 /*barriers*/;
-  // the deepest shared-memory ring that fits (at most 8 stages)
-  static constexpr int MAX_STAGES =
-      (SMEM_BUDGET - EXTRA) / STAGE_BYTES < 8 ? (SMEM_BUDGET - EXTRA) / STAGE_BYTES : 8;
-  static constexpr int smem(int stages) { return stages * STAGE_BYTES + EXTRA; }
+  // staged epilogue operand: per epilogue thread (row, half) its BN/2 floats
+  // of V or w, each segment padded by 16 bytes (conflict-free float4 reads)
+  static constexpr int EPI_SEG = BN / 2 * 4 + 16;
+  static constexpr int EPI_BYTES = 2 * BM * EPI_SEG;
+  static constexpr int fit(int extra) {
+    return (SMEM_BUDGET - EXTRA - extra) / STAGE_BYTES < 8
+               ? (SMEM_BUDGET - EXTRA - extra) / STAGE_BYTES : 8;
+  }
+  // the deepest shared-memory ring that fits (at most 8 stages), without
+  // and with the staged epilogue operand
+  static constexpr int MAX_STAGES = fit(0);
+  static constexpr int MAX_STAGES_EPI = fit(EPI_BYTES);
+  static constexpr int smem(int stages, bool epi) {
+    return stages * STAGE_BYTES + (epi ? EPI_BYTES : 0) + EXTRA;
+  }
   static constexpr int TMEM_COLS = 512;
   static constexpr int NACC = 512 / BN;                          // accumulators of BN columns
   static constexpr int NMAIN = K::NOPS == 2 ? NACC - 1 : NACC;   // for hi*hi (or BF16) products
@@ -106,6 +117,8 @@ struct TcArgs {
   int brows, bvalid, bstride;
   int stages;                     // depth of the shared-memory ring (2 .. MAX_STAGES)
   int prefetch;                   // K-blocks beyond the ring brought into L2 ahead (0: none)
+  int epi_stage;                  // 1: the epilogue's V (or w) tile is copied into shared
+                                  // memory before its accumulator is awaited
   // test hook, 0 in normal use: the MMA thread first waits this many
   // nanoseconds on a barrier nothing arrives on, so that the wait gives up
   // and the CTA takes its wind-down path (error word ERR_TIMEOUT)
@@ -129,7 +142,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * Cfg::STAGE_BYTES);
+  uint8_t* epi_buf = smem + STAGES * Cfg::STAGE_BYTES;   // staged epilogue operand (if used)
+  uint64_t* full =
+      reinterpret_cast<uint64_t*>(epi_buf + (p.epi_stage ? Cfg::EPI_BYTES : 0));
   uint64_t* empty = full + STAGES;
   uint64_t* accum = empty + STAGES;        // MMA -> epilogue: a tile's accumulator is complete
   uint64_t* tmem_free = accum + 1;         // epilogue -> MMA: it has been read out
@@ -292,6 +307,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     const int half = (warp - 2) >> 2;
     const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * HALF);
     const int nmain = nkb < Cfg::NMAIN ? nkb : Cfg::NMAIN;   // accumulators written
+    // this thread's segment of the staged epilogue operand
+    // (segments by half, then row: consecutive lanes 16 bytes apart mod 128)
+    float* eseg = reinterpret_cast<float*>(epi_buf + (size_t)(half * BM + quarter * 32 + lane) *
+                                                           Cfg::EPI_SEG);
     int j = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++j) {
       const int row0 = p.row_off + (tile / ncol) * BM, col0 = (tile % ncol) * BN;
@@ -301,6 +320,20 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       const int tl = t - bitem * p.brows;               // row within its batch item
       const bool rv = p.brows ? tl < p.bvalid : t < p.row_off + p.rows;
       const int cbase = col0 + half * HALF;
+      const float* erow = EPI == TEPI_RATIO ? p.V + (size_t)tl * p.ldv : p.w + (size_t)t * p.ldw;
+      if (p.epi_stage) {
+        // the tile's V (or w) for this thread's row and columns, copied while
+        // the tile's MMAs run; the thread reads only what it copied itself
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch) {
+          const int c = cbase + 16 * ch;
+          if (rv && c < p.cols) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) cp_async16_sm(eseg + 16 * ch + 4 * i, erow + c + 4 * i);
+          }
+        }
+        cp_async_commit_group();
+      }
       if (!mbar_wait(accum, (uint32_t)j & 1, abort_flag)) {
         give_up();
         break;
@@ -335,6 +368,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(tmem_free);
+      if (p.epi_stage) cp_async_wait_all();
       // the epilogue proper, from registers, beside the next tile's MMAs
       double part = 0.0;
       unsigned bad = 0;
@@ -349,8 +383,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 #pragma unroll
             for (int i = 0; i < 16; ++i) x16[i] = acc[16 * cc + i];
           }
-        const float* src = EPI == TEPI_RATIO ? p.V + (size_t)tl * p.ldv + c
-                                             : p.w + (size_t)t * p.ldw + c;
+        const float* src = p.epi_stage ? eseg + 16 * ch : erow + c;
         float vv[16];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -505,13 +538,15 @@ cudaError_t launch_gemm(const Maps& maps, TcArgs a, cudaStream_t st, int reserve
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  if (a.stages < 2 || a.stages > Cfg::MAX_STAGES) a.stages = Cfg::MAX_STAGES;
+  const int deepest = a.epi_stage ? Cfg::MAX_STAGES_EPI : Cfg::MAX_STAGES;
+  if (deepest < 2) return cudaErrorInvalidValue;   // no room for a staged epilogue operand
+  if (a.stages < 2 || a.stages > deepest) a.stages = deepest;
   static cudaError_t attr[kMaxDevices];
   static bool attr_set[kMaxDevices] = {};
   if (!attr_set[dev]) {
     attr[dev] = cudaFuncSetAttribute(k_tc_gemm<KIND, BN, EPI>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     Cfg::smem(Cfg::MAX_STAGES));
+                                     SMEM_BUDGET);
     attr_set[dev] = true;
   }
   if (attr[dev] != cudaSuccess) return attr[dev];
@@ -521,7 +556,8 @@ cudaError_t launch_gemm(const Maps& maps, TcArgs a, cudaStream_t st, int reserve
   // persistent: one CTA per SM, less the SMs reserved (at most half of them)
   const int avail = sms - (reserve < sms / 2 ? reserve : sms / 2);
   const int grid = (int)(tiles < avail ? tiles : avail);
-  k_tc_gemm<KIND, BN, EPI><<<grid, NUM_THREADS, Cfg::smem(a.stages), st>>>(maps, a);
+  k_tc_gemm<KIND, BN, EPI><<<grid, NUM_THREADS, Cfg::smem(a.stages, a.epi_stage != 0), st>>>(
+      maps, a);
   return cudaGetLastError();
 }
 
@@ -546,13 +582,13 @@ cudaError_t launch_tile(int bn, const Maps& maps, const TcArgs& a, cudaStream_t 
 }
 
 template <int KIND>
-int max_stages(int bn) {
+int max_stages(int bn, bool epi) {
   switch (bn) {
-    case 64: return TileCfg<KIND, 64>::MAX_STAGES;
-    case 96: return TileCfg<KIND, 96>::MAX_STAGES;
-    case 128: return TileCfg<KIND, 128>::MAX_STAGES;
-    case 160: return TileCfg<KIND, 160>::MAX_STAGES;
-    case 192: return TileCfg<KIND, 192>::MAX_STAGES;
+    case 64: return epi ? TileCfg<KIND, 64>::MAX_STAGES_EPI : TileCfg<KIND, 64>::MAX_STAGES;
+    case 96: return epi ? TileCfg<KIND, 96>::MAX_STAGES_EPI : TileCfg<KIND, 96>::MAX_STAGES;
+    case 128: return epi ? TileCfg<KIND, 128>::MAX_STAGES_EPI : TileCfg<KIND, 128>::MAX_STAGES;
+    case 160: return epi ? TileCfg<KIND, 160>::MAX_STAGES_EPI : TileCfg<KIND, 160>::MAX_STAGES;
+    case 192: return epi ? TileCfg<KIND, 192>::MAX_STAGES_EPI : TileCfg<KIND, 192>::MAX_STAGES;
     default: return 0;
   }
 }
@@ -590,8 +626,8 @@ int tc_tile_candidates(int precision, int which, int* out, int max_out) {
   return n;
 }
 
-int tc_max_stages(int precision, int bn) {
-  return precision == 1 ? max_stages<KIND_BF16>(bn) : max_stages<KIND_TF32X3>(bn);
+int tc_max_stages(int precision, int bn, bool epi) {
+  return precision == 1 ? max_stages<KIND_BF16>(bn, epi) : max_stages<KIND_TF32X3>(bn, epi);
 }
 
 int tc_bpart_columns_max(int Fp) { return 2 * ((Fp + 63) / 64); }
@@ -616,7 +652,7 @@ static bool encode_b_maps(TcPlan& p) {
   return ok;
 }
 
-int tc_set_tiles(TcPlan& p, int bn1, int bn2, int st1, int st2) {
+int tc_set_tiles(TcPlan& p, int bn1, int bn2, int st1, int st2, int ep1, int ep2) {
   int c1[8], c2[8];
   const int n1 = tc_tile_candidates(p.precision, 0, c1, 8);
   const int n2 = tc_tile_candidates(p.precision, 1, c2, 8);
@@ -627,10 +663,15 @@ int tc_set_tiles(TcPlan& p, int bn1, int bn2, int st1, int st2) {
     g_tc_err = "column tile not among the tuner's shapes for this precision";
     return -1;
   }
-  if ((st1 != 0 && (st1 < 2 || st1 > tc_max_stages(p.precision, bn1))) ||
-      (st2 != 0 && (st2 < 2 || st2 > tc_max_stages(p.precision, bn2)))) {
-    g_tc_err = "ring depth must be 0 (deepest) or 2.." + std::to_string(tc_max_stages(p.precision, bn1)) +
-               " / " + std::to_string(tc_max_stages(p.precision, bn2));
+  const int m1 = tc_max_stages(p.precision, bn1, ep1 != 0);
+  const int m2 = tc_max_stages(p.precision, bn2, ep2 != 0);
+  if (m1 < 2 || m2 < 2) {
+    g_tc_err = "no room for a staged epilogue operand beside a two-stage ring at this tile";
+    return -1;
+  }
+  if ((st1 != 0 && (st1 < 2 || st1 > m1)) || (st2 != 0 && (st2 < 2 || st2 > m2))) {
+    g_tc_err = "ring depth must be 0 (deepest) or 2.." + std::to_string(m1) + " / " +
+               std::to_string(m2);
     return -1;
   }
   const int o1 = p.bn1, o2 = p.bn2;
@@ -644,6 +685,8 @@ int tc_set_tiles(TcPlan& p, int bn1, int bn2, int st1, int st2) {
   }
   p.st1 = st1;
   p.st2 = st2;
+  p.ep1 = ep1 != 0;
+  p.ep2 = ep2 != 0;
   return 0;
 }
 
@@ -734,6 +777,7 @@ int tc_gemm1(TcPlan& p, int row_off, int rows, double* bpart, int reserve, cudaS
   cudaError_t e;
   a.stages = p.st1;
   a.prefetch = p.pf1;
+  a.epi_stage = p.ep1;
   if (p.precision == 1) {
     a.out_bf16 = reinterpret_cast<__nv_bfloat16*>(p.q_hi);
     e = launch_tile<TEPI_RATIO, KIND_BF16>(p.bn1, *maps_of(p, 0), a, st, reserve);
@@ -763,6 +807,7 @@ int tc_gemm2(TcPlan& p, int row_off, int rows, int reserve, cudaStream_t st) {
   cudaError_t e;
   a.stages = p.st2;
   a.prefetch = p.pf2;
+  a.epi_stage = p.ep2;
   if (p.precision == 1)
     e = launch_tile<TEPI_SCALE, KIND_BF16>(p.bn2, *maps_of(p, 1), a, st, reserve);
   else

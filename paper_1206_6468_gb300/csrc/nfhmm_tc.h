@@ -29,6 +29,8 @@ struct TcPlan {
   int bn1 = 128, bn2 = 160, st1 = 0, st2 = 0;
   // L2 prefetch distance of each contraction's operand loads, in K-blocks (0: none)
   int pf1 = 0, pf2 = 0;
+  // 1: the epilogue's V (or w) is staged in shared memory (ep1, ep2)
+  int ep1 = 0, ep2 = 0;
   // test hook: the next tc_gemm1 launch makes its MMA thread wait this long on
   // a barrier nothing arrives on (see k_tc_gemm); cleared by that launch
   unsigned long long inject_wait_ns = 0;
@@ -72,11 +74,11 @@ void tc_exact_free(ExactTc& p);
 bool tc_available();
 // Tile shapes: the column tiles the tuner may choose for contraction `which`
 // (0 reconstruction, 1 back-projection) at a precision; the deepest ring for
-// a column tile; set a plan's shape (re-encodes its tensor maps; 0 on
-// success, -1 with tc_last_error otherwise).
+// a column tile (with or without the staged epilogue operand); set a plan's
+// shape (re-encodes its tensor maps; 0 on success, -1 with tc_last_error).
 int tc_tile_candidates(int precision, int which, int* out, int max_out);
-int tc_max_stages(int precision, int bn);
-int tc_set_tiles(TcPlan& p, int bn1, int bn2, int st1, int st2);
+int tc_max_stages(int precision, int bn, bool epi_stage);
+int tc_set_tiles(TcPlan& p, int bn1, int bn2, int st1, int st2, int ep1, int ep2);
 // bound partials per frame: allocated for the narrowest tile, used by the plan's
 int tc_bpart_columns_max(int Fp);
 int tc_bpart_used(const TcPlan& p);

@@ -77,6 +77,18 @@ __device__ __forceinline__ void tma_prefetch_l2_2d(const CUtensorMap* map, int x
                "r"(x), "r"(y)
                : "memory");
 }
+// 16-byte asynchronous copy global -> shared (cp.async.cg, bypassing L1),
+// its group commit, and the wait for every group this thread committed
+__device__ __forceinline__ void cp_async16_sm(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(smem)), "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_group() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
 // Bulk copy global -> shared (no tensor map); both addresses 16-byte
 // aligned, bytes a multiple of 16; completes bytes on the mbarrier.
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,

@@ -31,10 +31,11 @@ STAGES = {"weights": 0, "gemm1": 1, "gemm2": 2, "fb": 3, "bound": 4, "init": 5}
 QUERIES = {"tensor_cores": 0, "fb_chunk": 1, "sweeps_done": 2, "device_bytes": 3,
            "frame_capacity": 4, "max_jobs": 5, "fb_group": 6, "fb_mode": 7, "tile_gemm1": 8,
            "tile_gemm2": 9, "tile_stages1": 10, "tile_stages2": 11, "tile_prefetch1": 12,
-           "tile_prefetch2": 13}
+           "tile_prefetch2": 13, "tile_epi_stage1": 14, "tile_epi_stage2": 15}
 OPTIONS = {"fb_chunk": 0, "fb_products": 1, "graphs": 2, "fb_group": 3, "profile_stride": 4,
            "fb_mode": 5, "test_wait_timeout": 6, "tile_gemm1": 7, "tile_gemm2": 8,
-           "tile_stages1": 9, "tile_stages2": 10, "tile_prefetch1": 11, "tile_prefetch2": 12}
+           "tile_stages1": 9, "tile_stages2": 10, "tile_prefetch1": 11, "tile_prefetch2": 12,
+           "tile_epi_stage1": 13, "tile_epi_stage2": 14}
 FB_PRODUCTS = {"simt": 0, "tc": 1}
 PRECISIONS = {"fp32": FP32, "bf16": BF16, "fp32_simt": FP32_SIMT}
 
@@ -263,13 +264,16 @@ class VIContext:
     def tiles(self) -> dict:
         """The contractions' tile shapes: column tile and ring depth of each."""
         return {k: self.query(k) for k in ("tile_gemm1", "tile_gemm2", "tile_stages1",
-                                           "tile_stages2", "tile_prefetch1", "tile_prefetch2")}
+                                           "tile_stages2", "tile_prefetch1", "tile_prefetch2",
+                                           "tile_epi_stage1", "tile_epi_stage2")}
 
     def set_tiles(self, gemm1=None, gemm2=None, stages1=None, stages2=None, prefetch1=None,
-                  prefetch2=None):
-        for k, v in (("tile_gemm1", gemm1), ("tile_gemm2", gemm2), ("tile_stages1", stages1),
-                     ("tile_stages2", stages2), ("tile_prefetch1", prefetch1),
-                     ("tile_prefetch2", prefetch2)):
+                  prefetch2=None, epi_stage1=None, epi_stage2=None):
+        # column tiles, then staging (it sets the deepest ring), then depths
+        for k, v in (("tile_gemm1", gemm1), ("tile_gemm2", gemm2),
+                     ("tile_epi_stage1", epi_stage1), ("tile_epi_stage2", epi_stage2),
+                     ("tile_stages1", stages1), ("tile_stages2", stages2),
+                     ("tile_prefetch1", prefetch1), ("tile_prefetch2", prefetch2)):
             if v is not None:
                 self.set_option(k, v)
 

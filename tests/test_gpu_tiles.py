@@ -70,14 +70,16 @@ def _check(p, ref, L, alpha, phi, counts, dhat):
     assert abs(L - ref["bound"]) <= BOUND_RTOL * abs(ref["bound"])
 
 
-@pytest.mark.parametrize("gemm1,gemm2,stages,prefetch", [
-    (64, 64, 0, 0), (96, 96, 0, 8), (128, 128, 0, 4), (64, 160, 2, 0), (96, 160, 3, 16),
-    (128, 96, 2, 0)])
-def test_tile_shape_one_sweep_from_oracle_state(nf, paper_case, gemm1, gemm2, stages, prefetch):
+@pytest.mark.parametrize("gemm1,gemm2,stages,prefetch,epi", [
+    (64, 64, 0, 0, 0), (96, 96, 0, 8, 0), (128, 128, 0, 4, 0), (64, 160, 2, 0, 0),
+    (96, 160, 3, 16, 0), (128, 96, 2, 0, 0), (128, 128, 0, 0, 1), (64, 96, 3, 4, 1)])
+def test_tile_shape_one_sweep_from_oracle_state(nf, paper_case, gemm1, gemm2, stages, prefetch,
+                                                epi):
     p, c32, d32, ref = paper_case
     f = p.as_f32()
     with nf.VIContext(f["V"], f["W"], f["A"], f["pi"], p.S, p.N, p.K, gamma=p.gamma) as ctx:
-        ctx.set_tiles(gemm1, gemm2, stages, stages, prefetch, prefetch)
+        ctx.set_tiles(gemm1, gemm2, stages, stages, prefetch, prefetch, epi, epi)
+        assert (ctx.tiles()["tile_epi_stage1"], ctx.tiles()["tile_epi_stage2"]) == (epi, epi)
         t = ctx.tiles()
         assert (t["tile_gemm1"], t["tile_gemm2"]) == (gemm1, gemm2)
         if stages:
@@ -166,7 +168,8 @@ def test_tuned_context_equals_hand_set(nf, job_frames):
         b.set_option("fb_mode", tuned["fb_mode"])
         t = tuned["tiles"]
         b.set_tiles(t["tile_gemm1"], t["tile_gemm2"], t["tile_stages1"], t["tile_stages2"],
-                    t["tile_prefetch1"], t["tile_prefetch2"])
+                    t["tile_prefetch1"], t["tile_prefetch2"], t["tile_epi_stage1"],
+                    t["tile_epi_stage2"])
         assert b.tiles() == t
         Lb = b.sweep(3, bound=True)
         db = b.posteriors()
@@ -174,3 +177,22 @@ def test_tuned_context_equals_hand_set(nf, job_frames):
     print("tuned:", tuned)
     assert La == Lb
     assert np.array_equal(da, db) and np.array_equal(ca, cb)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_staged_epilogue_operand_is_bit_neutral(nf, precision):
+    """Staging V and w in shared memory moves the same values by another
+    route: the state is bit for bit that of the unstaged epilogue, over a
+    batch whose CTAs walk several tiles."""
+    lengths = [1500, 700, 2300, 41, 3000]
+    jobs = synth.make_jobs(2, 40, 10, 513, lengths, self_prob=0.95, energy_sigma=1.5, seed=9)
+    W, A, pi = (np.ascontiguousarray(getattr(jobs, k), dtype=np.float32) for k in ("W", "A", "pi"))
+    out = []
+    for epi in (0, 1):
+        with nf.VIContext(jobs.stacked_V(), W, A, pi, jobs.S, jobs.N, jobs.K,
+                          precision=precision, job_frames=lengths) as ctx:
+            ctx.set_tiles(128, 128, epi_stage1=epi, epi_stage2=epi)
+            L = ctx.sweep(3, bound=True)
+            out.append((L, ctx.posteriors(), ctx.get_state()[0]))
+    assert out[0][0] == out[1][0]
+    assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][2], out[1][2])
