@@ -326,8 +326,8 @@ def test_autotune_picks_a_geometry_and_keeps_the_state(nf):
     """The autotuner times whole sweeps from a saved copy of the state: it
     needs a sweep, leaves posteriors and bound untouched, applies one of its
     candidates, and later sweeps equal those of a context set to that
-    geometry by hand at the same point (bit for bit: the same kernels run on
-    the same state)."""
+    geometry and tile shape by hand at the same point (bit for bit: the same
+    kernels run on the same state)."""
     p = synth.make_problem(seed=12, **synth.SMALL)
     f = p.as_f32()
     with nf.VIContext(f["V"], f["W"], f["A"], f["pi"], p.S, p.N, p.K) as ctx:
@@ -350,6 +350,10 @@ def test_autotune_picks_a_geometry_and_keeps_the_state(nf):
         ref.set_option("fb_chunk", r["fb_chunk"])
         ref.set_option("fb_group", r["fb_group"])
         ref.set_option("fb_mode", r["fb_mode"])
+        t = r["tiles"]   # the tuner also chose the contractions' tile shapes
+        ref.set_tiles(t["tile_gemm1"], t["tile_gemm2"], t["tile_stages1"], t["tile_stages2"],
+                      t["tile_prefetch1"], t["tile_prefetch2"], t["tile_epi_stage1"],
+                      t["tile_epi_stage2"])
         L1r, d1r = ref.sweep(2, bound=True), ref.posteriors()
     assert L0 == L0r
     assert L1 == L1r
