@@ -460,7 +460,7 @@ NFHMM_API int nfhmm_forward_backward(int S, int N, int T, const float *phi, cons
  * The call allocates nothing: its scratch is one fixed device array of
  * NFHMM_NOALLOC_SCRATCH_BYTES compiled into the library, which every GPU that
  * loads the library holds until the process exits.  A problem needs about
- * 8*S*(C + C')*(P*(P + 4) + N) + 12*S*(C + C') bytes, C = ceil(T/L) chunks of L frames
+ * 8*S*(C + C')*(P*P + N) + 12*S*(C + C') bytes, C = ceil(T/L) chunks of L frames
  * (L at most 128; by default 0.3*sqrt(T) rounded, clamped to [8, 64]), C' =
  * ceil(C/G) groups of G = ceil(sqrt(C/2)) chunks (none below 24 chunks),
  * P = 8*ceil(N/8), plus, when there are groups, 256*S*C*ceil(P/32)*P16 bytes

@@ -148,11 +148,7 @@ int fb_default_chunk(int N, int T) {
   return L;
 }
 
-// A chunk or group matrix in global memory: NP rows of NP values, each row
-// padded to NP + 4 floats -- the layout the scans read from shared memory
-// (conflict-free float4 reads), so that one bulk copy brings a whole matrix in.
-__host__ __device__ constexpr int mat_ld(int NP) { return NP + 4; }
-static inline size_t mat_floats(int N) { return (size_t)pad8(N) * mat_ld(pad8(N)); }
+static inline size_t mat_floats(int N) { return (size_t)pad8(N) * pad8(N); }
 
 // ------------------------------------------------- 1. chain products (tensor cores)
 // One 128-row tile of product rows advanced through a run of factors, one
@@ -387,7 +383,7 @@ __global__ void __launch_bounds__(256, MODE == CHAIN_CHUNK ? 2 : 1) k_fb_chain(F
       cur[jj] = v;
     }
   } else {
-    const float* Pr = a.P + (cb + c0) * (NP * mat_ld(NP)) + (size_t)i * mat_ld(NP);
+    const float* Pr = a.P + (cb + c0) * NP * NP + (size_t)i * NP;
 #pragma unroll
     for (int jj = 0; jj < HC; ++jj) {
       const int j = j0 + jj;
@@ -550,8 +546,7 @@ __global__ void __launch_bounds__(256, MODE == CHAIN_CHUNK ? 2 : 1) k_fb_chain(F
     const int best = ms->best[MODE == CHAIN_CHUNK ? q : 0];
     const bool nz = live && !zero_row && best != INT_MIN;
     const float g = nz ? ldexpf(1.f, ex_row - best) : 0.f;
-    const size_t base =
-        (MODE == CHAIN_CHUNK ? cb + c : ((size_t)s * a.NG + blockIdx.x)) * (NP * mat_ld(NP));
+    const size_t base = (MODE == CHAIN_CHUNK ? cb + c : ((size_t)s * a.NG + blockIdx.x)) * NP * NP;
     float* Pg = (MODE == CHAIN_CHUNK ? a.P : a.Q) + base;
     float* PTg = (MODE == CHAIN_CHUNK ? a.PT : a.QT) + base;
     float v[HC];
@@ -560,11 +555,11 @@ __global__ void __launch_bounds__(256, MODE == CHAIN_CHUNK ? 2 : 1) k_fb_chain(F
 #pragma unroll
     for (int jj = 0; jj < HC; jj += 4)
       if (j0 + jj < NP)
-        *reinterpret_cast<float4*>(Pg + (size_t)i * mat_ld(NP) + j0 + jj) =
+        *reinterpret_cast<float4*>(Pg + (size_t)i * NP + j0 + jj) =
             make_float4(v[jj], v[jj + 1], v[jj + 2], v[jj + 3]);
 #pragma unroll
     for (int jj = 0; jj < HC; ++jj)
-      if (j0 + jj < NP) PTg[(size_t)(j0 + jj) * mat_ld(NP) + i] = v[jj];
+      if (j0 + jj < NP) PTg[(size_t)(j0 + jj) * NP + i] = v[jj];
     if (MODE == CHAIN_CHUNK && a.Pimg) {
       // the chunk matrix as the group pass's B operand: B[j][k = i] = P[i][j]
       uint8_t* img = a.Pimg + (cb + c) * Cfg::IMG_BYTES;
@@ -729,14 +724,14 @@ __global__ void __launch_bounds__(128) k_fb_products_simt(FBArgs a) {
     const float g = (live && best >= 0 && rm[tid] > 0.f)
                         ? ldexpf(rm[tid] / rm[q * NP + best], re[tid] - re[q * NP + best])
                         : 0.f;
-    const size_t base = ((size_t)s * a.C + c) * (NP * mat_ld(NP));
+    const size_t base = ((size_t)s * a.C + c) * NP * NP;
     float* Pg = a.P + base;
     float* PTg = a.PT + base;
 #pragma unroll
     for (int j = 0; j < NP; ++j) {
       const float v = live ? y[j] * g : 0.f;
-      Pg[i * mat_ld(NP) + j] = v;
-      PTg[j * mat_ld(NP) + i] = v;
+      Pg[i * NP + j] = v;
+      PTg[j * NP + i] = v;
     }
     if (i == 0)
       a.Plog[(size_t)s * a.C + c] =
@@ -774,7 +769,6 @@ __global__ void __launch_bounds__(32) k_fb_scan(FBArgs a) {
   if (MODE == MODE_GROUP_REPLAY) griddep_launch_dependents();
   float* ring = sm;                      // RING x NP x LD
   float* v = ring + RING * NN;           // 64
-  uint64_t* bars = reinterpret_cast<uint64_t*>(v + 64);   // RING: a slot's matrix has landed
   int s, chain = 0, c0, c1;
   bool first = true, last = true;        // group replay: the group opens / closes its chain
   if (MODE == MODE_CHAINS) {
@@ -796,24 +790,26 @@ __global__ void __launch_bounds__(32) k_fb_scan(FBArgs a) {
   const float* src = fwd ? a.PT : a.P;
   const int nsteps = fwd ? c1 - c0 : c1 - c0 - 1;
   auto chunk_of = [&](int q) { return fwd ? c0 + q : c1 - 1 - q; };
-  // the matrices are stored with the ring's padded rows: one bulk copy (TMA)
-  // each, completing on the slot's mbarrier; every lane's reads of a slot are
-  // ordered before its refill by a proxy fence and the step's __syncwarp
-  if (lane == 0) {
-    for (int u = 0; u < RING; ++u) tc::mbar_init(&bars[u], 1);
-    tc::fence_barrier_init();
+  // this lane's 16-byte pieces of a matrix: source and padded destination offsets
+  constexpr int CPL = (NP * NP / 4 + 31) / 32;   // 16-byte copies per lane per matrix
+  int soff[CPL], doff[CPL];
+#pragma unroll
+  for (int m = 0; m < CPL; ++m) {
+    const int i = (lane + 32 * m) * 4;
+    soff[m] = i < NP * NP ? i : -1;
+    doff[m] = (i / NP) * LD + (i % NP);
   }
-  __syncwarp();
-  int issued = 0;   // matrices requested (copies q < issued), by lane 0
   auto prefetch = [&](int q) {
-    if (q < nsteps && lane == 0) {
-      const int slot = q % RING;
-      tc::mbar_expect_tx(&bars[slot], NN * 4);
-      tc::bulk_g2s(ring + slot * NN, src + (base + chunk_of(q)) * NN, NN * 4, &bars[slot]);
-      issued = q + 1;
+    if (q < nsteps) {
+      const float* g = src + (base + chunk_of(q)) * NP * NP;
+      float* d = ring + (q % RING) * NN;
+#pragma unroll
+      for (int m = 0; m < CPL; ++m)
+        if (soff[m] >= 0) cp_async16(d + doff[m], g + soff[m]);
     }
+    cp_async_commit();
   };
-#pragma unroll 1
+#pragma unroll
   for (int q = 0; q < RING - 1; ++q) prefetch(q);
 
   const bool h0 = lane < N, h1 = lane + 32 < N;
@@ -852,21 +848,12 @@ __global__ void __launch_bounds__(32) k_fb_scan(FBArgs a) {
       if (h1) a.bwd[(base + c - 1) * N + lane + 32] = w1 * il;
     }
   };
-  bool ok = true;
-  int consumed = 0;
   for (int q = 0; q < nsteps; ++q) {
-    tc::fence_proxy_async_smem();   // this lane's reads of step q - 1's slot, before its refill
-    __syncwarp();                   // every lane is past them
+    __syncwarp();   // every lane is past step q - 1's reads of the slot refilled here
     prefetch(q + RING - 1);
     v[lane] = u0;
     v[lane + 32] = u1;
-    const bool got = tc::mbar_wait(&bars[q % RING], (uint32_t)(q / RING) & 1);
-    if (!__all_sync(0xffffffffu, got)) {   // a bounded wait gave up: stop the chain
-      if (lane == 0) atomicOr(a.err, ERR_TIMEOUT);
-      ok = false;
-      break;
-    }
-    consumed = q + 1;
+    cp_async_wait<RING - 1>();
     __syncwarp();
     float lam_prev = warp_sum(u0 + u1);
     if (q > 0 && (!(lam_prev > 0.f) || !isfinite(lam_prev))) {
@@ -898,13 +885,6 @@ __global__ void __launch_bounds__(32) k_fb_scan(FBArgs a) {
     u1 = h1 ? ((y1[0] + y1[1]) + (y1[2] + y1[3])) * inv : 0.f;
   }
   if (MODE == MODE_CHAINS) griddep_launch_dependents();
-  if (!ok) {
-    // every copy requested must land before the block exits
-    if (lane == 0)
-      for (int q = consumed; q < issued; ++q)
-        if (!tc::mbar_wait(&bars[q % RING], (uint32_t)(q / RING) & 1)) atomicOr(a.err, ERR_TIMEOUT);
-    return;
-  }
   if (nsteps > 0) {
     float lam = warp_sum(u0 + u1);
     if (!(lam > 0.f) || !isfinite(lam)) {
@@ -913,6 +893,7 @@ __global__ void __launch_bounds__(32) k_fb_scan(FBArgs a) {
     }
     emit(nsteps - 1, lam, u0, u1);
   }
+  cp_async_wait<0>();
   if (MODE == MODE_CHAINS && fwd) {
     __syncwarp();
     __threadfence_block();
@@ -937,7 +918,7 @@ __global__ void __launch_bounds__(NP * 16) k_fb_group_products(FBArgs a) {
   constexpr int LD = NP + 4;
   constexpr int NN = NP * LD;
   constexpr int NT = NP * 16;                       // threads: NP/2 warps
-  constexpr int CPT = (NN / 4 + NT - 1) / NT;       // 16-byte copies per thread per matrix
+  constexpr int CPT = (NP * NP / 4 + NT - 1) / NT;  // 16-byte copies per thread per matrix
   extern __shared__ float sm[];
   double* rl = reinterpret_cast<double*>(sm);       // NP row log scales
   float* ring = sm + 2 * NP;                        // GRING x NP x LD
@@ -953,12 +934,12 @@ __global__ void __launch_bounds__(NP * 16) k_fb_group_products(FBArgs a) {
 #pragma unroll
   for (int m = 0; m < CPT; ++m) {
     const int i = (tid + NT * m) * 4;
-    soff[m] = i < NN ? i : -1;   // the stored matrix has the ring's padded layout
-    doff[m] = i;
+    soff[m] = i < NP * NP ? i : -1;
+    doff[m] = (i / NP) * LD + (i % NP);
   }
   auto prefetch = [&](int q) {
     if (q < nsteps) {
-      const float* gsrc = a.PT + (cbase + c0 + q) * NN;
+      const float* gsrc = a.PT + (cbase + c0 + q) * NP * NP;
       float* d = ring + (q % GRING) * NN;
 #pragma unroll
       for (int m = 0; m < CPT; ++m)
@@ -1054,19 +1035,18 @@ __global__ void __launch_bounds__(NP * 16) k_fb_group_products(FBArgs a) {
   const float gb = (best >= 0 && rm[ib] > 0.f)
                        ? ldexpf(rm[ib] / rm[best], re[ib] - re[best]) * fb : 0.f;
   const double rmax = best >= 0 ? (double)re[best] * LN2 + log((double)rm[best]) : -INFINITY;
-  constexpr int MLD = mat_ld(NP);
-  const size_t qb = ((size_t)s * a.NG + g) * (NP * MLD);
+  const size_t qb = ((size_t)s * a.NG + g) * NP * NP;
   if (lane < NP) {
-    a.Q[qb + (size_t)ia * MLD + lane] = ua0 * ga;
-    a.Q[qb + (size_t)ib * MLD + lane] = ub0 * gb;
-    a.QT[qb + (size_t)lane * MLD + ia] = ua0 * ga;
-    a.QT[qb + (size_t)lane * MLD + ib] = ub0 * gb;
+    a.Q[qb + (size_t)ia * NP + lane] = ua0 * ga;
+    a.Q[qb + (size_t)ib * NP + lane] = ub0 * gb;
+    a.QT[qb + (size_t)lane * NP + ia] = ua0 * ga;
+    a.QT[qb + (size_t)lane * NP + ib] = ub0 * gb;
   }
   if (lane + 32 < NP) {
-    a.Q[qb + (size_t)ia * MLD + lane + 32] = ua1 * ga;
-    a.Q[qb + (size_t)ib * MLD + lane + 32] = ub1 * gb;
-    a.QT[qb + (size_t)(lane + 32) * MLD + ia] = ua1 * ga;
-    a.QT[qb + (size_t)(lane + 32) * MLD + ib] = ub1 * gb;
+    a.Q[qb + (size_t)ia * NP + lane + 32] = ua1 * ga;
+    a.Q[qb + (size_t)ib * NP + lane + 32] = ub1 * gb;
+    a.QT[qb + (size_t)(lane + 32) * NP + ia] = ua1 * ga;
+    a.QT[qb + (size_t)(lane + 32) * NP + ib] = ub1 * gb;
   }
   if (warp == 0) {   // the group's scale: its chunks' scales (loaded in parallel) and rmax
     double lg = 0.0;
@@ -1570,8 +1550,7 @@ static size_t smem_group() {
 }
 template <int NP>
 static size_t smem_scan() {
-  return (size_t)(ScanRing<NP>::R * NP * (NP + 4) + 64) * sizeof(float) +
-         ScanRing<NP>::R * sizeof(uint64_t);
+  return (size_t)(ScanRing<NP>::R * NP * (NP + 4) + 64) * sizeof(float);
 }
 static size_t smem_replay_chunk(int NP, int L) { return (size_t)(3 * L * NP + 128) * sizeof(float); }
 static int replay_chunks(int NP, int L) {
