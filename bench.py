@@ -75,9 +75,10 @@ def parse():
                          "autotuner's choice; with --workload serving for the serving batches "
                          "(default: the scan)")
     ap.add_argument("--fb-chunk", type=int, default=None,
-                    help="with --ncu-case (single workload): frames per forward-backward chunk")
+                    help="single workload: frames per forward-backward chunk instead of the "
+                         "autotuner's choice (for profiler runs)")
     ap.add_argument("--fb-group", type=int, default=None,
-                    help="with --ncu-case (single workload): chunks per group (0: none)")
+                    help="with --fb-chunk: chunks per group (0: none)")
     ap.add_argument("--workload", default="single",
                     choices=["single", "batched", "serving", "exact"],
                     help="single: one S2 N40 K10 F513 T3000 job per step (the headline); "
@@ -789,9 +790,19 @@ def run_single(args, rank, world, local):
         ctx.close()
         return None
     # forward-backward geometry picked by the library's autotuner (whole sweeps
-    # from a saved state, before the warm-up; the step re-initialises anyway)
+    # from a saved state, before the warm-up; the step re-initialises anyway),
+    # or given on the command line (a profiler's serialised kernels would
+    # steer the autotuner elsewhere)
     ctx.sweep(1)
-    tuned = ctx.autotune(reps=5)
+    if args.fb_chunk is not None:
+        ctx.set_option("fb_chunk", args.fb_chunk)
+        if args.fb_group is not None:
+            ctx.set_option("fb_group", args.fb_group)
+        tuned = {"fb_chunk": ctx.query("fb_chunk"), "fb_group": ctx.query("fb_group"),
+                 "fb_mode": ctx.query("fb_mode"), "us": float("nan"), "tiles": ctx.tiles(),
+                 "picked_by": "command line"}
+    else:
+        tuned = ctx.autotune(reps=5)
 
     def step_device():
         ctx.reinit(d_in["V"], d_in["W"], d_in["A"], d_in["pi"])
@@ -849,9 +860,10 @@ def run_single(args, rank, world, local):
                    "fb_geometry": {"chunk": tuned["fb_chunk"], "group": tuned["fb_group"],
                                    "mode": "sequential x%d" % tuned["fb_mode"]
                                    if tuned["fb_mode"] else "scan",
-                                   "picked_by": "nfhmm_autotune",
+                                   "picked_by": tuned.get("picked_by", "nfhmm_autotune"),
                                    "sweep_us": round(tuned["us"], 1)},
-                   "contraction_tiles": dict(tuned.get("tiles") or {}, picked_by="nfhmm_autotune"),
+                   "contraction_tiles": dict(tuned.get("tiles") or {},
+                                             picked_by=tuned.get("picked_by", "nfhmm_autotune")),
                    "parallelism": f"replicas x{world}"},
         "roofline": dict(roofline_of(prof, p.T, p.S, p.N, p.K, p.F, args.precision, tc, peaks,
                                      args.steps * sweeps, f"paper_size_{args.precision}",
