@@ -799,7 +799,7 @@ def run_single(args, rank, world, local):
         if args.fb_group is not None:
             ctx.set_option("fb_group", args.fb_group)
         tuned = {"fb_chunk": ctx.query("fb_chunk"), "fb_group": ctx.query("fb_group"),
-                 "fb_mode": ctx.query("fb_mode"), "us": float("nan"), "tiles": ctx.tiles(),
+                 "fb_mode": ctx.query("fb_mode"), "us": None, "tiles": ctx.tiles(),
                  "picked_by": "command line"}
     else:
         tuned = ctx.autotune(reps=5)
@@ -861,7 +861,7 @@ def run_single(args, rank, world, local):
                                    "mode": "sequential x%d" % tuned["fb_mode"]
                                    if tuned["fb_mode"] else "scan",
                                    "picked_by": tuned.get("picked_by", "nfhmm_autotune"),
-                                   "sweep_us": round(tuned["us"], 1)},
+                                   "sweep_us": round(tuned["us"], 1) if tuned["us"] else None},
                    "contraction_tiles": dict(tuned.get("tiles") or {},
                                              picked_by=tuned.get("picked_by", "nfhmm_autotune")),
                    "parallelism": f"replicas x{world}"},
