@@ -8,6 +8,7 @@
 #include <math.h>
 
 #include <climits>
+#include <type_traits>
 
 #include "nfhmm_device.cuh"
 #include "nfhmm_kernels.h"
@@ -55,7 +56,8 @@ __device__ __forceinline__ void weights_elem(float alpha, float& psi, float& w, 
   }
 }
 
-template <int FMT, bool BOUND>
+// WIDE: unit indices in 64 bits (frames x units per frame beyond 2^31)
+template <int FMT, bool BOUND, bool WIDE>
 __global__ void __launch_bounds__(256) k_weights(WeightsArgs a) {
   extern __shared__ float wsm[];
   griddep_wait();
@@ -63,9 +65,10 @@ __global__ void __launch_bounds__(256) k_weights(WeightsArgs a) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int NB = a.S * a.N;                 // blocks per frame
   const int NH = (NB + WB - 1) / WB;        // units per frame
-  const long long u = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
-  if (u >= (long long)a.T * NH) return;     // whole warps
-  const int t = (int)(u / NH), h = (int)(u - (long long)t * NH);
+  using U = typename std::conditional<WIDE, unsigned long long, unsigned>::type;
+  const U u = (U)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (u >= (U)a.T * NH) return;             // whole warps
+  const int t = (int)(u / (U)NH), h = (int)(u - (U)t * NH);
   const int UE = WB * a.K;
   const int k0 = h * UE, k1 = min(k0 + UE, a.M);
   const size_t SN = (size_t)a.Tstride * a.N;
@@ -140,13 +143,23 @@ void launch_weights(const WeightsArgs& a, int fmt, cudaStream_t st) {
   void (*k)(WeightsArgs) = nullptr;
   cudaLaunchConfig_t cfg = {};
   {
-    switch (fmt) {
-      case WF_TF32X2: k = b ? k_weights<WF_TF32X2, true> : k_weights<WF_TF32X2, false>; break;
-      case WF_BF16: k = b ? k_weights<WF_BF16, true> : k_weights<WF_BF16, false>; break;
-      default: k = b ? k_weights<WF_F32, true> : k_weights<WF_F32, false>; break;
-    }
     const int warps = 8;
     const long long units = (long long)a.T * ((a.S * a.N + WB - 1) / WB);
+    const bool wide = units >= (1ll << 31);
+    switch (fmt) {
+      case WF_TF32X2:
+        k = b ? (wide ? k_weights<WF_TF32X2, true, true> : k_weights<WF_TF32X2, true, false>)
+              : (wide ? k_weights<WF_TF32X2, false, true> : k_weights<WF_TF32X2, false, false>);
+        break;
+      case WF_BF16:
+        k = b ? (wide ? k_weights<WF_BF16, true, true> : k_weights<WF_BF16, true, false>)
+              : (wide ? k_weights<WF_BF16, false, true> : k_weights<WF_BF16, false, false>);
+        break;
+      default:
+        k = b ? (wide ? k_weights<WF_F32, true, true> : k_weights<WF_F32, true, false>)
+              : (wide ? k_weights<WF_F32, false, true> : k_weights<WF_F32, false, false>);
+        break;
+    }
     cfg.gridDim = dim3((unsigned)((units + warps - 1) / warps));
     cfg.blockDim = dim3(warps * 32);
     cfg.dynamicSmemBytes = (size_t)warps * WB * a.K * sizeof(float);

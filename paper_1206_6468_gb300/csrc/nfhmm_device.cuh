@@ -57,8 +57,19 @@ __device__ __forceinline__ void digamma_impl(float x, float& psi, float& w, floa
     prod *= x;
     x += 1.f;
   }
-  const float acc = n > 0 ? num * __frcp_rn(prod) : 0.f;
-  const float r = __frcp_rn(x);
+  // FAST: the hardware's approximate reciprocal (within 1 ulp; the shifted x
+  // is >= 3 and prod >= 1 here, so neither is subnormal); otherwise the
+  // correctly rounded one
+  float rp_, rx_;
+  if (FAST) {
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rp_) : "f"(prod));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rx_) : "f"(x));
+  } else {
+    rp_ = __frcp_rn(prod);
+    rx_ = __frcp_rn(x);
+  }
+  const float acc = n > 0 ? num * rp_ : 0.f;
+  const float r = rx_;
   const float r2 = r * r;
   const float series =
       r2 * (1.f / 12.f -
@@ -68,9 +79,10 @@ __device__ __forceinline__ void digamma_impl(float x, float& psi, float& w, floa
                               r2 * (1.f / 132.f - r2 * (691.f / 32760.f - r2 * (1.f / 12.f)))))));
   const float d = -0.5f * r - series;
   // FAST: psi and w from the hardware log2/exp2 approximations (x >= 3 here,
-  // d - acc in (-3, 0): within a few 1e-7 relative) -- the weights kernel of
-  // every sweep, so that forming the bound does not change the state; the
-  // bound's own terms and every other caller take the correctly rounded ones
+  // d - acc in (-3, 0): within a few 1e-7 relative) and the approximate
+  // reciprocals above -- the weights kernel of every sweep, so that forming
+  // the bound does not change the state; the bound's own terms and every
+  // other caller take the correctly rounded ones
   const float lx = FAST ? __logf(x) : logf(x);
   psi = lx + d - acc;
   w = x * (FAST ? __expf(d - acc) : expf(d - acc));
