@@ -7,8 +7,10 @@
 #include <cuda_bf16.h>
 #include <math.h>
 
+#include <algorithm>
 #include <climits>
 #include <type_traits>
+#include <utility>
 
 #include "nfhmm_device.cuh"
 #include "nfhmm_kernels.h"
@@ -21,18 +23,19 @@ constexpr unsigned FULL = 0xffffffffu;
 // Per element: alpha-hat (Eq. 6), psi and w = exp(psi) (the weights of
 // Eq. 7), written as float and as the contraction's operand format; per
 // dictionary block (s, n): Eq. 8's sum of psi over its K consecutive
-// elements, in element order (deterministic, no shuffles or atomics).
-// The element table ktab[k] = (s, n) of element k replaces integer division
-// on the hot path; d-hat and phi-hat are S x Tstride x N.
-// With BOUND, the kernel also sums alpha-hat and the bound's element terms
-// g(alpha) (Kahan-compensated in float per lane, then double) into
-// fterm[t][h] for unit h of the frame.
+// elements, in a fixed order (deterministic, no atomics).  d-hat and
+// phi-hat are S x Tstride x N.  With BOUND, the kernel also sums alpha-hat
+// and the bound's element terms g(alpha) (Kahan-compensated in float per
+// lane, then double) into fterm[t][h] for unit h of the frame.
 //
-// One warp per unit of WB consecutive blocks g = (s, n) of one frame t (WB*K
-// consecutive elements): each lane takes every 32nd element of the unit
-// (coalesced loads and stores), forms alpha-hat, psi and w, and parks psi in
-// shared memory; then lane b sums the K values of the unit's block b in
-// element order.  (Forms with four consecutive elements per lane and
+// Units: WB consecutive blocks g = (s, n) of one frame t (WB*K consecutive
+// elements).  Dictionaries of K <= 16 elements take the slab form below;
+// larger ones this per-unit form, one warp per unit: each lane takes every
+// 32nd element of the unit (coalesced loads and stores; the element table
+// ktab[k] = (s, n) of element k in place of integer division), forms
+// alpha-hat, psi and w, and parks psi in shared memory; then lane b sums the
+// K values of the unit's block b in element order.  (Forms with four
+// consecutive elements per lane and
 // 16-byte vectors -- a warp per frame, or per segment of whole blocks --
 // measured slower on GB300: fewer resident warps for the same work.)
 constexpr int WB = 16;
@@ -118,6 +121,180 @@ __global__ void __launch_bounds__(256) k_weights(WeightsArgs a) {
   }
 }
 
+// Slab form, for dictionaries of K <= 16 elements (a unit of at most 256
+// elements, at most SLAB_EPL = 8 per lane): a warp walks `upw` consecutive
+// units, frame after frame, with the next unit's counts and d-hat loads in
+// flight while it forms the current one; the index arithmetic is done once
+// per warp and the addresses once per unit.  Lane l takes elements l + 32 j
+// of a unit, as above; lanes 2b and 2b + 1 load block b's d-hat value, and an
+// element's value comes from lane 2 ((l + 32 j) / K) by one shuffle.  When
+// every alpha-hat of the unit lies in [1, 2^60) -- always, for a valid state
+// -- one warp vote sends the unit down the straight-line psi (no fallback
+// branch, no NaN test: psi and w are finite there); otherwise the general
+// psi with the NaN test.  Eq. 8: lanes 2b and 2b + 1 sum the first
+// ceil(K/2) and the last floor(K/2) of block b's psi values (shared memory,
+// element order), and the two halves are added.  KT: K as a compile-time
+// constant (1..16), or 0 for any K <= 16 at run time.
+constexpr int SLAB_EPL = 8;
+constexpr int SLAB_MAX_K = SLAB_EPL * 32 / WB;
+
+template <int FMT, bool BOUND, int KT>
+__global__ void __launch_bounds__(256, (BOUND || KT == 0) ? 2 : KT <= 10 ? 4 : 3)
+    k_weights_slab(WeightsArgs a) {
+  constexpr int EPL = KT > 0 ? (WB * KT + 31) / 32 : SLAB_EPL;
+  extern __shared__ float wsm[];
+  griddep_wait();
+  griddep_launch_dependents();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int K = KT > 0 ? KT : a.K;
+  const int N = a.N, NB = a.S * N, NH = (NB + WB - 1) / WB, UE = WB * K;
+  const long long nunits = (long long)a.T * NH;
+  const long long ub = ((long long)blockIdx.x * (blockDim.x >> 5) + warp) * a.upw;
+  if (ub >= nunits) return;   // whole warps
+  const int nu = (int)min((long long)a.upw, nunits - ub);
+  int t = nunits < (1ll << 31) ? (int)((unsigned)ub / (unsigned)NH) : (int)(ub / NH);
+  int h = (int)(ub - (long long)t * NH);
+  const size_t SN = (size_t)a.Tstride * N;
+  float* ps = wsm + warp * UE;
+  // shuffle source of this lane's element j: lane 2 ((lane + 32 j) / K)
+  int src[EPL];
+#pragma unroll
+  for (int j = 0; j < EPL; ++j)
+    src[j] = KT > 0 ? 2 * ((lane + 32 * j) / KT)
+                    : 2 * (int)(((unsigned)(lane + 32 * j) * a.kdiv) >> 16);
+  const int hk = (K + 1) >> 1;
+  const int jn = (lane & 1) ? K - hk : hk;   // psi values this lane sums
+  const float* psb = ps + (lane >> 1) * K + ((lane & 1) ? hk : 0);
+  float chk = 0.f;
+
+  // counts and d-hat of unit (tu, hu); off: the d-hat (and phi-hat) offset of
+  // this lane's block, -1 past the frame's last block
+  auto load = [&](int tu, int hu, float* c, float& d, long long& off, int& nk, size_t& ro) {
+    const int k0 = hu * UE;
+    nk = min(UE, a.M - k0);
+    ro = (size_t)tu * a.Mp + k0;
+    const float* cp = a.counts + ro + lane;
+#pragma unroll
+    for (int j = 0; j < EPL; ++j) c[j] = lane + 32 * j < nk ? __ldg(cp + 32 * j) : 0.f;
+    const int g = hu * WB + (lane >> 1);
+    off = -1;
+    d = 0.f;
+    if (g < NB) {
+      const int sg = (int)(((unsigned long long)g * a.ndiv) >> 32);
+      off = (long long)sg * (long long)SN + (long long)tu * N + (g - sg * N);
+      d = __ldg(a.dhat + off);
+    }
+  };
+  auto process = [&](int tu, int hu, const float* c, float d, long long off, int nk, size_t ro) {
+    float* pw = a.w32 + ro + lane;
+    float* ph = FMT == WF_TF32X2 ? reinterpret_cast<float*>(a.wop_hi) + ro + lane : nullptr;
+    float* pl = FMT == WF_TF32X2 ? reinterpret_cast<float*>(a.wop_lo) + ro + lane : nullptr;
+    __nv_bfloat16* pb =
+        FMT == WF_BF16 ? reinterpret_cast<__nv_bfloat16*>(a.wop_hi) + ro + lane : nullptr;
+    float* pa = a.alpha ? a.alpha + ro + lane : nullptr;
+    float al[EPL];
+    unsigned span = 0u;   // largest bits(alpha) - bits(1): below bits(2^60) - bits(1) iff all in range
+#pragma unroll
+    for (int j = 0; j < EPL; ++j) {
+      if (KT == 0 && 32 * j >= nk) break;   // warp-uniform
+      const float dj = __shfl_sync(FULL, d, src[j]);
+      al[j] = c[j] + a.gamma * dj + 1.f;
+      span = max(span, __float_as_uint(al[j]) - 0x3f800000u);
+    }
+    const bool fast = !BOUND && __all_sync(FULL, span < 0x1e000000u);
+    float sa = 0.f, ca = 0.f, sgk = 0.f, cg = 0.f;
+    double big = 0.0;
+#pragma unroll
+    for (int j = 0; j < EPL; ++j) {
+      if (KT == 0 && 32 * j >= nk) break;
+      const int e = lane + 32 * j;
+      if (e < nk) {
+        float psi, w;
+        if (fast) {
+          float u0, u1;
+          digamma_ge1_straight<false>(al[j], psi, w, u0, u1);
+        } else {
+          weights_elem<FMT, BOUND>(al[j], psi, w, sa, ca, sgk, cg, big);
+          chk = fmaf(0.f, psi + w, chk);   // stays 0 unless psi or w is NaN or infinite
+        }
+        if (pa) pa[32 * j] = al[j];
+        pw[32 * j] = w;
+        if (FMT == WF_TF32X2) {
+          const float hi = tf32_hi(w);
+          ph[32 * j] = hi;
+          pl[32 * j] = tf32_hi(w - hi);
+        } else if (FMT == WF_BF16) {
+          pb[32 * j] = __float2bfloat16_rn(w);
+        }
+        ps[e] = psi;
+      }
+    }
+    __syncwarp();
+    float x = 0.f;
+    if (off >= 0) {
+      if (KT > 0) {
+#pragma unroll
+        for (int j = 0; j < (KT + 1) / 2; ++j)
+          if (j < jn) x += psb[j];
+      } else {
+        for (int j = 0; j < jn; ++j) x += psb[j];
+      }
+    }
+    x += __shfl_xor_sync(FULL, x, 1);
+    if (off >= 0 && !(lane & 1)) a.phi[off] = a.gamma * x;
+    if (BOUND) {
+      const double s0 = warp_sum_d((double)sa - (double)ca);
+      const double sgt = warp_sum_d(((double)sgk - (double)cg) + big);
+      if (lane == 0) {
+        const size_t u = (size_t)tu * NH + hu;
+        a.fterm[2 * u] = s0;
+        a.fterm[2 * u + 1] = sgt;
+      }
+    }
+    __syncwarp();   // every lane's sums read before the next unit's psi
+  };
+
+  // two register sets: unit i in one while unit i + 1 loads into the other
+  float c0[EPL], c1[EPL], d0, d1;
+  long long o0, o1;
+  int n0, n1;
+  size_t r0, r1;
+  load(t, h, c0, d0, o0, n0, r0);
+  for (int i = 0;;) {
+    int tn = t, hn = h + 1;
+    if (hn == NH) {
+      hn = 0;
+      ++tn;
+    }
+    if (i + 1 < nu) load(tn, hn, c1, d1, o1, n1, r1);
+    process(t, h, c0, d0, o0, n0, r0);
+    if (++i >= nu) break;
+    t = tn;
+    h = hn;
+    tn = t;
+    hn = h + 1;
+    if (hn == NH) {
+      hn = 0;
+      ++tn;
+    }
+    if (i + 1 < nu) load(tn, hn, c0, d0, o0, n0, r0);
+    process(t, h, c1, d1, o1, n1, r1);
+    if (++i >= nu) break;
+    t = tn;
+    h = hn;
+  }
+  unsigned bad = !(chk == 0.f) ? ERR_NONFINITE : 0u;
+  bad = __reduce_or_sync(FULL, bad);
+  if (bad && lane == 0) atomicOr(a.err, bad);
+}
+
+// the slab kernels with K fixed at compile time, by K - 1
+template <int FMT, int... KS>
+static void (*slab_fixed_k(int K, std::integer_sequence<int, KS...>))(WeightsArgs) {
+  void (*const tab[])(WeightsArgs) = {k_weights_slab<FMT, false, KS + 1>...};
+  return tab[K - 1];
+}
+
 int weights_units(int S, int N, int K, int T) {
   (void)K;
   (void)T;
@@ -138,11 +315,51 @@ void launch_element_table(int M, int Mp, int K, int N, int2* ktab, cudaStream_t 
   k_element_table<<<(Mp + 255) / 256, 256, 0, st>>>(M, Mp, K, N, ktab);
 }
 
-void launch_weights(const WeightsArgs& a, int fmt, cudaStream_t st) {
+// multiprocessors of the current device (cached per device)
+static int device_sms() {
+  static int sms[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return 148;
+  if (sms[dev] == 0) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    sms[dev] = v > 0 ? v : 148;
+  }
+  return sms[dev];
+}
+
+void launch_weights(const WeightsArgs& a_in, int fmt, cudaStream_t st) {
+  WeightsArgs a = a_in;
   const bool b = a.fterm != nullptr;
   void (*k)(WeightsArgs) = nullptr;
   cudaLaunchConfig_t cfg = {};
-  {
+  if (a.K <= SLAB_MAX_K) {
+    // slab form: enough units per warp that the grid is about one wave of
+    // 64 warps per multiprocessor (at least one unit, at most 16)
+    const int warps = 8;
+    const long long units = (long long)a.T * ((a.S * a.N + WB - 1) / WB);
+    const long long wave = (long long)device_sms() * 64;
+    a.upw = (int)std::max(1ll, std::min(16ll, (units + wave - 1) / wave));
+    a.kdiv = (65536u + (unsigned)a.K - 1u) / (unsigned)a.K;
+    a.ndiv = ((1ull << 32) + (unsigned long long)a.N - 1ull) / (unsigned long long)a.N;
+    const auto ks = std::make_integer_sequence<int, SLAB_MAX_K>{};
+    switch (fmt) {
+      case WF_TF32X2:
+        k = b ? k_weights_slab<WF_TF32X2, true, 0> : slab_fixed_k<WF_TF32X2>(a.K, ks);
+        break;
+      case WF_BF16:
+        k = b ? k_weights_slab<WF_BF16, true, 0> : slab_fixed_k<WF_BF16>(a.K, ks);
+        break;
+      default:
+        k = b ? k_weights_slab<WF_F32, true, 0> : k_weights_slab<WF_F32, false, 0>;
+        break;
+    }
+    const long long nwarps = (units + a.upw - 1) / a.upw;
+    cfg.gridDim = dim3((unsigned)((nwarps + warps - 1) / warps));
+    cfg.blockDim = dim3(warps * 32);
+    cfg.dynamicSmemBytes = (size_t)warps * WB * a.K * sizeof(float);
+  } else {
     const int warps = 8;
     const long long units = (long long)a.T * ((a.S * a.N + WB - 1) / WB);
     const bool wide = units >= (1ll << 31);

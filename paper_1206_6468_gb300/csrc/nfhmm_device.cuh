@@ -19,12 +19,7 @@ namespace nfhmm {
 // needed for large x.  Returns NaN for x <= 0 or NaN.  (A float32 emulation
 // over the accuracy test's arguments: 2.4e-7 in psi / (1 + |psi|) against
 // 5.3e-7 with the shift to 6, as fewer recurrence steps are rounded.)
-// GE1: the caller's x is >= 1 as a rule (alpha-hat of Eq. 6 is counts +
-// gamma d-hat + 1 with all three terms >= 0): the first two recurrence steps,
-// all that x >= 1 needs, run as straight-line selects; the loop finishes any
-// smaller x.  The same operations in the same order as the loop: the result
-// is bit for bit that of GE1 = false.
-template <bool G, bool FAST = false, bool GE1 = false>
+template <bool G, bool FAST = false>
 __device__ __forceinline__ void digamma_impl(float x, float& psi, float& w, float& gsmall,
                                              float& gbig) {
   if (!(x > 0.f)) {
@@ -41,16 +36,6 @@ __device__ __forceinline__ void digamma_impl(float x, float& psi, float& w, floa
   // (x)(x+1)...(x+n-1) of the lnGamma shift.
   float num = 0.f, prod = 1.f;
   int n = 0;
-  if (GE1) {
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      const bool step = x < 3.f;
-      num = step ? fmaf(num, x, prod) : num;
-      prod = step ? prod * x : prod;
-      x = step ? x + 1.f : x;
-      n += step ? 1 : 0;
-    }
-  }
 #pragma unroll 1
   for (; n < 7 && x < 3.f; ++n) {
     num = fmaf(num, x, prod);
@@ -121,14 +106,64 @@ __device__ __forceinline__ void digamma_exp_g(float x, float& psi, float& w, flo
                                               float& gbig) {
   digamma_impl<true, true>(x, psi, w, gsmall, gbig);   // psi, w as digamma_exp_fast
 }
-// the two above for arguments >= 1 as a rule (the weights kernel's alpha-hat)
+// The two above for arguments >= 1 as a rule (alpha-hat of Eq. 6 is counts +
+// gamma d-hat + 1, every term >= 0; the weights kernel): always two
+// recurrence steps, x' = x + 2 >= 3, straight-line -- the recurrence sum and
+// the lnGamma shift product in closed form,
+//   acc = 1/x + 1/(x+1) = (2x + 1) / (x (x + 1)),   prod = x (x + 1),
+// one approximate reciprocal for acc and one for the series at x', which is
+// that of digamma_impl (FAST).  digamma_ge1_straight is the closed form alone,
+// for callers that have checked 1 <= x < 2^60 themselves (from 2^60 on,
+// x (x + 1) leaves float's range); digamma_ge1_fast sends other arguments
+// (below 1, from 2^60 on, NaN, <= 0) to digamma_impl.  (A float32 emulation
+// over the accuracy test's arguments, correctly rounded reciprocals, log and
+// exp: 2.4e-7 in psi / (1 + |psi|), 3.2e-7 relative in w.)
+template <bool G>
+__device__ __forceinline__ void digamma_ge1_straight(float x, float& psi, float& w, float& gsmall,
+                                                     float& gbig) {
+  const float a = x;
+  const float prod = fmaf(x, x, x);
+  const float num = fmaf(2.f, x, 1.f);
+  x += 2.f;
+  float rp, r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rp) : "f"(prod));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  const float acc = num * rp;
+  const float r2 = r * r;
+  const float series =
+      r2 * (1.f / 12.f -
+            r2 * (1.f / 120.f -
+                  r2 * (1.f / 252.f -
+                        r2 * (1.f / 240.f -
+                              r2 * (1.f / 132.f - r2 * (691.f / 32760.f - r2 * (1.f / 12.f)))))));
+  const float d = -0.5f * r - series;
+  psi = __logf(x) + d - acc;
+  w = x * __expf(d - acc);
+  if (G) {
+    const float st =
+        r * (1.f / 12.f -
+             r2 * (1.f / 360.f -
+                   r2 * (1.f / 1260.f -
+                         r2 * (1.f / 1680.f - r2 * (1.f / 1188.f - r2 * (691.f / 360360.f))))));
+    gsmall = 2.5f * logf(x) + 0.91893853320467274f + st - logf(prod) - (a - 1.f) * (d - acc);
+    gbig = -(2.f + a);
+  }
+}
+template <bool G>
+__device__ __forceinline__ void digamma_ge1_fast(float x, float& psi, float& w, float& gsmall,
+                                                 float& gbig) {
+  if (x >= 1.f && x < 0x1p60f)
+    digamma_ge1_straight<G>(x, psi, w, gsmall, gbig);
+  else
+    digamma_impl<G, true>(x, psi, w, gsmall, gbig);
+}
 __device__ __forceinline__ void digamma_exp_fast_ge1(float x, float& psi, float& w) {
   float unused0, unused1;
-  digamma_impl<false, true, true>(x, psi, w, unused0, unused1);
+  digamma_ge1_fast<false>(x, psi, w, unused0, unused1);
 }
 __device__ __forceinline__ void digamma_exp_g_ge1(float x, float& psi, float& w, float& gsmall,
                                                   float& gbig) {
-  digamma_impl<true, true, true>(x, psi, w, gsmall, gbig);
+  digamma_ge1_fast<true>(x, psi, w, gsmall, gbig);
 }
 
 __device__ __forceinline__ float digamma_f(float x) {

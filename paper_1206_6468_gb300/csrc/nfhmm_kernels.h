@@ -39,6 +39,11 @@ struct WeightsArgs {
   double* fterm;        // null, or T x weights_units(S, N, K, Tstride) x 2: per unit of the frame,
                         // (sum_k alpha_tk, sum_k g(alpha_tk)) for the bound
   unsigned* err;
+  // set by launch_weights for the slab form: units per warp, and the
+  // multipliers ceil(2^16 / K) and ceil(2^32 / N) of its exact divisions
+  int upw;
+  unsigned kdiv;
+  unsigned long long ndiv;
 };
 void launch_weights(const WeightsArgs& a, int fmt, cudaStream_t st);
 // units per frame of the weights kernel's bound sums (T: frame capacity)

@@ -158,6 +158,21 @@ def test_one_sweep_from_oracle_state(nf, workload, k, products, bound):
     formed in it (the state must not depend on that)."""
     cfg = getattr(synth, workload)
     p = _f32_problem(synth.make_problem(seed=3, **cfg))
+    _check_one_sweep(nf, p, k, products, bound)
+
+
+@pytest.mark.parametrize("bound", [True, False])
+@pytest.mark.parametrize("K", [1, 7, 13, 16, 17, 20])
+def test_one_sweep_dictionary_sizes(nf, K, bound):
+    """The weights kernel's forms over the dictionary size: K fixed at
+    compile time (1 to 16, odd and even), and the per-unit form beyond 16;
+    21 blocks per frame, so every frame ends in a partial unit."""
+    p = _f32_problem(synth.make_problem(seed=11, S=3, N=7, K=K, F=129, T=150, self_prob=0.9,
+                                        energy_sigma=0.5))
+    _check_one_sweep(nf, p, 2, "tc", bound)
+
+
+def _check_one_sweep(nf, p, k, products, bound):
     counts, dhat, _ = _oracle_state(p, k)
     c32 = counts.astype(np.float32)
     d32 = dhat.astype(np.float32)
