@@ -31,6 +31,7 @@
 // emissions and zero initial probability, so padded states never carry mass;
 // every kernel is instantiated per NP and its loops unroll fully.
 // Limits: chunk length 1 <= L <= FB_MAX_L, states N <= FB_MAX_N.
+#include <float.h>
 #include <limits.h>
 #include <math.h>
 
@@ -48,6 +49,13 @@ constexpr int FB_MAX_L = 128;
 template <int NP>
 struct ScanRing {
   static constexpr int R = NP <= 48 ? 16 : 8;
+};
+// the group replay (a group's few chunks per warp, up to 2 x S x groups
+// one-warp blocks launched beside a contraction that holds most SMs) keeps a
+// shallow ring, so that its blocks fit many to an SM
+template <int NP>
+struct ScanRingGroupReplay {
+  static constexpr int R = 4;
 };
 constexpr int R_CHUNKS_MAX = 4;     // replay: chunks per block (2 warps each)
 constexpr size_t SMEM_OPTIN = 227 * 1024;
@@ -759,7 +767,7 @@ enum { MODE_CHAINS = 0, MODE_GROUP_REPLAY = 1 };
 template <int NP, int MODE>
 __global__ void __launch_bounds__(32) k_fb_scan(FBArgs a) {
   extern __shared__ float sm[];
-  constexpr int RING = ScanRing<NP>::R;
+  constexpr int RING = MODE == MODE_GROUP_REPLAY ? ScanRingGroupReplay<NP>::R : ScanRing<NP>::R;
   constexpr int LD = NP + 4;
   constexpr int NN = NP * LD;
   const int N = a.N, C = a.C;
@@ -848,18 +856,19 @@ __global__ void __launch_bounds__(32) k_fb_scan(FBArgs a) {
       if (h1) a.bwd[(base + c - 1) * N + lane + 32] = w1 * il;
     }
   };
+  // The step's serial chain runs u -> v (shared memory) -> products -> u; the
+  // sum of u (this step's normaliser) is reduced beside the products, so no
+  // branch stands between them (a vanishing or non-finite sum is flagged once
+  // at the end), and the previous output is stored after the new one is formed.
+  bool vanished = false;
   for (int q = 0; q < nsteps; ++q) {
-    __syncwarp();   // every lane is past step q - 1's reads of the slot refilled here
-    prefetch(q + RING - 1);
+    __syncwarp();   // every lane is past step q - 1's reads of v and of the slot refilled here
     v[lane] = u0;
     v[lane + 32] = u1;
+    prefetch(q + RING - 1);
     cp_async_wait<RING - 1>();
     __syncwarp();
     float lam_prev = warp_sum(u0 + u1);
-    if (q > 0 && (!(lam_prev > 0.f) || !isfinite(lam_prev))) {
-      if (lane == 0) atomicOr(a.err, ERR_FB_ZERO);
-      lam_prev = 1.f;
-    }
     const float* P = ring + (q % RING) * NN;
     float y0[4] = {0.f, 0.f, 0.f, 0.f}, y1[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
@@ -878,12 +887,17 @@ __global__ void __launch_bounds__(32) k_fb_scan(FBArgs a) {
         y1[3] = fmaf(vv.w, p1.w, y1[3]);
       }
     }
+    const bool bad_sum = q > 0 && !(lam_prev > 0.f && lam_prev <= FLT_MAX);
+    vanished |= bad_sum;
+    lam_prev = bad_sum ? 1.f : lam_prev;
     // the start vector (pi, or ones) enters unnormalised
     const float inv = q > 0 ? renorm_factor(lam_prev) : 1.f;
-    if (q > 0) emit(q - 1, lam_prev, u0, u1);
+    const float w0 = u0, w1 = u1;
     u0 = h0 ? ((y0[0] + y0[1]) + (y0[2] + y0[3])) * inv : 0.f;
     u1 = h1 ? ((y1[0] + y1[1]) + (y1[2] + y1[3])) * inv : 0.f;
+    if (q > 0) emit(q - 1, lam_prev, w0, w1);
   }
+  if (vanished && lane == 0) atomicOr(a.err, ERR_FB_ZERO);
   if (MODE == MODE_CHAINS) griddep_launch_dependents();
   if (nsteps > 0) {
     float lam = warp_sum(u0 + u1);
@@ -1548,9 +1562,10 @@ template <int NP>
 static size_t smem_group() {
   return (size_t)(2 * NP + GRING * NP * (NP + 4) + (NP / 2) * 128) * sizeof(float);
 }
-template <int NP>
+template <int NP, int MODE>
 static size_t smem_scan() {
-  return (size_t)(ScanRing<NP>::R * NP * (NP + 4) + 64) * sizeof(float);
+  const int ring = MODE == MODE_GROUP_REPLAY ? ScanRingGroupReplay<NP>::R : ScanRing<NP>::R;
+  return (size_t)(ring * NP * (NP + 4) + 64) * sizeof(float);
 }
 static size_t smem_replay_chunk(int NP, int L) { return (size_t)(3 * L * NP + 128) * sizeof(float); }
 static int replay_chunks(int NP, int L) {
@@ -1594,11 +1609,11 @@ static cudaError_t launch_np(const FBArgs& a, cudaStream_t st) {
     if (attr == cudaSuccess)
       attr = cudaFuncSetAttribute(k_fb_scan<NP, MODE_CHAINS>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem_scan<NP>());
+                                  (int)smem_scan<NP, MODE_CHAINS>());
     if (attr == cudaSuccess)
       attr = cudaFuncSetAttribute(k_fb_scan<NP, MODE_GROUP_REPLAY>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem_scan<NP>());
+                                  (int)smem_scan<NP, MODE_GROUP_REPLAY>());
     if (attr == cudaSuccess)
       attr = cudaFuncSetAttribute(k_fb_group_products<NP>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1670,13 +1685,13 @@ static cudaError_t launch_np(const FBArgs& a, cudaStream_t st) {
     b.lam = a.glam;
     if (e == cudaSuccess)
       e = launch_dependent(k_fb_scan<NP, MODE_CHAINS>, dim3(a.S * a.nchains, 2), 32,
-                           smem_scan<NP>(), st, b);
+                           smem_scan<NP, MODE_CHAINS>(), st, b);
     if (e == cudaSuccess)
       e = launch_dependent(k_fb_scan<NP, MODE_GROUP_REPLAY>, dim3(a.S * a.NG, 2), 32,
-                           smem_scan<NP>(), st, a);
+                           smem_scan<NP, MODE_GROUP_REPLAY>(), st, a);
   } else {
     e = launch_dependent(k_fb_scan<NP, MODE_CHAINS>, dim3(a.S * a.nchains, 2), 32,
-                         smem_scan<NP>(), st, a);
+                         smem_scan<NP, MODE_CHAINS>(), st, a);
   }
   if (e == cudaSuccess)
     e = launch_dependent(k_fb_replay<NP>, dim3((a.C + rc - 1) / rc, a.S), rc * 64,
