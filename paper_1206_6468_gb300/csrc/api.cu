@@ -889,11 +889,11 @@ int create_ctx(nfhmm_ctx** out, const nfhmm_dims* dp, int max_jobs, const float*
   return NFHMM_OK;
 }
 
-// The launch configuration a captured sweep depends on; timed: its stages
-// are bracketed by events (then slot alternates between two instances, so
-// that one may still be in flight while the other is launched).
+// The launch configuration a captured run of `count` sweeps depends on;
+// timed: its stages are bracketed by events (then slot alternates between two
+// instances, so that one may still be in flight while the other is launched).
 long long graph_key_of(const nfhmm_ctx* c, bool want_bpart, bool timed, int slot,
-                       bool keep_alpha) {
+                       bool keep_alpha, int count) {
   long long k = c->T_active;
   k = k * 1000003 + c->fb.C;
   k = k * 1048583 + c->fb.nchains;
@@ -912,6 +912,7 @@ long long graph_key_of(const nfhmm_ctx* c, bool want_bpart, bool timed, int slot
   k = k * 2 + (want_bpart ? 1 : 0);
   k = k * 2 + (keep_alpha ? 1 : 0);
   k = k * 3 + (timed ? 1 + slot : 0);
+  k = k * 17 + count;
   return k;
 }
 
@@ -928,29 +929,40 @@ int sweeps_direct(nfhmm_ctx* c, int n, bool want_bpart, long long first = 0,
   return NFHMM_OK;
 }
 
-// n sweeps (the last with the bound's terms if want_bpart), each replayed
-// from a captured one-sweep CUDA graph once the same launch configuration has
-// run uncaptured once, else launched one by one.  With profiling, every
-// prof_stride-th sweep replays a graph with stage events (two instances in
-// turn; an instance's previous events are read before it is launched again).
-int run_graph(nfhmm_ctx* c, bool want_bpart, long long index, bool keep_alpha);
+// n sweeps (the last with the bound's terms if want_bpart), replayed from
+// captured CUDA graphs once the same launch configuration has run uncaptured
+// once, else launched one by one.  The run's last sweep (which keeps
+// alpha-hat and may form the bound's terms) and, with profiling, every
+// prof_stride-th sweep (stage events; two instances in turn, an instance's
+// previous events read before it is launched again) replay one-sweep graphs;
+// the plain sweeps between them replay graphs of up to kSweepsPerGraph sweeps,
+// which saves the gap between graph launches (the sweeps themselves are the
+// same kernels in the same order).
+constexpr int kSweepsPerGraph = 8;
+int run_graph(nfhmm_ctx* c, bool want_bpart, long long index, bool keep_alpha, int count);
 int run_sweeps(nfhmm_ctx* c, int n, bool want_bpart) {
   // a sweep carrying the wait hook is launched directly (a graph would keep it)
   if (!c->use_graphs || c->T_active == 0 || n < 1 || c->inject_wait_ns)
     return sweeps_direct(c, n, want_bpart);
-  for (int i = 0; i < n; ++i) {
-    const int rc = run_graph(c, want_bpart && i == n - 1, i, i == n - 1);
+  auto plain = [&](int i) { return i < n - 1 && !(c->profiling && i % c->prof_stride == 0); };
+  for (int i = 0; i < n;) {
+    int m = 1;
+    if (plain(i))
+      while (m < kSweepsPerGraph && plain(i + m)) ++m;
+    const int rc = run_graph(c, want_bpart && i == n - 1, i, i == n - 1, m);
     if (rc) return rc;
+    i += m;
   }
   return NFHMM_OK;
 }
 
-int run_graph(nfhmm_ctx* c, bool want_bpart, long long index, bool keep_alpha) {
+int run_graph(nfhmm_ctx* c, bool want_bpart, long long index, bool keep_alpha, int count) {
   const bool timed = c->profiling && index % c->prof_stride == 0;
   const int slot = (int)((index / c->prof_stride) & 1);
-  // the index the sweep is captured with: one that gives it the same gate
+  // the index the sweeps are captured with: one that gives them the same
+  // gates (a run of plain sweeps is shorter than the profiling stride)
   const long long cap_index = timed || c->prof_stride == 1 ? 0 : 1;
-  const long long key = graph_key_of(c, want_bpart, timed, slot, keep_alpha);
+  const long long key = graph_key_of(c, want_bpart, timed, slot, keep_alpha, count);
   SweepGraph* g = nullptr;
   for (auto& x : c->graphs)
     if (x.key == key) g = &x;
@@ -963,7 +975,8 @@ int run_graph(nfhmm_ctx* c, bool want_bpart, long long index, bool keep_alpha) {
   }
   g->last_use = ++c->graph_clock;
   if (!g->exec) {
-    if (g->seen++ == 0) return sweeps_direct(c, 1, want_bpart, index, keep_alpha);   // first uncaptured
+    if (g->seen++ == 0)   // first uncaptured
+      return sweeps_direct(c, count, want_bpart, index, keep_alpha);
     const long long l0 = c->launches;
     long long s0[NFHMM_NUM_STAGES];
     for (int i = 0; i < NFHMM_NUM_STAGES; ++i) s0[i] = c->stages[i].launches;
@@ -971,10 +984,10 @@ int run_graph(nfhmm_ctx* c, bool want_bpart, long long index, bool keep_alpha) {
     if (cudaStreamBeginCapture(c->s_main, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
       cudaGetLastError();
       c->use_graphs = false;
-      return sweeps_direct(c, 1, want_bpart, index, keep_alpha);
+      return sweeps_direct(c, count, want_bpart, index, keep_alpha);
     }
     c->capturing = g;
-    const int rc = sweeps_direct(c, 1, want_bpart, cap_index, keep_alpha);
+    const int rc = sweeps_direct(c, count, want_bpart, cap_index, keep_alpha);
     c->capturing = nullptr;
     const cudaError_t e = cudaStreamEndCapture(c->s_main, &graph);
     const bool good = !rc && e == cudaSuccess && graph &&
@@ -991,7 +1004,8 @@ int run_graph(nfhmm_ctx* c, bool want_bpart, long long index, bool keep_alpha) {
       drop_graph(c, *g);
       c->use_graphs = false;
       if (rc) return rc;
-      return sweeps_direct(c, 1, want_bpart, index, keep_alpha);   // capture unavailable: launch directly
+      // capture unavailable: launch directly
+      return sweeps_direct(c, count, want_bpart, index, keep_alpha);
     }
   }
   harvest(c, *g);   // its events are about to be recorded again

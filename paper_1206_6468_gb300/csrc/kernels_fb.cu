@@ -1077,7 +1077,7 @@ __global__ void __launch_bounds__(NP * 16) k_fb_group_products(FBArgs a) {
 // j, j+32 in registers), concurrently; then both combine a_t b_t into d-hat.
 // Vectors are stored unnormalised and rescaled by the previous step's sum.
 template <int NP>
-__global__ void __launch_bounds__(R_CHUNKS_MAX * 64) k_fb_replay(FBArgs a) {
+__global__ void __launch_bounds__(R_CHUNKS_MAX * 64, NP <= 48 ? 2 : 1) k_fb_replay(FBArgs a) {
   extern __shared__ float sm[];
   const int N = a.N, L = a.L;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1568,10 +1568,14 @@ static size_t smem_scan() {
   return (size_t)(ring * NP * (NP + 4) + 64) * sizeof(float);
 }
 static size_t smem_replay_chunk(int NP, int L) { return (size_t)(3 * L * NP + 128) * sizeof(float); }
+// One chunk (two warps, <= 128 registers a thread, a few KB of shared memory)
+// per block: such a block fits on an SM beside a persistent contraction CTA
+// (which leaves ~11k registers and ~10-30 KB of shared memory), so the replay
+// does not wait for the contraction's SMs; blocks of four chunks did.
 static int replay_chunks(int NP, int L) {
-  int rc = R_CHUNKS_MAX;
-  while (rc > 1 && rc * smem_replay_chunk(NP, L) > SMEM_OPTIN) --rc;
-  return rc;
+  (void)NP;
+  (void)L;
+  return 1;
 }
 
 // Launch a pass that consumes the previous pass's results as a programmatic
