@@ -383,15 +383,22 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 #pragma unroll
             for (int i = 0; i < 16; ++i) x16[i] = acc[16 * cc + i];
           }
-        const float* src = p.epi_stage ? eseg + 16 * ch : erow + c;
+        // rows are padded to a multiple of 32 floats and c is a multiple of
+        // 16, so the row segments are 64-byte aligned: 256-bit accesses, one
+        // whole sector per thread
         float vv[16];
+        if (p.epi_stage) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const float4 v4 = reinterpret_cast<const float4*>(src)[i];
-          vv[4 * i] = v4.x;
-          vv[4 * i + 1] = v4.y;
-          vv[4 * i + 2] = v4.z;
-          vv[4 * i + 3] = v4.w;
+          for (int i = 0; i < 4; ++i) {
+            const float4 v4 = reinterpret_cast<const float4*>(eseg + 16 * ch)[i];
+            vv[4 * i] = v4.x;
+            vv[4 * i + 1] = v4.y;
+            vv[4 * i + 2] = v4.z;
+            vv[4 * i + 3] = v4.w;
+          }
+        } else {
+          ld_global_v8(erow + c, vv);
+          ld_global_v8(erow + c + 8, vv + 8);
         }
         if (EPI == TEPI_RATIO) {
           float* q = vv;     // Q = V / Vhat over V's registers, the bound terms over x16's
@@ -422,38 +429,35 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             part += (double)vl[0];
           }
           if (KIND == KIND_TF32X3) {
-            float4* hp = reinterpret_cast<float4*>(p.out_f32 + (size_t)t * p.ldo + c);
-            float4* lp = reinterpret_cast<float4*>(p.out_lo + (size_t)t * p.ldo + c);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-              float h[4], l[4];
-#pragma unroll
-              for (int u = 0; u < 4; ++u) {
-                h[u] = tf32_hi(q[4 * i + u]);
-                l[u] = tf32_hi(q[4 * i + u] - h[u]);
-              }
-              hp[i] = make_float4(h[0], h[1], h[2], h[3]);
-              lp[i] = make_float4(l[0], l[1], l[2], l[3]);
-            }
-          } else {
-            uint4* bp = reinterpret_cast<uint4*>(p.out_bf16 + (size_t)t * p.ldo + c);
+            float* hp = p.out_f32 + (size_t)t * p.ldo + c;
+            float* lp = p.out_lo + (size_t)t * p.ldo + c;
 #pragma unroll
             for (int i = 0; i < 2; ++i) {
-              uint32_t u[4];
+              float h[8], l[8];
 #pragma unroll
-              for (int k = 0; k < 4; ++k) {
-                const __nv_bfloat162 b2 = __floats2bfloat162_rn(q[8 * i + 2 * k], q[8 * i + 2 * k + 1]);
-                u[k] = *reinterpret_cast<const uint32_t*>(&b2);
+              for (int u = 0; u < 8; ++u) {
+                h[u] = tf32_hi(q[8 * i + u]);
+                l[u] = tf32_hi(q[8 * i + u] - h[u]);
               }
-              bp[i] = make_uint4(u[0], u[1], u[2], u[3]);
+              st_global_v8(hp + 8 * i, h);
+              st_global_v8(lp + 8 * i, l);
             }
+          } else {
+            uint32_t u[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              const __nv_bfloat162 b2 = __floats2bfloat162_rn(q[2 * k], q[2 * k + 1]);
+              u[k] = *reinterpret_cast<const uint32_t*>(&b2);
+            }
+            st_global_v8(static_cast<void*>(p.out_bf16 + (size_t)t * p.ldo + c), u);
           }
         } else {
-          float4* op = reinterpret_cast<float4*>(p.out_f32 + (size_t)t * p.ldo + c);
+          float* op = p.out_f32 + (size_t)t * p.ldo + c;
+          float o[16];
 #pragma unroll
-          for (int i = 0; i < 4; ++i)
-            op[i] = make_float4(vv[4 * i] * x16[4 * i], vv[4 * i + 1] * x16[4 * i + 1],
-                                vv[4 * i + 2] * x16[4 * i + 2], vv[4 * i + 3] * x16[4 * i + 3]);
+          for (int i = 0; i < 16; ++i) o[i] = vv[i] * x16[i];
+          st_global_v8(op, o);
+          st_global_v8(op + 8, o + 8);
         }
       }
       if (EPI == TEPI_RATIO && p.bpart && rv)
