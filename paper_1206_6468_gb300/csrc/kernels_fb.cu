@@ -193,6 +193,11 @@ struct ChainCfg {
   static constexpr int IMG_BYTES = KATOMS * BATOM;  // the stacked B operand of one factor
   static constexpr int RING = 4;                    // group pass: chunk images in flight
   static constexpr int TMEM_COLS = 2 * NOUT <= 32 ? 32 : 2 * NOUT <= 64 ? 64 : 128;
+  // chunk pass: A staged with rows LDA floats apart, LDA / 4 odd, so that
+  // 16-byte reads of 8 consecutive rows fall in distinct bank groups; NOUT
+  // floats of slack after the last row for a thread's masked columns
+  static constexpr int LDA = ((NP + 3) & ~3) + ((((NP + 3) & ~3) / 4) % 2 == 0 ? 4 : 0);
+  static constexpr int A_FLOATS = NP * LDA + NOUT;
 };
 struct ChainMisc {
   double msum[16];       // chunk pass: summed frame maxima per chunk; group pass: [0] = chunk logs
@@ -221,6 +226,15 @@ __device__ __forceinline__ void tmem_ld8_nw(uint32_t taddr, uint32_t* r) {
         "=r"(r[7])
       : "r"(taddr));
 }
+// hi + lo += x, with hi + x formed exactly (Knuth's two-sum) and its rounding
+// error carried in lo
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bp = s - hi;
+  const float err = (hi - (s - bp)) + (x - bp);
+  hi = s;
+  lo += err;
+}
 // exact power of two 2^k for -126 <= k <= 127
 __device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }
 
@@ -240,8 +254,8 @@ __global__ void __launch_bounds__(256, MODE == CHAIN_CHUNK ? 2 : 1) k_fb_chain(F
   float* e = reinterpret_cast<float*>(bbuf + BBUF);
   const int ne = MODE == CHAIN_CHUNK ? Cfg::RCH * a.L * NP : 0;
   float* rmax = e + ne;
-  float* As = rmax + (MODE == CHAIN_CHUNK ? ((Cfg::RCH * a.L + 1) & ~1) : 0);
-  const int na = MODE == CHAIN_CHUNK ? ((a.N * a.N + 1) & ~1) : 0;
+  float* As = rmax + (MODE == CHAIN_CHUNK ? ((Cfg::RCH * a.L + 3) & ~3) : 0);
+  const int na = MODE == CHAIN_CHUNK ? Cfg::A_FLOATS : 0;
   ChainMisc* ms = reinterpret_cast<ChainMisc*>(As + na);
 
   const int N = a.N, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -290,7 +304,7 @@ __global__ void __launch_bounds__(256, MODE == CHAIN_CHUNK ? 2 : 1) k_fb_chain(F
     // A by asynchronous gathers: before the wait for the emissions' writer
     // when A is the caller's stable copy, else after it
     if (!a.inputs_stable) griddep_wait();
-    for (int u = tid; u < N * N; u += 256) cp_async4(As + u, Ag + u);
+    for (int u = tid; u < N * N; u += 256) cp_async4(As + (u / N) * Cfg::LDA + u % N, Ag + u);
     cp_async_commit();
     if (tid < Cfg::RCH) ms->clen[tid] = cbase + tid < a.C ? chunk_info(a, cbase + tid).len : 0;
     cp_async_wait<0>();
@@ -300,7 +314,7 @@ __global__ void __launch_bounds__(256, MODE == CHAIN_CHUNK ? 2 : 1) k_fb_chain(F
     // columns the MMAs read
     for (int idx = tid; idx < NOUT * NP; idx += 256) {
       const int j = idx / NP, k = idx - j * NP;
-      const float v = (j < N && k < N) ? As[k * N + j] : 0.f;
+      const float v = (j < N && k < N) ? As[k * Cfg::LDA + j] : 0.f;
       const float h = tf32_hi(v);
       *reinterpret_cast<float*>(bbuf + sw128_off(j, k, Cfg::BATOM)) = h;
       *reinterpret_cast<float*>(bbuf + sw128_off(j + NOUT, k, Cfg::BATOM)) = tf32_hi(v - h);
@@ -350,10 +364,19 @@ __global__ void __launch_bounds__(256, MODE == CHAIN_CHUNK ? 2 : 1) k_fb_chain(F
     }
     __syncthreads();
     for (int qq = warp; qq < Cfg::RCH; qq += 8) {
-      double t = 0.0;
-      for (int f = lane; f < ms->clen[qq]; f += 32) t += (double)rmax[qq * a.L + f];
-      t = warp_sum_d(t);
-      if (lane == 0) ms->msum[qq] = t;
+      // an unevaluated float pair (hi + lo, error-free sums): FP64 arithmetic
+      // is a small fraction of FP32's rate on this GPU, and this sits on the
+      // pass's critical path
+      float hi = 0.f, lo = 0.f;
+      for (int f = lane; f < ms->clen[qq]; f += 32) two_sum_acc(hi, lo, rmax[qq * a.L + f]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+        two_sum_acc(hi, lo, h2);
+        lo += l2;
+      }
+      if (lane == 0) ms->msum[qq] = (double)hi + (double)lo;
     }
   } else {
     griddep_wait();    // the chunk pass's matrices, images and scales
@@ -383,12 +406,20 @@ __global__ void __launch_bounds__(256, MODE == CHAIN_CHUNK ? 2 : 1) k_fb_chain(F
   bool zero_row = false;   // once zero, a row stays zero
   unsigned bad = 0;
   if (MODE == CHAIN_CHUNK) {
+    // the chunk's first factor: row i of A diag(e_t0), or e_t0 on state i
+    // when the chunk opens its job; row i of A by 16-byte reads
+    const float* Ai = As + (live ? i : 0) * Cfg::LDA + j0;
 #pragma unroll
-    for (int jj = 0; jj < HC; ++jj) {
-      const int j = j0 + jj;
-      float v = 0.f;
-      if (live && j < N) v = first ? (j == i ? eq[j] : 0.f) : As[i * N + j] * eq[j];
-      cur[jj] = v;
+    for (int jj = 0; jj < HC; jj += 4) {
+      const float4 a4 = *reinterpret_cast<const float4*>(Ai + jj);
+      const float av[4] = {a4.x, a4.y, a4.z, a4.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int j = j0 + jj + u;
+        float v = 0.f;
+        if (live && j < N) v = first ? (j == i ? eq[j] : 0.f) : av[u] * eq[j];
+        cur[jj + u] = v;
+      }
     }
   } else {
     const float* Pr = a.P + (cb + c0) * NP * NP + (size_t)i * NP;
@@ -1548,7 +1579,7 @@ static size_t smem_chain(int mode, int L) {
   using Cfg = ChainCfg<NP>;
   const size_t bb = mode == CHAIN_CHUNK ? Cfg::IMG_BYTES : Cfg::RING * Cfg::IMG_BYTES;
   const size_t ee = mode == CHAIN_CHUNK
-                        ? ((size_t)Cfg::RCH * L * NP + ((Cfg::RCH * L + 1) & ~1) + NP * NP) *
+                        ? ((size_t)Cfg::RCH * L * NP + ((Cfg::RCH * L + 3) & ~3) + Cfg::A_FLOATS) *
                               sizeof(float)
                         : 0;
   return 1024 + 2 * (size_t)Cfg::ROWS_BYTES + bb + ee + sizeof(ChainMisc);
