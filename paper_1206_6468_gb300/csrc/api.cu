@@ -95,6 +95,7 @@ struct nfhmm_ctx {
   float* w32 = nullptr;     // T x Mp
   float* c = nullptr;       // T x Mp
   float* Q = nullptr;       // T x Fp
+  float* wcol = nullptr;    // Fp: column sums of W (the initial state's reconstruction)
   float* phi = nullptr;     // S x T x N
   float* dhat = nullptr;    // S x T x N
   float* wts = nullptr;     // T x Mp (separation weights)
@@ -209,7 +210,7 @@ void free_ctx(nfhmm_ctx* c) {
   void* bufs[] = {c->V, c->WM, c->WF, c->A, c->pi, c->alpha, c->w32, c->c, c->Q, c->phi,
                   c->dhat, c->wts, c->sep_tmp, c->v, c->bpart, c->frame_terms, c->logZ,
                   c->bound_dev, c->err, c->ktab, c->fb_scratch, c->d_tab, c->fterm,
-                  c->fb_seg, c->fb.beta, c->fb.emis};
+                  c->fb_seg, c->fb.beta, c->fb.emis, c->wcol};
   for (void* p : bufs)
     if (p) cudaFree(p);
   tc_free(c->tc);
@@ -281,24 +282,31 @@ int contract(nfhmm_ctx* c, bool want_bpart, bool init, int t0, int rows,
   cudaStream_t st = on ? on : c->s_main;
   if (rows <= 0) return NFHMM_OK;
   // the sweep's contractions run on the tensor cores; so does the initial
-  // state's (w = 1 on frames [t0, t0 + rows)) in split-TF32 mode, whose
-  // accuracy is FP32's (BF16 contexts keep the FP32 CUDA-core initial state)
-  if (c->use_tc && (!init || c->tc.w_format == WF_TF32X2)) {
-    if (init) {
-      // the operand copies of the initial w, on the frames being initialised;
-      // nothing runs beside these contractions
-      const size_t o = (size_t)t0 * c->Mp;
-      stage_begin(c, NFHMM_STAGE_INIT, st);
-      launch_split_tf32(c->w32 + o, reinterpret_cast<float*>(c->tc.w_hi) + o,
-                        reinterpret_cast<float*>(c->tc.w_lo) + o, (size_t)rows * c->Mp, st);
-      stage_end(c, NFHMM_STAGE_INIT, st, 1);
-      reserve = 0;
-    }
+  // state's back-projection (w = 1 on frames [t0, t0 + rows)) in split-TF32
+  // mode, whose accuracy is FP32's (BF16 contexts form the initial state on
+  // the CUDA cores in FP32)
+  const bool tc = c->use_tc && (!init || c->tc.w_format == WF_TF32X2);
+  if (init) {
+    // every weight is 1, so the reconstruction is W's column sum b_l in every
+    // frame: Q = V / b, in the form the back-projection reads; nothing runs
+    // beside the initial state's contractions
+    const size_t oF = (size_t)t0 * c->Fp;
+    stage_begin(c, NFHMM_STAGE_INIT, st);
+    launch_init_ratio(c->V + oF, c->wcol, rows, c->Fp, tc ? nullptr : c->Q + oF,
+                      tc ? reinterpret_cast<float*>(c->tc.q_hi) + oF : nullptr,
+                      tc ? reinterpret_cast<float*>(c->tc.q_lo) + oF : nullptr, c->err, st);
+    stage_end(c, NFHMM_STAGE_INIT, st, 1);
+    reserve = 0;
+  }
+  if (tc) {
     const int stage1 = init ? NFHMM_STAGE_INIT : NFHMM_STAGE_GEMM1;
     const int stage2 = init ? NFHMM_STAGE_INIT : NFHMM_STAGE_GEMM2;
-    stage_begin(c, stage1, st);
-    const int n1 = tc_gemm1(c->tc, t0, rows, want_bpart ? c->bpart : nullptr, reserve, st);
-    if (n1 >= 0) stage_end(c, stage1, st, n1);
+    int n1 = 0;
+    if (!init) {
+      stage_begin(c, stage1, st);
+      n1 = tc_gemm1(c->tc, t0, rows, want_bpart ? c->bpart : nullptr, reserve, st);
+      if (n1 >= 0) stage_end(c, stage1, st, n1);
+    }
     int n2 = -1;
     if (n1 >= 0) {
       stage_begin(c, stage2, st);
@@ -326,9 +334,11 @@ int contract(nfhmm_ctx* c, bool want_bpart, bool init, int t0, int rows,
   g1.bpart = want_bpart ? c->bpart + (size_t)t0 * c->nbpart : nullptr;
   g1.nbpart = c->nbpart;
   g1.err = c->err;
-  stage_begin(c, stage1, st);
-  launch_gemm_simt(g1, EPI_RATIO, st);
-  stage_end(c, stage1, st, 1);
+  if (!init) {
+    stage_begin(c, stage1, st);
+    launch_gemm_simt(g1, EPI_RATIO, st);
+    stage_end(c, stage1, st, 1);
+  }
   GemmArgs g2{};
   g2.rows = rows;
   g2.cols = c->Mp;
@@ -457,7 +467,8 @@ int load_model(nfhmm_ctx* c, const float* W, const float* A, const float* pi, in
   launch_validate(c->V, 0, d.F, c->Fp, c->WM, c->M, c->A, c->pi, d.S, d.N, c->err, st);
   launch_transpose(c->WM, c->Mp, c->Fp, c->Fp, c->WF, c->Mp, c->Mp, c->Fp, st);
   launch_element_table(c->M, c->Mp, d.K, d.N, c->ktab, st);
-  int n = 3;
+  launch_col_sums(c->WM, c->M, c->Fp, c->wcol, st);
+  int n = 4;
   if (c->use_tc) n += tc_refresh_beta(c->tc, st);
   stage_end(c, NFHMM_STAGE_INIT, st, n);
   return NFHMM_OK;
@@ -827,6 +838,7 @@ int create_ctx(nfhmm_ctx** out, const nfhmm_dims* dp, int max_jobs, const float*
   DMALLOC(c->w32, T * Mp * 4);
   DMALLOC(c->c, T * Mp * 4);
   DMALLOC(c->Q, T * Fp * 4);
+  DMALLOC(c->wcol, Fp * 4);
   DMALLOC(c->phi, S * T * N * 4);
   DMALLOC(c->dhat, S * T * N * 4);
   DMALLOC(c->v, T * 8);

@@ -500,6 +500,55 @@ void launch_transpose(const float* in, int R, int Cc, int ldi, float* out, int l
   k_transpose<<<grid, dim3(32, 8), 0, st>>>(in, R, Cc, ldi, out, ldo, Rp, Cp);
 }
 
+// Column sums b_l = sum_k W[k][l] of the dictionary (Mp x Fp, padding zero),
+// accumulated in double: the reconstruction of the initial state, whose
+// weights are all 1, is b_l in every frame.
+__global__ void k_col_sums(const float* W, int M, int Fp, float* b) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= Fp) return;
+  double s = 0.0;
+  for (int k = 0; k < M; ++k) s += (double)W[(size_t)k * Fp + l];
+  b[l] = (float)s;
+}
+void launch_col_sums(const float* W, int M, int Fp, float* b, cudaStream_t st) {
+  k_col_sums<<<(Fp + 127) / 128, 128, 0, st>>>(W, M, Fp, b);
+}
+
+// The initial state's ratio Q = V / Vhat with Vhat_tl = b_l (Eq. 7 at w = 1),
+// for frames [0, T): float (out) or split into tf32 hi / lo; a frequency with
+// energy but b_l <= 0 (or not finite) sets ERR_VHAT_ZERO and gives 0, as the
+// contraction's ratio epilogue does.
+__global__ void k_init_ratio(const float* V, const float* b, int T, int Fp, float* out,
+                             float* hi, float* lo, unsigned* err) {
+  const size_t n = (size_t)T * Fp;
+  unsigned bad = 0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const float v = V[i], x = b[i % Fp];
+    float q = 0.f;
+    if (v > 0.f) {
+      if (x > 0.f && isfinite(x))
+        q = v / x;
+      else
+        bad |= ERR_VHAT_ZERO;
+    }
+    if (out) out[i] = q;
+    if (hi) {
+      const float h = tf32_hi(q);
+      hi[i] = h;
+      lo[i] = tf32_hi(q - h);
+    }
+  }
+  bad = __reduce_or_sync(FULL, bad);
+  if (bad && (threadIdx.x & 31) == 0) atomicOr(err, bad);
+}
+void launch_init_ratio(const float* V, const float* b, int T, int Fp, float* out, float* hi,
+                       float* lo, unsigned* err, cudaStream_t st) {
+  const size_t n = (size_t)T * Fp;
+  const int blocks = (int)std::min<size_t>(4096, (n + 255) / 256);
+  if (blocks > 0) k_init_ratio<<<blocks, 256, 0, st>>>(V, b, T, Fp, out, hi, lo, err);
+}
+
 __global__ void k_split_tf32(const float* in, float* hi, float* lo, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x) {

@@ -67,6 +67,12 @@ void launch_transpose(const float* in, int R, int Cc, int ldi, float* out, int l
 
 // Simple split copies used by the tensor-core path.
 void launch_split_tf32(const float* in, float* hi, float* lo, size_t n, cudaStream_t st);
+// b_l = sum_k W[k][l] (the initial state's reconstruction, every weight 1).
+void launch_col_sums(const float* W, int M, int Fp, float* b, cudaStream_t st);
+// Q = V / b_l on T frames (T x Fp), as float (out) and/or split tf32 hi / lo.
+void launch_init_ratio(const float* V, const float* b, int T, int Fp, float* out, float* hi,
+                       float* lo, unsigned* err, cudaStream_t st);
+
 void launch_to_bf16(const float* in, void* out, size_t n, cudaStream_t st);
 
 // SIMT FP32 contraction C[t][n] = sum_k A[t][k] B[n][k] with epilogues.
