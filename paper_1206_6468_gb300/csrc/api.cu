@@ -487,19 +487,36 @@ int load_frames(nfhmm_ctx* c, int t0, int T, const float* const* Vs, int on_devi
   cudaStream_t st = c->s_main;
   if (T <= 0) return NFHMM_OK;
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDefault;
-  CK(cudaMemsetAsync(c->V + (size_t)t0 * Fp, 0, (size_t)T * Fp * 4, st));
   CK(cudaMemsetAsync(c->c + (size_t)t0 * Mp, 0, (size_t)T * Mp * 4, st));
   CK(cudaMemsetAsync(c->alpha + (size_t)t0 * Mp, 0, (size_t)T * Mp * 4, st));
   CK(cudaMemsetAsync(c->bpart + (size_t)t0 * c->nbpart, 0, (size_t)T * c->nbpart * 8, st));
-  for (int j = 0, t = t0; j < n; t += frames[j], ++j)
-    CK(cudaMemcpy2DAsync(c->V + (size_t)t * Fp, Fp * 4, Vs[j], (size_t)d.F * 4, (size_t)d.F * 4,
-                         frames[j], kind, st));
+  // the jobs' spectrograms: one contiguous copy per run of jobs that follow
+  // each other in the caller's memory (a copy of F-float rows into the
+  // padded layout would move one short row at a time), staged packed in the
+  // ratio buffer Q (free until the initial state's ratio below), then padded
+  // into the frame store by a kernel
+  int pads = 0;
+  for (int j = 0, t = t0; j < n;) {
+    int k = j;
+    size_t rows = (size_t)frames[j];
+    while (k + 1 < n && Vs[k + 1] == Vs[k] + (size_t)frames[k] * d.F) rows += frames[++k];
+    if (d.F == (int)Fp) {
+      CK(cudaMemcpyAsync(c->V + (size_t)t * Fp, Vs[j], rows * Fp * 4, kind, st));
+    } else {
+      float* stage = c->Q + (size_t)t * Fp;
+      CK(cudaMemcpyAsync(stage, Vs[j], rows * d.F * 4, kind, st));
+      launch_pad_rows(stage, (int)rows, d.F, c->V + (size_t)t * Fp, (int)Fp, st);
+      ++pads;
+    }
+    t += (int)rows;
+    j = k + 1;
+  }
   stage_begin(c, NFHMM_STAGE_INIT, st);
   launch_validate(c->V + (size_t)t0 * Fp, T, d.F, c->Fp, c->WM, c->M, c->A, c->pi, d.S, d.N,
                   c->err, st);
   launch_row_sums(c->V + (size_t)t0 * Fp, T, d.F, c->Fp, c->v + t0, st);
   launch_fill_rows(c->w32 + (size_t)t0 * Mp, T, c->M, c->Mp, 1.f, st);
-  stage_end(c, NFHMM_STAGE_INIT, st, 3);
+  stage_end(c, NFHMM_STAGE_INIT, st, 3 + pads);
   int rc = contract(c, false, true, t0, T);
   if (rc) return rc;
   stage_begin(c, NFHMM_STAGE_INIT, st);

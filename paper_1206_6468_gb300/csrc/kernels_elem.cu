@@ -500,6 +500,23 @@ void launch_transpose(const float* in, int R, int Cc, int ldi, float* out, int l
   k_transpose<<<grid, dim3(32, 8), 0, st>>>(in, R, Cc, ldi, out, ldo, Rp, Cp);
 }
 
+// dst[r][l] = src[r][l] for l < F, 0 for F <= l < Fp: rows of F floats,
+// packed, into rows of Fp (the frame store's padded layout).
+__global__ void k_pad_rows(const float* src, int rows, int F, float* dst, int Fp) {
+  const size_t n = (size_t)rows * Fp;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const size_t r = i / Fp;
+    const int l = (int)(i - r * Fp);
+    dst[i] = l < F ? src[r * F + l] : 0.f;
+  }
+}
+void launch_pad_rows(const float* src, int rows, int F, float* dst, int Fp, cudaStream_t st) {
+  const size_t n = (size_t)rows * Fp;
+  const int blocks = (int)std::min<size_t>(8192, (n + 255) / 256);
+  if (blocks > 0) k_pad_rows<<<blocks, 256, 0, st>>>(src, rows, F, dst, Fp);
+}
+
 // Column sums b_l = sum_k W[k][l] of the dictionary (Mp x Fp, padding zero),
 // accumulated in double: the reconstruction of the initial state, whose
 // weights are all 1, is b_l in every frame.

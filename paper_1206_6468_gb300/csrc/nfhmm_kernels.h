@@ -67,6 +67,8 @@ void launch_transpose(const float* in, int R, int Cc, int ldi, float* out, int l
 
 // Simple split copies used by the tensor-core path.
 void launch_split_tf32(const float* in, float* hi, float* lo, size_t n, cudaStream_t st);
+// rows of F floats, packed in src, into rows of Fp in dst (padding zero).
+void launch_pad_rows(const float* src, int rows, int F, float* dst, int Fp, cudaStream_t st);
 // b_l = sum_k W[k][l] (the initial state's reconstruction, every weight 1).
 void launch_col_sums(const float* W, int M, int Fp, float* b, cudaStream_t st);
 // Q = V / b_l on T frames (T x Fp), as float (out) and/or split tf32 hi / lo.
