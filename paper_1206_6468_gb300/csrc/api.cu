@@ -490,17 +490,31 @@ int load_frames(nfhmm_ctx* c, int t0, int T, const float* const* Vs, int on_devi
   CK(cudaMemsetAsync(c->c + (size_t)t0 * Mp, 0, (size_t)T * Mp * 4, st));
   CK(cudaMemsetAsync(c->alpha + (size_t)t0 * Mp, 0, (size_t)T * Mp * 4, st));
   CK(cudaMemsetAsync(c->bpart + (size_t)t0 * c->nbpart, 0, (size_t)T * c->nbpart * 8, st));
-  // the jobs' spectrograms: one contiguous copy per run of jobs that follow
-  // each other in the caller's memory (a copy of F-float rows into the
-  // padded layout would move one short row at a time), staged packed in the
-  // ratio buffer Q (free until the initial state's ratio below), then padded
-  // into the frame store by a kernel
+  // the jobs' spectrograms, per run of jobs that follow each other in the
+  // caller's memory: read in place by the padding kernel when the device can
+  // address them (device memory, or mapped pinned host memory, read over the
+  // host link); otherwise one contiguous copy (a copy of F-float rows into
+  // the padded layout would move one short row at a time) staged packed in
+  // the ratio buffer Q (free until the initial state's ratio below), then
+  // padded into the frame store
   int pads = 0;
   for (int j = 0, t = t0; j < n;) {
     int k = j;
     size_t rows = (size_t)frames[j];
     while (k + 1 < n && Vs[k + 1] == Vs[k] + (size_t)frames[k] * d.F) rows += frames[++k];
-    if (d.F == (int)Fp) {
+    const float* direct = on_device ? Vs[j] : nullptr;
+    if (!on_device) {
+      cudaPointerAttributes pa{};
+      if (cudaPointerGetAttributes(&pa, Vs[j]) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+          pa.devicePointer)
+        direct = static_cast<const float*>(pa.devicePointer);
+      else
+        cudaGetLastError();   // an unregistered host pointer is not an error here
+    }
+    if (direct) {
+      launch_pad_rows(direct, (int)rows, d.F, c->V + (size_t)t * Fp, (int)Fp, st);
+      ++pads;
+    } else if (d.F == (int)Fp) {
       CK(cudaMemcpyAsync(c->V + (size_t)t * Fp, Vs[j], rows * Fp * 4, kind, st));
     } else {
       float* stage = c->Q + (size_t)t * Fp;
