@@ -30,7 +30,9 @@
  * Ownership: the caller owns every buffer it passes; the library copies what
  * it keeps.  A context owns its device memory until nfhmm_destroy.
  * Pointers flagged "on device" are CUDA device pointers of the current
- * device; otherwise they are host pointers (pinned or pageable).
+ * device; otherwise they are host pointers (pinned or pageable).  Spectrograms
+ * in device memory or in mapped pinned host memory are read in place by a
+ * kernel (over the host link for host memory); pageable ones are copied.
  * Streams: a context orders all its work after the work already queued on
  * the stream given to nfhmm_vi_init, and the stream waits for the context's
  * work before anything queued later.  Calls return once the work is queued,
