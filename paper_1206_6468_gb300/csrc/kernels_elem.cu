@@ -517,18 +517,39 @@ void launch_pad_rows(const float* src, int rows, int F, float* dst, int Fp, cuda
   if (blocks > 0) k_pad_rows<<<blocks, 256, 0, st>>>(src, rows, F, dst, Fp);
 }
 
-// Column sums b_l = sum_k W[k][l] of the dictionary (Mp x Fp, padding zero),
-// accumulated in double: the reconstruction of the initial state, whose
-// weights are all 1, is b_l in every frame.
-__global__ void k_col_sums(const float* W, int M, int Fp, float* b) {
-  const int l = blockIdx.x * blockDim.x + threadIdx.x;
-  if (l >= Fp) return;
-  double s = 0.0;
-  for (int k = 0; k < M; ++k) s += (double)W[(size_t)k * Fp + l];
-  b[l] = (float)s;
+// Column sums b_l = sum_k W[k][l] of the dictionary (Mp x Fp, padding zero):
+// the reconstruction of the initial state, whose weights are all 1, is b_l in
+// every frame.  32 columns per block (coalesced rows), eight groups of rows
+// per column, each summed as an unevaluated float pair (hi + lo, error-free
+// two-sums: FP64 arithmetic is a small fraction of FP32's rate on this GPU),
+// the groups combined in shared memory and rounded once.
+__device__ __forceinline__ void two_sum_acc_e(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bp = s - hi;
+  lo += (hi - (s - bp)) + (x - bp);
+  hi = s;
+}
+__global__ void __launch_bounds__(256) k_col_sums(const float* W, int M, int Fp, float* b) {
+  __shared__ float part[2][8][32];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int l = blockIdx.x * 32 + tx;
+  float hi = 0.f, lo = 0.f;
+  if (l < Fp)
+    for (int k = ty; k < M; k += 8) two_sum_acc_e(hi, lo, W[(size_t)k * Fp + l]);
+  part[0][ty][tx] = hi;
+  part[1][ty][tx] = lo;
+  __syncthreads();
+  if (ty == 0 && l < Fp) {
+    float h = part[0][0][tx], o = part[1][0][tx];
+    for (int g = 1; g < 8; ++g) {
+      two_sum_acc_e(h, o, part[0][g][tx]);
+      o += part[1][g][tx];
+    }
+    b[l] = (float)((double)h + (double)o);
+  }
 }
 void launch_col_sums(const float* W, int M, int Fp, float* b, cudaStream_t st) {
-  k_col_sums<<<(Fp + 127) / 128, 128, 0, st>>>(W, M, Fp, b);
+  k_col_sums<<<(Fp + 31) / 32, 256, 0, st>>>(W, M, Fp, b);
 }
 
 // The initial state's ratio Q = V / Vhat with Vhat_tl = b_l (Eq. 7 at w = 1),
