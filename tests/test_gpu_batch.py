@@ -279,6 +279,64 @@ def test_profiling_through_graphs_counts_every_launch(nf):
     assert np.array_equal(res[0][1], res[1][1])
 
 
+def test_multi_sweep_graphs_with_profiling_match_direct(nf):
+    """Runs of plain sweeps replay from graphs of several sweeps, between the
+    profiled sweeps (every 7th) and the run's last: the state, the bounds,
+    the kernel launches and the stage invocations equal those of sweeps
+    launched one by one."""
+    lengths = [150, 77, 260]
+    jobs = _jobs(lengths, seed=23, sigma=1.0)
+    V, W, A, pi = (_f32(x) for x in (jobs.stacked_V(), jobs.W, jobs.A, jobs.pi))
+    res = []
+    for graphs in (1, 0):
+        with nf.VIContext(V, W, A, pi, jobs.S, jobs.N, jobs.K, job_frames=lengths) as ctx:
+            ctx.set_option("graphs", graphs)
+            ctx.set_option("profile_stride", 7)
+            ctx.profile_enable(True)
+            Ls = [ctx.sweep(30, bound=True), ctx.sweep(11, bound=True)]
+            ctx.profile_enable(False)
+            Ls.append(ctx.sweep(19, bound=True))
+            prof = {st: ctx.profile_read(st)[1:] for st in ("weights", "gemm1", "gemm2", "fb")}
+            res.append((Ls, ctx.posteriors(), ctx.get_state()[0], ctx.kernel_launches(), prof))
+    assert res[0][0] == res[1][0]
+    assert np.array_equal(res[0][1], res[1][1]) and np.array_equal(res[0][2], res[1][2])
+    assert res[0][3] == res[1][3]
+    assert res[0][4] == res[1][4]
+
+
+@pytest.mark.parametrize("where", ["pinned", "device"])
+def test_inputs_read_in_place_equal_copied(nf, where):
+    """Spectrograms in mapped pinned host memory or in device memory are read
+    in place by the kernel that pads them into the frame store; pageable host
+    memory is copied first: the same state either way, for a batch whose
+    jobs lie back to back and for jobs added from buffers of their own."""
+    import torch
+    lengths = [300, 41, 777, 128]
+    jobs = _jobs(lengths, seed=21, sigma=1.0)
+    V, W, A, pi = (_f32(x) for x in (jobs.stacked_V(), jobs.W, jobs.A, jobs.pi))
+
+    def place(x):
+        t = torch.from_numpy(np.array(x, dtype=np.float32, copy=True))
+        return t.pin_memory() if where == "pinned" else t.cuda()
+
+    def run(Vx, Wx, Ax, pix):
+        with nf.VIContext(Vx, Wx, Ax, pix, jobs.S, jobs.N, jobs.K, job_frames=lengths) as ctx:
+            L = ctx.sweep(4, bound=True)
+            return L, ctx.posteriors(), ctx.get_state()[0]
+
+    ref = run(V, W, A, pi)
+    got = run(*(place(x) for x in (V, W, A, pi)))
+    assert got[0] == ref[0]
+    assert np.array_equal(got[1], ref[1]) and np.array_equal(got[2], ref[2])
+    out = []
+    for per_job in ([_f32(v) for v in jobs.V], [place(v) for v in jobs.V]):
+        with nf.Batch(W, A, pi, jobs.S, jobs.N, jobs.K, capacity=2000, max_jobs=8) as b:
+            b.add_many(per_job)
+            L = b.sweep(4, bound=True)
+            out.append((L, b.posteriors()))
+    assert out[0][0] == out[1][0] and np.array_equal(out[0][1], out[1][1])
+
+
 def test_graphs_dropped_when_scratch_is_reallocated(nf):
     """A chunk length that needs more forward-backward scratch reallocates it;
     sweeps captured before then must not be replayed afterwards.  Going back
