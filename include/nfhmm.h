@@ -244,10 +244,12 @@ NFHMM_API int nfhmm_job_posteriors(nfhmm_ctx *c, long long job_id, float *dhat, 
  *                          for a size that follows the chunk length (the
  *                          default of one-job contexts; batches default to 0
  *                          and chunks of 32 frames)
- *   NFHMM_OPT_GRAPHS       1 (default): a sweep whose launch configuration
+ *   NFHMM_OPT_GRAPHS       1 (default): sweeps whose launch configuration
  *                          (frames, chunks, bound terms, timed by profiling
- *                          or not) has run before is replayed from a captured
- *                          one-sweep CUDA graph, profiling events included;
+ *                          or not) has run before are replayed from captured
+ *                          CUDA graphs: the run's last sweep and each profiled
+ *                          sweep (events included) from one-sweep graphs, the
+ *                          plain sweeps between them up to 8 to a graph;
  *                          0: launch by launch
  *   NFHMM_OPT_PROFILE_STRIDE  k >= 1 (default 1): with profiling on, the
  *                          stages of every k-th sweep of a run (the 1st,
