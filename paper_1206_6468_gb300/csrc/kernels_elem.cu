@@ -131,7 +131,8 @@ __global__ void __launch_bounds__(256) k_weights(WeightsArgs a) {
 // every alpha-hat of the unit lies in [1, 2^60) -- always, for a valid state
 // -- one warp vote sends the unit down the straight-line psi (no fallback
 // branch, no NaN test: psi and w are finite there); otherwise the general
-// psi with the NaN test.  Eq. 8: lanes 2b and 2b + 1 sum the first
+// psi with the NaN test (with BOUND, both forms also sum alpha-hat and the
+// bound's element terms).  Eq. 8: lanes 2b and 2b + 1 sum the first
 // ceil(K/2) and the last floor(K/2) of block b's psi values (shared memory,
 // element order), and the two halves are added.  KT: K as a compile-time
 // constant (1..16), or 0 for any K <= 16 at run time.
@@ -201,7 +202,7 @@ __global__ void __launch_bounds__(256, (BOUND || KT == 0) ? 2 : KT <= 10 ? 4 : 3
       al[j] = c[j] + a.gamma * dj + 1.f;
       span = max(span, __float_as_uint(al[j]) - 0x3f800000u);
     }
-    const bool fast = !BOUND && __all_sync(FULL, span < 0x1e000000u);
+    const bool fast = __all_sync(FULL, span < 0x1e000000u);
     float sa = 0.f, ca = 0.f, sgk = 0.f, cg = 0.f;
     double big = 0.0;
 #pragma unroll
@@ -211,8 +212,18 @@ __global__ void __launch_bounds__(256, (BOUND || KT == 0) ? 2 : KT <= 10 ? 4 : 3
       if (e < nk) {
         float psi, w;
         if (fast) {
-          float u0, u1;
-          digamma_ge1_straight<false>(al[j], psi, w, u0, u1);
+          float gs, gb;
+          digamma_ge1_straight<BOUND>(al[j], psi, w, gs, gb);
+          if (BOUND) {   // Kahan sums of alpha and of g's small part, as weights_elem
+            float y = al[j] - ca, z = sa + y;
+            ca = (z - sa) - y;
+            sa = z;
+            y = gs - cg;
+            z = sgk + y;
+            cg = (z - sgk) - y;
+            sgk = z;
+            big += (double)gb;
+          }
         } else {
           weights_elem<FMT, BOUND>(al[j], psi, w, sa, ca, sgk, cg, big);
           chk = fmaf(0.f, psi + w, chk);   // stays 0 unless psi or w is NaN or infinite
@@ -289,9 +300,9 @@ __global__ void __launch_bounds__(256, (BOUND || KT == 0) ? 2 : KT <= 10 ? 4 : 3
 }
 
 // the slab kernels with K fixed at compile time, by K - 1
-template <int FMT, int... KS>
+template <int FMT, bool BOUND, int... KS>
 static void (*slab_fixed_k(int K, std::integer_sequence<int, KS...>))(WeightsArgs) {
-  void (*const tab[])(WeightsArgs) = {k_weights_slab<FMT, false, KS + 1>...};
+  void (*const tab[])(WeightsArgs) = {k_weights_slab<FMT, BOUND, KS + 1>...};
   return tab[K - 1];
 }
 
@@ -346,10 +357,10 @@ void launch_weights(const WeightsArgs& a_in, int fmt, cudaStream_t st) {
     const auto ks = std::make_integer_sequence<int, SLAB_MAX_K>{};
     switch (fmt) {
       case WF_TF32X2:
-        k = b ? k_weights_slab<WF_TF32X2, true, 0> : slab_fixed_k<WF_TF32X2>(a.K, ks);
+        k = b ? slab_fixed_k<WF_TF32X2, true>(a.K, ks) : slab_fixed_k<WF_TF32X2, false>(a.K, ks);
         break;
       case WF_BF16:
-        k = b ? k_weights_slab<WF_BF16, true, 0> : slab_fixed_k<WF_BF16>(a.K, ks);
+        k = b ? slab_fixed_k<WF_BF16, true>(a.K, ks) : slab_fixed_k<WF_BF16, false>(a.K, ks);
         break;
       default:
         k = b ? k_weights_slab<WF_F32, true, 0> : k_weights_slab<WF_F32, false, 0>;
