@@ -119,3 +119,26 @@ def test_bench_tensor_peaks_and_split_tf32_ceiling():
     dom = bench.roofline_of(prof, 3000, 2, 40, 10, 513, "fp32", True, peaks, 10,
                             fb_path=(57, "scan"))
     assert dom["kernel"] in prof and dom["peak"] > 0
+
+
+def test_bench_traffic_summary_is_keyed_to_the_sources(monkeypatch):
+    """The committed DRAM-traffic summary carries every stage and the hash of
+    the library sources it was captured from; the bench reports its figures
+    only while the sources still hash to that value."""
+    import importlib.util
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    spec = importlib.util.spec_from_file_location("bench_mod3", os.path.join(root, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    text = open(os.path.join(root, "profiles", "traffic_paper_size_fp32.txt")).read().split("\n")
+    digest = [l.split()[1] for l in text if l.startswith("csrc_sha256 ")]
+    stages = {l.split()[1]: float(l.split()[2]) for l in text if l.startswith("stage ")}
+    assert len(digest) == 1 and len(digest[0]) == 64
+    assert set(stages) == {"fb", "weights", "gemm1", "gemm2", "bound"}
+    assert all(v > 0 for v in stages.values())
+    monkeypatch.setattr(bench, "csrc_digest", lambda: digest[0])
+    assert bench.measured_traffic("fb", "paper_size_fp32") == stages["fb"]
+    monkeypatch.setattr(bench, "csrc_digest", lambda: "0" * 64)
+    assert bench.measured_traffic("fb", "paper_size_fp32") is None
+    assert bench.measured_traffic("fb", "no_such_workload") is None
