@@ -124,6 +124,18 @@ def test_responsibilities_and_collapsed_counts():
     assert np.allclose(col.sum(axis=1), p.V.sum(axis=1), rtol=1e-13, atol=1e-13)
 
 
+def test_initial_counts_are_eq7_at_equal_weights():
+    """The initial state's counts (z-hat from equal weights, formed from the
+    dictionary's column sums) equal Eq. 7's counts with z-hat materialised
+    element by element at any constant alpha-hat, where every psi is equal
+    and cancels in the normalisation."""
+    p = _small_problem(5)
+    counts, _ = vi.init_state(p.V, p.W, p.S, p.N, p.K)
+    for a in (1.0, 3.7):
+        lit = vi.expected_counts_literal(p.V, p.W, np.full((p.T, p.M), a))
+        assert np.max(np.abs(lit - counts)) < 1e-12 * max(1.0, np.abs(lit).max())
+
+
 def test_dirichlet_update_total_mass():
     """sum_k alpha_tk = v_t + M + gamma S K when each d-hat row sums to 1."""
     p = _small_problem(2)
